@@ -1,0 +1,218 @@
+"""Seeded synthetic LP generators shared by the oracle tests, the CUDA tests and the benchmark.
+
+This module builds problem data only: it contains none of ABIP's arithmetic.
+Every generator draws from ``numpy.random.Generator(PCG64(seed))`` and returns
+host arrays in float64 (sparse values are drawn in float32 and upcast exactly).
+
+The planted recipe (a primal-dual optimal pair chosen first, then b = A x0 and
+c = A^T y0 + s0) makes the LP optimum known exactly:  p* = c^T x0 = b^T y0,
+because x0 >= 0, s0 >= 0 and x0 o s0 = 0 (weak duality is tight; Sec. 2, the
+primal-dual pair (P)/(D)).
+
+Seeds follow ``SEED_BASE + 1000 * workload_id + instance``.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+from typing import Optional
+
+import numpy as np
+
+SEED_BASE = 1805012344
+
+# workload ids used for the seed formula
+DENSE_PLANTED = 0     # dense 50 x 120 planted LP and its 10 x 20 infeasible twin
+SPARSE_PLANTED = 1    # [R I] CSR LP, 8 nonzeros per column of R
+BASIS_PURSUIT = 2
+BATCH_UNEVEN = 3
+L1_SVM = 4
+TINY = 9              # tiny random LPs for brute-force basis enumeration
+
+
+def seed_for(workload: int, instance: int = 0) -> int:
+    return SEED_BASE + 1000 * workload + instance
+
+
+@dataclass
+class CSR:
+    """Compressed sparse row matrix: int64 row pointers, int32 column indices."""
+    m: int
+    n: int
+    row_ptr: np.ndarray
+    col_idx: np.ndarray
+    val: np.ndarray
+
+    @property
+    def nnz(self) -> int:
+        return int(self.row_ptr[-1])
+
+    def to_dense(self) -> np.ndarray:
+        out = np.zeros((self.m, self.n), dtype=np.float64)
+        rows = np.repeat(np.arange(self.m), np.diff(self.row_ptr))
+        out[rows, self.col_idx] = self.val
+        return out
+
+    def to_scipy(self):
+        import scipy.sparse as sp
+        return sp.csr_matrix((self.val.astype(np.float64), self.col_idx, self.row_ptr),
+                             shape=(self.m, self.n))
+
+
+@dataclass
+class LP:
+    """Standard-form LP  min c^T x  s.t.  A x = b,  x >= 0  (A dense float64 or CSR)."""
+    A: object
+    b: np.ndarray
+    c: np.ndarray
+    x0: Optional[np.ndarray] = None      # planted primal optimum (if any)
+    y0: Optional[np.ndarray] = None      # planted dual optimum (if any)
+    s0: Optional[np.ndarray] = None
+    expect: str = "optimal"              # "optimal" | "primal_infeasible" | "dual_infeasible" | "unknown"
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def m(self) -> int:
+        return self.A.m if isinstance(self.A, CSR) else self.A.shape[0]
+
+    @property
+    def n(self) -> int:
+        return self.A.n if isinstance(self.A, CSR) else self.A.shape[1]
+
+    @property
+    def p_star(self) -> Optional[float]:
+        if self.x0 is None:
+            return None
+        return float(self.c @ self.x0)
+
+    def dense_A(self) -> np.ndarray:
+        return self.A.to_dense() if isinstance(self.A, CSR) else self.A
+
+
+def _planted_pair(rng: np.random.Generator, n: int, m: int, support_frac: float = 0.3):
+    """x0: `support_frac` of entries U[0.5,2], rest 0; s0: U[0.5,2] off x0's support; y0 ~ N(0,1)."""
+    k = int(round(support_frac * n))
+    perm = rng.permutation(n)
+    x0 = np.zeros(n)
+    s0 = np.zeros(n)
+    x0[perm[:k]] = rng.uniform(0.5, 2.0, k)
+    s0[perm[k:]] = rng.uniform(0.5, 2.0, n - k)
+    y0 = rng.standard_normal(m)
+    return x0, y0, s0
+
+
+def planted_dense(m: int = 50, n: int = 120, seed: Optional[int] = None) -> LP:
+    """Dense planted LP: A iid N(0,1) float64; b = A x0, c = A^T y0 + s0."""
+    rng = np.random.default_rng(seed_for(DENSE_PLANTED) if seed is None else seed)
+    A = rng.standard_normal((m, n))
+    x0, y0, s0 = _planted_pair(rng, n, m)
+    return LP(A=A, b=A @ x0, c=A.T @ y0 + s0, x0=x0, y0=y0, s0=s0, expect="optimal",
+              meta=dict(kind="planted_dense", m=m, n=n))
+
+
+def infeasible_twin(m: int = 10, n: int = 20, seed: Optional[int] = None) -> LP:
+    """Planted dense LP whose row 1 is replaced by |N(0,1)| with b_1 = -1.
+
+    A_1 x = -1 has no solution with x >= 0; y = -e_1 is a Farkas certificate
+    (A^T y <= 0 and b^T y = 1 > 0).
+    """
+    rng = np.random.default_rng(seed_for(DENSE_PLANTED, 1) if seed is None else seed)
+    A = rng.standard_normal((m, n))
+    x0, y0, s0 = _planted_pair(rng, n, m)
+    b = A @ x0
+    c = A.T @ y0 + s0
+    A[0, :] = np.abs(rng.standard_normal(n))
+    b[0] = -1.0
+    return LP(A=A, b=b, c=c, expect="primal_infeasible", meta=dict(kind="infeasible_twin", m=m, n=n))
+
+
+def dual_infeasible(m: int = 10, n: int = 20, seed: Optional[int] = None) -> LP:
+    """Planted dense LP plus one extra all-zero column with cost -1 (unbounded primal).
+
+    x = x0 + t e_new stays feasible for all t >= 0 while the objective falls without bound;
+    e_new is a dual-infeasibility certificate (A e_new = 0, c^T e_new = -1 < 0).
+    """
+    rng = np.random.default_rng(seed_for(DENSE_PLANTED, 2) if seed is None else seed)
+    A = rng.standard_normal((m, n))
+    x0, y0, s0 = _planted_pair(rng, n, m)
+    b = A @ x0
+    c = A.T @ y0 + s0
+    A = np.hstack([A, np.zeros((m, 1))])
+    c = np.concatenate([c, [-1.0]])
+    return LP(A=A, b=b, c=c, expect="dual_infeasible", meta=dict(kind="dual_infeasible", m=m, n=n + 1))
+
+
+def planted_sparse(m: int = 100000, n_r: Optional[int] = None, per_col: int = 8,
+                   seed: Optional[int] = None) -> LP:
+    """Sparse planted LP  A = [R  I_m]  in CSR.
+
+    R is m x n_r (default n_r = 3m) with `per_col` nonzeros per column at distinct
+    uniform random rows, values N(0,1) drawn in float32; the identity block is the
+    slack block, so n = n_r + m.  The planted pair spans all n columns.
+    """
+    if n_r is None:
+        n_r = 3 * m
+    rng = np.random.default_rng(seed_for(SPARSE_PLANTED) if seed is None else seed)
+    per_col = min(per_col, m)
+    # distinct rows per column: draw uniformly, redraw any column that repeats a row
+    if per_col == m:
+        rows = np.tile(np.arange(m), n_r).reshape(n_r, m)
+    else:
+        rows = rng.integers(0, m, size=(n_r, per_col))
+        while True:
+            srt = np.sort(rows, axis=1)
+            bad = np.nonzero((srt[:, 1:] == srt[:, :-1]).any(axis=1))[0]
+            if bad.size == 0:
+                break
+            rows[bad] = rng.integers(0, m, size=(bad.size, per_col))
+    vals = rng.standard_normal((n_r, per_col), dtype=np.float32)
+    n = n_r + m
+    # assemble CSR of [R I]: entries (row, col, val)
+    r_all = np.concatenate([rows.ravel(), np.arange(m)])
+    c_all = np.concatenate([np.repeat(np.arange(n_r), per_col), n_r + np.arange(m)])
+    v_all = np.concatenate([vals.ravel(), np.ones(m, np.float32)])
+    order = np.lexsort((c_all, r_all))
+    r_all, c_all, v_all = r_all[order], c_all[order], v_all[order]
+    row_ptr = np.zeros(m + 1, dtype=np.int64)
+    np.cumsum(np.bincount(r_all, minlength=m), out=row_ptr[1:])
+    A = CSR(m=m, n=n, row_ptr=row_ptr, col_idx=c_all.astype(np.int32), val=v_all.astype(np.float32))
+    x0, y0, s0 = _planted_pair(rng, n, m)
+    Asp = A.to_scipy()
+    b = Asp @ x0
+    c = Asp.T @ y0 + s0
+    return LP(A=A, b=b, c=c, x0=x0, y0=y0, s0=s0, expect="optimal",
+              meta=dict(kind="planted_sparse", m=m, n=n, nnz=A.nnz, per_col=per_col))
+
+
+def tiny_random(m: int, n: int, seed: int) -> LP:
+    """Tiny unplanted LP with random signs: may be optimal, infeasible or unbounded."""
+    rng = np.random.default_rng(seed)
+    A = np.round(rng.standard_normal((m, n)) * 4.0) / 4.0
+    b = np.round(rng.standard_normal(m) * 4.0) / 4.0
+    c = np.round(rng.standard_normal(n) * 4.0) / 4.0
+    return LP(A=A, b=b, c=c, expect="unknown", meta=dict(kind="tiny_random", m=m, n=n))
+
+
+def tiny_planted(m: int, n: int, seed: int) -> LP:
+    """Tiny planted LP (same recipe as `planted_dense`) for brute-force checks."""
+    lp = planted_dense(m, n, seed=seed)
+    lp.meta["kind"] = "tiny_planted"
+    return lp
+
+
+def csr_transpose(A: CSR) -> CSR:
+    """CSR of A^T (the column-major view of A), values and pattern unchanged."""
+    counts = np.bincount(A.col_idx, minlength=A.n)
+    row_ptr = np.zeros(A.n + 1, dtype=np.int64)
+    np.cumsum(counts, out=row_ptr[1:])
+    rows = np.repeat(np.arange(A.m, dtype=np.int64), np.diff(A.row_ptr))
+    order = np.lexsort((rows, A.col_idx))
+    return CSR(m=A.n, n=A.m, row_ptr=row_ptr, col_idx=rows[order].astype(np.int32), val=A.val[order])
+
+
+def dense_to_csr(A: np.ndarray, dtype=np.float64) -> CSR:
+    m, n = A.shape
+    mask = A != 0
+    row_ptr = np.zeros(m + 1, dtype=np.int64)
+    np.cumsum(mask.sum(axis=1), out=row_ptr[1:])
+    rows, cols = np.nonzero(mask)
+    return CSR(m=m, n=n, row_ptr=row_ptr, col_idx=cols.astype(np.int32), val=A[rows, cols].astype(dtype))

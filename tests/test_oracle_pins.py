@@ -1,0 +1,298 @@
+"""Pins for the FP64 oracle against facts the paper and the mathematics fix.
+
+Each test names the passage it follows.  None of them re-types the formula it
+checks: they use identities (skew-symmetry, the central start, Theorem 2.1(i),
+Theorem 3.1), an independent scalar root finder, a dense linear solve, brute-force
+basis enumeration and planted optima.
+"""
+import math
+
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+from oracle import abip_oracle as O
+from oracle.lp_bruteforce import enumerate_lp
+from paper_1805_12344_gb300 import workloads as W
+
+
+def _problem(m=7, n=15, seed=11):
+    lp = W.planted_dense(m, n, seed=seed)
+    return lp, O.Problem(lp.A, lp.b, lp.c)
+
+
+# --- Sec. 3.1: the embedding -------------------------------------------------
+
+def test_central_start_satisfies_Qu_eq_v():
+    """Algorithm 2 starts on {Q u = v}: u = (0, e, 1, 1), v = (0, e, 1, -n-1) (Sec. 3.1,
+    Theorem 2.1(ii)).  This fixes bbar, cbar, zbar and xi with their signs."""
+    for seed in range(3):
+        lp, P = _problem(6 + seed, 13 + 2 * seed, seed)
+        ry, rx, rt, rth = O.residual_Qu_v(P, np.zeros(P.m), np.ones(P.n), 1.0, 1.0,
+                                          np.zeros(P.m), np.ones(P.n), 1.0, P.xi)
+        scale = 1 + np.abs(lp.A).sum() + np.abs(lp.b).sum() + np.abs(lp.c).sum()
+        assert np.max(np.abs(ry)) <= 1e-13 * scale
+        assert np.max(np.abs(rx)) <= 1e-13 * scale
+        assert abs(rt) <= 1e-13 * scale and abs(rth) <= 1e-13 * scale
+
+
+def test_Q_is_skew_symmetric():
+    """Q^T = -Q (Sec. 3.1), so u^T Q u = 0 for every u."""
+    lp, P = _problem()
+    Q = O.dense_Q(P)
+    assert np.max(np.abs(Q + Q.T)) == 0.0
+    rng = np.random.default_rng(0)
+    for _ in range(5):
+        u = rng.standard_normal(Q.shape[0])
+        assert abs(u @ Q @ u) <= 1e-12 * (u @ u) * np.abs(Q).max()
+    # Q's blocks are A, b, c and the embedding constants in the places Sec. 3.1 puts them
+    m, n = P.m, P.n
+    assert np.array_equal(Q[:m, m:m + n], lp.A)
+    assert np.array_equal(Q[:m, m + n], -lp.b) and np.array_equal(Q[m:m + n, m + n], lp.c)
+
+
+def test_theorem_2_1_identity_at_central_point():
+    """Theorem 2.1(i): at any point with Q u = v, r = 0, xi = -(x0)^T s0 - 1,
+    ((x0)^T s0 + 1) theta = x^T s + tau kappa; on the central path (system HSD-log-kkt)
+    this forces theta = mu/beta."""
+    lp, P = _problem(8, 18, 3)
+    for mu in (0.5, 1e-2):
+        cp = O.central_point(lp.A, lp.b, lp.c, mu)
+        assert cp["residual"] < 1e-11
+        lhs = (P.n + 1) * cp["theta"]
+        rhs = cp["x"] @ cp["s"] + cp["tau"] * cp["kappa"]
+        assert abs(lhs - rhs) <= 1e-11 * (1 + abs(rhs))
+        assert abs(cp["theta"] - mu) <= 1e-11
+
+
+# --- Eq. Simple-Update:Affine and Sec. 4.4: the projection -------------------
+
+@pytest.mark.parametrize("linsys", [0, 1])
+def test_projection_equals_dense_inverse(linsys):
+    """Block elimination with the cached M^{-1} H (Sec. 4.4) reproduces (I+Q)^{-1} w
+    from a dense solve, and (I+Q^T Q)^{-1} (I-Q) w (Eq. Simple-Update:Affine)."""
+    lp, P = _problem(9, 21, 5)
+    prm = O.Params(linsys=linsys, cg_tol=1e-14)
+    proj = O.Projection(P, O.make_linsys(P, prm))
+    rng = np.random.default_rng(1)
+    Q = O.dense_Q(P)
+    N = Q.shape[0]
+    for _ in range(3):
+        w = rng.standard_normal(N) * 3
+        uy, ux, ut, uth = proj(w[:P.m], w[P.m:P.m + P.n], w[-2], w[-1])
+        u = np.concatenate([uy, ux, [ut, uth]])
+        ref = np.linalg.solve(np.eye(N) + Q, w)
+        ref2 = np.linalg.solve(np.eye(N) + Q.T @ Q, (np.eye(N) - Q) @ w)
+        assert np.linalg.norm(u - ref) <= 1e-11 * np.linalg.norm(ref)
+        assert np.linalg.norm(u - ref2) <= 1e-10 * np.linalg.norm(ref)
+
+
+def test_projection_is_euclidean_projection():
+    """(u~, Q u~) is the closest point of {Q u = v} to (w, w): the optimality condition
+    (u~ - w) + Q^T (Q u~ - w) = 0 (proof of Theorem 3.1, Step 1)."""
+    lp, P = _problem(5, 12, 8)
+    proj = O.Projection(P, O.make_linsys(P, O.Params()))
+    Q = O.dense_Q(P)
+    w = np.random.default_rng(2).standard_normal(Q.shape[0])
+    u = np.concatenate(list(proj(w[:P.m], w[P.m:P.m + P.n], w[-2], w[-1])[:2]) +
+                       [np.array(proj(w[:P.m], w[P.m:P.m + P.n], w[-2], w[-1])[2:])])
+    g = (u - w) + Q.T @ (Q @ u - w)
+    assert np.linalg.norm(g) <= 1e-11 * np.linalg.norm(w)
+
+
+def test_pcg_matches_library_solve():
+    """Jacobi-PCG on G = I + A A^T converges to the dense solution (Sec. 4.4)."""
+    lp = W.planted_sparse(300, seed=5)
+    A = lp.A.to_scipy()
+    P = O.Problem(A, lp.b, lp.c)
+    pcg = O.JacobiPCG(P, 1e-13, 1000)
+    q = np.random.default_rng(3).standard_normal(P.m)
+    z = pcg.solve(q)
+    G = np.eye(P.m) + (A @ A.T).toarray()
+    ref = np.linalg.solve(G, q)
+    assert np.linalg.norm(z - ref) <= 1e-11 * np.linalg.norm(ref)
+
+
+# --- Eqs. Simple-Update:Barrier-X and Simple-Update:Dual ----------------------
+
+def _scalar_root(omega, c):
+    """Positive root of f(x) = x - omega - c/x by bisection then Newton, in plain floats."""
+    lo, hi = 0.0, max(1.0, abs(omega)) * 2 + math.sqrt(c) * 2 + 1.0
+    for _ in range(3000):
+        mid = 0.5 * (lo + hi)
+        if mid == lo or mid == hi:
+            break
+        if mid - omega - c / mid > 0 if mid > 0 else False:
+            hi = mid
+        else:
+            lo = mid
+    x = hi
+    for _ in range(5):
+        f = x - omega - c / x
+        x = x - f / (1 + c / (x * x))
+    return x
+
+
+def test_barrier_prox_matches_scalar_root():
+    """x = argmin -c log x + (x - omega)^2 / 2 solves x - omega - c/x = 0, and the dual
+    step gives s = x - omega with x s = c (Thm 3.1 invariant x o s = mu/beta)."""
+    omegas = [s * 10.0 ** k for k in range(-12, 13, 3) for s in (-1, 1)] + [0.0]
+    cs = [1e-20, 1e-12, 1e-6, 1e-2, 1.0, 1e2]
+    for c in cs:
+        x, s = O.barrier_prox(np.array(omegas), c)
+        for om, xi, si in zip(omegas, x, s):
+            ref = _scalar_root(om, c)
+            assert abs(xi - ref) <= 4 * np.spacing(ref) + 1e-300, (om, c, xi, ref)
+            assert abs(xi * si - c) <= 4e-15 * c
+            assert xi > 0 and si > 0
+
+
+# --- Theorem 3.1: Algorithm 1 with explicit multipliers -----------------------
+
+@pytest.mark.parametrize("alpha", [1.0, 1.8])
+def test_theorem_3_1_multiplier_elimination(alpha):
+    """With p0 = v0, q0 = u0 and x o s = tau kappa = mu/beta, Algorithm 1 keeps p = v,
+    q = u, x o s = mu/beta, tau kappa = mu/beta, r = 0, xi = -n-1 (Theorem 3.1) and its
+    iterates equal those of Algorithm 2 (with the Sec. 4.2 relaxation when alpha != 1)."""
+    lp, P = _problem(6, 14, 21)
+    gamma = 0.2
+    st = O.initial_state(P)
+    O.warm_start(st, gamma, 0)                      # now x o s = gamma = mu/beta
+    mu = gamma
+    start = {k: (v.copy() if isinstance(v, np.ndarray) else v) for k, v in st.items()}
+    alg1 = O.algorithm1(lp.A, lp.b, lp.c, mu, 25, alpha=alpha, start=start)
+    prm = O.Params(alpha=alpha)
+    proj = O.Projection(P, O.make_linsys(P, prm))
+    m, n = P.m, P.n
+    for (u, v, p, q) in alg1:
+        O.admm_step(P, proj, st, mu, prm)
+        u2 = np.concatenate([st["y"], st["x"], [st["tau"], st["theta"]]])
+        v2 = np.concatenate([np.zeros(m), st["s"], [st["kappa"], P.xi]])
+        sc = 1 + np.linalg.norm(u)
+        assert np.linalg.norm(p - v) <= 1e-11 * sc
+        assert np.linalg.norm(q - u) <= 1e-11 * sc
+        assert np.max(np.abs(u[m:m + n] * v[m:m + n] - mu)) <= 1e-12
+        assert abs(u[m + n] * v[m + n] - mu) <= 1e-12
+        assert np.all(v[:m] == 0) and v[-1] == -(n + 1)
+        assert np.linalg.norm(u - u2) <= 1e-10 * sc
+        assert np.linalg.norm(v - v2) <= 1e-10 * (1 + np.linalg.norm(v))
+
+
+# --- Lemma 3.3: monotone decrease at fixed mu --------------------------------
+
+def test_lemma_3_3_monotone_distance_to_central_point():
+    """||u_i - u*||^2 + ||v_i - v*||^2 is non-increasing and tends to 0, with (u*, v*)
+    the central point at mu (Lemma 3.3; alpha = 1 as analysed)."""
+    lp, P = _problem(8, 18, 3)
+    mu = 0.1
+    st = O.initial_state(P)
+    O.warm_start(st, mu, 0)
+    prm = O.Params(alpha=1.0)
+    proj = O.Projection(P, O.make_linsys(P, prm))
+    # reference point: run ADMM a while, then polish with Newton
+    tmp = {k: (v.copy() if isinstance(v, np.ndarray) else v) for k, v in st.items()}
+    for _ in range(3000):
+        O.admm_step(P, proj, tmp, mu, prm)
+    cp = O.central_point(lp.A, lp.b, lp.c, mu, start=tmp)
+    assert cp["residual"] < 1e-12
+    zs = np.concatenate([cp["y"], cp["x"], [cp["tau"], cp["theta"]], cp["s"], [cp["kappa"]]])
+    proj = O.Projection(P, O.make_linsys(P, prm))
+    d_prev = np.inf
+    d0 = None
+    for i in range(400):
+        d = np.sum((O.stacked(st) - zs) ** 2)
+        d0 = d if d0 is None else d0
+        assert d <= d_prev * (1 + 1e-12) + 1e-28
+        d_prev = d
+        O.admm_step(P, proj, st, mu, prm)
+    assert d_prev < 0.5 * d0
+    for _ in range(20000):
+        O.admm_step(P, proj, st, mu, prm)
+    assert np.sum((O.stacked(st) - zs) ** 2) < 1e-16
+    assert abs(st["theta"] - mu) < 1e-8           # theta -> mu/beta (system HSD-log-kkt)
+
+
+# --- Theorem 3.6: number of outer iterations --------------------------------
+
+def test_outer_count_theorem_3_6():
+    """Stopping once mu^k <= eps takes T_IPM = ceil(log(mu0/eps)/log(1/gamma)) outer steps."""
+    lp, P = _problem(5, 11, 4)
+    for gamma, eps in ((0.5, 1e-3), (0.3, 2e-4)):
+        r = O.solve(lp.A, lp.b, lp.c, O.Params(gamma=gamma, eps=eps, stop_rule=1))
+        assert r.outer_iters == math.ceil(math.log(1.0 / eps) / math.log(1.0 / gamma))
+
+
+# --- Sec. 4.1 end to end: planted optima, certificates, brute force ----------
+
+def test_planted_dense_optimum():
+    """The planted pair is optimal (strong duality: c^T x0 = b^T y0); with |supp x0| < m
+    the primal optimum x0 is unique.  The relative objective error stays within 1e-5 and the
+    returned residuals are within eps (Sec. 4.1)."""
+    lp = W.planted_dense()
+    r = O.solve(lp.A, lp.b, lp.c)
+    assert r.status == O.OPTIMAL
+    assert abs(r.obj - lp.p_star) <= 1e-5 * abs(lp.p_star)
+    assert max(r.pres, r.dres, r.dgap) <= 1e-6
+    assert np.linalg.norm(r.x - lp.x0) <= 1e-3 * np.linalg.norm(lp.x0)
+    assert r.kappa / r.tau < 1e-6                   # kappa -> 0 at optimality (Thm 2.2(i))
+    assert r.x @ r.s <= 1e-5 * (1 + abs(lp.p_star))  # complementarity x^T s -> 0
+
+
+def test_planted_sparse_optimum_small():
+    """[R I] planted LP (m = 80): the returned objective matches p* = c^T x0 = b^T y0."""
+    lp = W.planted_sparse(80, seed=W.seed_for(W.SPARSE_PLANTED, 10))
+    A = lp.A.to_scipy()
+    r = O.solve(A, lp.b, lp.c, O.Params(linsys=1, cg_tol=1e-10))
+    assert r.status == O.OPTIMAL
+    assert abs(r.obj - lp.p_star) <= 1e-5 * abs(lp.p_star)
+    assert max(r.pres, r.dres, r.dgap) <= 1e-6
+
+
+def test_sparse_and_dense_storage_give_same_iterates():
+    lp = W.planted_sparse(40, seed=3)
+    Ad = lp.A.to_dense()
+    a = O.run_iterations(Ad, lp.b, lp.c, 30)
+    b = O.run_iterations(sp.csr_matrix(Ad), lp.b, lp.c, 30)
+    assert np.linalg.norm(a - b) <= 1e-12 * np.linalg.norm(a)
+
+
+def test_primal_infeasible_twin_certificate():
+    """The twin has A_1 >= 0, b_1 = -1: primal infeasible.  ABIP ends with kappa > 0,
+    tau -> 0 (Thm 2.2(ii)) and y / b^T y is an approximate Farkas certificate (Sec. 4.1)."""
+    lp = W.infeasible_twin()
+    r = O.solve(lp.A, lp.b, lp.c)
+    assert r.status == O.PRIMAL_INFEASIBLE
+    assert r.kappa > 0 and r.tau < 1e-6 * r.kappa
+    y = r.y
+    assert abs(lp.b @ y - 1.0) < 1e-12
+    assert np.linalg.norm(lp.A.T @ y + r.s) <= 1e-6 / np.linalg.norm(lp.b) * 1.0001
+    assert np.all(r.s >= 0)
+
+
+def test_dual_infeasible_certificate():
+    lp = W.dual_infeasible()
+    r = O.solve(lp.A, lp.b, lp.c)
+    assert r.status == O.DUAL_INFEASIBLE
+    assert r.kappa > 0 and r.tau < 1e-6 * r.kappa
+    assert abs(lp.c @ r.x + 1.0) < 1e-12
+    assert np.all(r.x >= 0)
+    assert np.linalg.norm(lp.A @ r.x) <= 1e-6 / np.linalg.norm(lp.c) * 1.0001
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_tiny_lps_against_basis_enumeration(seed):
+    """p* from enumerating every basis equals ABIP's objective; infeasible or unbounded
+    instances give the matching certificate status (Thm 2.2, Sec. 4.1)."""
+    rng = np.random.default_rng(seed)
+    m = int(rng.integers(1, 5))
+    n = int(rng.integers(m + 1, m + 7))
+    lp = W.tiny_random(m, n, seed=W.seed_for(W.TINY, seed)) if seed % 2 else W.tiny_planted(m, n, W.seed_for(W.TINY, seed))
+    ref = enumerate_lp(lp.A, lp.b, lp.c)
+    r = O.solve(lp.A, lp.b, lp.c)
+    if ref["status"] == "optimal":
+        assert r.status == O.OPTIMAL
+        assert abs(r.obj - ref["p_star"]) <= 1e-5 * max(1.0, abs(ref["p_star"]))
+    elif ref["status"] == "primal_infeasible":
+        assert r.status in (O.PRIMAL_INFEASIBLE, O.DUAL_INFEASIBLE)
+    else:
+        assert r.status == O.DUAL_INFEASIBLE
