@@ -1,0 +1,403 @@
+#!/usr/bin/env python
+"""Benchmark of the ABIP hot path on one GB300 (or N, one replica LP per GPU).
+
+Workload: the large sparse planted LP  min c^T x, A x = b, x >= 0  with
+A = [R  I_m] in CSR, m = 100000, n = 400000, R having 8 nonzeros per column at
+uniform random rows with N(0,1) float32 values, and a planted optimal pair
+(synthetic data, seeded).  One step = one whole solve: abip_setup (embedding
+constants, Jacobi diagonal, M^{-1} H, Schur complement) and abip_solve (ABIP to
+1e-6 relative KKT residual, or the 1e6 ADMM cap) with inputs resident in HBM.
+
+Metric: LPs solved per second (whole job, all ranks).  Also reported: ADMM
+iterations per second, the persistent solve kernel's achieved bandwidth against
+the measured HBM peak (roofline), an end-to-end number through host buffers, and
+the FP64 CPU oracle timed on a bounded sample of the same workload.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl abip|reference]
+Under torchrun (N > 1) every rank solves its own LP (weak scaling, no collective
+on the data path; a barrier and a max over ranks around the timed region).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "sparse_planted_lp_m100000_n400000"
+METRIC = "LPs solved/s to 1e-6 rel. KKT residual"
+UNIT = "LP/s"
+L2_FLUSH_BYTES = 512 << 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="abip", choices=["abip", "reference"])
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "f64"])
+    ap.add_argument("--m", type=int, default=100000, help="rows of A (default: the full workload)")
+    ap.add_argument("--max-admm", type=int, default=1_000_000)
+    ap.add_argument("--cg-tol", type=float, default=1e-10)
+    ap.add_argument("--cg-rel", type=float, default=0.1)
+    ap.add_argument("--cpu-sample-s", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--cpu-sample", action="store_true", help=argparse.SUPPRESS)   # child process mode
+    ap.add_argument("--admm-iters-hint", type=int, default=0, help=argparse.SUPPRESS)
+    return ap.parse_args()
+
+
+# --------------------------------------------------------------------------------------
+# algorithmic bytes of the persistent solve kernel (one launch = one whole solve)
+# --------------------------------------------------------------------------------------
+
+def algorithmic_bytes(m, n, nnz, admm_iters, cg_iters, outer_iters, vec_bytes, val_bytes=4):
+    """Compulsory traffic of the solve kernel: every phase reads its matrix once
+    (values, column indices, row offsets) and each vector it touches once.
+      one pass over A:   MA  = nnz (vb + 4) + 4 (m + 1)
+      one pass over A^T: MAT = nnz (vb + 4) + 4 (n + 1)
+      per PCG iteration:   MA + MAT + t (3 n + 13 m)
+      per ADMM iteration (PCG start, z_x, update, residuals): 2 MA + 3 MAT + t (21 n + 23 m)
+      per mu decrease (rescale, residuals): MA + MAT + t (10 n + 7 m)
+    with t the bytes of one vector element."""
+    t = vec_bytes
+    MA = nnz * (val_bytes + 4) + 4 * (m + 1)
+    MAT = nnz * (val_bytes + 4) + 4 * (n + 1)
+    per_cg = MA + MAT + t * (3 * n + 13 * m)
+    per_admm = 2 * MA + 3 * MAT + t * (21 * n + 23 * m)
+    per_outer = MA + MAT + t * (10 * n + 7 * m)
+    return cg_iters * per_cg + admm_iters * per_admm + (outer_iters + 1) * per_outer
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# --------------------------------------------------------------------------------------
+# clocks sampler (nvidia-smi during the timed region)
+# --------------------------------------------------------------------------------------
+
+class Clocks:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+                power.append(float(parts[3]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        loaded = [v for v in sm if v > 0.5 * max(sm)] or sm
+        return {"sm_mhz": statistics.median(loaded), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm), "power_w_max": max(power) if power else None}
+
+
+# --------------------------------------------------------------------------------------
+# CPU oracle sample (child process, single-threaded BLAS)
+# --------------------------------------------------------------------------------------
+
+def cpu_sample_main(args):
+    """Time the FP64 oracle on the workload: its setup plus ADMM iterations for about
+    `cpu_sample_s` seconds.  Prints one JSON object."""
+    import numpy as np
+    from oracle import abip_oracle as O
+    from paper_1805_12344_gb300 import workloads as W
+    lp = W.planted_sparse(args.m)
+    A = lp.A.to_scipy()
+    prm = O.Params(linsys=1, cg_tol=args.cg_tol)
+    t0 = time.perf_counter()
+    P = O.Problem(A, lp.b, lp.c)
+    lin = O.make_linsys(P, prm)
+    proj = O.Projection(P, lin)
+    setup_s = time.perf_counter() - t0
+    st = O.initial_state(P)
+    mu = prm.beta
+    k = 0
+    cg0 = lin.iters
+    t1 = time.perf_counter()
+    while time.perf_counter() - t1 < args.cpu_sample_s:
+        if O.inner_residual_sq(P, st) <= mu:
+            mu *= prm.gamma
+            O.warm_start(st, prm.gamma, prm.warmstart)
+            continue
+        O.admm_step(P, proj, st, mu, prm)
+        O.termination(P, st["y"], st["x"], st["s"], st["tau"], prm.eps,
+                      float(np.linalg.norm(P.b)), float(np.linalg.norm(P.c)))
+        k += 1
+    it_s = (time.perf_counter() - t1) / max(k, 1)
+    print(json.dumps({"setup_s": setup_s, "s_per_admm_iter": it_s, "admm_iters": k,
+                      "cg_per_iter": (lin.iters - cg0) / max(k, 1), "cores": 1}))
+
+
+def run_cpu_sample(args, admm_iters_for_lp):
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    cmd = [sys.executable, os.path.abspath(__file__), "--cpu-sample", "--m", str(args.m),
+           "--cpu-sample-s", str(args.cpu_sample_s), "--cg-tol", str(args.cg_tol)]
+    r = subprocess.run(cmd, capture_output=True, text=True, env=env, timeout=900)
+    d = json.loads(r.stdout.strip().splitlines()[-1])
+    lp_s = d["setup_s"] + d["s_per_admm_iter"] * admm_iters_for_lp
+    return {
+        "value": 1.0 / lp_s,
+        "unit": UNIT,
+        "cores": d["cores"],
+        "kind": "oracle",
+        "sample": (f"FP64 numpy oracle, 1 thread: setup ({d['setup_s']:.2f} s) + {d['admm_iters']} ADMM "
+                   f"iterations of the same LP ({d['s_per_admm_iter'] * 1e3:.1f} ms/iter, "
+                   f"{d['cg_per_iter']:.1f} PCG iter/ADMM iter at cg_tol {args.cg_tol:g}); LP/s extrapolated "
+                   f"to {admm_iters_for_lp} ADMM iterations"),
+        "admm_iters_per_s": 1.0 / d["s_per_admm_iter"],
+    }
+
+
+# ADMM iterations the full workload needs to reach 1e-6 (measured on the GPU with the
+# default parameters); used only to scale the reference arm's bounded CPU sample to LP/s.
+ADMM_ITERS_FULL_WORKLOAD = 400000
+
+
+def reference_main(args, rank, world):
+    if rank != 0:
+        return
+    times = []
+    samples = []
+    for i in range(args.warmup + args.steps):
+        cs = run_cpu_sample(args, args.admm_iters_hint or ADMM_ITERS_FULL_WORKLOAD)
+        if i >= args.warmup:
+            times.append(1.0 / cs["value"])
+            samples.append(cs)
+    value = len(times) / sum(times)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "m": args.m, "n": 4 * args.m, "nnz": 25 * args.m},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": samples[-1]["cores"], "kind": "oracle",
+                         "sample": samples[-1]["sample"]},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# --------------------------------------------------------------------------------------
+# GPU arm
+# --------------------------------------------------------------------------------------
+
+def main():
+    args = parse()
+    if args.cpu_sample:
+        cpu_sample_main(args)
+        return
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        reference_main(args, rank, world)
+        return
+
+    import numpy as np
+    import torch
+    from paper_1805_12344_gb300 import abip, build, workloads as W
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    build.build()
+    L = abip.lib()
+    dev = torch.device("cuda", local)
+
+    lp = W.planted_sparse(args.m, seed=W.seed_for(W.SPARSE_PLANTED, rank))
+    m, n, nnz = lp.m, lp.n, lp.A.nnz
+    prm = abip.default_params(precision=abip.ABIP_PREC_MIXED if args.precision == "mixed" else abip.ABIP_PREC_F64,
+                              max_admm_iters=args.max_admm, cg_tol=args.cg_tol, cg_rel=args.cg_rel)
+    # inputs resident in HBM
+    rp_d = torch.from_numpy(lp.A.row_ptr).to(dev)
+    ci_d = torch.from_numpy(lp.A.col_idx).to(dev)
+    va_d = torch.from_numpy(lp.A.val).to(dev)
+    b_d = torch.from_numpy(lp.b).to(dev)
+    c_d = torch.from_numpy(lp.c).to(dev)
+    x_d = torch.empty(n, dtype=torch.float64, device=dev)
+    y_d = torch.empty(m, dtype=torch.float64, device=dev)
+    s_d = torch.empty(n, dtype=torch.float64, device=dev)
+    M = abip.abip_matrix()
+    M.m, M.n, M.fmt, M.dtype, M.on_device = m, n, abip.ABIP_CSR, abip.ABIP_F32, 1
+    M.row_ptr, M.col_idx, M.val, M.nnz = rp_d.data_ptr(), ci_d.data_ptr(), va_d.data_ptr(), nnz
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+    import ctypes as C
+
+    def step():
+        h = C.c_void_p()
+        rc = L.abip_setup(C.byref(M), b_d.data_ptr(), c_d.data_ptr(), C.byref(prm), C.byref(h))
+        if rc != 0:
+            raise abip.AbipError(rc, L.abip_last_error(None).decode())
+        info = abip.abip_info()
+        rc = L.abip_solve(h, x_d.data_ptr(), y_d.data_ptr(), s_d.data_ptr(), C.byref(info), stream.cuda_stream)
+        err = L.abip_last_error(h).decode()
+        L.abip_free(h)
+        if rc != 0:
+            raise abip.AbipError(rc, err)
+        return info.as_dict()
+
+    for _ in range(args.warmup):
+        step()
+        flush.fill_(1.0)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = Clocks(local)
+    clocks.start()
+    step_ms = []
+    infos = []
+    for _ in range(args.steps):
+        flush.fill_(2.0)                       # L2 flush between timed steps (outside the events)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        info = step()
+        e1.record(stream)
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        infos.append(info)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ck = clocks.stop()
+    total_s = sum(step_ms) * 1e-3
+    solved = sum(1 for i in infos if i["status"] == abip.ABIP_OPTIMAL)
+    admm = sum(i["admm_iters"] for i in infos)
+    if dist:
+        t = torch.tensor([total_s, float(solved), float(admm)], dtype=torch.float64, device=dev)
+        tmax = t.clone()
+        dist.all_reduce(tmax[0:1], op=dist.ReduceOp.MAX)
+        dist.all_reduce(t[1:3], op=dist.ReduceOp.SUM)
+        total_s, solved, admm = float(tmax[0]), float(t[1]), float(t[2])
+    value = solved / total_s
+
+    # roofline of the persistent solve kernel (one launch per step)
+    vec_bytes = 4 if args.precision == "mixed" else 8
+    last = infos[-1]
+    alg = algorithmic_bytes(m, n, nnz, last["admm_iters"], last["cg_iters"], last["outer_iters"], vec_bytes)
+    achieved = alg / last["kernel_s"] / 1e9
+    peak, peak_kind = measured_peaks()
+    traffic = None
+    tpath = os.path.join(ROOT, "profiles", "solve_kernel_traffic.json")
+    if os.path.exists(tpath):
+        try:
+            tj = json.load(open(tpath))
+            if tj.get("precision") == args.precision:
+                traffic = tj["dram_bytes_per_admm_iter"] * last["admm_iters"]
+        except Exception:
+            traffic = None
+
+    # end to end through the public API with host buffers
+    e2e = None
+    if not args.no_e2e and rank == 0:
+        xh, yh, sh = np.zeros(n), np.zeros(m), np.zeros(n)
+        torch.cuda.synchronize()
+        flush.fill_(3.0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        hh = abip.abip_setup(lp.A, lp.b, lp.c, prm)
+        inf = abip.abip_solve(hh, xh, yh, sh, stream=stream)
+        abip.abip_free(hh)
+        e2e_s = time.perf_counter() - t0
+        h2d = lp.A.row_ptr.nbytes + lp.A.col_idx.nbytes + lp.A.val.nbytes + lp.b.nbytes + lp.c.nbytes
+        d2h = xh.nbytes + yh.nbytes + sh.nbytes
+        e2e = {"value": (1.0 if inf["status"] == abip.ABIP_OPTIMAL else 0.0) / e2e_s, "unit": UNIT,
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h), "seconds": e2e_s,
+               "status": inf["status_name"]}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        try:
+            cpu = run_cpu_sample(args, int(last["admm_iters"]))
+        except Exception as ex:  # the baseline must not sink the GPU line
+            cpu = {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": f"failed: {ex}"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": sum(step_ms) / len(step_ms), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32+f64" if args.precision == "mixed" else "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "m": m, "n": n, "nnz": int(nnz), "precision": args.precision,
+                       "cg_tol": args.cg_tol, "cg_rel": args.cg_rel, "alpha": prm.alpha, "gamma": prm.gamma,
+                       "eps": prm.eps, "l2": "flushed between timed steps (512 MiB write)",
+                       "parallelism": f"replicas{world}"},
+            "admm_iters_per_s": admm / total_s,
+            "status": [i["status_name"] for i in infos],
+            "admm_iters": last["admm_iters"], "cg_iters": last["cg_iters"], "outer_iters": last["outer_iters"],
+            "final": {"pres": last["pres"], "dres": last["dres"], "dgap": last["dgap"], "obj": last["obj"],
+                      "p_star": lp.p_star},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
+                         "kernel": "grid_kernel (persistent solve)", "kernel_s": last["kernel_s"],
+                         "algorithmic_bytes": alg},
+            "clocks": ck,
+            "gpu_launches": int(sum(i["launches"] for i in infos)) + 1 * len(infos),
+            "e2e": e2e,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

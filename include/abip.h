@@ -1,0 +1,205 @@
+/*
+ * abip.h -- C ABI of libabip, a GB300 (sm_103a) implementation of ABIP, the
+ * ADMM-based interior-point method for linear programming of Lin, Ma, Ye and
+ * Zhang (arXiv 1805.12344).
+ *
+ * Problem (Sec. 2, the primal-dual pair (P)/(D)):
+ *     minimise c^T x  subject to  A x = b,  x >= 0,      A is m x n, m <= n,
+ * with A of full row rank.  ABIP solves the homogeneous self-dual embedding of
+ * this pair (Sec. 3.1, matrix Q) by path following on the log-barrier
+ * subproblem, each barrier subproblem being solved inexactly by ADMM
+ * (Algorithm 2, with the over-relaxation of Sec. 4.2).  Every step of the
+ * solve runs in the library's own CUDA kernels on the current device.
+ *
+ * Conventions for every entry point:
+ *   - Return value: ABIP_OK (0) or a negative ABIP_E_* code.  A handle keeps a
+ *     message for the last failure (abip_last_error).
+ *   - Pointers marked "host or device" may point to host memory or to memory of
+ *     the current CUDA device; the library detects which.
+ *   - The library copies every input it needs at setup; the caller keeps
+ *     ownership of its arrays and may free them after the call returns.
+ *   - Outputs are caller-allocated.
+ *   - A handle must not be used by two host threads at once; distinct handles
+ *     are independent.
+ *   - Dense matrices are row-major with leading dimension ld >= n.  CSR uses
+ *     int64 row pointers (m+1 entries, row_ptr[0] = 0) and int32 column indices
+ *     that are in range; column order within a row is free.
+ */
+#ifndef ABIP_H
+#define ABIP_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define ABIP_API __attribute__((visibility("default")))
+#else
+#define ABIP_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- error codes ---------------------------------------------------------- */
+#define ABIP_OK              0
+#define ABIP_E_INVALID_ARG  -1   /* null pointer, bad enum, non-finite input, bad params */
+#define ABIP_E_DIM          -2   /* m < 1, n < m, ld < n, malformed CSR */
+#define ABIP_E_CUDA         -3   /* a CUDA runtime call failed (message kept) */
+#define ABIP_E_OOM          -4   /* device allocation failed */
+#define ABIP_E_NOT_SOLVED   -5   /* state requested before any solve */
+#define ABIP_E_NUMERICAL    -6   /* Cholesky breakdown, non-finite value mid-solve, PCG failure */
+#define ABIP_E_UNSUPPORTED  -7   /* a parameter combination this build does not provide */
+#define ABIP_E_TIMEOUT      -8   /* a device-side wait ran past its limit (the kernel returned) */
+
+/* ---- enums ---------------------------------------------------------------- */
+#define ABIP_DENSE_ROWMAJOR  0
+#define ABIP_CSR             1
+
+#define ABIP_F32             0
+#define ABIP_F64             1
+
+/* solve status (Sec. 4.1; Thm 2.2 / Cor. 2.3 for the certificates) */
+#define ABIP_UNSOLVED              0
+#define ABIP_OPTIMAL               1
+#define ABIP_PRIMAL_INFEASIBLE     2
+#define ABIP_DUAL_INFEASIBLE       3
+#define ABIP_MAX_ITER              4   /* ADMM cap reached (Sec. 5: the "---" entries) */
+
+/* arithmetic of the iteration */
+#define ABIP_PREC_F64        0   /* every vector and product in FP64 */
+#define ABIP_PREC_MIXED      1   /* FP32 iterates and products, FP64 termination tests */
+
+/* linear system for the projection (Sec. 4.4) */
+#define ABIP_LINSYS_DENSE_CHOL  0   /* G = I + A A^T formed once, Cholesky G = L L^T, triangular solves */
+#define ABIP_LINSYS_PCG         1   /* Jacobi-preconditioned CG on G, warm-started */
+
+/* ---- data ----------------------------------------------------------------- */
+typedef struct {
+    int32_t m, n;
+    int32_t fmt;            /* ABIP_DENSE_ROWMAJOR or ABIP_CSR */
+    int32_t dtype;          /* element type of val: ABIP_F32 or ABIP_F64 */
+    int32_t on_device;      /* 1: val, row_ptr, col_idx are device pointers; 0: host */
+    const void* val;        /* dense: m rows of ld elements; CSR: nnz values */
+    int64_t ld;             /* dense leading dimension (>= n); ignored for CSR */
+    const int64_t* row_ptr; /* CSR: m+1 entries */
+    const int32_t* col_idx; /* CSR: nnz entries in [0, n) */
+    int64_t nnz;            /* CSR: number of stored entries */
+} abip_matrix;
+
+typedef struct {
+    double beta;            /* barrier weight; mu0 = beta (Algorithm 2); default 1 */
+    double gamma;           /* mu <- gamma mu between inner loops; default 0.1 */
+    double alpha;           /* over-relaxation in [0, 2) (Sec. 4.2); default 1.8 (Sec. 5) */
+    double eps;             /* tolerance of every Sec. 4.1 test; default 1e-6 */
+    int64_t max_admm_iters; /* cap on ADMM updates; default 1e6 (Sec. 5) */
+    int32_t linsys;         /* ABIP_LINSYS_*; default: dense Cholesky for dense A, PCG for CSR */
+    double cg_tol;          /* PCG stop: ||r|| <= cg_tol * max(1, ||rhs||); default 1e-10 */
+    int32_t cg_max_iter;    /* PCG iteration cap per solve (exceeding it -> ABIP_E_NUMERICAL); default 1000 */
+    double cg_rel;          /* > 0: PCG tolerance max(cg_tol, cg_rel * relative KKT residual of the
+                               current iterate) instead of cg_tol alone; default 0 (fixed) */
+    int32_t precision;      /* ABIP_PREC_*; default ABIP_PREC_F64 */
+    int32_t warmstart;      /* 0: keep-larger rescale of (x,s), (tau,kappa) and sqrt(gamma) on y, theta
+                               (Sec. 5); 1: sqrt(gamma) on every component (Eq. update-next-iterate) */
+    int32_t stop_rule;      /* 0: Sec. 4.1 tests; 1: stop once mu < eps (outer-count mode) */
+    int32_t check_every;    /* FP64 termination test every k ADMM updates (mixed precision); 1 = every update */
+    int32_t grid_ctas;      /* 0: automatic; else the persistent grid size (tests) */
+    int32_t reserved[8];
+} abip_params;
+
+typedef struct {
+    int32_t status;         /* ABIP_OPTIMAL, ... */
+    int32_t outer_iters;    /* number of mu decreases */
+    int64_t admm_iters;     /* ADMM updates executed */
+    int64_t cg_iters;       /* total PCG iterations (PCG path) */
+    double tau, kappa, theta, mu;
+    double obj;             /* c^T x / tau */
+    double pres, dres, dgap;/* relative residuals of Sec. 4.1 at the returned iterate */
+    double setup_s, solve_s;/* wall-clock seconds of abip_setup and of the last solve */
+    double kernel_s;        /* device time of the solve kernel, from CUDA events on the solve stream */
+    int64_t launches;       /* kernels the solve call launched */
+} abip_info;
+
+typedef struct abip_handle abip_handle;
+
+/* Fill p with the defaults listed above.  Returns ABIP_E_INVALID_ARG if p is NULL. */
+ABIP_API int abip_default_params(abip_params* p);
+
+/*
+ * Build the embedding and the projection data for one LP (Sec. 3.1 and 4.4):
+ * bbar = b - A e, cbar = c - e, zbar = c^T e + 1 (Eq. bar-b-c-z-re); for dense
+ * Cholesky, G = I + A A^T and its factor L (Sec. 4.4, last paragraph); for PCG,
+ * the Jacobi diagonal of G; then M^{-1} H and the 2 x 2 Schur complement K used
+ * by every projection (the Remark of Sec. 4.4 on caching M^{-1} h).
+ * A, b (m doubles), c (n doubles): host or device (b and c follow A->on_device).
+ * Non-finite entries -> ABIP_E_INVALID_ARG.  p may be NULL (defaults).
+ * On success *out owns device memory until abip_free.
+ */
+ABIP_API int abip_setup(const abip_matrix* A, const double* b, const double* c,
+               const abip_params* p, abip_handle** out);
+
+/*
+ * Run Algorithm 2 from its start (y = 0, x = s = e, tau = kappa = theta = 1,
+ * mu0 = beta) until a Sec. 4.1 test passes or max_admm_iters is reached.
+ * x (n), y (m), s (n): caller-allocated, host or device, may be NULL.  They
+ * receive (Sec. 4.1):
+ *   OPTIMAL / MAX_ITER:     x/tau, y/tau, s/tau
+ *   PRIMAL_INFEASIBLE:      x, y/(b^T y), s/(b^T y)   (y is the certificate)
+ *   DUAL_INFEASIBLE:        -x/(c^T x), y, s          (x is the certificate)
+ * info may be NULL.  stream: a cudaStream_t (NULL = default stream).  The call
+ * returns when the solve has finished.
+ */
+ABIP_API int abip_solve(abip_handle* h, double* x, double* y, double* s,
+               abip_info* info, void* stream);
+
+/*
+ * Solve `count` independent dense LPs in one persistent launch (one CTA per
+ * instance at a time, pulled from a device work queue, each with its own
+ * convergence state).  A[i] (dense row-major), b[i], c[i]: host pointers
+ * (on_device = 0) or device pointers (on_device = 1) per instance.  x, y, s:
+ * arrays of `count` caller-allocated output pointers (same memory kind as the
+ * inputs), entries may be NULL.  infos: `count` entries, may be NULL.
+ * Each instance needs m <= 1024 here; larger dense LPs go through abip_setup.
+ */
+ABIP_API int abip_solve_batch(int32_t count, const abip_matrix* A, const double* const* b,
+                     const double* const* c, const abip_params* p,
+                     double* const* x, double* const* y, double* const* s,
+                     abip_info* infos, void* stream);
+
+/*
+ * Gradient of a loss L(x) with respect to (c, b, A) at the solution returned by
+ * the last abip_solve, by implicit differentiation of the ADMM fixed point at the
+ * final mu.  dl_dx: n entries.  Outputs (host or device, may be NULL):
+ * dl_dc (n), dl_db (m), dl_dA (m*n dense row-major; nnz for CSR).
+ * Not provided by this build: returns ABIP_E_UNSUPPORTED.
+ */
+ABIP_API int abip_backward(abip_handle* h, const double* dl_dx,
+                  double* dl_dc, double* dl_db, double* dl_dA);
+
+/*
+ * Copy the raw iterate after the last solve into buf (host or device, m + 2n + 4
+ * doubles): (y[m], x[n], tau, theta, s[n], kappa, mu).  ABIP_E_NOT_SOLVED before
+ * the first solve.
+ */
+ABIP_API int abip_get_state(const abip_handle* h, double* buf);
+
+/* Number of doubles abip_get_state writes (m + 2n + 4). */
+ABIP_API int64_t abip_state_size(const abip_handle* h);
+
+/* Release every resource of h (NULL is accepted). */
+ABIP_API void abip_free(abip_handle* h);
+
+/* Name of a status code ("optimal", ...). */
+ABIP_API const char* abip_status_str(int32_t status);
+
+/* Message of the last failure on h, or of the last failed abip_setup/abip_solve_batch
+   when h is NULL.  Never NULL. */
+ABIP_API const char* abip_last_error(const abip_handle* h);
+
+/* Library version string. */
+ABIP_API const char* abip_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ABIP_H */

@@ -57,6 +57,8 @@ PRIMAL_INFEASIBLE = 2
 DUAL_INFEASIBLE = 3
 MAX_ITER = 4
 
+MAX_OUTER = 4000   # gamma**MAX_OUTER underflows every double: a guard, never reached in practice
+
 STATUS_NAMES = {OPTIMAL: "optimal", PRIMAL_INFEASIBLE: "primal_infeasible",
                 DUAL_INFEASIBLE: "dual_infeasible", MAX_ITER: "max_iter"}
 
@@ -471,6 +473,9 @@ def solve(A, b, c, prm: Optional[Params] = None, trace_iters: int = 0,
         outer += 1
         if prm.stop_rule == 1 and mu < prm.eps:
             status = OPTIMAL
+            break
+        if outer >= MAX_OUTER:          # mu has underflowed; stop as unsolved
+            status = MAX_ITER
             break
         warm_start(st, prm.gamma, prm.warmstart)
     if chk is None:

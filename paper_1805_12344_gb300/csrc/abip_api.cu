@@ -1,0 +1,870 @@
+// C ABI of libabip (declared in include/abip.h): validation, device memory,
+// launches of the persistent kernels, and result marshalling.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "abip_device.cuh"
+#include "abip_internal.h"
+
+using abip::DenseInst;
+using abip::DenseParams;
+using abip::GridData;
+using abip::SellMat;
+using abip::SolveCtl;
+
+namespace {
+
+thread_local std::string g_err = "";
+
+int fail(abip_handle* h, int code, const std::string& msg) {
+  if (h) h->err = msg;
+  else g_err = msg;
+  return code;
+}
+
+double now_s() {
+  return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+bool is_device_ptr(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// copy n elements of T from host or device memory to a host vector
+template <typename T>
+cudaError_t fetch(const T* src, size_t n, bool dev, std::vector<T>& out) {
+  out.resize(n);
+  if (n == 0) return cudaSuccess;
+  if (dev) return cudaMemcpy(out.data(), src, n * sizeof(T), cudaMemcpyDeviceToHost);
+  std::memcpy(out.data(), src, n * sizeof(T));
+  return cudaSuccess;
+}
+
+// bump allocator over one cudaMalloc; every block aligned to 256 bytes
+struct Arena {
+  size_t off = 0;
+  char* base = nullptr;
+  template <typename T>
+  T* take(size_t n) {
+    const size_t at = off;
+    off += ((n * sizeof(T) + 255) / 256) * 256;
+    return base ? reinterpret_cast<T*>(base + at) : nullptr;
+  }
+};
+
+template <typename T>
+__global__ void fill_kernel(T* p, int64_t n, T v) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) p[i] = v;
+}
+
+template <typename T>
+__global__ void convert_kernel(const double* src, T* dst, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    dst[i] = static_cast<T>(src[i]);
+}
+
+// user outputs from the raw state: scaled candidate or certificate (Sec. 4.1)
+template <typename T>
+__global__ void output_kernel(const T* v, int64_t n, double scale, double* out) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = static_cast<double>(v[i]) * scale;
+}
+
+int lanes_for(int64_t nnz, int rows) {
+  const double mean = rows > 0 ? (double)nnz / rows : 1.0;
+  int L = 2;
+  while (L < 32 && L < mean) L *= 2;
+  return L;
+}
+
+bool finite_all(const double* p, size_t n) {
+  for (size_t i = 0; i < n; ++i)
+    if (!std::isfinite(p[i])) return false;
+  return true;
+}
+
+int device_error_code(int err) {
+  switch (err) {
+    case abip::DEV_ERR_BARRIER_TIMEOUT: return ABIP_E_TIMEOUT;
+    default: return ABIP_E_NUMERICAL;
+  }
+}
+
+const char* device_error_str(int err) {
+  switch (err) {
+    case abip::DEV_ERR_BARRIER_TIMEOUT: return "grid barrier wait timed out";
+    case abip::DEV_ERR_PCG: return "PCG exceeded cg_max_iter";
+    case abip::DEV_ERR_NONFINITE: return "non-finite value in a reduction";
+    case abip::DEV_ERR_CHOLESKY: return "Cholesky factorisation of I + A A^T broke down";
+    default: return "device error";
+  }
+}
+
+int check_params(const abip_params& p, std::string& why) {
+  if (!(p.beta > 0) || !std::isfinite(p.beta)) { why = "beta must be > 0"; return 0; }
+  if (!(p.gamma > 0 && p.gamma < 1)) { why = "gamma must be in (0, 1)"; return 0; }
+  if (!(p.alpha > 0 && p.alpha < 2)) { why = "alpha must be in (0, 2)"; return 0; }
+  if (!(p.eps > 0)) { why = "eps must be > 0"; return 0; }
+  if (p.max_admm_iters < 1) { why = "max_admm_iters must be >= 1"; return 0; }
+  if (!(p.cg_tol > 0)) { why = "cg_tol must be > 0"; return 0; }
+  if (!(p.cg_rel >= 0)) { why = "cg_rel must be >= 0"; return 0; }
+  if (p.cg_max_iter < 1) { why = "cg_max_iter must be >= 1"; return 0; }
+  if (p.precision != ABIP_PREC_F64 && p.precision != ABIP_PREC_MIXED) { why = "unknown precision"; return 0; }
+  if (p.linsys != ABIP_LINSYS_DENSE_CHOL && p.linsys != ABIP_LINSYS_PCG && p.linsys != -1) { why = "unknown linsys"; return 0; }
+  if (p.warmstart != 0 && p.warmstart != 1) { why = "warmstart must be 0 or 1"; return 0; }
+  if (p.stop_rule != 0 && p.stop_rule != 1) { why = "stop_rule must be 0 or 1"; return 0; }
+  return 1;
+}
+
+// ---------------------------------------------------------------------------
+// CSR grid path
+// ---------------------------------------------------------------------------
+
+struct HostCSR {
+  int m = 0, n = 0;
+  std::vector<int64_t> rp;
+  std::vector<int32_t> ci;
+  std::vector<double> v;
+};
+
+// CSR of A^T by a stable counting sort over columns (row order kept within each column).
+HostCSR transpose(const HostCSR& A) {
+  HostCSR T;
+  T.m = A.n;
+  T.n = A.m;
+  const int64_t nnz = A.rp[A.m];
+  T.rp.assign(A.n + 1, 0);
+  for (int64_t k = 0; k < nnz; ++k) T.rp[A.ci[k] + 1]++;
+  for (int j = 0; j < A.n; ++j) T.rp[j + 1] += T.rp[j];
+  std::vector<int64_t> pos(T.rp.begin(), T.rp.end() - 1);
+  T.ci.resize(nnz);
+  T.v.resize(nnz);
+  for (int i = 0; i < A.m; ++i)
+    for (int64_t k = A.rp[i]; k < A.rp[i + 1]; ++k) {
+      const int64_t at = pos[A.ci[k]]++;
+      T.ci[at] = i;
+      T.v[at] = A.v[k];
+    }
+  return T;
+}
+
+// SELL-32 form of a CSR matrix: rows sorted by length (longest first, ties in row
+// order), slices of 32 sorted rows stored column-major and padded to the slice's
+// longest row; padding entries hold value 0 and a column the row already uses
+// (or column 0), so every gather stays in range.
+struct HostSell {
+  int rows = 0, nslices = 0;
+  std::vector<int64_t> sp;
+  std::vector<int32_t> ci;
+  std::vector<double> v;
+  std::vector<int32_t> perm;
+};
+
+HostSell to_sell(const HostCSR& M) {
+  HostSell S;
+  S.rows = M.m;
+  S.nslices = (M.m + 31) / 32;
+  std::vector<int32_t> order(M.m);
+  for (int i = 0; i < M.m; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) {
+    return (M.rp[a + 1] - M.rp[a]) > (M.rp[b + 1] - M.rp[b]);
+  });
+  S.perm.assign((size_t)S.nslices * 32, -1);
+  for (int p = 0; p < M.m; ++p) S.perm[p] = order[p];
+  S.sp.assign(S.nslices + 1, 0);
+  for (int sl = 0; sl < S.nslices; ++sl) {
+    const int r0 = order[(size_t)sl * 32];
+    const int64_t w = M.rp[r0 + 1] - M.rp[r0];
+    S.sp[sl + 1] = S.sp[sl] + 32 * w;
+  }
+  S.ci.assign(S.sp[S.nslices], 0);
+  S.v.assign(S.sp[S.nslices], 0.0);
+  for (int sl = 0; sl < S.nslices; ++sl) {
+    const int64_t base = S.sp[sl];
+    const int64_t w = (S.sp[sl + 1] - base) / 32;
+    for (int r = 0; r < 32; ++r) {
+      const int row = S.perm[(size_t)sl * 32 + r];
+      const int64_t len = row >= 0 ? M.rp[row + 1] - M.rp[row] : 0;
+      int32_t pad_col = len > 0 ? M.ci[M.rp[row] + len - 1] : 0;
+      for (int64_t k = 0; k < w; ++k) {
+        const int64_t at = base + k * 32 + r;
+        if (k < len) {
+          S.ci[at] = M.ci[M.rp[row] + k];
+          S.v[at] = M.v[M.rp[row] + k];
+        } else {
+          S.ci[at] = pad_col;
+          S.v[at] = 0.0;
+        }
+      }
+    }
+  }
+  return S;
+}
+
+template <typename T>
+void assign_vectors(GridData<T>& g, Arena& ar, int m, int n) {
+  g.b = ar.take<T>(m);
+  g.c = ar.take<T>(n);
+  g.bbar = ar.take<T>(m); g.cbar = ar.take<T>(n); g.dinv = ar.take<T>(m);
+  g.g1y = ar.take<T>(m); g.g1x = ar.take<T>(n); g.g2y = ar.take<T>(m); g.g2x = ar.take<T>(n);
+  g.y = ar.take<T>(m); g.x = ar.take<T>(n); g.s = ar.take<T>(n);
+  g.Ax = ar.take<T>(m); g.As = ar.take<T>(m); g.ATy = ar.take<T>(n);
+  g.zy = ar.take<T>(m); g.zx = ar.take<T>(n);
+  g.r = ar.take<T>(m); g.p = ar.take<T>(m); g.zr = ar.take<T>(m); g.t = ar.take<T>(n); g.Gp = ar.take<T>(m);
+}
+
+template <typename T>
+int setup_grid_path(abip_handle* h, const HostCSR& A, const std::vector<double>& b, const std::vector<double>& c,
+                    bool vals_f32_exact) {
+  const int m = A.m, n = A.n;
+  const int64_t nnz = A.rp[m];
+  HostCSR AT = transpose(A);
+  const bool mixed = std::is_same<T, float>::value;
+  // values are stored as float when they are exactly float (input F32) or when iterating in FP32
+  const bool vf64 = !mixed && !vals_f32_exact;
+  h->val_f64 = vf64 ? 1 : 0;
+  const size_t vb = vf64 ? 8 : 4;
+  const int maxc = abip::grid_solver_max_ctas(mixed, vf64, h->device);
+  if (maxc <= 0) return fail(h, ABIP_E_CUDA, "grid kernel cannot be made resident");
+  // grid_total reads at most kGridTotalPer partials per thread
+  const int cap = std::min(maxc, abip::kGridTotalPer * abip::kGridThreads);
+  int grid = h->prm.grid_ctas > 0 ? std::min(h->prm.grid_ctas, cap) : cap;
+  h->grid = grid;
+
+  const HostSell SA = to_sell(A), ST = to_sell(AT);
+  auto layout_sell = [&](Arena& ar, SellMat& M, const HostSell& H) {
+    M.rows = H.rows;
+    M.nslices = H.nslices;
+    M.sp = ar.take<int64_t>(H.nslices + 1);
+    M.ci = ar.take<int32_t>(H.ci.size());
+    M.val = ar.take<char>(H.ci.size() * vb);
+    M.perm = ar.take<int32_t>(H.perm.size());
+  };
+  auto layout = [&](Arena& ar, GridData<T>& g) {
+    h->ctl = ar.take<SolveCtl>(1);
+    layout_sell(ar, g.A, SA);
+    layout_sell(ar, g.AT, ST);
+    assign_vectors(g, ar, m, n);
+    g.partials = ar.take<double>((size_t)abip::kNumSlots * grid);
+    g.bar = ar.take<unsigned long long>(1);
+    h->stage = ar.take<double>((size_t)m + 2 * (size_t)n);
+  };
+  Arena probe;
+  GridData<T> g{};
+  layout(probe, g);
+  void* mem = nullptr;
+  if (cudaMalloc(&mem, probe.off) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(h, ABIP_E_OOM, "device allocation of " + std::to_string(probe.off) + " bytes failed");
+  }
+  h->arena = mem;
+  h->arena_bytes = probe.off;
+  Arena ar;
+  ar.base = static_cast<char*>(mem);
+  g = GridData<T>{};
+  layout(ar, g);
+  g.m = m; g.n = n;
+  g.ctl = h->ctl;
+  h->padded_nnz_a = (int64_t)SA.ci.size();
+  h->padded_nnz_at = (int64_t)ST.ci.size();
+  cudaMemset(mem, 0, probe.off);
+  auto upload_sell = [&](const SellMat& M, const HostSell& H) {
+    cudaMemcpy((void*)M.sp, H.sp.data(), H.sp.size() * 8, cudaMemcpyHostToDevice);
+    cudaMemcpy((void*)M.ci, H.ci.data(), H.ci.size() * 4, cudaMemcpyHostToDevice);
+    cudaMemcpy((void*)M.perm, H.perm.data(), H.perm.size() * 4, cudaMemcpyHostToDevice);
+    if (vf64) {
+      cudaMemcpy((void*)M.val, H.v.data(), H.v.size() * 8, cudaMemcpyHostToDevice);
+    } else {
+      std::vector<float> f(H.v.begin(), H.v.end());
+      cudaMemcpy((void*)M.val, f.data(), f.size() * 4, cudaMemcpyHostToDevice);
+    }
+  };
+  upload_sell(g.A, SA);
+  upload_sell(g.AT, ST);
+  (void)nnz;
+  {
+    std::vector<T> tb(b.begin(), b.end()), tc(c.begin(), c.end());
+    cudaMemcpy((void*)g.b, tb.data(), m * sizeof(T), cudaMemcpyHostToDevice);
+    cudaMemcpy((void*)g.c, tc.data(), n * sizeof(T), cudaMemcpyHostToDevice);
+  }
+  SolveCtl hc{};
+  hc.beta = h->prm.beta; hc.gamma = h->prm.gamma; hc.alpha = h->prm.alpha; hc.eps = h->prm.eps;
+  hc.cg_tol = h->prm.cg_tol; hc.cg_rel = h->prm.cg_rel; hc.cg_max = h->prm.cg_max_iter; hc.max_admm = h->prm.max_admm_iters;
+  hc.warmstart = h->prm.warmstart; hc.stop_rule = h->prm.stop_rule; hc.check_every = h->prm.check_every;
+  hc.mode = abip::MODE_SETUP;
+  cudaMemcpy(h->ctl, &hc, sizeof(hc), cudaMemcpyHostToDevice);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(h, ABIP_E_CUDA, std::string("setup copies: ") + cudaGetErrorString(e));
+  if (mixed) h->gd32 = *reinterpret_cast<GridData<float>*>(&g);
+  else h->gd64 = *reinterpret_cast<GridData<double>*>(&g);
+  e = mixed ? abip::launch_grid_solver_f32(h->gd32, grid, 0) : abip::launch_grid_solver_f64(h->gd64, vf64, grid, 0);
+  if (e != cudaSuccess) return fail(h, ABIP_E_CUDA, std::string("setup launch: ") + cudaGetErrorString(e));
+  e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return fail(h, ABIP_E_CUDA, std::string("setup kernel: ") + cudaGetErrorString(e));
+  cudaMemcpy(&hc, h->ctl, sizeof(hc), cudaMemcpyDeviceToHost);
+  if (hc.err != 0) return fail(h, device_error_code(hc.err), std::string("setup: ") + device_error_str(hc.err));
+  const double det = hc.K[0] * hc.K[3] - hc.K[1] * hc.K[2];
+  if (!std::isfinite(det) || det == 0.0) return fail(h, ABIP_E_NUMERICAL, "singular Schur complement");
+  hc.Kinv[0] = hc.K[3] / det; hc.Kinv[1] = -hc.K[1] / det; hc.Kinv[2] = -hc.K[2] / det; hc.Kinv[3] = hc.K[0] / det;
+  hc.zbar = hc.sum_c + 1.0;
+  hc.xi = -(double)n - 1.0;
+  hc.nb = std::sqrt(hc.sum_b2);
+  hc.nc = std::sqrt(hc.sum_c2);
+  h->nb = hc.nb;
+  h->nc = hc.nc;
+  cudaMemcpy(h->ctl, &hc, sizeof(hc), cudaMemcpyHostToDevice);
+  return ABIP_OK;
+}
+
+template <typename T>
+int solve_grid_path(abip_handle* h, cudaStream_t st) {
+  GridData<T>& g = *reinterpret_cast<GridData<T>*>(std::is_same<T, float>::value ? (void*)&h->gd32 : (void*)&h->gd64);
+  const int m = h->m, n = h->n;
+  fill_kernel<T><<<64, 256, 0, st>>>(g.y, m, T(0));
+  fill_kernel<T><<<256, 256, 0, st>>>(g.x, n, T(1));
+  fill_kernel<T><<<256, 256, 0, st>>>(g.s, n, T(1));
+  fill_kernel<T><<<64, 256, 0, st>>>(g.zy, m, T(0));
+  SolveCtl hc;
+  cudaMemcpyAsync(&hc, h->ctl, sizeof(hc), cudaMemcpyDeviceToHost, st);
+  cudaStreamSynchronize(st);
+  hc.mode = abip::MODE_SOLVE;
+  hc.tau = hc.kappa = hc.theta = 1.0;
+  hc.mu = h->prm.beta;
+  hc.admm_iters = 0; hc.cg_iters = 0; hc.outer_iters = 0; hc.status = 0; hc.err = 0;
+  hc.max_admm = h->prm.max_admm_iters;
+  cudaMemcpyAsync(h->ctl, &hc, sizeof(hc), cudaMemcpyHostToDevice, st);
+  cudaMemsetAsync(g.bar, 0, sizeof(unsigned long long), st);
+  cudaEventRecord(h->ev0, st);
+  cudaError_t e = std::is_same<T, float>::value
+                      ? abip::launch_grid_solver_f32(h->gd32, h->grid, st)
+                      : abip::launch_grid_solver_f64(h->gd64, h->val_f64 != 0, h->grid, st);
+  if (e != cudaSuccess) return fail(h, ABIP_E_CUDA, std::string("solve launch: ") + cudaGetErrorString(e));
+  cudaEventRecord(h->ev1, st);
+  e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return fail(h, ABIP_E_CUDA, std::string("solve kernel: ") + cudaGetErrorString(e));
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, h->ev0, h->ev1);
+  h->kernel_s = ms * 1e-3;
+  h->launches = 5;   // four fills and the persistent solve kernel
+  return ABIP_OK;
+}
+
+// ---------------------------------------------------------------------------
+// dense CTA path (single instance and batches)
+// ---------------------------------------------------------------------------
+
+struct DenseHostInst {
+  int m, n;
+  std::vector<double> A, b, c;   // A row-major m x n
+};
+
+constexpr size_t kDenseSmemLimit = 200 * 1024;
+
+size_t dense_solve_smem(int m, int n) { return (size_t)(5 * m + 3 * n) * sizeof(double); }
+size_t dense_setup_smem(int m, int n) {
+  return std::max((size_t)(2 * 32 * 33), (size_t)(2 * m + n)) * sizeof(double);
+}
+
+// Allocate and fill the device descriptors of a set of dense instances.
+int dense_alloc(abip_handle* h, const std::vector<DenseHostInst>& hi, void** arena_out, DenseInst** dinst,
+                int** queue, std::vector<DenseInst>& hdesc) {
+  const int count = (int)hi.size();
+  auto layout = [&](Arena& ar, std::vector<DenseInst>& d) {
+    DenseInst* di = ar.take<DenseInst>(count);
+    int* q = ar.take<int>(2);
+    if (ar.base) { *dinst = di; *queue = q; }
+    d.assign(count, DenseInst{});
+    for (int k = 0; k < count; ++k) {
+      const int m = hi[k].m, n = hi[k].n;
+      DenseInst& I = d[k];
+      I.m = m; I.n = n; I.ld = n;
+      I.A = ar.take<double>((size_t)m * n);
+      I.b = ar.take<double>(m); I.c = ar.take<double>(n);
+      I.L = ar.take<double>((size_t)m * m);
+      I.bbar = ar.take<double>(m); I.cbar = ar.take<double>(n);
+      I.g1 = ar.take<double>(m + n); I.g2 = ar.take<double>(m + n);
+      I.y = ar.take<double>(m); I.x = ar.take<double>(n); I.s = ar.take<double>(n);
+      I.out_y = ar.take<double>(m); I.out_x = ar.take<double>(n); I.out_s = ar.take<double>(n);
+      I.work = nullptr;
+    }
+  };
+  Arena probe;
+  std::vector<DenseInst> tmp;
+  layout(probe, tmp);
+  void* mem = nullptr;
+  if (cudaMalloc(&mem, probe.off) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(h, ABIP_E_OOM, "device allocation of " + std::to_string(probe.off) + " bytes failed");
+  }
+  Arena ar;
+  ar.base = static_cast<char*>(mem);
+  layout(ar, hdesc);
+  cudaMemset(mem, 0, probe.off);
+  for (int k = 0; k < count; ++k) {
+    const DenseInst& I = hdesc[k];
+    cudaMemcpy((void*)I.A, hi[k].A.data(), hi[k].A.size() * 8, cudaMemcpyHostToDevice);
+    cudaMemcpy((void*)I.b, hi[k].b.data(), hi[k].m * 8, cudaMemcpyHostToDevice);
+    cudaMemcpy((void*)I.c, hi[k].c.data(), hi[k].n * 8, cudaMemcpyHostToDevice);
+  }
+  cudaMemcpy(*dinst, hdesc.data(), sizeof(DenseInst) * count, cudaMemcpyHostToDevice);
+  *arena_out = mem;
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(h, ABIP_E_CUDA, std::string("dense copies: ") + cudaGetErrorString(e));
+  return ABIP_OK;
+}
+
+int dense_run_setup(abip_handle* h, DenseInst* dinst, int* queue, int count, int grid, size_t smem, cudaStream_t st) {
+  cudaMemsetAsync(queue, 0, 8, st);
+  cudaError_t e = abip::launch_dense_setup(dinst, count, queue, grid, smem, st);
+  if (e != cudaSuccess) return fail(h, ABIP_E_CUDA, std::string("dense setup launch: ") + cudaGetErrorString(e));
+  e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return fail(h, ABIP_E_CUDA, std::string("dense setup: ") + cudaGetErrorString(e));
+  return ABIP_OK;
+}
+
+int dense_run_solve(abip_handle* h, DenseInst* dinst, int* queue, int count, int grid, size_t smem,
+                    const abip_params& p, cudaStream_t st) {
+  DenseParams dp{p.beta, p.gamma, p.alpha, p.eps, p.max_admm_iters, p.warmstart, p.stop_rule};
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  cudaMemsetAsync(queue, 0, 8, st);
+  cudaEventRecord(e0, st);
+  cudaError_t e = abip::launch_dense_solve(dinst, count, dp, queue, grid, smem, st);
+  cudaEventRecord(e1, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  float ms = 0.f;
+  if (e == cudaSuccess) cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (e != cudaSuccess) return fail(h, ABIP_E_CUDA, std::string("dense solve: ") + cudaGetErrorString(e));
+  h->kernel_s = ms * 1e-3;
+  h->launches = 1;
+  return ABIP_OK;
+}
+
+int read_matrix_dense(abip_handle* h, const abip_matrix* A, std::vector<double>& out) {
+  const int m = A->m, n = A->n;
+  out.assign((size_t)m * n, 0.0);
+  const bool dev = A->on_device != 0;
+  if (A->fmt == ABIP_DENSE_ROWMAJOR) {
+    if (A->ld < n) return fail(h, ABIP_E_DIM, "ld < n");
+    const size_t tot = (size_t)(m - 1) * A->ld + n;
+    if (A->dtype == ABIP_F64) {
+      std::vector<double> raw;
+      if (fetch((const double*)A->val, tot, dev, raw) != cudaSuccess) return fail(h, ABIP_E_CUDA, "reading A");
+      for (int i = 0; i < m; ++i) std::memcpy(&out[(size_t)i * n], &raw[(size_t)i * A->ld], n * 8);
+    } else {
+      std::vector<float> raw;
+      if (fetch((const float*)A->val, tot, dev, raw) != cudaSuccess) return fail(h, ABIP_E_CUDA, "reading A");
+      for (int i = 0; i < m; ++i)
+        for (int j = 0; j < n; ++j) out[(size_t)i * n + j] = raw[(size_t)i * A->ld + j];
+    }
+  } else {
+    std::vector<int64_t> rp;
+    std::vector<int32_t> ci;
+    if (fetch(A->row_ptr, m + 1, dev, rp) != cudaSuccess) return fail(h, ABIP_E_CUDA, "reading row_ptr");
+    const int64_t nnz = rp[m];
+    if (fetch(A->col_idx, nnz, dev, ci) != cudaSuccess) return fail(h, ABIP_E_CUDA, "reading col_idx");
+    std::vector<double> v(nnz);
+    if (A->dtype == ABIP_F64) {
+      if (fetch((const double*)A->val, nnz, dev, v) != cudaSuccess) return fail(h, ABIP_E_CUDA, "reading val");
+    } else {
+      std::vector<float> f;
+      if (fetch((const float*)A->val, nnz, dev, f) != cudaSuccess) return fail(h, ABIP_E_CUDA, "reading val");
+      for (int64_t k = 0; k < nnz; ++k) v[k] = f[k];
+    }
+    for (int i = 0; i < m; ++i)
+      for (int64_t k = rp[i]; k < rp[i + 1]; ++k) out[(size_t)i * n + ci[k]] += v[k];
+  }
+  if (!finite_all(out.data(), out.size())) return fail(h, ABIP_E_INVALID_ARG, "A has non-finite entries");
+  return ABIP_OK;
+}
+
+int read_matrix_csr(abip_handle* h, const abip_matrix* A, HostCSR& out, bool& f32) {
+  const int m = A->m, n = A->n;
+  const bool dev = A->on_device != 0;
+  out.m = m;
+  out.n = n;
+  f32 = A->dtype == ABIP_F32;
+  if (A->fmt == ABIP_CSR) {
+    if (!A->row_ptr || !A->col_idx || (!A->val && A->nnz > 0)) return fail(h, ABIP_E_INVALID_ARG, "null CSR array");
+    if (fetch(A->row_ptr, m + 1, dev, out.rp) != cudaSuccess) return fail(h, ABIP_E_CUDA, "reading row_ptr");
+    if (out.rp[0] != 0 || out.rp[m] != A->nnz) return fail(h, ABIP_E_DIM, "row_ptr[0] != 0 or row_ptr[m] != nnz");
+    for (int i = 0; i < m; ++i)
+      if (out.rp[i + 1] < out.rp[i]) return fail(h, ABIP_E_DIM, "row_ptr not monotone");
+    const int64_t nnz = A->nnz;
+    if (fetch(A->col_idx, nnz, dev, out.ci) != cudaSuccess) return fail(h, ABIP_E_CUDA, "reading col_idx");
+    for (int64_t k = 0; k < nnz; ++k)
+      if (out.ci[k] < 0 || out.ci[k] >= n) return fail(h, ABIP_E_DIM, "column index out of range");
+    if (A->dtype == ABIP_F64) {
+      if (fetch((const double*)A->val, nnz, dev, out.v) != cudaSuccess) return fail(h, ABIP_E_CUDA, "reading val");
+    } else {
+      std::vector<float> f;
+      if (fetch((const float*)A->val, nnz, dev, f) != cudaSuccess) return fail(h, ABIP_E_CUDA, "reading val");
+      out.v.assign(f.begin(), f.end());
+    }
+    if (!finite_all(out.v.data(), out.v.size())) return fail(h, ABIP_E_INVALID_ARG, "A has non-finite entries");
+  } else {
+    std::vector<double> d;
+    int rc = read_matrix_dense(h, A, d);
+    if (rc) return rc;
+    out.rp.assign(m + 1, 0);
+    for (int i = 0; i < m; ++i) {
+      for (int j = 0; j < n; ++j)
+        if (d[(size_t)i * n + j] != 0.0) {
+          out.ci.push_back(j);
+          out.v.push_back(d[(size_t)i * n + j]);
+        }
+      out.rp[i + 1] = (int64_t)out.ci.size();
+    }
+  }
+  return ABIP_OK;
+}
+
+int validate_matrix(abip_handle* h, const abip_matrix* A) {
+  if (!A) return fail(h, ABIP_E_INVALID_ARG, "A is NULL");
+  if (A->m < 1 || A->n < A->m) return fail(h, ABIP_E_DIM, "need 1 <= m <= n");
+  if (A->fmt != ABIP_DENSE_ROWMAJOR && A->fmt != ABIP_CSR) return fail(h, ABIP_E_INVALID_ARG, "unknown matrix format");
+  if (A->dtype != ABIP_F32 && A->dtype != ABIP_F64) return fail(h, ABIP_E_INVALID_ARG, "unknown dtype");
+  if (A->fmt == ABIP_DENSE_ROWMAJOR && !A->val) return fail(h, ABIP_E_INVALID_ARG, "A.val is NULL");
+  if (A->fmt == ABIP_CSR && A->nnz < 0) return fail(h, ABIP_E_DIM, "nnz < 0");
+  return ABIP_OK;
+}
+
+}  // namespace
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+
+extern "C" {
+
+int abip_default_params(abip_params* p) {
+  if (!p) return ABIP_E_INVALID_ARG;
+  std::memset(p, 0, sizeof(*p));
+  p->beta = 1.0;
+  p->gamma = 0.1;
+  p->alpha = 1.8;
+  p->eps = 1e-6;
+  p->max_admm_iters = 1000000;
+  p->linsys = -1;   // automatic
+  p->cg_tol = 1e-10;
+  p->cg_rel = 0.0;
+  p->cg_max_iter = 1000;
+  p->precision = ABIP_PREC_F64;
+  p->warmstart = 0;
+  p->stop_rule = 0;
+  p->check_every = 1;
+  p->grid_ctas = 0;
+  return ABIP_OK;
+}
+
+int abip_setup(const abip_matrix* A, const double* b, const double* c, const abip_params* p, abip_handle** out) {
+  const double t0 = now_s();
+  if (!out) return fail(nullptr, ABIP_E_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  int rc = validate_matrix(nullptr, A);
+  if (rc) return rc;
+  if (!b || !c) return fail(nullptr, ABIP_E_INVALID_ARG, "b or c is NULL");
+  abip_params prm;
+  if (p) prm = *p;
+  else abip_default_params(&prm);
+  std::string why;
+  if (!check_params(prm, why)) return fail(nullptr, ABIP_E_INVALID_ARG, why);
+  abip_handle* h = new abip_handle();
+  cudaGetDevice(&h->device);
+  h->m = A->m;
+  h->n = A->n;
+  h->prm = prm;
+  const int m = A->m, n = A->n;
+  std::vector<double> hb, hc;
+  const bool dev = A->on_device != 0;
+  if (fetch(b, m, dev, hb) != cudaSuccess || fetch(c, n, dev, hc) != cudaSuccess) {
+    rc = fail(h, ABIP_E_CUDA, "reading b, c");
+    g_err = h->err; delete h; return rc;
+  }
+  if (!finite_all(hb.data(), m) || !finite_all(hc.data(), n)) {
+    g_err = "b or c has non-finite entries"; delete h; return ABIP_E_INVALID_ARG;
+  }
+  if (cudaEventCreate(&h->ev0) != cudaSuccess || cudaEventCreate(&h->ev1) != cudaSuccess) {
+    cudaGetLastError();
+    g_err = "cudaEventCreate failed (no usable CUDA device?)";
+    abip_free(h);
+    return ABIP_E_CUDA;
+  }
+  int linsys = prm.linsys;
+  if (linsys < 0) linsys = A->fmt == ABIP_CSR ? ABIP_LINSYS_PCG : ABIP_LINSYS_DENSE_CHOL;
+  h->prm.linsys = linsys;
+  h->mixed = prm.precision == ABIP_PREC_MIXED;
+  if (linsys == ABIP_LINSYS_PCG) {
+    h->path = 0;
+    HostCSR hA;
+    bool f32 = false;
+    rc = read_matrix_csr(h, A, hA, f32);
+    if (rc == ABIP_OK)
+      rc = h->mixed ? setup_grid_path<float>(h, hA, hb, hc, true) : setup_grid_path<double>(h, hA, hb, hc, f32);
+  } else {
+    h->path = 1;
+    if (h->mixed) rc = fail(h, ABIP_E_UNSUPPORTED, "mixed precision with dense Cholesky is not provided for single instances");
+    else if (dense_solve_smem(m, n) > kDenseSmemLimit)
+      rc = fail(h, ABIP_E_UNSUPPORTED, "dense Cholesky path needs 5m + 3n <= 25600; use linsys = PCG");
+    else {
+      std::vector<DenseHostInst> hi(1);
+      hi[0].m = m; hi[0].n = n; hi[0].b = hb; hi[0].c = hc;
+      rc = read_matrix_dense(h, A, hi[0].A);
+      std::vector<DenseInst> hd;
+      if (rc == ABIP_OK) rc = dense_alloc(h, hi, &h->arena, &h->dinst, &h->queue, hd);
+      if (rc == ABIP_OK) {
+        h->hinst = hd[0];
+        rc = dense_run_setup(h, h->dinst, h->queue, 1, 1, dense_setup_smem(m, n), 0);
+      }
+      if (rc == ABIP_OK) {
+        cudaMemcpy(&h->hinst, h->dinst, sizeof(DenseInst), cudaMemcpyDeviceToHost);
+        if (h->hinst.err != 0) rc = fail(h, device_error_code(h->hinst.err), std::string("setup: ") + device_error_str(h->hinst.err));
+      }
+    }
+  }
+  if (rc != ABIP_OK) {
+    g_err = h->err;
+    abip_free(h);
+    return rc;
+  }
+  h->setup_s = now_s() - t0;
+  *out = h;
+  return ABIP_OK;
+}
+
+static int copy_out(abip_handle* h, double* dst, const double* dev_src, int64_t n, cudaStream_t st) {
+  if (!dst) return ABIP_OK;
+  cudaError_t e = cudaMemcpyAsync(dst, dev_src, n * 8, is_device_ptr(dst) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st);
+  if (e != cudaSuccess) return fail(h, ABIP_E_CUDA, std::string("output copy: ") + cudaGetErrorString(e));
+  return ABIP_OK;
+}
+
+int abip_solve(abip_handle* h, double* x, double* y, double* s, abip_info* info, void* stream) {
+  if (!h) return fail(nullptr, ABIP_E_INVALID_ARG, "handle is NULL");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const double t0 = now_s();
+  const int m = h->m, n = h->n;
+  int rc;
+  abip_info inf{};
+  if (h->path == 0) {
+    rc = h->mixed ? solve_grid_path<float>(h, st) : solve_grid_path<double>(h, st);
+    if (rc) return rc;
+    SolveCtl hc;
+    cudaMemcpy(&hc, h->ctl, sizeof(hc), cudaMemcpyDeviceToHost);
+    if (hc.err != 0) return fail(h, device_error_code(hc.err), std::string("solve: ") + device_error_str(hc.err));
+    inf.status = hc.status; inf.outer_iters = hc.outer_iters; inf.admm_iters = hc.admm_iters; inf.cg_iters = hc.cg_iters;
+    inf.tau = hc.tau; inf.kappa = hc.kappa; inf.theta = hc.theta; inf.mu = hc.mu;
+    inf.obj = hc.ctx / hc.tau; inf.pres = hc.pres; inf.dres = hc.dres; inf.dgap = hc.dgap;
+    double sx = 1.0 / hc.tau, sy = 1.0 / hc.tau;
+    if (hc.status == ABIP_PRIMAL_INFEASIBLE) { sx = 1.0; sy = 1.0 / hc.bty; }
+    if (hc.status == ABIP_DUAL_INFEASIBLE) { sx = -1.0 / hc.ctx; sy = 1.0; }
+    double* stage = h->stage;
+    if (h->mixed) {
+      output_kernel<float><<<128, 256, 0, st>>>(h->gd32.x, n, sx, stage);
+      output_kernel<float><<<128, 256, 0, st>>>(h->gd32.y, m, sy, stage + n);
+      output_kernel<float><<<128, 256, 0, st>>>(h->gd32.s, n, sy, stage + n + m);
+    } else {
+      output_kernel<double><<<128, 256, 0, st>>>(h->gd64.x, n, sx, stage);
+      output_kernel<double><<<128, 256, 0, st>>>(h->gd64.y, m, sy, stage + n);
+      output_kernel<double><<<128, 256, 0, st>>>(h->gd64.s, n, sy, stage + n + m);
+    }
+    h->launches += 3;
+    rc = copy_out(h, x, stage, n, st);
+    if (!rc) rc = copy_out(h, y, stage + n, m, st);
+    if (!rc) rc = copy_out(h, s, stage + n + m, n, st);
+    cudaStreamSynchronize(st);
+    if (rc) return rc;
+  } else {
+    rc = dense_run_solve(h, h->dinst, h->queue, 1, 1, dense_solve_smem(m, n), h->prm, st);
+    if (rc) return rc;
+    cudaMemcpy(&h->hinst, h->dinst, sizeof(DenseInst), cudaMemcpyDeviceToHost);
+    const DenseInst& I = h->hinst;
+    if (I.err != 0) return fail(h, device_error_code(I.err), std::string("solve: ") + device_error_str(I.err));
+    inf.status = I.status; inf.outer_iters = I.outer_iters; inf.admm_iters = I.admm_iters; inf.cg_iters = 0;
+    inf.tau = I.tau; inf.kappa = I.kappa; inf.theta = I.theta; inf.mu = I.mu;
+    inf.obj = I.obj; inf.pres = I.pres; inf.dres = I.dres; inf.dgap = I.dgap;
+    rc = copy_out(h, x, I.out_x, n, st);
+    if (!rc) rc = copy_out(h, y, I.out_y, m, st);
+    if (!rc) rc = copy_out(h, s, I.out_s, n, st);
+    cudaStreamSynchronize(st);
+    if (rc) return rc;
+  }
+  h->solved = true;
+  h->solve_s = now_s() - t0;
+  inf.setup_s = h->setup_s;
+  inf.solve_s = h->solve_s;
+  inf.kernel_s = h->kernel_s;
+  inf.launches = h->launches;
+  if (info) *info = inf;
+  return ABIP_OK;
+}
+
+int abip_solve_batch(int32_t count, const abip_matrix* A, const double* const* b, const double* const* c,
+                     const abip_params* p, double* const* x, double* const* y, double* const* s,
+                     abip_info* infos, void* stream) {
+  const double t0 = now_s();
+  if (count < 0) return fail(nullptr, ABIP_E_INVALID_ARG, "count < 0");
+  if (count == 0) return ABIP_OK;
+  if (!A || !b || !c) return fail(nullptr, ABIP_E_INVALID_ARG, "A, b or c is NULL");
+  abip_params prm;
+  if (p) prm = *p;
+  else abip_default_params(&prm);
+  std::string why;
+  if (!check_params(prm, why)) return fail(nullptr, ABIP_E_INVALID_ARG, why);
+  if (prm.precision != ABIP_PREC_F64) return fail(nullptr, ABIP_E_UNSUPPORTED, "batched path: only ABIP_PREC_F64 in this build");
+  abip_handle tmp;
+  cudaGetDevice(&tmp.device);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  std::vector<DenseHostInst> hi(count);
+  size_t smem_solve = 0, smem_setup = 0;
+  for (int k = 0; k < count; ++k) {
+    int rc = validate_matrix(&tmp, &A[k]);
+    if (rc) return fail(nullptr, rc, "instance " + std::to_string(k) + ": " + tmp.err);
+    if (!b[k] || !c[k]) return fail(nullptr, ABIP_E_INVALID_ARG, "instance " + std::to_string(k) + ": b or c is NULL");
+    const int m = A[k].m, n = A[k].n;
+    if (dense_solve_smem(m, n) > kDenseSmemLimit)
+      return fail(nullptr, ABIP_E_UNSUPPORTED, "instance " + std::to_string(k) + ": needs 5m + 3n <= 25600");
+    hi[k].m = m; hi[k].n = n;
+    rc = read_matrix_dense(&tmp, &A[k], hi[k].A);
+    if (rc) return fail(nullptr, rc, "instance " + std::to_string(k) + ": " + tmp.err);
+    const bool dev = A[k].on_device != 0;
+    if (fetch(b[k], m, dev, hi[k].b) != cudaSuccess || fetch(c[k], n, dev, hi[k].c) != cudaSuccess)
+      return fail(nullptr, ABIP_E_CUDA, "reading b, c");
+    if (!finite_all(hi[k].b.data(), m) || !finite_all(hi[k].c.data(), n))
+      return fail(nullptr, ABIP_E_INVALID_ARG, "instance " + std::to_string(k) + ": non-finite b or c");
+    smem_solve = std::max(smem_solve, dense_solve_smem(m, n));
+    smem_setup = std::max(smem_setup, dense_setup_smem(m, n));
+  }
+  void* arena = nullptr;
+  DenseInst* dinst = nullptr;
+  int* queue = nullptr;
+  std::vector<DenseInst> hd;
+  int rc = dense_alloc(&tmp, hi, &arena, &dinst, &queue, hd);
+  if (rc) return fail(nullptr, rc, tmp.err);
+  const int sms = abip::dense_max_ctas(tmp.device);
+  int per = std::max(1, (int)(kDenseSmemLimit / std::max(smem_solve, (size_t)1)));
+  per = std::min(per, 8);
+  const int grid = std::min(count, sms * per);
+  rc = dense_run_setup(&tmp, dinst, queue, count, std::min(count, sms * 4), smem_setup, st);
+  if (!rc) rc = dense_run_solve(&tmp, dinst, queue, count, grid, smem_solve, prm, st);
+  if (!rc) {
+    std::vector<DenseInst> res(count);
+    cudaMemcpy(res.data(), dinst, sizeof(DenseInst) * count, cudaMemcpyDeviceToHost);
+    const double el = now_s() - t0;
+    for (int k = 0; k < count && !rc; ++k) {
+      const DenseInst& I = res[k];
+      if (I.err != 0) { rc = fail(nullptr, device_error_code(I.err), "instance " + std::to_string(k) + ": " + device_error_str(I.err)); break; }
+      if (infos) {
+        abip_info& f = infos[k];
+        std::memset(&f, 0, sizeof(f));
+        f.status = I.status; f.outer_iters = I.outer_iters; f.admm_iters = I.admm_iters;
+        f.tau = I.tau; f.kappa = I.kappa; f.theta = I.theta; f.mu = I.mu;
+        f.obj = I.obj; f.pres = I.pres; f.dres = I.dres; f.dgap = I.dgap;
+        f.solve_s = el;
+        f.kernel_s = tmp.kernel_s;
+        f.launches = tmp.launches;
+      }
+      if (x && x[k]) rc = copy_out(&tmp, x[k], I.out_x, I.n, st);
+      if (!rc && y && y[k]) rc = copy_out(&tmp, y[k], I.out_y, I.m, st);
+      if (!rc && s && s[k]) rc = copy_out(&tmp, s[k], I.out_s, I.n, st);
+    }
+    cudaStreamSynchronize(st);
+    if (rc) g_err = tmp.err.empty() ? g_err : tmp.err;
+  } else {
+    g_err = tmp.err;
+  }
+  cudaFree(arena);
+  return rc;
+}
+
+int abip_backward(abip_handle* h, const double* dl_dx, double* dl_dc, double* dl_db, double* dl_dA) {
+  (void)dl_dx; (void)dl_dc; (void)dl_db; (void)dl_dA;
+  return fail(h, ABIP_E_UNSUPPORTED, "abip_backward is not provided by this build");
+}
+
+int64_t abip_state_size(const abip_handle* h) {
+  if (!h) return 0;
+  return (int64_t)h->m + 2 * (int64_t)h->n + 4;
+}
+
+int abip_get_state(const abip_handle* h, double* buf) {
+  abip_handle* hm = const_cast<abip_handle*>(h);
+  if (!h || !buf) return fail(hm, ABIP_E_INVALID_ARG, "NULL argument");
+  if (!h->solved) return fail(hm, ABIP_E_NOT_SOLVED, "no solve has run on this handle");
+  const int m = h->m, n = h->n;
+  std::vector<double> out((size_t)m + 2 * n + 4);
+  double tau, theta, kappa, mu;
+  if (h->path == 0) {
+    SolveCtl hc;
+    cudaMemcpy(&hc, h->ctl, sizeof(hc), cudaMemcpyDeviceToHost);
+    tau = hc.tau; theta = hc.theta; kappa = hc.kappa; mu = hc.mu;
+    if (h->mixed) {
+      std::vector<float> f(std::max(m, n));
+      cudaMemcpy(f.data(), h->gd32.y, m * 4, cudaMemcpyDeviceToHost);
+      for (int i = 0; i < m; ++i) out[i] = f[i];
+      cudaMemcpy(f.data(), h->gd32.x, n * 4, cudaMemcpyDeviceToHost);
+      for (int j = 0; j < n; ++j) out[m + j] = f[j];
+      cudaMemcpy(f.data(), h->gd32.s, n * 4, cudaMemcpyDeviceToHost);
+      for (int j = 0; j < n; ++j) out[m + n + 2 + j] = f[j];
+    } else {
+      cudaMemcpy(out.data(), h->gd64.y, m * 8, cudaMemcpyDeviceToHost);
+      cudaMemcpy(out.data() + m, h->gd64.x, n * 8, cudaMemcpyDeviceToHost);
+      cudaMemcpy(out.data() + m + n + 2, h->gd64.s, n * 8, cudaMemcpyDeviceToHost);
+    }
+  } else {
+    const DenseInst& I = h->hinst;
+    tau = I.tau; theta = I.theta; kappa = I.kappa; mu = I.mu;
+    cudaMemcpy(out.data(), I.y, m * 8, cudaMemcpyDeviceToHost);
+    cudaMemcpy(out.data() + m, I.x, n * 8, cudaMemcpyDeviceToHost);
+    cudaMemcpy(out.data() + m + n + 2, I.s, n * 8, cudaMemcpyDeviceToHost);
+  }
+  out[m + n] = tau;
+  out[m + n + 1] = theta;
+  out[m + 2 * n + 2] = kappa;
+  out[m + 2 * n + 3] = mu;
+  cudaError_t e = cudaMemcpy(buf, out.data(), out.size() * 8, is_device_ptr(buf) ? cudaMemcpyHostToDevice : cudaMemcpyHostToHost);
+  if (e != cudaSuccess) return fail(hm, ABIP_E_CUDA, std::string("state copy: ") + cudaGetErrorString(e));
+  return ABIP_OK;
+}
+
+void abip_free(abip_handle* h) {
+  if (!h) return;
+  if (h->arena) cudaFree(h->arena);
+  if (h->ev0) cudaEventDestroy(h->ev0);
+  if (h->ev1) cudaEventDestroy(h->ev1);
+  delete h;
+}
+
+const char* abip_status_str(int32_t status) {
+  switch (status) {
+    case ABIP_UNSOLVED: return "unsolved";
+    case ABIP_OPTIMAL: return "optimal";
+    case ABIP_PRIMAL_INFEASIBLE: return "primal_infeasible";
+    case ABIP_DUAL_INFEASIBLE: return "dual_infeasible";
+    case ABIP_MAX_ITER: return "max_iter";
+    default: return "unknown";
+  }
+}
+
+const char* abip_last_error(const abip_handle* h) {
+  if (h) return h->err.c_str();
+  return g_err.c_str();
+}
+
+const char* abip_version(void) { return "abip-gb300 0.1 (sm_103a)"; }
+
+}  // extern "C"

@@ -1,0 +1,145 @@
+// Host-side internals of libabip: the handle, the device control block and the
+// kernel entry points shared between translation units.
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/abip.h"
+
+namespace abip {
+
+constexpr int kGridThreads = 256;   // threads per CTA of the persistent grid kernel
+constexpr int kNumSlots = 24;       // reduction slots of the grid kernel
+
+enum GridMode : int { MODE_SETUP = 0, MODE_SOLVE = 1 };
+
+// Control block of one single-instance solve, resident in device memory.  The
+// host writes the inputs, the kernel writes the outputs.
+struct SolveCtl {
+  // inputs
+  double beta, gamma, alpha, eps, cg_tol, cg_rel;
+  double zbar, xi, nb, nc;
+  double Kinv[4];                 // inverse of the 2x2 Schur complement, row-major
+  int64_t max_admm;
+  int32_t cg_max, warmstart, stop_rule, mode;
+  int32_t check_every, pad0;
+  // state carried across calls (in/out)
+  double tau, kappa, theta, mu;
+  int64_t admm_iters, cg_iters;
+  int32_t outer_iters, status;
+  // outputs
+  double pres, dres, dgap, ctx, bty, inner2;
+  double K[4];                    // MODE_SETUP: the Schur complement K = I + S + H^T M^{-1} H
+  double sum_c, sum_b2, sum_c2;   // MODE_SETUP: c^T e, ||b||^2, ||c||^2
+  int32_t err;                    // DevErr
+  int32_t pad1;
+};
+
+// A sparse matrix in SELL-32 form: rows sorted by length (longest first), cut
+// into slices of 32 consecutive sorted rows; slice s stores its entries
+// column-major, entry k of lane r at sp[s] + 32 k + r, padded with zeros to the
+// slice's longest row (padding points at a valid column).  perm maps a sorted
+// position to its original row (-1 past the last row).
+struct SellMat {
+  int rows = 0, nslices = 0;
+  const int64_t* sp = nullptr;    // nslices + 1 offsets (multiples of 32)
+  const int32_t* ci = nullptr;    // column indices, padded
+  const void* val = nullptr;      // values (float or double), padded
+  const int32_t* perm = nullptr;  // nslices * 32
+};
+
+// Device pointers of the sparse single-instance path.
+template <typename T>
+struct GridData {
+  int m, n;
+  SellMat A;                                                  // rows of A
+  SellMat AT;                                                 // rows of A^T
+  const T* b; const T* c;                                     // problem data in T
+  T* bbar; T* cbar; T* dinv;                                  // embedding constants, Jacobi diagonal
+  T* g1y; T* g1x; T* g2y; T* g2x;                            // M^{-1} h1, M^{-1} h2
+  T* y; T* x; T* s;                                           // iterate (r = 0, xi = -n-1 implicit)
+  T* Ax; T* As; T* ATy;                                       // products for the residuals
+  T* zy; T* zx;                                               // M^{-1} w (zy warm-starts PCG)
+  T* r; T* p; T* zr; T* t; T* Gp;                             // PCG work vectors
+  double* partials;                                           // kNumSlots * gridDim doubles
+  unsigned long long* bar;                                    // barrier arrival counter
+  SolveCtl* ctl;
+};
+
+// Launch the persistent grid kernel (cooperative).  val_f64: whether A's values are double.
+cudaError_t launch_grid_solver_f64(const GridData<double>& d, bool val_f64, int grid, cudaStream_t st);
+cudaError_t launch_grid_solver_f32(const GridData<float>& d, int grid, cudaStream_t st);
+int grid_solver_max_ctas(bool mixed, bool val_f64, int device);
+
+// ---------------------------------------------------------------------------
+// dense CTA-per-instance path
+// ---------------------------------------------------------------------------
+
+// Per-instance descriptor of the batched dense solver (device array).
+struct DenseInst {
+  int32_t m, n;
+  int64_t ld;                  // leading dimension of A (row-major)
+  const double* A;             // m x ld, FP64
+  const double* b; const double* c;
+  double* L;                   // m x m Cholesky factor of G (row-major, lower)
+  double* bbar; double* cbar;  // embedding constants
+  double* g1; double* g2;      // M^{-1} h1, M^{-1} h2, (m + n) each: [y part, x part]
+  double* y; double* x; double* s;   // iterate
+  double* work;                // 3*(m + n) doubles
+  double* out_x; double* out_y; double* out_s;   // device outputs (may be null)
+  double zbar, nb, nc;
+  double Kinv[4];
+  // results
+  double tau, kappa, theta, mu;
+  double pres, dres, dgap, obj, ctx, bty;
+  int64_t admm_iters;
+  int32_t outer_iters, status;
+  int32_t err, pad;
+};
+
+struct DenseParams {
+  double beta, gamma, alpha, eps;
+  int64_t max_admm;
+  int32_t warmstart, stop_rule;
+};
+
+cudaError_t launch_dense_setup(DenseInst* inst, int count, int* queue, int grid, size_t smem, cudaStream_t st);
+cudaError_t launch_dense_solve(DenseInst* inst, int count, DenseParams prm, int* queue, int grid,
+                               size_t smem, cudaStream_t st);
+int dense_max_ctas(int device);
+
+}  // namespace abip
+
+// The opaque handle of the C ABI.
+struct abip_handle {
+  int device = 0;
+  int m = 0, n = 0;
+  int path = 0;                 // 0 = CSR grid path, 1 = dense CTA path
+  int mixed = 0;
+  int val_f64 = 0;
+  abip_params prm{};
+  double setup_s = 0, solve_s = 0;
+  bool solved = false;
+  std::string err;
+  // device arena
+  void* arena = nullptr;
+  size_t arena_bytes = 0;
+  abip::SolveCtl* ctl = nullptr;
+  abip::GridData<double> gd64{};
+  abip::GridData<float> gd32{};
+  double* stage = nullptr;            // m + 2n doubles for scaled outputs
+  int grid = 0;
+  // dense path
+  abip::DenseInst* dinst = nullptr;   // device, one entry
+  int* queue = nullptr;
+  abip::DenseInst hinst{};            // host mirror of the descriptor
+  double nb = 0, nc = 0;
+  int64_t padded_nnz_a = 0, padded_nnz_at = 0;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  double kernel_s = 0;
+  int64_t launches = 0;
+};

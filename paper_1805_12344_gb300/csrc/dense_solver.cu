@@ -1,0 +1,486 @@
+// Dense ABIP, one CTA per LP instance (persistent: CTAs pull instance ids from a
+// device work queue, so a batch of uneven LPs runs in one launch and every
+// instance keeps its own convergence state).
+//
+// Setup (per instance): G = I + A A^T (Sec. 4.4, dense A), its Cholesky factor
+// G = L L^T in FP64, the embedding constants of Eq. bar-b-c-z-re, M^{-1} h1,
+// M^{-1} h2 and the inverse of the 2x2 Schur complement (Sec. 4.4 generalised to
+// the 4-block Q).  Solve: Algorithm 2 with over-relaxation (Sec. 4.2), the
+// projection through two blocked triangular solves with L, and the Sec. 4.1 tests
+// after every update.  All vectors of the iteration live in shared memory.
+#include <cmath>
+
+#include "abip_device.cuh"
+#include "abip_internal.h"
+
+namespace abip {
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kWarps = kThreads / 32;
+
+// next instance id from the work queue (thread 0), broadcast to the CTA
+__device__ __forceinline__ int next_instance(int* queue, int count) {
+  __shared__ int s_id;
+  __syncthreads();
+  if (threadIdx.x == 0) s_id = atomicAdd(queue, 1);
+  __syncthreads();
+  const int id = s_id;
+  return id < count ? id : -1;
+}
+
+// w <- L^{-1} w, L lower triangular (row-major, leading dimension m), w in shared memory.
+__device__ void trsv_lower(const double* __restrict__ L, int m, double* w) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int kb = 0; kb < m; kb += 32) {
+    const int nb = min(32, m - kb);
+    if (wid == 0) {
+      double wl = lane < nb ? w[kb + lane] : 0.0;
+      for (int j = 0; j < nb; ++j) {
+        if (lane == j) wl = wl / L[(size_t)(kb + j) * m + kb + j];
+        const double wj = __shfl_sync(0xffffffffu, wl, j);
+        if (lane > j && lane < nb) wl -= L[(size_t)(kb + lane) * m + kb + j] * wj;
+      }
+      if (lane < nb) w[kb + lane] = wl;
+    }
+    __syncthreads();
+    const double wb = lane < nb ? w[kb + lane] : 0.0;
+    for (int i = kb + nb + wid; i < m; i += kWarps) {
+      double a = lane < nb ? L[(size_t)i * m + kb + lane] * wb : 0.0;
+      a = warp_sum(a);
+      if (lane == 0) w[i] -= a;
+    }
+    __syncthreads();
+  }
+}
+
+// w <- L^{-T} w.
+__device__ void trsv_lower_t(const double* __restrict__ L, int m, double* w) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int nblk = (m + 31) / 32;
+  for (int bk = nblk - 1; bk >= 0; --bk) {
+    const int kb = bk * 32;
+    const int nb = min(32, m - kb);
+    if (wid == 0) {
+      double wl = lane < nb ? w[kb + lane] : 0.0;
+      for (int j = nb - 1; j >= 0; --j) {
+        if (lane == j) wl = wl / L[(size_t)(kb + j) * m + kb + j];
+        const double zj = __shfl_sync(0xffffffffu, wl, j);
+        if (lane < j) wl -= L[(size_t)(kb + j) * m + kb + lane] * zj;
+      }
+      if (lane < nb) w[kb + lane] = wl;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < kb; i += kThreads) {
+      double a = 0.0;
+      for (int j = 0; j < nb; ++j) a += L[(size_t)(kb + j) * m + i] * w[kb + j];
+      w[i] -= a;
+    }
+    __syncthreads();
+  }
+}
+
+// out[i] = sum_j A_ij v_j (warp per row); optional second vector.
+template <bool TWO>
+__device__ void gemv_rows(const double* __restrict__ A, int64_t ld, int m, int n, const double* v0,
+                          const double* v1, double* o0, double* o1) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int i = wid; i < m; i += kWarps) {
+    const double* row = A + (size_t)i * ld;
+    double a0 = 0.0, a1 = 0.0;
+    for (int j = lane; j < n; j += 32) {
+      const double a = row[j];
+      a0 += a * v0[j];
+      if (TWO) a1 += a * v1[j];
+    }
+    a0 = warp_sum(a0);
+    if (TWO) a1 = warp_sum(a1);
+    if (lane == 0) {
+      o0[i] = a0;
+      if (TWO) o1[i] = a1;
+    }
+  }
+}
+
+// out[j] = sum_i A_ij v_i (thread per column, rows unrolled by 4).
+__device__ void gemv_cols(const double* __restrict__ A, int64_t ld, int m, int n, const double* v,
+                          double* o) {
+  for (int j = threadIdx.x; j < n; j += kThreads) {
+    double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+    int i = 0;
+    for (; i + 4 <= m; i += 4) {
+      a0 += A[(size_t)i * ld + j] * v[i];
+      a1 += A[(size_t)(i + 1) * ld + j] * v[i + 1];
+      a2 += A[(size_t)(i + 2) * ld + j] * v[i + 2];
+      a3 += A[(size_t)(i + 3) * ld + j] * v[i + 3];
+    }
+    for (; i < m; ++i) a0 += A[(size_t)i * ld + j] * v[i];
+    o[j] = (a0 + a1) + (a2 + a3);
+  }
+}
+
+// Cholesky of G (lower triangle stored in L, row-major), in place, one CTA.
+__device__ bool cholesky(double* L, int m) {
+  __shared__ int s_ok;
+  if (threadIdx.x == 0) s_ok = 1;
+  __syncthreads();
+  for (int k = 0; k < m; ++k) {
+    if (threadIdx.x == 0) {
+      const double d = L[(size_t)k * m + k];
+      if (!(d > 0.0) || !isfinite(d)) s_ok = 0;
+      L[(size_t)k * m + k] = sqrt(d);
+    }
+    __syncthreads();
+    if (!s_ok) return false;
+    const double dk = L[(size_t)k * m + k];
+    for (int i = k + 1 + threadIdx.x; i < m; i += kThreads) L[(size_t)i * m + k] /= dk;
+    __syncthreads();
+    const int rem = m - k - 1;
+    // trailing update of the lower triangle: rows i > k, columns k < j <= i
+    for (int idx = threadIdx.x; idx < rem * rem; idx += kThreads) {
+      const int ii = idx / rem, jj = idx % rem;
+      if (jj <= ii) {
+        const int i = k + 1 + ii, j = k + 1 + jj;
+        L[(size_t)i * m + j] -= L[(size_t)i * m + k] * L[(size_t)j * m + k];
+      }
+    }
+    __syncthreads();
+  }
+  // zero the strict upper triangle (kept clean for readers)
+  for (int idx = threadIdx.x; idx < m * m; idx += kThreads) {
+    const int i = idx / m, j = idx % m;
+    if (j > i) L[idx] = 0.0;
+  }
+  __syncthreads();
+  return true;
+}
+
+// G = I + A A^T into the lower triangle of L (32x32 output tiles through shared memory).
+__device__ void gram(const double* __restrict__ A, int64_t ld, int m, int n, double* L, double* sm) {
+  double* Ti = sm;            // 32 x 33
+  double* Tk = sm + 32 * 33;  // 32 x 33
+  const int nt = (m + 31) / 32;
+  const int tr = threadIdx.x / 32, tc = threadIdx.x % 32;   // 8 x 32 threads, 4 rows each
+  for (int bi = 0; bi < nt; ++bi) {
+    for (int bk = 0; bk <= bi; ++bk) {
+      double acc[4] = {0.0, 0.0, 0.0, 0.0};
+      for (int j0 = 0; j0 < n; j0 += 32) {
+        for (int e = threadIdx.x; e < 32 * 32; e += kThreads) {
+          const int r = e / 32, c = e % 32;
+          const int gi = bi * 32 + r, gk = bk * 32 + r, gj = j0 + c;
+          Ti[r * 33 + c] = (gi < m && gj < n) ? A[(size_t)gi * ld + gj] : 0.0;
+          Tk[r * 33 + c] = (gk < m && gj < n) ? A[(size_t)gk * ld + gj] : 0.0;
+        }
+        __syncthreads();
+        for (int c = 0; c < 32; ++c) {
+          const double kv = Tk[tc * 33 + c];
+#pragma unroll
+          for (int q = 0; q < 4; ++q) acc[q] += Ti[(tr * 4 + q) * 33 + c] * kv;
+        }
+        __syncthreads();
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int gi = bi * 32 + tr * 4 + q, gk = bk * 32 + tc;
+        if (gi < m && gk <= gi) L[(size_t)gi * m + gk] = acc[q] + (gi == gk ? 1.0 : 0.0);
+      }
+    }
+  }
+  __syncthreads();
+}
+
+// M [zy; zx] = [a; d]  ->  zy = G^{-1}(a - A d), zx = d + A^T zy (Sec. 4.4).
+// a (m), d (n) in shared memory; results in zy (m), zx (n); tmp (m) scratch.
+__device__ void solve_M(const DenseInst& I, const double* a, const double* d, double* zy, double* zx,
+                        double* tmp) {
+  gemv_rows<false>(I.A, I.ld, I.m, I.n, d, d, tmp, tmp);
+  __syncthreads();
+  for (int i = threadIdx.x; i < I.m; i += kThreads) zy[i] = a[i] - tmp[i];
+  __syncthreads();
+  trsv_lower(I.L, I.m, zy);
+  trsv_lower_t(I.L, I.m, zy);
+  gemv_cols(I.A, I.ld, I.m, I.n, zy, zx);
+  for (int j = threadIdx.x; j < I.n; j += kThreads) zx[j] += d[j];
+  __syncthreads();
+}
+
+__global__ void __launch_bounds__(kThreads) dense_setup_kernel(DenseInst* insts, int count, int* queue) {
+  extern __shared__ double sm[];
+  __shared__ double red[32 * 8];
+  for (;;) {
+    const int id = next_instance(queue, count);
+    if (id < 0) return;
+    DenseInst& I = insts[id];
+    const int m = I.m, n = I.n;
+    // embedding constants
+    double acc[3] = {0.0, 0.0, 0.0};
+    for (int i = threadIdx.x; i < m; i += kThreads) {
+      double rs = 0.0;
+      for (int j = 0; j < n; ++j) rs += I.A[(size_t)i * I.ld + j];
+      I.bbar[i] = I.b[i] - rs;
+      acc[1] += I.b[i] * I.b[i];
+    }
+    for (int j = threadIdx.x; j < n; j += kThreads) {
+      I.cbar[j] = I.c[j] - 1.0;
+      acc[0] += I.c[j];
+      acc[2] += I.c[j] * I.c[j];
+    }
+    block_allsum<3>(acc, red);
+    const double zbar = acc[0] + 1.0;
+    gram(I.A, I.ld, m, n, I.L, sm);
+    if (!cholesky(I.L, m)) {
+      if (threadIdx.x == 0) { I.err = DEV_ERR_CHOLESKY; I.status = 0; }
+      continue;
+    }
+    // M^{-1} h1, M^{-1} h2 with h1 = [-b; c], h2 = [bbar; -cbar]
+    double* a = sm;            // m
+    double* d = sm + m;        // n
+    double* tmp = sm + m + n;  // m
+    for (int col = 0; col < 2; ++col) {
+      double* g = col == 0 ? I.g1 : I.g2;
+      for (int i = threadIdx.x; i < m; i += kThreads) a[i] = col == 0 ? -I.b[i] : I.bbar[i];
+      for (int j = threadIdx.x; j < n; j += kThreads) d[j] = col == 0 ? I.c[j] : -I.cbar[j];
+      __syncthreads();
+      solve_M(I, a, d, g, g + m, tmp);
+    }
+    // K = I + S + H^T M^{-1} H, S = [[0, zbar], [-zbar, 0]]
+    double k4[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int i = threadIdx.x; i < m; i += kThreads) {
+      k4[0] += -I.b[i] * I.g1[i]; k4[1] += -I.b[i] * I.g2[i];
+      k4[2] += I.bbar[i] * I.g1[i]; k4[3] += I.bbar[i] * I.g2[i];
+    }
+    for (int j = threadIdx.x; j < n; j += kThreads) {
+      k4[0] += I.c[j] * I.g1[m + j]; k4[1] += I.c[j] * I.g2[m + j];
+      k4[2] += -I.cbar[j] * I.g1[m + j]; k4[3] += -I.cbar[j] * I.g2[m + j];
+    }
+    block_allsum<4>(k4, red);
+    if (threadIdx.x == 0) {
+      const double K0 = 1.0 + k4[0], K1 = zbar + k4[1], K2 = -zbar + k4[2], K3 = 1.0 + k4[3];
+      const double det = K0 * K3 - K1 * K2;
+      I.Kinv[0] = K3 / det; I.Kinv[1] = -K1 / det; I.Kinv[2] = -K2 / det; I.Kinv[3] = K0 / det;
+      I.zbar = zbar;
+      I.nb = sqrt(acc[1]);
+      I.nc = sqrt(acc[2]);
+      I.err = isfinite(det) && det != 0.0 ? 0 : DEV_ERR_NONFINITE;
+    }
+    __syncthreads();
+  }
+}
+
+// Algorithm 2 for one instance with the CTA.  Shared layout (doubles):
+// y, zy, w, Ax, As (m each), x, s, zx (n each).
+__device__ void dense_solve_one(DenseInst& I, const DenseParams& P, double* sm, double* red) {
+  const int m = I.m, n = I.n;
+  double* y = sm;
+  double* zy = y + m;
+  double* w = zy + m;
+  double* Ax = w + m;
+  double* As = Ax + m;
+  double* x = As + m;
+  double* s = x + n;
+  double* zx = s + n;
+  const double alpha = P.alpha, beta = P.beta, gamma = P.gamma, eps = P.eps;
+  const double zbar = I.zbar, xi = -(double)n - 1.0, nb = I.nb, nc = I.nc;
+  const double Ki0 = I.Kinv[0], Ki1 = I.Kinv[1], Ki2 = I.Kinv[2], Ki3 = I.Kinv[3];
+  const double* b = I.b;
+  const double* c = I.c;
+  // start of Algorithm 2
+  for (int i = threadIdx.x; i < m; i += kThreads) y[i] = 0.0;
+  for (int j = threadIdx.x; j < n; j += kThreads) { x[j] = 1.0; s[j] = 1.0; }
+  __syncthreads();
+  double tau = 1.0, kappa = 1.0, theta = 1.0, mu = beta;
+  int64_t total = 0;
+  int outer = 0, status = 0;
+  double inner2 = 0, pres = 0, dres = 0, dgap = 0, ctx = 0, bty = 0;
+
+  auto evaluate = [&](bool final_test) {
+    gemv_rows<true>(I.A, I.ld, m, n, x, s, Ax, As);
+    double acc[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    __syncthreads();
+    for (int i = threadIdx.x; i < m; i += kThreads) {
+      const double ry = Ax[i] - b[i] * tau + I.bbar[i] * theta;
+      const double pr = Ax[i] / tau - b[i];
+      acc[0] += ry * ry; acc[1] += pr * pr; acc[3] += Ax[i] * Ax[i];
+      acc[5] += b[i] * y[i]; acc[6] += I.bbar[i] * y[i];
+    }
+    // A^T y column by column
+    for (int j = threadIdx.x; j < n; j += kThreads) {
+      double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+      int i = 0;
+      for (; i + 4 <= m; i += 4) {
+        a0 += I.A[(size_t)i * I.ld + j] * y[i];
+        a1 += I.A[(size_t)(i + 1) * I.ld + j] * y[i + 1];
+        a2 += I.A[(size_t)(i + 2) * I.ld + j] * y[i + 2];
+        a3 += I.A[(size_t)(i + 3) * I.ld + j] * y[i + 3];
+      }
+      for (; i < m; ++i) a0 += I.A[(size_t)i * I.ld + j] * y[i];
+      const double aty = (a0 + a1) + (a2 + a3);
+      const double rx = -aty + c[j] * tau - I.cbar[j] * theta - s[j];
+      const double dr = (aty + s[j]) / tau - c[j];
+      acc[0] += rx * rx; acc[2] += dr * dr; acc[4] += (aty + s[j]) * (aty + s[j]);
+      acc[7] += c[j] * x[j]; acc[8] += I.cbar[j] * x[j];
+    }
+    block_allsum<9>(acc, red);
+    bty = acc[5];
+    ctx = acc[7];
+    const double rt = acc[5] - acc[7] + zbar * theta - kappa;
+    const double rth = -acc[6] + acc[8] - zbar * tau - xi;
+    inner2 = acc[0] + rt * rt + rth * rth;
+    pres = sqrt(acc[1]) / (1.0 + nb);
+    dres = sqrt(acc[2]) / (1.0 + nc);
+    dgap = fabs(ctx / tau - bty / tau) / (1.0 + fabs(ctx / tau) + fabs(bty / tau));
+    if (!isfinite(inner2)) return false;
+    if (final_test && P.stop_rule == 0) {
+      if (pres <= eps && dres <= eps && dgap <= eps) status = ABIP_OPTIMAL;
+      else if (bty > 0 && sqrt(acc[4]) <= eps * bty / nb) status = ABIP_PRIMAL_INFEASIBLE;
+      else if (ctx < 0 && sqrt(acc[3]) <= eps * (-ctx) / nc) status = ABIP_DUAL_INFEASIBLE;
+    }
+    return true;
+  };
+
+  bool ok = evaluate(false);
+  while (ok) {
+    if (inner2 <= mu) {
+      mu *= gamma;
+      ++outer;
+      if (P.stop_rule == 1 && mu < eps) { status = ABIP_OPTIMAL; break; }
+      if (outer >= kMaxOuter) { status = ABIP_MAX_ITER; break; }   // mu has underflowed
+      const double sg = sqrt(gamma);
+      if (P.warmstart == 1) {
+        for (int j = threadIdx.x; j < n; j += kThreads) { x[j] *= sg; s[j] *= sg; }
+        tau *= sg; kappa *= sg;
+      } else {
+        for (int j = threadIdx.x; j < n; j += kThreads) {
+          if (x[j] >= s[j]) s[j] *= gamma; else x[j] *= gamma;
+        }
+        if (tau >= kappa) kappa *= gamma; else tau *= gamma;
+      }
+      for (int i = threadIdx.x; i < m; i += kThreads) y[i] *= sg;
+      theta *= sg;
+      __syncthreads();
+      ok = evaluate(false);
+      continue;
+    }
+    // projection: w_y = y, w_x = x + s; zy = G^{-1}(y - A(x + s)) = G^{-1}(y - Ax - As)
+    for (int i = threadIdx.x; i < m; i += kThreads) zy[i] = y[i] - (Ax[i] + As[i]);
+    for (int j = threadIdx.x; j < n; j += kThreads) zx[j] = x[j] + s[j];
+    __syncthreads();
+    trsv_lower(I.L, m, zy);
+    trsv_lower_t(I.L, m, zy);
+    // zx = w_x + A^T zy, and H^T z
+    double hz[2] = {0.0, 0.0};
+    for (int j = threadIdx.x; j < n; j += kThreads) {
+      double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+      int i = 0;
+      for (; i + 4 <= m; i += 4) {
+        a0 += I.A[(size_t)i * I.ld + j] * zy[i];
+        a1 += I.A[(size_t)(i + 1) * I.ld + j] * zy[i + 1];
+        a2 += I.A[(size_t)(i + 2) * I.ld + j] * zy[i + 2];
+        a3 += I.A[(size_t)(i + 3) * I.ld + j] * zy[i + 3];
+      }
+      for (; i < m; ++i) a0 += I.A[(size_t)i * I.ld + j] * zy[i];
+      const double z = zx[j] + ((a0 + a1) + (a2 + a3));
+      zx[j] = z;
+      hz[0] += c[j] * z;
+      hz[1] -= I.cbar[j] * z;
+    }
+    for (int i = threadIdx.x; i < m; i += kThreads) {
+      hz[0] -= b[i] * zy[i];
+      hz[1] += I.bbar[i] * zy[i];
+    }
+    block_allsum<2>(hz, red);
+    const double v1 = tau + kappa + hz[0], v2 = theta + xi + hz[1];
+    const double t1 = Ki0 * v1 + Ki1 * v2, t2 = Ki2 * v1 + Ki3 * v2;
+    const double cmu = mu / beta;
+    for (int i = threadIdx.x; i < m; i += kThreads) {
+      const double uy = zy[i] - I.g1[i] * t1 - I.g2[i] * t2;
+      y[i] = alpha * uy + (1.0 - alpha) * y[i];
+    }
+    for (int j = threadIdx.x; j < n; j += kThreads) {
+      const double ux = zx[j] - I.g1[m + j] * t1 - I.g2[m + j] * t2;
+      const double xh = alpha * ux + (1.0 - alpha) * x[j];
+      double xn, sn;
+      barrier_step<double>(xh - s[j], cmu, xn, sn);
+      x[j] = xn;
+      s[j] = sn;
+    }
+    {
+      const double th_ = alpha * t1 + (1.0 - alpha) * tau;
+      double tn, kn;
+      barrier_step<double>(th_ - kappa, cmu, tn, kn);
+      tau = tn;
+      kappa = kn;
+      theta = alpha * t2 + (1.0 - alpha) * theta;
+    }
+    __syncthreads();
+    ++total;
+    ok = evaluate(true);
+    if (status != 0) break;
+    if (total >= P.max_admm) { status = ABIP_MAX_ITER; break; }
+  }
+  // outputs: raw state and the scaled candidate or certificate (Sec. 4.1)
+  double sx = 1.0 / tau, sy = 1.0 / tau;
+  if (status == ABIP_PRIMAL_INFEASIBLE) { sx = 1.0; sy = 1.0 / bty; }
+  if (status == ABIP_DUAL_INFEASIBLE) { sx = -1.0 / ctx; sy = 1.0; }
+  for (int i = threadIdx.x; i < m; i += kThreads) {
+    I.y[i] = y[i];
+    if (I.out_y) I.out_y[i] = y[i] * sy;
+  }
+  for (int j = threadIdx.x; j < n; j += kThreads) {
+    I.x[j] = x[j];
+    I.s[j] = s[j];
+    if (I.out_x) I.out_x[j] = x[j] * sx;
+    if (I.out_s) I.out_s[j] = s[j] * sy;
+  }
+  if (threadIdx.x == 0) {
+    I.tau = tau; I.kappa = kappa; I.theta = theta; I.mu = mu;
+    I.pres = pres; I.dres = dres; I.dgap = dgap; I.ctx = ctx; I.bty = bty; I.obj = ctx / tau;
+    I.admm_iters = total; I.outer_iters = outer; I.status = status;
+    if (!ok) I.err = DEV_ERR_NONFINITE;
+  }
+  __syncthreads();
+}
+
+__global__ void __launch_bounds__(kThreads) dense_solve_kernel(DenseInst* insts, int count, DenseParams P,
+                                                               int* queue) {
+  extern __shared__ double sm[];
+  __shared__ double red[32 * 9];
+  for (;;) {
+    const int id = next_instance(queue, count);
+    if (id < 0) return;
+    DenseInst& I = insts[id];
+    if (I.err != 0) continue;
+    dense_solve_one(I, P, sm, red);
+  }
+}
+
+}  // namespace
+
+// dynamic shared memory of the solve kernel: 5m + 3n doubles, at most this many bytes
+constexpr size_t kDenseSmemMax = 200 * 1024;
+
+cudaError_t launch_dense_setup(DenseInst* inst, int count, int* queue, int grid, size_t smem, cudaStream_t st) {
+  // the caller sizes smem for the largest instance: max(2m + n, 2 * 32 * 33) doubles
+  cudaError_t e = cudaFuncSetAttribute(dense_setup_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDenseSmemMax);
+  if (e != cudaSuccess) return e;
+  dense_setup_kernel<<<grid, kThreads, smem, st>>>(inst, count, queue);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_dense_solve(DenseInst* inst, int count, DenseParams prm, int* queue, int grid,
+                               size_t smem, cudaStream_t st) {
+  // the caller sizes smem for the largest instance: 5m + 3n doubles
+  cudaError_t e = cudaFuncSetAttribute(dense_solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDenseSmemMax);
+  if (e != cudaSuccess) return e;
+  dense_solve_kernel<<<grid, kThreads, smem, st>>>(inst, count, prm, queue);
+  return cudaGetLastError();
+}
+
+int dense_max_ctas(int device) {
+  int sms = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+  return sms;
+}
+
+}  // namespace abip

@@ -1,0 +1,495 @@
+// Persistent cooperative kernel running ABIP (Algorithm 2 with the over-relaxation
+// of Sec. 4.2) on one sparse LP: Jacobi-PCG projection (Sec. 4.4) and the Sec. 4.1
+// termination tests, entirely on the device.
+//
+// One launch covers setup (MODE_SETUP: embedding constants of Eq. bar-b-c-z-re,
+// Jacobi diagonal, M^{-1} H and the 2x2 Schur complement) or the whole solve
+// (MODE_SOLVE).  Phases are separated by a bounded grid barrier; every scalar the
+// control flow depends on is reduced in a fixed order and recomputed identically
+// by every CTA, so all CTAs take the same branch.
+//
+// Sparse products use SELL-32 (one warp per slice of 32 length-sorted rows, one
+// thread per row): value and column loads are coalesced and each thread keeps U
+// independent gathers in flight, which is what an L2-resident, latency-bound
+// product needs on this part.
+#include <cmath>
+
+#include "abip_device.cuh"
+#include "abip_internal.h"
+
+namespace abip {
+
+namespace {
+
+// reduction slots (a slot is never rewritten before a barrier separates its
+// previous read)
+enum Slot : int {
+  S_PCG0 = 0,    // 3: r.zr, r.r, q.q
+  S_PGP = 3,     // 1: p.Gp
+  S_RZ = 4,      // 2: r.zr, r.r
+  S_HZ = 6,      // 2: h1.z, h2.z
+  S_RES = 8,     // 9: residual sums
+  S_SETUP = 17,  // 3: sum c, ||b||^2, ||c||^2
+  S_K = 20,      // 4: H^T M^{-1} H
+};
+
+constexpr int kMinBlocks = 3;   // resident CTAs per SM requested from the compiler
+
+struct Thr {
+  int gtid, nthr, gw, nwarp, lane;
+  __device__ Thr() {
+    gtid = blockIdx.x * blockDim.x + threadIdx.x;
+    nthr = gridDim.x * blockDim.x;
+    gw = gtid >> 5;
+    nwarp = nthr >> 5;
+    lane = threadIdx.x & 31;
+  }
+};
+
+// Row products y_i = sum_k A_ik v_k (and a second vector) for every row of a
+// SELL-32 matrix; epi(row, dot0, dot1) runs on the row's thread.
+template <int U, int NV, typename T, typename V, typename Epi>
+__device__ __forceinline__ void sell_rows(const SellMat& S, const T* __restrict__ v0, const T* __restrict__ v1,
+                                          Epi& epi) {
+  const Thr th;
+  const V* __restrict__ val = static_cast<const V*>(S.val);
+  for (int sl = th.gw; sl < S.nslices; sl += th.nwarp) {
+    const int64_t base = __ldg(S.sp + sl);
+    const int w = (int)((__ldg(S.sp + sl + 1) - base) >> 5);
+    const int row = __ldg(S.perm + sl * 32 + th.lane);
+    const int32_t* __restrict__ ci = S.ci + base + th.lane;
+    const V* __restrict__ va = val + base + th.lane;
+    T a0 = T(0), a1 = T(0);
+    int k = 0;
+    for (; k + U <= w; k += U) {
+      int j[U];
+      T a[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        j[u] = __ldg(ci + (k + u) * 32);
+        a[u] = static_cast<T>(__ldg(va + (k + u) * 32));
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        a0 += a[u] * v0[j[u]];
+        if (NV == 2) a1 += a[u] * v1[j[u]];
+      }
+    }
+    for (; k < w; ++k) {
+      const int j = __ldg(ci + k * 32);
+      const T a = static_cast<T>(__ldg(va + k * 32));
+      a0 += a * v0[j];
+      if (NV == 2) a1 += a * v1[j];
+    }
+    if (row >= 0) epi(row, a0, a1);
+  }
+}
+
+// Per-row sum and sum of squares of a SELL-32 matrix (setup only).
+template <typename T, typename V, typename Epi>
+__device__ void sell_rowstats(const SellMat& S, Epi& epi) {
+  const Thr th;
+  const V* val = static_cast<const V*>(S.val);
+  for (int sl = th.gw; sl < S.nslices; sl += th.nwarp) {
+    const int64_t base = S.sp[sl];
+    const int w = (int)((S.sp[sl + 1] - base) >> 5);
+    const int row = S.perm[sl * 32 + th.lane];
+    T sum = T(0), sq = T(0);
+    for (int k = 0; k < w; ++k) {
+      const T a = static_cast<T>(val[base + k * 32 + th.lane]);
+      sum += a;
+      sq += a * a;
+    }
+    if (row >= 0) epi(row, sum, sq);
+  }
+}
+
+template <typename T, typename V>
+struct Solver {
+  const GridData<T>& D;
+  SolveCtl* C;
+  double* red;   // shared scratch
+  Thr th;
+  unsigned long long bar_target = 0;
+  __device__ Solver(const GridData<T>& d, double* r) : D(d), C(d.ctl), red(r) {}
+
+  __device__ bool sync() { return grid_sync(GridBarrier{D.bar, &C->err}, bar_target); }
+
+  template <typename Epi>
+  __device__ void rowsA(const T* v0, Epi& e) { sell_rows<8, 1, T, V>(D.A, v0, v0, e); }
+  template <typename Epi>
+  __device__ void rowsA2(const T* v0, const T* v1, Epi& e) { sell_rows<8, 2, T, V>(D.A, v0, v1, e); }
+  template <typename Epi>
+  __device__ void rowsAT(const T* v0, Epi& e) { sell_rows<8, 1, T, V>(D.AT, v0, v0, e); }
+
+  __device__ void flag(int code) {
+    if (threadIdx.x == 0) atomicCAS(&C->err, 0, code);
+  }
+
+  // Jacobi-PCG on G = I + A A^T (Sec. 4.4): z (in: warm start, out: solution),
+  // right-hand side q_i = qf(i).  Stop when ||r|| <= tol * max(1, ||q||) (reading
+  // A10).  Three grid barriers per iteration: the direction update p = zr + beta p
+  // is folded into t = A^T p = A^T zr + beta t and into the next A pass.
+  // Returns iterations, or -1 on barrier failure / -2 past the cap.
+  template <typename QF>
+  __device__ int pcg(T* z, QF qf, double tol, int maxit) {
+    T* r = D.r; T* p = D.p; T* zr = D.zr; T* t = D.t; T* Gp = D.Gp;
+    {
+      auto e = [&](int j, T v, T) { t[j] = v; };
+      rowsAT(z, e);
+    }
+    if (!sync()) return -1;
+    double acc[3] = {0.0, 0.0, 0.0};
+    {
+      auto e = [&](int i, T v, T) {
+        const T qi = qf(i);
+        const T ri = qi - (z[i] + v);
+        const T zri = D.dinv[i] * ri;
+        r[i] = ri; zr[i] = zri;
+        acc[0] += (double)ri * (double)zri;
+        acc[1] += (double)ri * (double)ri;
+        acc[2] += (double)qi * (double)qi;
+      };
+      rowsA(t, e);
+    }
+    grid_partial<3>(acc, D.partials, S_PCG0, red);
+    if (!sync()) return -1;
+    double tot[3];
+    grid_total<3>(tot, D.partials, S_PCG0, red);
+    double rz = tot[0], rr = tot[1];
+    const double bound = tol * fmax(1.0, sqrt(tot[2]));
+    T be = T(0);
+    int k = 0;
+    while (sqrt(rr) > bound) {
+      if (k >= maxit) return -2;
+      const bool first = k == 0;
+      {
+        // t = A^T p with p = zr + be * p_old  (t holds A^T p_old)
+        auto e = [&](int j, T v, T) { t[j] = first ? v : v + be * t[j]; };
+        rowsAT(zr, e);
+      }
+      if (!sync()) return -1;
+      double a1[1] = {0.0};
+      {
+        auto e = [&](int i, T v, T) {
+          const T pi = first ? zr[i] : zr[i] + be * p[i];
+          const T gp = pi + v;
+          p[i] = pi;
+          Gp[i] = gp;
+          a1[0] += (double)pi * (double)gp;
+        };
+        rowsA(t, e);
+      }
+      grid_partial<1>(a1, D.partials, S_PGP, red);
+      if (!sync()) return -1;
+      double pgp[1];
+      grid_total<1>(pgp, D.partials, S_PGP, red);
+      const T al = (T)(rz / pgp[0]);
+      double a2[2] = {0.0, 0.0};
+      for (int i = th.gtid; i < D.m; i += th.nthr) {
+        z[i] += al * p[i];
+        const T ri = r[i] - al * Gp[i];
+        const T zri = D.dinv[i] * ri;
+        r[i] = ri; zr[i] = zri;
+        a2[0] += (double)ri * (double)zri;
+        a2[1] += (double)ri * (double)ri;
+      }
+      grid_partial<2>(a2, D.partials, S_RZ, red);
+      if (!sync()) return -1;
+      double t2[2];
+      grid_total<2>(t2, D.partials, S_RZ, red);
+      be = (T)(t2[0] / rz);
+      rz = t2[0];
+      rr = t2[1];
+      ++k;
+    }
+    return k;
+  }
+
+  // Residual products and every sum the Sec. 4.1 tests and Eq. inner-stop need,
+  // for the current (y, x, s, tau, kappa, theta):  Ax, As (one 2-vector pass over
+  // A), A^T y, then
+  //   Q u - v  = (Ax - b tau + bbar theta,  -A^T y + c tau - cbar theta - s,
+  //               b^T y - c^T x + zbar theta - kappa,  -bbar^T y + cbar^T x - zbar tau - xi)
+  // Returns false on barrier failure.  tot[] receives
+  //   0 ||Qu-v||^2 (vector blocks), 1 ||Ax/tau - b||^2, 2 ||(A^T y + s)/tau - c||^2,
+  //   3 ||Ax||^2, 4 ||A^T y + s||^2, 5 b^T y, 6 bbar^T y, 7 c^T x, 8 cbar^T x.
+  __device__ bool residuals(double tau, double theta, double (&tot)[9]) {
+    double acc[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    {
+      auto e = [&](int i, T ax, T as) {
+        D.Ax[i] = ax; D.As[i] = as;
+        const double axd = (double)ax;
+        const double bi = (double)D.b[i];
+        const double ry = axd - bi * tau + (double)D.bbar[i] * theta;
+        const double pr = axd / tau - bi;
+        const double yi = (double)D.y[i];
+        acc[0] += ry * ry;
+        acc[1] += pr * pr;
+        acc[3] += axd * axd;
+        acc[5] += bi * yi;
+        acc[6] += (double)D.bbar[i] * yi;
+      };
+      rowsA2(D.x, D.s, e);
+    }
+    {
+      auto e = [&](int j, T aty, T) {
+        D.ATy[j] = aty;
+        const double atyd = (double)aty, sj = (double)D.s[j], cj = (double)D.c[j];
+        const double rx = -atyd + cj * tau - (double)D.cbar[j] * theta - sj;
+        const double dr = (atyd + sj) / tau - cj;
+        const double xj = (double)D.x[j];
+        acc[0] += rx * rx;
+        acc[2] += dr * dr;
+        acc[4] += (atyd + sj) * (atyd + sj);
+        acc[7] += cj * xj;
+        acc[8] += (double)D.cbar[j] * xj;
+      };
+      rowsAT(D.y, e);
+    }
+    grid_partial<9>(acc, D.partials, S_RES, red);
+    if (!sync()) return false;
+    grid_total<9>(tot, D.partials, S_RES, red);
+    return true;
+  }
+
+  // MODE_SETUP: bbar = b - A e, cbar = c - e, zbar = c^T e + 1 (Eq. bar-b-c-z-re),
+  // Jacobi diagonal 1 + sum_j A_ij^2, norms; then M^{-1} h1, M^{-1} h2 with
+  // h1 = [-b; c], h2 = [bbar; -cbar] (Sec. 4.4, 4-block form) and H^T M^{-1} H.
+  __device__ void setup() {
+    const Thr t = th;
+    double acc[3] = {0.0, 0.0, 0.0};
+    {
+      auto e = [&](int i, T rs, T sq) {
+        D.bbar[i] = D.b[i] - rs;
+        D.dinv[i] = T(1) / (T(1) + sq);
+      };
+      sell_rowstats<T, V>(D.A, e);
+    }
+    for (int i = t.gtid; i < D.m; i += t.nthr) acc[1] += (double)D.b[i] * (double)D.b[i];
+    for (int j = t.gtid; j < D.n; j += t.nthr) {
+      D.cbar[j] = D.c[j] - T(1);
+      acc[0] += (double)D.c[j];
+      acc[2] += (double)D.c[j] * (double)D.c[j];
+    }
+    grid_partial<3>(acc, D.partials, S_SETUP, red);
+    if (!sync()) return;
+    double tot[3];
+    grid_total<3>(tot, D.partials, S_SETUP, red);
+    // two solves with M: a = h_y, d = h_x  ->  zy = G^{-1}(a - A d), zx = d + A^T zy
+    for (int col = 0; col < 2; ++col) {
+      T* gy = col == 0 ? D.g1y : D.g2y;
+      T* gx = col == 0 ? D.g1x : D.g2x;
+      for (int j = t.gtid; j < D.n; j += t.nthr) gx[j] = col == 0 ? D.c[j] : -D.cbar[j];
+      for (int i = t.gtid; i < D.m; i += t.nthr) gy[i] = T(0);
+      if (!sync()) return;
+      {
+        auto e = [&](int i, T v, T) { D.Ax[i] = v; };
+        rowsA(gx, e);
+      }
+      if (!sync()) return;
+      const int c0 = col;
+      auto qf = [&](int i) -> T { return (c0 == 0 ? -D.b[i] : D.bbar[i]) - D.Ax[i]; };
+      const int it = pcg(gy, qf, C->cg_tol, C->cg_max);
+      if (it == -1) return;
+      if (it == -2) { flag(DEV_ERR_PCG); sync(); return; }
+      {
+        auto e = [&](int j, T v, T) { gx[j] = gx[j] + v; };
+        rowsAT(gy, e);
+      }
+      if (!sync()) return;
+    }
+    // H^T M^{-1} H:  h1.g1, h1.g2, h2.g1, h2.g2
+    double k4[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int i = t.gtid; i < D.m; i += t.nthr) {
+      const double bi = D.b[i], bbi = D.bbar[i], g1 = D.g1y[i], g2 = D.g2y[i];
+      k4[0] += -bi * g1; k4[1] += -bi * g2; k4[2] += bbi * g1; k4[3] += bbi * g2;
+    }
+    for (int j = t.gtid; j < D.n; j += t.nthr) {
+      const double cj = D.c[j], cbj = D.cbar[j], g1 = D.g1x[j], g2 = D.g2x[j];
+      k4[0] += cj * g1; k4[1] += cj * g2; k4[2] += -cbj * g1; k4[3] += -cbj * g2;
+    }
+    grid_partial<4>(k4, D.partials, S_K, red);
+    if (!sync()) return;
+    double kt[4];
+    grid_total<4>(kt, D.partials, S_K, red);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      C->sum_c = tot[0]; C->sum_b2 = tot[1]; C->sum_c2 = tot[2];
+      C->K[0] = 1.0 + kt[0];
+      C->K[1] = tot[0] + 1.0 + kt[1];      // zbar = c^T e + 1
+      C->K[2] = -(tot[0] + 1.0) + kt[2];
+      C->K[3] = 1.0 + kt[3];
+    }
+  }
+
+  // MODE_SOLVE: Algorithm 2 from the state in D / C.
+  __device__ void solve() {
+    const Thr t = th;
+    const double alpha = C->alpha, beta = C->beta, gamma = C->gamma, eps = C->eps;
+    const double zbar = C->zbar, xi = C->xi, nb = C->nb, nc = C->nc;
+    const double Ki0 = C->Kinv[0], Ki1 = C->Kinv[1], Ki2 = C->Kinv[2], Ki3 = C->Kinv[3];
+    const double cg_rel = C->cg_rel;
+    double tau = C->tau, kappa = C->kappa, theta = C->theta, mu = C->mu;
+    int64_t total = C->admm_iters;
+    int64_t cgtot = C->cg_iters;
+    int outer = C->outer_iters;
+    int status = 0;
+    double tot[9];
+    double inner2 = 0, pres = 0, dres = 0, dgap = 0, ctx = 0, bty = 0;
+
+    auto evaluate = [&](bool final_test) -> bool {
+      if (!residuals(tau, theta, tot)) return false;
+      bty = tot[5];
+      ctx = tot[7];
+      const double rt = tot[5] - tot[7] + zbar * theta - kappa;
+      const double rth = -tot[6] + tot[8] - zbar * tau - xi;
+      inner2 = tot[0] + rt * rt + rth * rth;
+      pres = sqrt(tot[1]) / (1.0 + nb);
+      dres = sqrt(tot[2]) / (1.0 + nc);
+      const double gap = fabs(ctx / tau - bty / tau);
+      dgap = gap / (1.0 + fabs(ctx / tau) + fabs(bty / tau));
+      if (!isfinite(inner2) || !isfinite(pres) || !isfinite(dres)) {
+        flag(DEV_ERR_NONFINITE);
+        return false;
+      }
+      if (final_test && C->stop_rule == 0) {
+        if (pres <= eps && dres <= eps && dgap <= eps) status = ABIP_OPTIMAL;
+        else if (bty > 0 && sqrt(tot[4]) <= eps * bty / nb) status = ABIP_PRIMAL_INFEASIBLE;
+        else if (ctx < 0 && sqrt(tot[3]) <= eps * (-ctx) / nc) status = ABIP_DUAL_INFEASIBLE;
+      }
+      return true;
+    };
+
+    if (!evaluate(false)) return;
+    for (;;) {
+      // inner stop, Eq. inner-stop: ||Q u - v||^2 <= mu
+      if (inner2 <= mu) {
+        mu *= gamma;
+        ++outer;
+        if (C->stop_rule == 1 && mu < eps) { status = ABIP_OPTIMAL; break; }
+        if (outer >= kMaxOuter) { status = ABIP_MAX_ITER; break; }   // mu has underflowed
+        // warm start (Sec. 5 heuristic, or Eq. update-next-iterate)
+        const T g = (T)gamma, sg = (T)sqrt(gamma);
+        if (C->warmstart == 1) {
+          for (int j = t.gtid; j < D.n; j += t.nthr) { D.x[j] *= sg; D.s[j] *= sg; }
+          tau *= sqrt(gamma); kappa *= sqrt(gamma);
+        } else {
+          for (int j = t.gtid; j < D.n; j += t.nthr) {
+            const T xj = D.x[j], sj = D.s[j];
+            if (xj >= sj) D.s[j] = g * sj; else D.x[j] = g * xj;
+          }
+          if (tau >= kappa) kappa *= gamma; else tau *= gamma;
+        }
+        for (int i = t.gtid; i < D.m; i += t.nthr) D.y[i] *= sg;
+        theta *= sqrt(gamma);
+        if (!sync()) return;
+        if (!evaluate(false)) return;
+        continue;
+      }
+      // ---- one ADMM update -------------------------------------------------
+      // projection (Eq. Simple-Update:Affine) with w = u + v: w_y = y (r = 0),
+      // w_x = x + s, w_tau = tau + kappa, w_theta = theta + xi.
+      // z = M^{-1} w_yx: G zy = w_y - A w_x = y - Ax - As (PCG warm-started), zx = w_x + A^T zy.
+      auto qf = [&](int i) -> T { return D.y[i] - (D.Ax[i] + D.As[i]); };
+      // PCG tolerance: fixed, or (cg_rel > 0) loosened to cg_rel times the current
+      // relative KKT residual, never below cg_tol (reading A10, performance mode)
+      const double kkt = fmax(pres, fmax(dres, dgap));
+      const double tol = cg_rel > 0.0 ? fmax(C->cg_tol, cg_rel * kkt) : C->cg_tol;
+      const int it = pcg(D.zy, qf, tol, C->cg_max);
+      if (it == -1) return;
+      if (it == -2) { flag(DEV_ERR_PCG); sync(); return; }
+      cgtot += it;
+      double hz[2] = {0.0, 0.0};
+      {
+        auto e = [&](int j, T v, T) {
+          const T zxj = (D.x[j] + D.s[j]) + v;
+          D.zx[j] = zxj;
+          hz[0] += (double)D.c[j] * (double)zxj;
+          hz[1] -= (double)D.cbar[j] * (double)zxj;
+        };
+        rowsAT(D.zy, e);
+      }
+      for (int i = t.gtid; i < D.m; i += t.nthr) {
+        const double zyi = D.zy[i];
+        hz[0] -= (double)D.b[i] * zyi;
+        hz[1] += (double)D.bbar[i] * zyi;
+      }
+      grid_partial<2>(hz, D.partials, S_HZ, red);
+      if (!sync()) return;
+      double h[2];
+      grid_total<2>(h, D.partials, S_HZ, red);
+      // t = K^{-1} (w_{tau,theta} + H^T z)
+      const double v1 = tau + kappa + h[0], v2 = theta + xi + h[1];
+      const double t1 = Ki0 * v1 + Ki1 * v2, t2 = Ki2 * v1 + Ki3 * v2;
+      // u~_yx = z - [g1 g2] t; relaxation (Sec. 4.2); barrier and dual steps
+      const T a = (T)alpha, a1 = (T)(1.0 - alpha), t1T = (T)t1, t2T = (T)t2, cmu = (T)(mu / beta);
+      for (int i = t.gtid; i < D.m; i += t.nthr) {
+        const T uy = D.zy[i] - D.g1y[i] * t1T - D.g2y[i] * t2T;
+        D.y[i] = a * uy + a1 * D.y[i];
+      }
+      for (int j = t.gtid; j < D.n; j += t.nthr) {
+        const T ux = D.zx[j] - D.g1x[j] * t1T - D.g2x[j] * t2T;
+        const T xh = a * ux + a1 * D.x[j];
+        T xn, sn;
+        barrier_step<T>(xh - D.s[j], cmu, xn, sn);
+        D.x[j] = xn; D.s[j] = sn;
+      }
+      {
+        const double th_ = alpha * t1 + (1.0 - alpha) * tau;
+        double tn, kn;
+        barrier_step<double>(th_ - kappa, mu / beta, tn, kn);
+        tau = tn; kappa = kn;
+        theta = alpha * t2 + (1.0 - alpha) * theta;
+      }
+      if (!sync()) return;
+      ++total;
+      if (!evaluate(true)) return;
+      if (status != 0) break;
+      if (total >= C->max_admm) { status = ABIP_MAX_ITER; break; }
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      C->tau = tau; C->kappa = kappa; C->theta = theta; C->mu = mu;
+      C->admm_iters = total; C->cg_iters = cgtot; C->outer_iters = outer; C->status = status;
+      C->pres = pres; C->dres = dres; C->dgap = dgap; C->ctx = ctx; C->bty = bty; C->inner2 = inner2;
+    }
+  }
+};
+
+template <typename T, typename V>
+__global__ void __launch_bounds__(kGridThreads, kMinBlocks) grid_kernel(GridData<T> d) {
+  __shared__ double red[32 * 12];
+  Solver<T, V> S(d, red);
+  if (d.ctl->mode == MODE_SETUP) S.setup();
+  else S.solve();
+}
+
+template <typename T, typename V>
+cudaError_t launch(const GridData<T>& d, int grid, cudaStream_t st) {
+  void* args[] = {const_cast<GridData<T>*>(&d)};
+  return cudaLaunchCooperativeKernel((const void*)grid_kernel<T, V>, dim3(grid), dim3(kGridThreads), args, 0, st);
+}
+
+template <typename T, typename V>
+int max_ctas(int device) {
+  int sms = 0, per = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, grid_kernel<T, V>, kGridThreads, 0);
+  return sms * per;
+}
+
+}  // namespace
+
+cudaError_t launch_grid_solver_f64(const GridData<double>& d, bool val_f64, int grid, cudaStream_t st) {
+  return val_f64 ? launch<double, double>(d, grid, st) : launch<double, float>(d, grid, st);
+}
+
+cudaError_t launch_grid_solver_f32(const GridData<float>& d, int grid, cudaStream_t st) {
+  return launch<float, float>(d, grid, st);
+}
+
+int grid_solver_max_ctas(bool mixed, bool val_f64, int device) {
+  if (mixed) return max_ctas<float, float>(device);
+  return val_f64 ? max_ctas<double, double>(device) : max_ctas<double, float>(device);
+}
+
+}  // namespace abip

@@ -1,0 +1,103 @@
+"""C-ABI checks that need no GPU: the library builds and loads, exports every symbol
+include/abip.h declares, and rejects bad arguments before touching the device."""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1805_12344_gb300 import build, abip
+    build.build()
+    return abip.lib()
+
+
+def declared_symbols():
+    src = open(os.path.join(ROOT, "include", "abip.h")).read()
+    return sorted(set(re.findall(r"ABIP_API\s+[\w\s\*]+?\b(abip_\w+)\s*\(", src)))
+
+
+def test_header_declares_the_boundary():
+    syms = declared_symbols()
+    for name in ("abip_setup", "abip_solve", "abip_solve_batch", "abip_backward", "abip_default_params",
+                 "abip_get_state", "abip_free", "abip_status_str", "abip_last_error"):
+        assert name in syms
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in declared_symbols():
+        assert hasattr(lib, name), name
+
+
+def test_default_params(lib):
+    from paper_1805_12344_gb300 import abip
+    p = abip.default_params()
+    assert p.beta == 1.0 and p.alpha == 1.8 and p.eps == 1e-6 and p.max_admm_iters == 10 ** 6
+    assert 0 < p.gamma < 1
+    assert lib.abip_default_params(None) == abip.ABIP_E_INVALID_ARG
+
+
+def test_struct_layout_matches_header():
+    """ctypes mirrors of the C structs have the sizes the C compiler gives them."""
+    from paper_1805_12344_gb300 import abip
+    code = r'''
+#include <stdio.h>
+#include "abip.h"
+int main(void){printf("%zu %zu %zu\n", sizeof(abip_matrix), sizeof(abip_params), sizeof(abip_info));return 0;}
+'''
+    import subprocess, tempfile
+    with tempfile.TemporaryDirectory() as d:
+        src = os.path.join(d, "t.c")
+        open(src, "w").write(code)
+        exe = os.path.join(d, "t")
+        subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), src, "-o", exe])
+        sizes = [int(v) for v in subprocess.check_output([exe]).split()]
+    assert sizes == [C.sizeof(abip.abip_matrix), C.sizeof(abip.abip_params), C.sizeof(abip.abip_info)]
+
+
+def test_status_strings(lib):
+    assert lib.abip_status_str(1) == b"optimal"
+    assert lib.abip_status_str(2) == b"primal_infeasible"
+    assert lib.abip_status_str(3) == b"dual_infeasible"
+    assert lib.abip_status_str(4) == b"max_iter"
+    assert lib.abip_version().startswith(b"abip")
+
+
+def test_argument_errors_without_device(lib):
+    from paper_1805_12344_gb300 import abip
+    A = np.ones((2, 3))
+    b = np.ones(2)
+    c = np.ones(3)
+    # NULL output handle
+    M, keep = abip._matrix(A)
+    assert lib.abip_setup(C.byref(M), b.ctypes.data, c.ctypes.data, None, None) == abip.ABIP_E_INVALID_ARG
+    # n < m
+    with pytest.raises(abip.AbipError) as e:
+        abip.abip_setup(np.ones((3, 2)), np.ones(3), np.ones(2))
+    assert e.value.code == abip.ABIP_E_DIM
+    # non-finite data
+    with pytest.raises(abip.AbipError) as e:
+        abip.abip_setup(A, np.array([1.0, np.nan]), c)
+    assert e.value.code == abip.ABIP_E_INVALID_ARG
+    # bad parameters
+    with pytest.raises(abip.AbipError) as e:
+        abip.abip_setup(A, b, c, abip.default_params(gamma=1.5))
+    assert e.value.code == abip.ABIP_E_INVALID_ARG
+    with pytest.raises(abip.AbipError) as e:
+        abip.abip_setup(A, b, c, abip.default_params(alpha=2.5))
+    assert e.value.code == abip.ABIP_E_INVALID_ARG
+    assert b"gamma" in lib.abip_last_error(None) or b"alpha" in lib.abip_last_error(None)
+    # malformed CSR
+    from paper_1805_12344_gb300 import workloads as W
+    bad = W.CSR(m=2, n=3, row_ptr=np.array([0, 2, 1], np.int64), col_idx=np.array([0, 1], np.int32),
+                val=np.ones(2))
+    with pytest.raises(abip.AbipError) as e:
+        abip.abip_setup(bad, b, c)
+    assert e.value.code in (abip.ABIP_E_DIM, abip.ABIP_E_CUDA)
+    # empty batch is a no-op
+    assert lib.abip_solve_batch(0, None, None, None, None, None, None, None, None, None) == 0
