@@ -46,8 +46,8 @@ def parse():
     ap.add_argument("--precision", default="mixed", choices=["mixed", "f64"])
     ap.add_argument("--m", type=int, default=100000, help="rows of A (default: the full workload)")
     ap.add_argument("--max-admm", type=int, default=1_000_000)
-    ap.add_argument("--cg-tol", type=float, default=1e-10)
-    ap.add_argument("--cg-rel", type=float, default=0.1)
+    ap.add_argument("--cg-tol", type=float, default=1e-8)
+    ap.add_argument("--cg-rel", type=float, default=0.0)
     ap.add_argument("--cpu-sample-s", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -162,6 +162,7 @@ def cpu_sample_main(args):
     P = O.Problem(A, lp.b, lp.c)
     lin = O.make_linsys(P, prm)
     proj = O.Projection(P, lin)
+    proj.cg_warm = prm.cg_warm
     setup_s = time.perf_counter() - t0
     st = O.initial_state(P)
     mu = prm.beta

@@ -73,6 +73,7 @@ class Params:
     linsys: int = 0              # 0 dense Cholesky of G, 1 Jacobi-PCG on G
     cg_tol: float = 1e-13        # reading A10: ||r|| <= cg_tol * max(1, ||rhs||)
     cg_max_iter: int = 10000
+    cg_warm: int = 1             # PCG start: 0 previous z_y, 1 linear extrapolation 2 z_k - z_{k-1} (reading A10)
     warmstart: int = 0           # 0 keep-larger heuristic (Sec. 5), 1 sqrt(gamma) (Eq. update-next-iterate)
     stop_rule: int = 0           # 0 Sec. 4.1 tests, 1 stop once mu < eps (outer-count check of Thm 3.6)
 
@@ -289,10 +290,22 @@ class Projection:
         S = np.array([[0.0, P.zbar], [-P.zbar, 0.0]])
         self.K = np.eye(2) + S + HtG
         self.zy_prev = np.zeros(P.m)
+        self.zy_prev2 = np.zeros(P.m)
+        self.solves = 0
+        self.cg_warm = 0
+
+    def start_point(self):
+        """Initial guess of the iterative M-solve (reading A10): the previous z_y, or with
+        cg_warm = 1 and two previous solves the linear extrapolation 2 z_k - z_{k-1}."""
+        if self.cg_warm == 1 and self.solves >= 2:
+            return 2.0 * self.zy_prev - self.zy_prev2
+        return self.zy_prev
 
     def __call__(self, wy, wx, wt, wth):
-        zy, zx = solve_M(self.P, self.lin, wy, wx, self.zy_prev)
+        zy, zx = solve_M(self.P, self.lin, wy, wx, self.start_point())
+        self.zy_prev2 = self.zy_prev
         self.zy_prev = zy
+        self.solves += 1
         Hz = np.array([self.h1y @ zy + self.h1x @ zx, self.h2y @ zy + self.h2x @ zx])
         t = np.linalg.solve(self.K, np.array([wt, wth]) + Hz)
         uy = zy - self.g1y * t[0] - self.g2y * t[1]
@@ -439,6 +452,7 @@ def solve(A, b, c, prm: Optional[Params] = None, trace_iters: int = 0,
     P = Problem(A, b, c)
     lin = make_linsys(P, prm)
     proj = Projection(P, lin)
+    proj.cg_warm = prm.cg_warm
     nb = float(np.linalg.norm(P.b))
     nc = float(np.linalg.norm(P.c))
     st = initial_state(P)
@@ -500,6 +514,7 @@ def run_iterations(A, b, c, k: int, prm: Optional[Params] = None) -> np.ndarray:
     prm = prm or Params()
     P = Problem(A, b, c)
     proj = Projection(P, make_linsys(P, prm))
+    proj.cg_warm = prm.cg_warm
     st = initial_state(P)
     mu = prm.beta
     done = 0

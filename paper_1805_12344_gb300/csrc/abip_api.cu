@@ -4,6 +4,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -123,6 +124,7 @@ int check_params(const abip_params& p, std::string& why) {
   if (p.precision != ABIP_PREC_F64 && p.precision != ABIP_PREC_MIXED) { why = "unknown precision"; return 0; }
   if (p.linsys != ABIP_LINSYS_DENSE_CHOL && p.linsys != ABIP_LINSYS_PCG && p.linsys != -1) { why = "unknown linsys"; return 0; }
   if (p.warmstart != 0 && p.warmstart != 1) { why = "warmstart must be 0 or 1"; return 0; }
+  if (p.cg_warm != 0 && p.cg_warm != 1) { why = "cg_warm must be 0 or 1"; return 0; }
   if (p.stop_rule != 0 && p.stop_rule != 1) { why = "stop_rule must be 0 or 1"; return 0; }
   return 1;
 }
@@ -220,8 +222,9 @@ void assign_vectors(GridData<T>& g, Arena& ar, int m, int n) {
   g.g1y = ar.take<T>(m); g.g1x = ar.take<T>(n); g.g2y = ar.take<T>(m); g.g2x = ar.take<T>(n);
   g.y = ar.take<T>(m); g.x = ar.take<T>(n); g.s = ar.take<T>(n);
   g.Ax = ar.take<T>(m); g.As = ar.take<T>(m); g.ATy = ar.take<T>(n);
-  g.zy = ar.take<T>(m); g.zx = ar.take<T>(n);
-  g.r = ar.take<T>(m); g.p = ar.take<T>(m); g.zr = ar.take<T>(m); g.t = ar.take<T>(n); g.Gp = ar.take<T>(m);
+  g.zy = ar.take<T>(m); g.zx = ar.take<T>(n); g.zp2 = ar.take<T>(m);
+  g.r = ar.take<T>(m); g.p = ar.take<T>(m); g.zr = ar.take<T>(m); g.zr2 = ar.take<T>(m);
+  g.t = ar.take<T>(n); g.u = ar.take<T>(n); g.Gp = ar.take<T>(m); g.dGp = ar.take<T>(m);
 }
 
 template <typename T>
@@ -302,6 +305,7 @@ int setup_grid_path(abip_handle* h, const HostCSR& A, const std::vector<double>&
   hc.beta = h->prm.beta; hc.gamma = h->prm.gamma; hc.alpha = h->prm.alpha; hc.eps = h->prm.eps;
   hc.cg_tol = h->prm.cg_tol; hc.cg_rel = h->prm.cg_rel; hc.cg_max = h->prm.cg_max_iter; hc.max_admm = h->prm.max_admm_iters;
   hc.warmstart = h->prm.warmstart; hc.stop_rule = h->prm.stop_rule; hc.check_every = h->prm.check_every;
+  hc.cg_warm = h->prm.cg_warm;
   hc.mode = abip::MODE_SETUP;
   cudaMemcpy(h->ctl, &hc, sizeof(hc), cudaMemcpyHostToDevice);
   cudaError_t e = cudaGetLastError();
@@ -335,6 +339,7 @@ int solve_grid_path(abip_handle* h, cudaStream_t st) {
   fill_kernel<T><<<256, 256, 0, st>>>(g.x, n, T(1));
   fill_kernel<T><<<256, 256, 0, st>>>(g.s, n, T(1));
   fill_kernel<T><<<64, 256, 0, st>>>(g.zy, m, T(0));
+  fill_kernel<T><<<64, 256, 0, st>>>(g.zp2, m, T(0));
   SolveCtl hc;
   cudaMemcpyAsync(&hc, h->ctl, sizeof(hc), cudaMemcpyDeviceToHost, st);
   cudaStreamSynchronize(st);
@@ -343,6 +348,15 @@ int solve_grid_path(abip_handle* h, cudaStream_t st) {
   hc.mu = h->prm.beta;
   hc.admm_iters = 0; hc.cg_iters = 0; hc.outer_iters = 0; hc.status = 0; hc.err = 0;
   hc.max_admm = h->prm.max_admm_iters;
+  // ABIP_PROFILE=1: phase timers of CTA 0, printed to stderr after the solve
+  const char* prof_env = std::getenv("ABIP_PROFILE");
+  unsigned long long* prof = nullptr;
+  if (prof_env && prof_env[0] == '1') {
+    if (cudaMalloc(&prof, abip::kProfBuckets * sizeof(unsigned long long)) == cudaSuccess)
+      cudaMemsetAsync(prof, 0, abip::kProfBuckets * sizeof(unsigned long long), st);
+    else { cudaGetLastError(); prof = nullptr; }
+  }
+  hc.prof = prof;
   cudaMemcpyAsync(h->ctl, &hc, sizeof(hc), cudaMemcpyHostToDevice, st);
   cudaMemsetAsync(g.bar, 0, sizeof(unsigned long long), st);
   cudaEventRecord(h->ev0, st);
@@ -356,7 +370,19 @@ int solve_grid_path(abip_handle* h, cudaStream_t st) {
   float ms = 0.f;
   cudaEventElapsedTime(&ms, h->ev0, h->ev1);
   h->kernel_s = ms * 1e-3;
-  h->launches = 5;   // four fills and the persistent solve kernel
+  h->launches = 6;   // five fills and the persistent solve kernel
+  if (prof) {
+    unsigned long long pv[abip::kProfBuckets];
+    cudaMemcpy(pv, prof, sizeof(pv), cudaMemcpyDeviceToHost);
+    cudaFree(prof);
+    const char* names[abip::kProfBuckets] = {"pcg_init", "cg_AT", "cg_A", "cg_upd", "zx", "upd", "res",
+                                             "warm", "barrier", "totals", "setup"};
+    std::fprintf(stderr, "[abip profile] kernel %.3f ms:", ms);
+    for (int b = 0; b < abip::kProfBuckets; ++b) std::fprintf(stderr, " %s=%.3f", names[b], pv[b] * 1e-6);
+    std::fprintf(stderr, " (ms, CTA 0)\n");
+    unsigned long long* none = nullptr;
+    cudaMemcpy(&h->ctl->prof, &none, sizeof(none), cudaMemcpyHostToDevice);
+  }
   return ABIP_OK;
 }
 
@@ -562,6 +588,7 @@ int abip_default_params(abip_params* p) {
   p->linsys = -1;   // automatic
   p->cg_tol = 1e-10;
   p->cg_rel = 0.0;
+  p->cg_warm = 1;
   p->cg_max_iter = 1000;
   p->precision = ABIP_PREC_F64;
   p->warmstart = 0;

@@ -67,6 +67,7 @@ __device__ __forceinline__ bool grid_sync(const GridBarrier& gb, unsigned long l
       const unsigned long long t0 = globaltimer_ns();
       unsigned spins = 0;
       while (ld_acquire_u64(gb.count) < target) {
+        __nanosleep(32);
         if (ld_relaxed_i32(gb.err) != 0) { ok = 0; break; }
         if ((++spins & 63u) == 0 && globaltimer_ns() - t0 > kBarrierLimitNs) {
           atomicCAS(gb.err, 0, (int)DEV_ERR_BARRIER_TIMEOUT);

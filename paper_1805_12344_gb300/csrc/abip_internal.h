@@ -12,7 +12,7 @@
 
 namespace abip {
 
-constexpr int kGridThreads = 256;   // threads per CTA of the persistent grid kernel
+constexpr int kGridThreads = 768;   // threads per CTA of the persistent grid kernel (one CTA per SM)
 constexpr int kNumSlots = 24;       // reduction slots of the grid kernel
 
 enum GridMode : int { MODE_SETUP = 0, MODE_SOLVE = 1 };
@@ -26,6 +26,7 @@ struct SolveCtl {
   double Kinv[4];                 // inverse of the 2x2 Schur complement, row-major
   int64_t max_admm;
   int32_t cg_max, warmstart, stop_rule, mode;
+  int32_t cg_warm, pad2;
   int32_t check_every, pad0;
   // state carried across calls (in/out)
   double tau, kappa, theta, mu;
@@ -37,6 +38,13 @@ struct SolveCtl {
   double sum_c, sum_b2, sum_c2;   // MODE_SETUP: c^T e, ||b||^2, ||c||^2
   int32_t err;                    // DevErr
   int32_t pad1;
+  unsigned long long* prof;       // optional phase timers (kProfBuckets ns counters), null = off
+};
+
+// phase timer buckets of the solve kernel (CTA 0's view, nanoseconds)
+enum ProfBucket : int {
+  P_PCG_INIT = 0, P_CG_AT, P_CG_A, P_CG_UPD, P_ZX, P_UPD, P_RES, P_WARM, P_BARRIER, P_TOTALS, P_SETUP,
+  kProfBuckets
 };
 
 // A sparse matrix in SELL-32 form: rows sorted by length (longest first), cut
@@ -64,7 +72,8 @@ struct GridData {
   T* y; T* x; T* s;                                           // iterate (r = 0, xi = -n-1 implicit)
   T* Ax; T* As; T* ATy;                                       // products for the residuals
   T* zy; T* zx;                                               // M^{-1} w (zy warm-starts PCG)
-  T* r; T* p; T* zr; T* t; T* Gp;                             // PCG work vectors
+  T* zp2;                                                     // previous zy (extrapolated start)
+  T* r; T* p; T* zr; T* zr2; T* t; T* u; T* Gp; T* dGp;       // PCG work vectors (zr double-buffered)
   double* partials;                                           // kNumSlots * gridDim doubles
   unsigned long long* bar;                                    // barrier arrival counter
   SolveCtl* ctl;

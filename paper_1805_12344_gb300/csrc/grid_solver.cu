@@ -33,7 +33,7 @@ enum Slot : int {
   S_K = 20,      // 4: H^T M^{-1} H
 };
 
-constexpr int kMinBlocks = 3;   // resident CTAs per SM requested from the compiler
+constexpr int kMinBlocks = 1;   // resident CTAs per SM requested from the compiler
 
 struct Thr {
   int gtid, nthr, gw, nwarp, lane;
@@ -46,11 +46,11 @@ struct Thr {
   }
 };
 
-// Row products y_i = sum_k A_ik v_k (and a second vector) for every row of a
-// SELL-32 matrix; epi(row, dot0, dot1) runs on the row's thread.
-template <int U, int NV, typename T, typename V, typename Epi>
-__device__ __forceinline__ void sell_rows(const SellMat& S, const T* __restrict__ v0, const T* __restrict__ v1,
-                                          Epi& epi) {
+// Row products for every row of a SELL-32 matrix: dot0 = sum_k A_ik g0(k),
+// dot1 = sum_k A_ik g1(k) (NV = 2), accumulated in Acc; epi(row, dot0, dot1)
+// runs on the row's thread.  g0/g1 map a column index to the gathered value.
+template <int U, int NV, typename Acc, typename V, typename G0, typename G1, typename Epi>
+__device__ __forceinline__ void sell_rows_g(const SellMat& S, G0& g0, G1& g1, Epi& epi) {
   const Thr th;
   const V* __restrict__ val = static_cast<const V*>(S.val);
   for (int sl = th.gw; sl < S.nslices; sl += th.nwarp) {
@@ -59,27 +59,27 @@ __device__ __forceinline__ void sell_rows(const SellMat& S, const T* __restrict_
     const int row = __ldg(S.perm + sl * 32 + th.lane);
     const int32_t* __restrict__ ci = S.ci + base + th.lane;
     const V* __restrict__ va = val + base + th.lane;
-    T a0 = T(0), a1 = T(0);
+    Acc a0 = Acc(0), a1 = Acc(0);
     int k = 0;
     for (; k + U <= w; k += U) {
       int j[U];
-      T a[U];
+      Acc a[U];
 #pragma unroll
       for (int u = 0; u < U; ++u) {
         j[u] = __ldg(ci + (k + u) * 32);
-        a[u] = static_cast<T>(__ldg(va + (k + u) * 32));
+        a[u] = static_cast<Acc>(__ldg(va + (k + u) * 32));
       }
 #pragma unroll
       for (int u = 0; u < U; ++u) {
-        a0 += a[u] * v0[j[u]];
-        if (NV == 2) a1 += a[u] * v1[j[u]];
+        a0 += a[u] * static_cast<Acc>(g0(j[u]));
+        if (NV == 2) a1 += a[u] * static_cast<Acc>(g1(j[u]));
       }
     }
     for (; k < w; ++k) {
       const int j = __ldg(ci + k * 32);
-      const T a = static_cast<T>(__ldg(va + k * 32));
-      a0 += a * v0[j];
-      if (NV == 2) a1 += a * v1[j];
+      const Acc a = static_cast<Acc>(__ldg(va + k * 32));
+      a0 += a * static_cast<Acc>(g0(j));
+      if (NV == 2) a1 += a * static_cast<Acc>(g1(j));
     }
     if (row >= 0) epi(row, a0, a1);
   }
@@ -111,16 +111,57 @@ struct Solver {
   double* red;   // shared scratch
   Thr th;
   unsigned long long bar_target = 0;
-  __device__ Solver(const GridData<T>& d, double* r) : D(d), C(d.ctl), red(r) {}
+  unsigned long long* prof;
+  unsigned long long t_last = 0;
+  __device__ Solver(const GridData<T>& d, double* r) : D(d), C(d.ctl), red(r) {
+    prof = (blockIdx.x == 0 && threadIdx.x == 0) ? d.ctl->prof : nullptr;
+    if (prof) t_last = globaltimer_ns();
+  }
 
-  __device__ bool sync() { return grid_sync(GridBarrier{D.bar, &C->err}, bar_target); }
+  // phase timer: charge the time since the previous mark to bucket b (CTA 0, thread 0)
+  __device__ __forceinline__ void mark(int b) {
+    if (prof) {
+      const unsigned long long t = globaltimer_ns();
+      prof[b] += t - t_last;
+      t_last = t;
+    }
+  }
 
+  __device__ bool sync(int phase) {
+    mark(phase);
+    const bool ok = grid_sync(GridBarrier{D.bar, &C->err}, bar_target);
+    mark(P_BARRIER);
+    return ok;
+  }
+  template <int K>
+  __device__ void totals(double (&out)[K], int slot) {
+    grid_total<K>(out, D.partials, slot, red);
+    mark(P_TOTALS);
+  }
+
+  // A v, A^T v with the iteration type T; the residual products use double
+  // accumulation (exact products of float data, summed in FP64)
   template <typename Epi>
-  __device__ void rowsA(const T* v0, Epi& e) { sell_rows<8, 1, T, V>(D.A, v0, v0, e); }
+  __device__ void rowsA(const T* v0, Epi& e) {
+    auto g = [&](int j) { return v0[j]; };
+    sell_rows_g<8, 1, T, V>(D.A, g, g, e);
+  }
   template <typename Epi>
-  __device__ void rowsA2(const T* v0, const T* v1, Epi& e) { sell_rows<8, 2, T, V>(D.A, v0, v1, e); }
+  __device__ void rowsAT(const T* v0, Epi& e) {
+    auto g = [&](int j) { return v0[j]; };
+    sell_rows_g<8, 1, T, V>(D.AT, g, g, e);
+  }
   template <typename Epi>
-  __device__ void rowsAT(const T* v0, Epi& e) { sell_rows<8, 1, T, V>(D.AT, v0, v0, e); }
+  __device__ void rowsA2_d(const T* v0, const T* v1, Epi& e) {
+    auto g0 = [&](int j) { return v0[j]; };
+    auto g1 = [&](int j) { return v1[j]; };
+    sell_rows_g<8, 2, double, V>(D.A, g0, g1, e);
+  }
+  template <typename Epi>
+  __device__ void rowsAT_d(const T* v0, Epi& e) {
+    auto g = [&](int j) { return v0[j]; };
+    sell_rows_g<8, 1, double, V>(D.AT, g, g, e);
+  }
 
   __device__ void flag(int code) {
     if (threadIdx.x == 0) atomicCAS(&C->err, 0, code);
@@ -128,24 +169,39 @@ struct Solver {
 
   // Jacobi-PCG on G = I + A A^T (Sec. 4.4): z (in: warm start, out: solution),
   // right-hand side q_i = qf(i).  Stop when ||r|| <= tol * max(1, ||q||) (reading
-  // A10).  Three grid barriers per iteration: the direction update p = zr + beta p
-  // is folded into t = A^T p = A^T zr + beta t and into the next A pass.
+  // A10).  Two phases and two grid barriers per iteration:
+  //   phase A (rows of A):   p = zr + beta p;  Gp = p + A (u + beta t);  p.Gp
+  //   phase B (rows of A^T): t <- u + beta t (= A^T p);  u <- A^T zr_new, gathering
+  //                          zr_new = zr - alpha D^{-1} Gp;  and for the rows of A
+  //                          z += alpha p, r -= alpha Gp, zr_new = D^{-1} r;  r.zr, r.r
+  // zr is double-buffered so phase B gathers the old values while writing the new.
   // Returns iterations, or -1 on barrier failure / -2 past the cap.
+  //
+  // Start point: z itself, or with `extrap` the linear extrapolation 2 z - zp2 from
+  // the two previous solutions (reading A10); when zp2 is given it receives the
+  // previous z.  The extrapolated start is gathered on the fly in the first A^T
+  // pass and stored by each row's owner in the first A pass.
   template <typename QF>
-  __device__ int pcg(T* z, QF qf, double tol, int maxit) {
-    T* r = D.r; T* p = D.p; T* zr = D.zr; T* t = D.t; T* Gp = D.Gp;
+  __device__ int pcg(T* z, QF qf, double tol, int maxit, bool extrap = false, T* zp2 = nullptr) {
+    T* r = D.r; T* p = D.p; T* t = D.t; T* u = D.u; T* Gp = D.Gp; T* dGp = D.dGp;
+    T* zr_cur = D.zr;
+    T* zr_nxt = D.zr2;
     {
+      auto g = [&](int i) -> T { return extrap ? T(2) * z[i] - zp2[i] : z[i]; };
       auto e = [&](int j, T v, T) { t[j] = v; };
-      rowsAT(z, e);
+      sell_rows_g<8, 1, T, V>(D.AT, g, g, e);
     }
-    if (!sync()) return -1;
+    if (!sync(P_PCG_INIT)) return -1;
     double acc[3] = {0.0, 0.0, 0.0};
     {
       auto e = [&](int i, T v, T) {
         const T qi = qf(i);
-        const T ri = qi - (z[i] + v);
+        const T zi = extrap ? T(2) * z[i] - zp2[i] : z[i];
+        if (zp2) zp2[i] = z[i];
+        z[i] = zi;
+        const T ri = qi - (zi + v);
         const T zri = D.dinv[i] * ri;
-        r[i] = ri; zr[i] = zri;
+        r[i] = ri; zr_cur[i] = zri;
         acc[0] += (double)ri * (double)zri;
         acc[1] += (double)ri * (double)ri;
         acc[2] += (double)qi * (double)qi;
@@ -153,55 +209,69 @@ struct Solver {
       rowsA(t, e);
     }
     grid_partial<3>(acc, D.partials, S_PCG0, red);
-    if (!sync()) return -1;
+    if (!sync(P_PCG_INIT)) return -1;
     double tot[3];
-    grid_total<3>(tot, D.partials, S_PCG0, red);
+    totals<3>(tot, S_PCG0);
     double rz = tot[0], rr = tot[1];
     const double bound = tol * fmax(1.0, sqrt(tot[2]));
+    if (!(sqrt(rr) > bound)) return 0;
+    // u = A^T zr (so that A^T p_0 = u with p_0 = zr)
+    {
+      auto e = [&](int j, T v, T) { u[j] = v; };
+      rowsAT(zr_cur, e);
+    }
+    if (!sync(P_PCG_INIT)) return -1;
     T be = T(0);
     int k = 0;
-    while (sqrt(rr) > bound) {
+    for (;;) {
       if (k >= maxit) return -2;
       const bool first = k == 0;
-      {
-        // t = A^T p with p = zr + be * p_old  (t holds A^T p_old)
-        auto e = [&](int j, T v, T) { t[j] = first ? v : v + be * t[j]; };
-        rowsAT(zr, e);
-      }
-      if (!sync()) return -1;
       double a1[1] = {0.0};
       {
+        auto g = [&](int j) -> T { return first ? u[j] : u[j] + be * t[j]; };
         auto e = [&](int i, T v, T) {
-          const T pi = first ? zr[i] : zr[i] + be * p[i];
+          const T pi = first ? zr_cur[i] : zr_cur[i] + be * p[i];
           const T gp = pi + v;
           p[i] = pi;
           Gp[i] = gp;
+          dGp[i] = D.dinv[i] * gp;
           a1[0] += (double)pi * (double)gp;
         };
-        rowsA(t, e);
+        sell_rows_g<8, 1, T, V>(D.A, g, g, e);
       }
       grid_partial<1>(a1, D.partials, S_PGP, red);
-      if (!sync()) return -1;
+      if (!sync(P_CG_A)) return -1;
       double pgp[1];
-      grid_total<1>(pgp, D.partials, S_PGP, red);
+      totals<1>(pgp, S_PGP);
       const T al = (T)(rz / pgp[0]);
+      {
+        auto g = [&](int i) -> T { return zr_cur[i] - al * dGp[i]; };
+        auto e = [&](int j, T v, T) {
+          t[j] = first ? u[j] : u[j] + be * t[j];
+          u[j] = v;
+        };
+        sell_rows_g<8, 1, T, V>(D.AT, g, g, e);
+      }
+      mark(P_CG_AT);
       double a2[2] = {0.0, 0.0};
       for (int i = th.gtid; i < D.m; i += th.nthr) {
         z[i] += al * p[i];
         const T ri = r[i] - al * Gp[i];
         const T zri = D.dinv[i] * ri;
-        r[i] = ri; zr[i] = zri;
+        r[i] = ri; zr_nxt[i] = zri;
         a2[0] += (double)ri * (double)zri;
         a2[1] += (double)ri * (double)ri;
       }
       grid_partial<2>(a2, D.partials, S_RZ, red);
-      if (!sync()) return -1;
+      if (!sync(P_CG_UPD)) return -1;
       double t2[2];
-      grid_total<2>(t2, D.partials, S_RZ, red);
+      totals<2>(t2, S_RZ);
       be = (T)(t2[0] / rz);
       rz = t2[0];
       rr = t2[1];
+      T* sw = zr_cur; zr_cur = zr_nxt; zr_nxt = sw;
       ++k;
+      if (!(sqrt(rr) > bound)) break;
     }
     return k;
   }
@@ -217,9 +287,9 @@ struct Solver {
   __device__ bool residuals(double tau, double theta, double (&tot)[9]) {
     double acc[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
     {
-      auto e = [&](int i, T ax, T as) {
-        D.Ax[i] = ax; D.As[i] = as;
-        const double axd = (double)ax;
+      auto e = [&](int i, double ax, double as) {
+        D.Ax[i] = (T)ax; D.As[i] = (T)as;
+        const double axd = ax;
         const double bi = (double)D.b[i];
         const double ry = axd - bi * tau + (double)D.bbar[i] * theta;
         const double pr = axd / tau - bi;
@@ -230,12 +300,12 @@ struct Solver {
         acc[5] += bi * yi;
         acc[6] += (double)D.bbar[i] * yi;
       };
-      rowsA2(D.x, D.s, e);
+      rowsA2_d(D.x, D.s, e);
     }
     {
-      auto e = [&](int j, T aty, T) {
-        D.ATy[j] = aty;
-        const double atyd = (double)aty, sj = (double)D.s[j], cj = (double)D.c[j];
+      auto e = [&](int j, double aty, double) {
+        D.ATy[j] = (T)aty;
+        const double atyd = aty, sj = (double)D.s[j], cj = (double)D.c[j];
         const double rx = -atyd + cj * tau - (double)D.cbar[j] * theta - sj;
         const double dr = (atyd + sj) / tau - cj;
         const double xj = (double)D.x[j];
@@ -245,11 +315,11 @@ struct Solver {
         acc[7] += cj * xj;
         acc[8] += (double)D.cbar[j] * xj;
       };
-      rowsAT(D.y, e);
+      rowsAT_d(D.y, e);
     }
     grid_partial<9>(acc, D.partials, S_RES, red);
-    if (!sync()) return false;
-    grid_total<9>(tot, D.partials, S_RES, red);
+    if (!sync(P_RES)) return false;
+    totals<9>(tot, S_RES);
     return true;
   }
 
@@ -273,31 +343,31 @@ struct Solver {
       acc[2] += (double)D.c[j] * (double)D.c[j];
     }
     grid_partial<3>(acc, D.partials, S_SETUP, red);
-    if (!sync()) return;
+    if (!sync(P_SETUP)) return;
     double tot[3];
-    grid_total<3>(tot, D.partials, S_SETUP, red);
+    totals<3>(tot, S_SETUP);
     // two solves with M: a = h_y, d = h_x  ->  zy = G^{-1}(a - A d), zx = d + A^T zy
     for (int col = 0; col < 2; ++col) {
       T* gy = col == 0 ? D.g1y : D.g2y;
       T* gx = col == 0 ? D.g1x : D.g2x;
       for (int j = t.gtid; j < D.n; j += t.nthr) gx[j] = col == 0 ? D.c[j] : -D.cbar[j];
       for (int i = t.gtid; i < D.m; i += t.nthr) gy[i] = T(0);
-      if (!sync()) return;
+      if (!sync(P_SETUP)) return;
       {
         auto e = [&](int i, T v, T) { D.Ax[i] = v; };
         rowsA(gx, e);
       }
-      if (!sync()) return;
+      if (!sync(P_SETUP)) return;
       const int c0 = col;
       auto qf = [&](int i) -> T { return (c0 == 0 ? -D.b[i] : D.bbar[i]) - D.Ax[i]; };
       const int it = pcg(gy, qf, C->cg_tol, C->cg_max);
       if (it == -1) return;
-      if (it == -2) { flag(DEV_ERR_PCG); sync(); return; }
+      if (it == -2) { flag(DEV_ERR_PCG); sync(P_SETUP); return; }
       {
         auto e = [&](int j, T v, T) { gx[j] = gx[j] + v; };
         rowsAT(gy, e);
       }
-      if (!sync()) return;
+      if (!sync(P_SETUP)) return;
     }
     // H^T M^{-1} H:  h1.g1, h1.g2, h2.g1, h2.g2
     double k4[4] = {0.0, 0.0, 0.0, 0.0};
@@ -310,9 +380,9 @@ struct Solver {
       k4[0] += cj * g1; k4[1] += cj * g2; k4[2] += -cbj * g1; k4[3] += -cbj * g2;
     }
     grid_partial<4>(k4, D.partials, S_K, red);
-    if (!sync()) return;
+    if (!sync(P_SETUP)) return;
     double kt[4];
-    grid_total<4>(kt, D.partials, S_K, red);
+    totals<4>(kt, S_K);
     if (blockIdx.x == 0 && threadIdx.x == 0) {
       C->sum_c = tot[0]; C->sum_b2 = tot[1]; C->sum_c2 = tot[2];
       C->K[0] = 1.0 + kt[0];
@@ -382,7 +452,7 @@ struct Solver {
         }
         for (int i = t.gtid; i < D.m; i += t.nthr) D.y[i] *= sg;
         theta *= sqrt(gamma);
-        if (!sync()) return;
+        if (!sync(P_WARM)) return;
         if (!evaluate(false)) return;
         continue;
       }
@@ -395,9 +465,9 @@ struct Solver {
       // relative KKT residual, never below cg_tol (reading A10, performance mode)
       const double kkt = fmax(pres, fmax(dres, dgap));
       const double tol = cg_rel > 0.0 ? fmax(C->cg_tol, cg_rel * kkt) : C->cg_tol;
-      const int it = pcg(D.zy, qf, tol, C->cg_max);
+      const int it = pcg(D.zy, qf, tol, C->cg_max, C->cg_warm == 1 && total >= 2, D.zp2);
       if (it == -1) return;
-      if (it == -2) { flag(DEV_ERR_PCG); sync(); return; }
+      if (it == -2) { flag(DEV_ERR_PCG); sync(P_CG_UPD); return; }
       cgtot += it;
       double hz[2] = {0.0, 0.0};
       {
@@ -415,9 +485,9 @@ struct Solver {
         hz[1] += (double)D.bbar[i] * zyi;
       }
       grid_partial<2>(hz, D.partials, S_HZ, red);
-      if (!sync()) return;
+      if (!sync(P_ZX)) return;
       double h[2];
-      grid_total<2>(h, D.partials, S_HZ, red);
+      totals<2>(h, S_HZ);
       // t = K^{-1} (w_{tau,theta} + H^T z)
       const double v1 = tau + kappa + h[0], v2 = theta + xi + h[1];
       const double t1 = Ki0 * v1 + Ki1 * v2, t2 = Ki2 * v1 + Ki3 * v2;
@@ -441,7 +511,7 @@ struct Solver {
         tau = tn; kappa = kn;
         theta = alpha * t2 + (1.0 - alpha) * theta;
       }
-      if (!sync()) return;
+      if (!sync(P_UPD)) return;
       ++total;
       if (!evaluate(true)) return;
       if (status != 0) break;
