@@ -48,6 +48,8 @@ def parse():
     ap.add_argument("--max-admm", type=int, default=1_000_000)
     ap.add_argument("--cg-tol", type=float, default=1e-8)
     ap.add_argument("--cg-rel", type=float, default=0.0)
+    ap.add_argument("--alpha", type=float, default=1.8, help="over-relaxation (the paper's value is 1.8)")
+    ap.add_argument("--gamma", type=float, default=0.1)
     ap.add_argument("--cpu-sample-s", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -157,7 +159,7 @@ def cpu_sample_main(args):
     from paper_1805_12344_gb300 import workloads as W
     lp = W.planted_sparse(args.m)
     A = lp.A.to_scipy()
-    prm = O.Params(linsys=1, cg_tol=args.cg_tol)
+    prm = O.Params(linsys=1, cg_tol=args.cg_tol, alpha=args.alpha, gamma=args.gamma)
     t0 = time.perf_counter()
     P = O.Problem(A, lp.b, lp.c)
     lin = O.make_linsys(P, prm)
@@ -186,7 +188,8 @@ def cpu_sample_main(args):
 def run_cpu_sample(args, admm_iters_for_lp):
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
     cmd = [sys.executable, os.path.abspath(__file__), "--cpu-sample", "--m", str(args.m),
-           "--cpu-sample-s", str(args.cpu_sample_s), "--cg-tol", str(args.cg_tol)]
+           "--cpu-sample-s", str(args.cpu_sample_s), "--cg-tol", str(args.cg_tol),
+           "--alpha", str(args.alpha), "--gamma", str(args.gamma)]
     r = subprocess.run(cmd, capture_output=True, text=True, env=env, timeout=900)
     d = json.loads(r.stdout.strip().splitlines()[-1])
     lp_s = d["setup_s"] + d["s_per_admm_iter"] * admm_iters_for_lp
@@ -263,7 +266,8 @@ def main():
     lp = W.planted_sparse(args.m, seed=W.seed_for(W.SPARSE_PLANTED, rank))
     m, n, nnz = lp.m, lp.n, lp.A.nnz
     prm = abip.default_params(precision=abip.ABIP_PREC_MIXED if args.precision == "mixed" else abip.ABIP_PREC_F64,
-                              max_admm_iters=args.max_admm, cg_tol=args.cg_tol, cg_rel=args.cg_rel)
+                              max_admm_iters=args.max_admm, cg_tol=args.cg_tol, cg_rel=args.cg_rel,
+                              alpha=args.alpha, gamma=args.gamma)
     # inputs resident in HBM
     rp_d = torch.from_numpy(lp.A.row_ptr).to(dev)
     ci_d = torch.from_numpy(lp.A.col_idx).to(dev)

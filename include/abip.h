@@ -183,6 +183,15 @@ ABIP_API int abip_backward(abip_handle* h, const double* dl_dx,
  */
 ABIP_API int abip_get_state(const abip_handle* h, double* buf);
 
+/*
+ * Load a raw iterate (same layout as abip_get_state: y[m], x[n], tau, theta, s[n],
+ * kappa, mu; host or device) into h.  The next abip_solve starts from it instead
+ * of Algorithm 2's start (resume or warm start); the solve after that starts
+ * from Algorithm 2's start again.  x, s, tau, kappa and mu must be > 0 and all
+ * entries finite, else ABIP_E_INVALID_ARG.
+ */
+ABIP_API int abip_set_state(abip_handle* h, const double* buf);
+
 /* Number of doubles abip_get_state writes (m + 2n + 4). */
 ABIP_API int64_t abip_state_size(const abip_handle* h);
 

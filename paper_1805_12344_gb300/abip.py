@@ -94,6 +94,7 @@ _SIGS = {
                                    C.c_void_p]),
     "abip_backward": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "abip_get_state": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "abip_set_state": (C.c_int, [C.c_void_p, C.c_void_p]),
     "abip_state_size": (C.c_int64, [C.c_void_p]),
     "abip_free": (None, [C.c_void_p]),
     "abip_status_str": (C.c_char_p, [C.c_int32]),
@@ -219,6 +220,11 @@ def abip_get_state(h) -> np.ndarray:
     return buf
 
 
+def abip_set_state(h, state):
+    buf = np.ascontiguousarray(state, dtype=np.float64)
+    _check(lib().abip_set_state(h, buf.ctypes.data), h)
+
+
 def abip_free(h):
     lib().abip_free(h)
 
@@ -285,6 +291,9 @@ class Solver:
 
     def state(self) -> np.ndarray:
         return abip_get_state(self.h)
+
+    def set_state(self, state) -> None:
+        abip_set_state(self.h, state)
 
     def stacked_state(self) -> np.ndarray:
         """(y, x, tau, theta, s, kappa): the iterate ordering of the parity tests."""

@@ -161,33 +161,61 @@ HostCSR transpose(const HostCSR& A) {
   return T;
 }
 
-// SELL-32 form of a CSR matrix: rows sorted by length (longest first, ties in row
-// order), slices of 32 sorted rows stored column-major and padded to the slice's
-// longest row; padding entries hold value 0 and a column the row already uses
-// (or column 0), so every gather stays in range.
+// SELL form of a CSR matrix with L lanes per row (see SellMat): rows sorted by
+// length (longest first, ties in row order), slices of C = 32/L sorted rows;
+// within a slice, lane r*L + q holds entries q, q+L, q+2L, ... of row r, stored
+// chunk-major and padded to the slice's longest lane with value 0 and a column the
+// row already uses (or column 0), so every gather stays in range.
 struct HostSell {
-  int rows = 0, nslices = 0;
+  int rows = 0, nslices = 0, lanes = 1;
   std::vector<int64_t> sp;
   std::vector<int32_t> ci;
   std::vector<double> v;
   std::vector<int32_t> perm;
 };
 
-HostSell to_sell(const HostCSR& M) {
+// Contiguous slice ranges per global warp with about equal work (slice width + 2).
+std::vector<int32_t> warp_partition(const HostSell& S, int nwarp) {
+  std::vector<int32_t> w(nwarp + 1, 0);
+  double total = 0;
+  for (int sl = 0; sl < S.nslices; ++sl) total += (double)((S.sp[sl + 1] - S.sp[sl]) / 32) + 2.0;
+  const double per = total / nwarp;
+  double acc = 0;
+  int k = 1;
+  for (int sl = 0; sl < S.nslices; ++sl) {
+    acc += (double)((S.sp[sl + 1] - S.sp[sl]) / 32) + 2.0;
+    while (k < nwarp && acc >= per * k - 1e-9) w[k++] = sl + 1;
+  }
+  while (k <= nwarp) w[k++] = S.nslices;
+  return w;
+}
+
+// lanes per row: the smallest power of two that leaves about 8 entries per lane
+int sell_lanes(const HostCSR& M) {
+  const double mean = M.m > 0 ? (double)M.rp[M.m] / M.m : 0.0;
+  int L = 1;
+  while (L < 32 && mean > 8.0 * L) L *= 2;
+  return L;
+}
+
+HostSell to_sell(const HostCSR& M, int L) {
   HostSell S;
   S.rows = M.m;
-  S.nslices = (M.m + 31) / 32;
+  S.lanes = L;
+  const int C = 32 / L;
+  S.nslices = (M.m + C - 1) / C;
   std::vector<int32_t> order(M.m);
   for (int i = 0; i < M.m; ++i) order[i] = i;
   std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) {
     return (M.rp[a + 1] - M.rp[a]) > (M.rp[b + 1] - M.rp[b]);
   });
-  S.perm.assign((size_t)S.nslices * 32, -1);
+  S.perm.assign((size_t)S.nslices * C, -1);
   for (int p = 0; p < M.m; ++p) S.perm[p] = order[p];
   S.sp.assign(S.nslices + 1, 0);
   for (int sl = 0; sl < S.nslices; ++sl) {
-    const int r0 = order[(size_t)sl * 32];
-    const int64_t w = M.rp[r0 + 1] - M.rp[r0];
+    const int r0 = order[(size_t)sl * C];
+    const int64_t len = M.rp[r0 + 1] - M.rp[r0];
+    const int64_t w = (len + L - 1) / L;          // chunks per lane
     S.sp[sl + 1] = S.sp[sl] + 32 * w;
   }
   S.ci.assign(S.sp[S.nslices], 0);
@@ -195,18 +223,21 @@ HostSell to_sell(const HostCSR& M) {
   for (int sl = 0; sl < S.nslices; ++sl) {
     const int64_t base = S.sp[sl];
     const int64_t w = (S.sp[sl + 1] - base) / 32;
-    for (int r = 0; r < 32; ++r) {
-      const int row = S.perm[(size_t)sl * 32 + r];
+    for (int r = 0; r < C; ++r) {
+      const int row = S.perm[(size_t)sl * C + r];
       const int64_t len = row >= 0 ? M.rp[row + 1] - M.rp[row] : 0;
-      int32_t pad_col = len > 0 ? M.ci[M.rp[row] + len - 1] : 0;
-      for (int64_t k = 0; k < w; ++k) {
-        const int64_t at = base + k * 32 + r;
-        if (k < len) {
-          S.ci[at] = M.ci[M.rp[row] + k];
-          S.v[at] = M.v[M.rp[row] + k];
-        } else {
-          S.ci[at] = pad_col;
-          S.v[at] = 0.0;
+      const int32_t pad_col = len > 0 ? M.ci[M.rp[row] + len - 1] : 0;
+      for (int q = 0; q < L; ++q) {
+        for (int64_t c = 0; c < w; ++c) {
+          const int64_t k = c * L + q;             // entry of the row
+          const int64_t at = base + c * 32 + r * L + q;
+          if (k < len) {
+            S.ci[at] = M.ci[M.rp[row] + k];
+            S.v[at] = M.v[M.rp[row] + k];
+          } else {
+            S.ci[at] = pad_col;
+            S.v[at] = 0.0;
+          }
         }
       }
     }
@@ -223,8 +254,9 @@ void assign_vectors(GridData<T>& g, Arena& ar, int m, int n) {
   g.y = ar.take<T>(m); g.x = ar.take<T>(n); g.s = ar.take<T>(n);
   g.Ax = ar.take<T>(m); g.As = ar.take<T>(m); g.ATy = ar.take<T>(n);
   g.zy = ar.take<T>(m); g.zx = ar.take<T>(n); g.zp2 = ar.take<T>(m);
-  g.r = ar.take<T>(m); g.p = ar.take<T>(m); g.zr = ar.take<T>(m); g.zr2 = ar.take<T>(m);
-  g.t = ar.take<T>(n); g.u = ar.take<T>(n); g.Gp = ar.take<T>(m); g.dGp = ar.take<T>(m);
+  g.r = ar.take<T>(m); g.p = ar.take<T>(m); g.Gp = ar.take<T>(m);
+  using T2 = typename abip::Vec2<T>::type;
+  g.ut = ar.take<T2>(n); g.zd = ar.take<T2>(m); g.zd2 = ar.take<T2>(m);
 }
 
 template <typename T>
@@ -241,18 +273,20 @@ int setup_grid_path(abip_handle* h, const HostCSR& A, const std::vector<double>&
   const int maxc = abip::grid_solver_max_ctas(mixed, vf64, h->device);
   if (maxc <= 0) return fail(h, ABIP_E_CUDA, "grid kernel cannot be made resident");
   // grid_total reads at most kGridTotalPer partials per thread
-  const int cap = std::min(maxc, abip::kGridTotalPer * abip::kGridThreads);
+  const int cap = std::min(maxc, abip::kGridTotalPer * 32);
   int grid = h->prm.grid_ctas > 0 ? std::min(h->prm.grid_ctas, cap) : cap;
   h->grid = grid;
 
-  const HostSell SA = to_sell(A), ST = to_sell(AT);
+  const HostSell SA = to_sell(A, sell_lanes(A)), ST = to_sell(AT, sell_lanes(AT));
   auto layout_sell = [&](Arena& ar, SellMat& M, const HostSell& H) {
     M.rows = H.rows;
     M.nslices = H.nslices;
+    M.lanes = H.lanes;
     M.sp = ar.take<int64_t>(H.nslices + 1);
     M.ci = ar.take<int32_t>(H.ci.size());
     M.val = ar.take<char>(H.ci.size() * vb);
     M.perm = ar.take<int32_t>(H.perm.size());
+    M.wsl = ar.take<int32_t>((size_t)grid * (abip::kGridThreads / 32) + 1);
   };
   auto layout = [&](Arena& ar, GridData<T>& g) {
     h->ctl = ar.take<SolveCtl>(1);
@@ -286,6 +320,8 @@ int setup_grid_path(abip_handle* h, const HostCSR& A, const std::vector<double>&
     cudaMemcpy((void*)M.sp, H.sp.data(), H.sp.size() * 8, cudaMemcpyHostToDevice);
     cudaMemcpy((void*)M.ci, H.ci.data(), H.ci.size() * 4, cudaMemcpyHostToDevice);
     cudaMemcpy((void*)M.perm, H.perm.data(), H.perm.size() * 4, cudaMemcpyHostToDevice);
+    const std::vector<int32_t> wp = warp_partition(H, grid * (abip::kGridThreads / 32));
+    cudaMemcpy((void*)M.wsl, wp.data(), wp.size() * 4, cudaMemcpyHostToDevice);
     if (vf64) {
       cudaMemcpy((void*)M.val, H.v.data(), H.v.size() * 8, cudaMemcpyHostToDevice);
     } else {
@@ -335,9 +371,21 @@ template <typename T>
 int solve_grid_path(abip_handle* h, cudaStream_t st) {
   GridData<T>& g = *reinterpret_cast<GridData<T>*>(std::is_same<T, float>::value ? (void*)&h->gd32 : (void*)&h->gd64);
   const int m = h->m, n = h->n;
-  fill_kernel<T><<<64, 256, 0, st>>>(g.y, m, T(0));
-  fill_kernel<T><<<256, 256, 0, st>>>(g.x, n, T(1));
-  fill_kernel<T><<<256, 256, 0, st>>>(g.s, n, T(1));
+  const bool resume = h->resume;
+  if (resume) {
+    const std::vector<double>& rs = h->resume_state;
+    std::vector<T> v(rs.begin(), rs.begin() + m);
+    cudaMemcpyAsync(g.y, v.data(), m * sizeof(T), cudaMemcpyHostToDevice, st);
+    std::vector<T> w(rs.begin() + m, rs.begin() + m + n);
+    cudaMemcpyAsync(g.x, w.data(), n * sizeof(T), cudaMemcpyHostToDevice, st);
+    std::vector<T> u(rs.begin() + m + n + 2, rs.begin() + m + 2 * n + 2);
+    cudaMemcpyAsync(g.s, u.data(), n * sizeof(T), cudaMemcpyHostToDevice, st);
+    cudaStreamSynchronize(st);
+  } else {
+    fill_kernel<T><<<64, 256, 0, st>>>(g.y, m, T(0));
+    fill_kernel<T><<<256, 256, 0, st>>>(g.x, n, T(1));
+    fill_kernel<T><<<256, 256, 0, st>>>(g.s, n, T(1));
+  }
   fill_kernel<T><<<64, 256, 0, st>>>(g.zy, m, T(0));
   fill_kernel<T><<<64, 256, 0, st>>>(g.zp2, m, T(0));
   SolveCtl hc;
@@ -346,6 +394,11 @@ int solve_grid_path(abip_handle* h, cudaStream_t st) {
   hc.mode = abip::MODE_SOLVE;
   hc.tau = hc.kappa = hc.theta = 1.0;
   hc.mu = h->prm.beta;
+  if (resume) {
+    const std::vector<double>& rs = h->resume_state;
+    hc.tau = rs[m + n]; hc.theta = rs[m + n + 1]; hc.kappa = rs[m + 2 * n + 2]; hc.mu = rs[m + 2 * n + 3];
+    h->resume = false;
+  }
   hc.admm_iters = 0; hc.cg_iters = 0; hc.outer_iters = 0; hc.status = 0; hc.err = 0;
   hc.max_admm = h->prm.max_admm_iters;
   // ABIP_PROFILE=1: phase timers of CTA 0, printed to stderr after the solve
@@ -370,7 +423,7 @@ int solve_grid_path(abip_handle* h, cudaStream_t st) {
   float ms = 0.f;
   cudaEventElapsedTime(&ms, h->ev0, h->ev1);
   h->kernel_s = ms * 1e-3;
-  h->launches = 6;   // five fills and the persistent solve kernel
+  h->launches = resume ? 3 : 6;   // fills and the persistent solve kernel
   if (prof) {
     unsigned long long pv[abip::kProfBuckets];
     cudaMemcpy(pv, prof, sizeof(pv), cudaMemcpyDeviceToHost);
@@ -397,14 +450,16 @@ struct DenseHostInst {
 
 constexpr size_t kDenseSmemLimit = 200 * 1024;
 
-size_t dense_solve_smem(int m, int n) { return (size_t)(5 * m + 3 * n) * sizeof(double); }
+size_t dense_solve_smem(int m, int n, bool mixed = false) {
+  return (size_t)(5 * m + 3 * n) * (mixed ? sizeof(float) : sizeof(double));
+}
 size_t dense_setup_smem(int m, int n) {
   return std::max((size_t)(2 * 32 * 33), (size_t)(2 * m + n)) * sizeof(double);
 }
 
 // Allocate and fill the device descriptors of a set of dense instances.
 int dense_alloc(abip_handle* h, const std::vector<DenseHostInst>& hi, void** arena_out, DenseInst** dinst,
-                int** queue, std::vector<DenseInst>& hdesc) {
+                int** queue, std::vector<DenseInst>& hdesc, bool mixed = false) {
   const int count = (int)hi.size();
   auto layout = [&](Arena& ar, std::vector<DenseInst>& d) {
     DenseInst* di = ar.take<DenseInst>(count);
@@ -423,6 +478,16 @@ int dense_alloc(abip_handle* h, const std::vector<DenseHostInst>& hi, void** are
       I.y = ar.take<double>(m); I.x = ar.take<double>(n); I.s = ar.take<double>(n);
       I.out_y = ar.take<double>(m); I.out_x = ar.take<double>(n); I.out_s = ar.take<double>(n);
       I.work = nullptr;
+      if (mixed) {
+        I.Af = ar.take<float>((size_t)m * n);
+        I.Lf = ar.take<float>((size_t)m * m);
+        I.g1f = ar.take<float>(m + n); I.g2f = ar.take<float>(m + n);
+        I.bf = ar.take<float>(m); I.cf = ar.take<float>(n);
+        I.bbarf = ar.take<float>(m); I.cbarf = ar.take<float>(n);
+      } else {
+        I.Af = nullptr; I.Lf = nullptr; I.g1f = I.g2f = nullptr;
+        I.bf = I.cf = I.bbarf = I.cbarf = nullptr;
+      }
     }
   };
   Arena probe;
@@ -442,6 +507,10 @@ int dense_alloc(abip_handle* h, const std::vector<DenseHostInst>& hi, void** are
     cudaMemcpy((void*)I.A, hi[k].A.data(), hi[k].A.size() * 8, cudaMemcpyHostToDevice);
     cudaMemcpy((void*)I.b, hi[k].b.data(), hi[k].m * 8, cudaMemcpyHostToDevice);
     cudaMemcpy((void*)I.c, hi[k].c.data(), hi[k].n * 8, cudaMemcpyHostToDevice);
+    if (mixed) {
+      std::vector<float> f(hi[k].A.begin(), hi[k].A.end());
+      cudaMemcpy((void*)I.Af, f.data(), f.size() * 4, cudaMemcpyHostToDevice);
+    }
   }
   cudaMemcpy(*dinst, hdesc.data(), sizeof(DenseInst) * count, cudaMemcpyHostToDevice);
   *arena_out = mem;
@@ -461,7 +530,8 @@ int dense_run_setup(abip_handle* h, DenseInst* dinst, int* queue, int count, int
 
 int dense_run_solve(abip_handle* h, DenseInst* dinst, int* queue, int count, int grid, size_t smem,
                     const abip_params& p, cudaStream_t st) {
-  DenseParams dp{p.beta, p.gamma, p.alpha, p.eps, p.max_admm_iters, p.warmstart, p.stop_rule};
+  DenseParams dp{p.beta, p.gamma, p.alpha, p.eps, p.max_admm_iters, p.warmstart, p.stop_rule,
+                 p.precision == ABIP_PREC_MIXED ? 1 : 0, std::max(1, p.check_every)};
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
@@ -644,15 +714,14 @@ int abip_setup(const abip_matrix* A, const double* b, const double* c, const abi
       rc = h->mixed ? setup_grid_path<float>(h, hA, hb, hc, true) : setup_grid_path<double>(h, hA, hb, hc, f32);
   } else {
     h->path = 1;
-    if (h->mixed) rc = fail(h, ABIP_E_UNSUPPORTED, "mixed precision with dense Cholesky is not provided for single instances");
-    else if (dense_solve_smem(m, n) > kDenseSmemLimit)
-      rc = fail(h, ABIP_E_UNSUPPORTED, "dense Cholesky path needs 5m + 3n <= 25600; use linsys = PCG");
+    if (dense_solve_smem(m, n, h->mixed) > kDenseSmemLimit)
+      rc = fail(h, ABIP_E_UNSUPPORTED, "dense Cholesky path needs (5m + 3n) elements in 200 KB of shared memory; use linsys = PCG");
     else {
       std::vector<DenseHostInst> hi(1);
       hi[0].m = m; hi[0].n = n; hi[0].b = hb; hi[0].c = hc;
       rc = read_matrix_dense(h, A, hi[0].A);
       std::vector<DenseInst> hd;
-      if (rc == ABIP_OK) rc = dense_alloc(h, hi, &h->arena, &h->dinst, &h->queue, hd);
+      if (rc == ABIP_OK) rc = dense_alloc(h, hi, &h->arena, &h->dinst, &h->queue, hd, h->mixed != 0);
       if (rc == ABIP_OK) {
         h->hinst = hd[0];
         rc = dense_run_setup(h, h->dinst, h->queue, 1, 1, dense_setup_smem(m, n), 0);
@@ -716,7 +785,18 @@ int abip_solve(abip_handle* h, double* x, double* y, double* s, abip_info* info,
     cudaStreamSynchronize(st);
     if (rc) return rc;
   } else {
-    rc = dense_run_solve(h, h->dinst, h->queue, 1, 1, dense_solve_smem(m, n), h->prm, st);
+    if (h->resume) {
+      const std::vector<double>& rs = h->resume_state;
+      DenseInst I = h->hinst;
+      cudaMemcpy(I.y, rs.data(), m * 8, cudaMemcpyHostToDevice);
+      cudaMemcpy(I.x, rs.data() + m, n * 8, cudaMemcpyHostToDevice);
+      cudaMemcpy(I.s, rs.data() + m + n + 2, n * 8, cudaMemcpyHostToDevice);
+      I.resume = 1;
+      I.r_tau = rs[m + n]; I.r_theta = rs[m + n + 1]; I.r_kappa = rs[m + 2 * n + 2]; I.r_mu = rs[m + 2 * n + 3];
+      cudaMemcpy(h->dinst, &I, sizeof(DenseInst), cudaMemcpyHostToDevice);
+      h->resume = false;
+    }
+    rc = dense_run_solve(h, h->dinst, h->queue, 1, 1, dense_solve_smem(m, n, h->mixed != 0), h->prm, st);
     if (rc) return rc;
     cudaMemcpy(&h->hinst, h->dinst, sizeof(DenseInst), cudaMemcpyDeviceToHost);
     const DenseInst& I = h->hinst;
@@ -752,7 +832,7 @@ int abip_solve_batch(int32_t count, const abip_matrix* A, const double* const* b
   else abip_default_params(&prm);
   std::string why;
   if (!check_params(prm, why)) return fail(nullptr, ABIP_E_INVALID_ARG, why);
-  if (prm.precision != ABIP_PREC_F64) return fail(nullptr, ABIP_E_UNSUPPORTED, "batched path: only ABIP_PREC_F64 in this build");
+  const bool mixed = prm.precision == ABIP_PREC_MIXED;
   abip_handle tmp;
   cudaGetDevice(&tmp.device);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -763,8 +843,9 @@ int abip_solve_batch(int32_t count, const abip_matrix* A, const double* const* b
     if (rc) return fail(nullptr, rc, "instance " + std::to_string(k) + ": " + tmp.err);
     if (!b[k] || !c[k]) return fail(nullptr, ABIP_E_INVALID_ARG, "instance " + std::to_string(k) + ": b or c is NULL");
     const int m = A[k].m, n = A[k].n;
-    if (dense_solve_smem(m, n) > kDenseSmemLimit)
-      return fail(nullptr, ABIP_E_UNSUPPORTED, "instance " + std::to_string(k) + ": needs 5m + 3n <= 25600");
+    if (dense_solve_smem(m, n, mixed) > kDenseSmemLimit)
+      return fail(nullptr, ABIP_E_UNSUPPORTED, "instance " + std::to_string(k) + ": needs 5m + 3n <= " +
+                                                  std::to_string(kDenseSmemLimit / (mixed ? 4 : 8)));
     hi[k].m = m; hi[k].n = n;
     rc = read_matrix_dense(&tmp, &A[k], hi[k].A);
     if (rc) return fail(nullptr, rc, "instance " + std::to_string(k) + ": " + tmp.err);
@@ -773,18 +854,17 @@ int abip_solve_batch(int32_t count, const abip_matrix* A, const double* const* b
       return fail(nullptr, ABIP_E_CUDA, "reading b, c");
     if (!finite_all(hi[k].b.data(), m) || !finite_all(hi[k].c.data(), n))
       return fail(nullptr, ABIP_E_INVALID_ARG, "instance " + std::to_string(k) + ": non-finite b or c");
-    smem_solve = std::max(smem_solve, dense_solve_smem(m, n));
+    smem_solve = std::max(smem_solve, dense_solve_smem(m, n, mixed));
     smem_setup = std::max(smem_setup, dense_setup_smem(m, n));
   }
   void* arena = nullptr;
   DenseInst* dinst = nullptr;
   int* queue = nullptr;
   std::vector<DenseInst> hd;
-  int rc = dense_alloc(&tmp, hi, &arena, &dinst, &queue, hd);
+  int rc = dense_alloc(&tmp, hi, &arena, &dinst, &queue, hd, mixed);
   if (rc) return fail(nullptr, rc, tmp.err);
   const int sms = abip::dense_max_ctas(tmp.device);
-  int per = std::max(1, (int)(kDenseSmemLimit / std::max(smem_solve, (size_t)1)));
-  per = std::min(per, 8);
+  const int per = std::max(1, abip::dense_solve_ctas_per_sm(mixed, smem_solve));
   const int grid = std::min(count, sms * per);
   rc = dense_run_setup(&tmp, dinst, queue, count, std::min(count, sms * 4), smem_setup, st);
   if (!rc) rc = dense_run_solve(&tmp, dinst, queue, count, grid, smem_solve, prm, st);
@@ -865,6 +945,27 @@ int abip_get_state(const abip_handle* h, double* buf) {
   out[m + 2 * n + 3] = mu;
   cudaError_t e = cudaMemcpy(buf, out.data(), out.size() * 8, is_device_ptr(buf) ? cudaMemcpyHostToDevice : cudaMemcpyHostToHost);
   if (e != cudaSuccess) return fail(hm, ABIP_E_CUDA, std::string("state copy: ") + cudaGetErrorString(e));
+  return ABIP_OK;
+}
+
+int abip_set_state(abip_handle* h, const double* buf) {
+  if (!h || !buf) return fail(h, ABIP_E_INVALID_ARG, "NULL argument");
+  const int m = h->m, n = h->n;
+  const size_t len = (size_t)m + 2 * (size_t)n + 4;
+  std::vector<double> v(len);
+  if (is_device_ptr(buf)) {
+    if (cudaMemcpy(v.data(), buf, len * 8, cudaMemcpyDeviceToHost) != cudaSuccess)
+      return fail(h, ABIP_E_CUDA, "reading the state");
+  } else {
+    std::memcpy(v.data(), buf, len * 8);
+  }
+  if (!finite_all(v.data(), len)) return fail(h, ABIP_E_INVALID_ARG, "state has non-finite entries");
+  for (int j = 0; j < n; ++j)
+    if (!(v[m + j] > 0) || !(v[m + n + 2 + j] > 0)) return fail(h, ABIP_E_INVALID_ARG, "x and s must be > 0");
+  if (!(v[m + n] > 0) || !(v[m + 2 * n + 2] > 0) || !(v[m + 2 * n + 3] > 0))
+    return fail(h, ABIP_E_INVALID_ARG, "tau, kappa and mu must be > 0");
+  h->resume_state = std::move(v);
+  h->resume = true;
   return ABIP_OK;
 }
 

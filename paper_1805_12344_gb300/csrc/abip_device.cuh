@@ -159,34 +159,37 @@ __device__ __forceinline__ void grid_partial(double (&v)[K], double* partials, i
   }
 }
 
-constexpr int kGridTotalPer = 2;   // partials per thread in grid_total
+constexpr int kGridTotalPer = 8;   // partials per lane of warp 0 in grid_total
 
-// Every thread of the CTA loads its share of every slot's partials at once (one
-// L2 round trip), then a fixed-order block reduction gives the same totals in
-// every CTA.  Needs gridDim.x <= kGridTotalPer * blockDim.x.
+// Warp 0 loads every slot's partials at once (kGridTotalPer per lane, one L2
+// round trip), sums them in a fixed order and broadcasts the K totals through
+// shared memory, so every CTA gets the same totals.  Needs gridDim.x <= 32 * kGridTotalPer.
 template <int K>
 __device__ __forceinline__ void grid_total(double (&out)[K], const double* partials, int slot0,
                                            double* scratch) {
-  constexpr int kMaxPer = kGridTotalPer;
   const int nb = gridDim.x;
-  double v[K];
+  if (threadIdx.x < 32) {
+    double v[K];
 #pragma unroll
-  for (int k = 0; k < K; ++k) {
-    const double* p = partials + (size_t)(slot0 + k) * nb;
-    double part[kMaxPer];
+    for (int k = 0; k < K; ++k) {
+      const double* p = partials + (size_t)(slot0 + k) * nb;
+      double t = 0.0;
 #pragma unroll
-    for (int q = 0; q < kMaxPer; ++q) {
-      const int i = threadIdx.x + q * blockDim.x;
-      part[q] = i < nb ? __ldcg(p + i) : 0.0;
+      for (int q = 0; q < kGridTotalPer; ++q) {
+        const int i = threadIdx.x + q * 32;
+        t += i < nb ? __ldcg(p + i) : 0.0;
+      }
+      v[k] = warp_sum(t);
     }
-    double t = 0.0;
+    if (threadIdx.x == 0) {
 #pragma unroll
-    for (int q = 0; q < kMaxPer; ++q) t += part[q];
-    v[k] = t;
+      for (int k = 0; k < K; ++k) scratch[k] = v[k];
+    }
   }
-  block_allsum<K>(v, scratch);
+  __syncthreads();
 #pragma unroll
-  for (int k = 0; k < K; ++k) out[k] = v[k];
+  for (int k = 0; k < K; ++k) out[k] = scratch[k];
+  __syncthreads();
 }
 
 // ---------------------------------------------------------------------------

@@ -47,18 +47,26 @@ enum ProfBucket : int {
   kProfBuckets
 };
 
-// A sparse matrix in SELL-32 form: rows sorted by length (longest first), cut
-// into slices of 32 consecutive sorted rows; slice s stores its entries
-// column-major, entry k of lane r at sp[s] + 32 k + r, padded with zeros to the
-// slice's longest row (padding points at a valid column).  perm maps a sorted
-// position to its original row (-1 past the last row).
+// A sparse matrix in SELL form with L lanes per row: rows sorted by length
+// (longest first), cut into slices of C = 32/L consecutive sorted rows (one warp
+// per slice).  Row r of a slice is handled by lanes r*L .. r*L+L-1; entry k of the
+// row belongs to lane r*L + k%L at chunk k/L, stored at sp[s] + 32 (k/L) + r*L + k%L.
+// Every lane of a slice is padded with zeros to the slice's longest lane (padding
+// points at a column the row uses).  perm maps sorted position to row (-1 = none).
 struct SellMat {
   int rows = 0, nslices = 0;
+  int lanes = 1;                  // L: lanes per row (1, 2, 4, 8, 16 or 32)
   const int64_t* sp = nullptr;    // nslices + 1 offsets (multiples of 32)
   const int32_t* ci = nullptr;    // column indices, padded
   const void* val = nullptr;      // values (float or double), padded
-  const int32_t* perm = nullptr;  // nslices * 32
+  const int32_t* perm = nullptr;  // nslices * C
+  const int32_t* wsl = nullptr;   // per global warp w: slices [wsl[w], wsl[w+1]), balanced by nonzeros
 };
+
+// two interleaved vectors, gathered together with one load
+template <typename T> struct Vec2;
+template <> struct Vec2<float> { using type = float2; };
+template <> struct Vec2<double> { using type = double2; };
 
 // Device pointers of the sparse single-instance path.
 template <typename T>
@@ -73,7 +81,10 @@ struct GridData {
   T* Ax; T* As; T* ATy;                                       // products for the residuals
   T* zy; T* zx;                                               // M^{-1} w (zy warm-starts PCG)
   T* zp2;                                                     // previous zy (extrapolated start)
-  T* r; T* p; T* zr; T* zr2; T* t; T* u; T* Gp; T* dGp;       // PCG work vectors (zr double-buffered)
+  T* r; T* p; T* Gp;                                          // PCG work vectors
+  typename Vec2<T>::type* ut;                                 // (u, t) per column: A^T zr and A^T p
+  typename Vec2<T>::type* zd;                                 // (zr, D^{-1} Gp) per row, double-buffered
+  typename Vec2<T>::type* zd2;
   double* partials;                                           // kNumSlots * gridDim doubles
   unsigned long long* bar;                                    // barrier arrival counter
   SolveCtl* ctl;
@@ -100,6 +111,8 @@ struct DenseInst {
   double* y; double* x; double* s;   // iterate
   double* work;                // 3*(m + n) doubles
   double* out_x; double* out_y; double* out_s;   // device outputs (may be null)
+  // FP32 copies for the mixed-precision solve (null on the FP64 path)
+  const float* Af; float* Lf; float* g1f; float* g2f; float* bf; float* cf; float* bbarf; float* cbarf;
   double zbar, nb, nc;
   double Kinv[4];
   // results
@@ -107,18 +120,23 @@ struct DenseInst {
   double pres, dres, dgap, obj, ctx, bty;
   int64_t admm_iters;
   int32_t outer_iters, status;
-  int32_t err, pad;
+  int32_t err;
+  int32_t resume;              // 1: start from y, x, s and the scalars below instead of Algorithm 2's start
+  double r_tau, r_kappa, r_theta, r_mu;
 };
 
 struct DenseParams {
   double beta, gamma, alpha, eps;
   int64_t max_admm;
   int32_t warmstart, stop_rule;
+  int32_t mixed;          // 1: FP32 iterates with FP64 termination decisions
+  int32_t check_every;    // mixed: minimum spacing of FP64 confirmations (updates)
 };
 
 cudaError_t launch_dense_setup(DenseInst* inst, int count, int* queue, int grid, size_t smem, cudaStream_t st);
 cudaError_t launch_dense_solve(DenseInst* inst, int count, DenseParams prm, int* queue, int grid,
                                size_t smem, cudaStream_t st);
+int dense_solve_ctas_per_sm(bool mixed, size_t smem);
 int dense_max_ctas(int device);
 
 }  // namespace abip
@@ -151,4 +169,6 @@ struct abip_handle {
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   double kernel_s = 0;
   int64_t launches = 0;
+  bool resume = false;                // next solve starts from a state set by abip_set_state
+  std::vector<double> resume_state;   // y, x, tau, theta, s, kappa, mu
 };

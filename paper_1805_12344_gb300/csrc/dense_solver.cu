@@ -31,23 +31,24 @@ __device__ __forceinline__ int next_instance(int* queue, int count) {
 }
 
 // w <- L^{-1} w, L lower triangular (row-major, leading dimension m), w in shared memory.
-__device__ void trsv_lower(const double* __restrict__ L, int m, double* w) {
+template <typename T>
+__device__ void trsv_lower(const T* __restrict__ L, int m, T* w) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   for (int kb = 0; kb < m; kb += 32) {
     const int nb = min(32, m - kb);
     if (wid == 0) {
-      double wl = lane < nb ? w[kb + lane] : 0.0;
+      T wl = lane < nb ? w[kb + lane] : T(0);
       for (int j = 0; j < nb; ++j) {
         if (lane == j) wl = wl / L[(size_t)(kb + j) * m + kb + j];
-        const double wj = __shfl_sync(0xffffffffu, wl, j);
+        const T wj = __shfl_sync(0xffffffffu, wl, j);
         if (lane > j && lane < nb) wl -= L[(size_t)(kb + lane) * m + kb + j] * wj;
       }
       if (lane < nb) w[kb + lane] = wl;
     }
     __syncthreads();
-    const double wb = lane < nb ? w[kb + lane] : 0.0;
+    const T wb = lane < nb ? w[kb + lane] : T(0);
     for (int i = kb + nb + wid; i < m; i += kWarps) {
-      double a = lane < nb ? L[(size_t)i * m + kb + lane] * wb : 0.0;
+      T a = lane < nb ? L[(size_t)i * m + kb + lane] * wb : T(0);
       a = warp_sum(a);
       if (lane == 0) w[i] -= a;
     }
@@ -56,24 +57,25 @@ __device__ void trsv_lower(const double* __restrict__ L, int m, double* w) {
 }
 
 // w <- L^{-T} w.
-__device__ void trsv_lower_t(const double* __restrict__ L, int m, double* w) {
+template <typename T>
+__device__ void trsv_lower_t(const T* __restrict__ L, int m, T* w) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int nblk = (m + 31) / 32;
   for (int bk = nblk - 1; bk >= 0; --bk) {
     const int kb = bk * 32;
     const int nb = min(32, m - kb);
     if (wid == 0) {
-      double wl = lane < nb ? w[kb + lane] : 0.0;
+      T wl = lane < nb ? w[kb + lane] : T(0);
       for (int j = nb - 1; j >= 0; --j) {
         if (lane == j) wl = wl / L[(size_t)(kb + j) * m + kb + j];
-        const double zj = __shfl_sync(0xffffffffu, wl, j);
+        const T zj = __shfl_sync(0xffffffffu, wl, j);
         if (lane < j) wl -= L[(size_t)(kb + j) * m + kb + lane] * zj;
       }
       if (lane < nb) w[kb + lane] = wl;
     }
     __syncthreads();
     for (int i = threadIdx.x; i < kb; i += kThreads) {
-      double a = 0.0;
+      T a = T(0);
       for (int j = 0; j < nb; ++j) a += L[(size_t)(kb + j) * m + i] * w[kb + j];
       w[i] -= a;
     }
@@ -81,24 +83,24 @@ __device__ void trsv_lower_t(const double* __restrict__ L, int m, double* w) {
   }
 }
 
-// out[i] = sum_j A_ij v_j (warp per row); optional second vector.
-template <bool TWO>
-__device__ void gemv_rows(const double* __restrict__ A, int64_t ld, int m, int n, const double* v0,
-                          const double* v1, double* o0, double* o1) {
+// out[i] = sum_j A_ij v_j (warp per row, accumulated in Acc); optional second vector.
+template <bool TWO, typename Acc, typename TA, typename TV, typename TO>
+__device__ void gemv_rows(const TA* __restrict__ A, int64_t ld, int m, int n, const TV* v0,
+                          const TV* v1, TO* o0, TO* o1) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   for (int i = wid; i < m; i += kWarps) {
-    const double* row = A + (size_t)i * ld;
-    double a0 = 0.0, a1 = 0.0;
+    const TA* row = A + (size_t)i * ld;
+    Acc a0 = Acc(0), a1 = Acc(0);
     for (int j = lane; j < n; j += 32) {
-      const double a = row[j];
-      a0 += a * v0[j];
-      if (TWO) a1 += a * v1[j];
+      const Acc a = (Acc)row[j];
+      a0 += a * (Acc)v0[j];
+      if (TWO) a1 += a * (Acc)v1[j];
     }
     a0 = warp_sum(a0);
     if (TWO) a1 = warp_sum(a1);
     if (lane == 0) {
-      o0[i] = a0;
-      if (TWO) o1[i] = a1;
+      o0[i] = (TO)a0;
+      if (TWO) o1[i] = (TO)a1;
     }
   }
 }
@@ -194,12 +196,12 @@ __device__ void gram(const double* __restrict__ A, int64_t ld, int m, int n, dou
 // a (m), d (n) in shared memory; results in zy (m), zx (n); tmp (m) scratch.
 __device__ void solve_M(const DenseInst& I, const double* a, const double* d, double* zy, double* zx,
                         double* tmp) {
-  gemv_rows<false>(I.A, I.ld, I.m, I.n, d, d, tmp, tmp);
+  gemv_rows<false, double>(I.A, I.ld, I.m, I.n, d, d, tmp, tmp);
   __syncthreads();
   for (int i = threadIdx.x; i < I.m; i += kThreads) zy[i] = a[i] - tmp[i];
   __syncthreads();
-  trsv_lower(I.L, I.m, zy);
-  trsv_lower_t(I.L, I.m, zy);
+  trsv_lower<double>(I.L, I.m, zy);
+  trsv_lower_t<double>(I.L, I.m, zy);
   gemv_cols(I.A, I.ld, I.m, I.n, zy, zx);
   for (int j = threadIdx.x; j < I.n; j += kThreads) zx[j] += d[j];
   __syncthreads();
@@ -265,76 +267,142 @@ __global__ void __launch_bounds__(kThreads) dense_setup_kernel(DenseInst* insts,
       I.err = isfinite(det) && det != 0.0 ? 0 : DEV_ERR_NONFINITE;
     }
     __syncthreads();
+    if (I.Lf) {   // FP32 copies for the mixed-precision solve
+      for (int idx = threadIdx.x; idx < m * m; idx += kThreads) I.Lf[idx] = (float)I.L[idx];
+      for (int k = threadIdx.x; k < m + n; k += kThreads) {
+        I.g1f[k] = (float)I.g1[k];
+        I.g2f[k] = (float)I.g2[k];
+      }
+      for (int i = threadIdx.x; i < m; i += kThreads) { I.bf[i] = (float)I.b[i]; I.bbarf[i] = (float)I.bbar[i]; }
+      for (int j = threadIdx.x; j < n; j += kThreads) { I.cf[j] = (float)I.c[j]; I.cbarf[j] = (float)I.cbar[j]; }
+      __syncthreads();
+    }
   }
 }
 
-// Algorithm 2 for one instance with the CTA.  Shared layout (doubles):
-// y, zy, w, Ax, As (m each), x, s, zx (n each).
-__device__ void dense_solve_one(DenseInst& I, const DenseParams& P, double* sm, double* red) {
+// The instance data a solve of iteration type T reads.
+template <typename T>
+struct DView {
+  const T* A; const T* L; const T* g1; const T* g2; const T* b; const T* c; const T* bbar; const T* cbar;
+};
+__device__ __forceinline__ DView<double> view(const DenseInst& I, double) {
+  return {I.A, I.L, I.g1, I.g2, I.b, I.c, I.bbar, I.cbar};
+}
+__device__ __forceinline__ DView<float> view(const DenseInst& I, float) {
+  return {I.Af, I.Lf, I.g1f, I.g2f, I.bf, I.cf, I.bbarf, I.cbarf};
+}
+
+// Residual products Ax, As, A^T y and the nine sums of the Sec. 4.1 tests and
+// Eq. inner-stop, with products accumulated in Acc:
+//   0 ||Qu-v||^2 (vector blocks), 1 ||Ax/tau - b||^2, 2 ||(A^T y + s)/tau - c||^2,
+//   3 ||Ax||^2, 4 ||A^T y + s||^2, 5 b^T y, 6 bbar^T y, 7 c^T x, 8 cbar^T x.
+template <typename Acc, typename T>
+__device__ void residual_sums(const DView<T>& V, int m, int n, int64_t ld, const T* x, const T* s, const T* y,
+                              double tau, double theta, T* Ax, T* As, double (&out)[9], double* red) {
+  gemv_rows<true, Acc>(V.A, ld, m, n, x, s, Ax, As);
+  __syncthreads();
+  Acc acc[9] = {Acc(0), Acc(0), Acc(0), Acc(0), Acc(0), Acc(0), Acc(0), Acc(0), Acc(0)};
+  const Acc ta = (Acc)tau, th = (Acc)theta;
+  for (int i = threadIdx.x; i < m; i += kThreads) {
+    const Acc ax = (Acc)Ax[i], bi = (Acc)V.b[i], yi = (Acc)y[i], bb = (Acc)V.bbar[i];
+    const Acc ry = ax - bi * ta + bb * th;
+    const Acc pr = ax / ta - bi;
+    acc[0] += ry * ry; acc[1] += pr * pr; acc[3] += ax * ax;
+    acc[5] += bi * yi; acc[6] += bb * yi;
+  }
+  for (int j = threadIdx.x; j < n; j += kThreads) {
+    Acc a0 = Acc(0), a1 = Acc(0), a2 = Acc(0), a3 = Acc(0);
+    int i = 0;
+    for (; i + 4 <= m; i += 4) {
+      a0 += (Acc)V.A[(size_t)i * ld + j] * (Acc)y[i];
+      a1 += (Acc)V.A[(size_t)(i + 1) * ld + j] * (Acc)y[i + 1];
+      a2 += (Acc)V.A[(size_t)(i + 2) * ld + j] * (Acc)y[i + 2];
+      a3 += (Acc)V.A[(size_t)(i + 3) * ld + j] * (Acc)y[i + 3];
+    }
+    for (; i < m; ++i) a0 += (Acc)V.A[(size_t)i * ld + j] * (Acc)y[i];
+    const Acc aty = (a0 + a1) + (a2 + a3);
+    const Acc sj = (Acc)s[j], cj = (Acc)V.c[j], cb = (Acc)V.cbar[j], xj = (Acc)x[j];
+    const Acc rx = -aty + cj * ta - cb * th - sj;
+    const Acc dr = (aty + sj) / ta - cj;
+    acc[0] += rx * rx; acc[2] += dr * dr; acc[4] += (aty + sj) * (aty + sj);
+    acc[7] += cj * xj; acc[8] += cb * xj;
+  }
+#pragma unroll
+  for (int k = 0; k < 9; ++k) out[k] = (double)acc[k];
+  block_allsum<9>(out, red);
+}
+
+// Algorithm 2 for one instance with the CTA, iterates of type T.  Shared layout:
+// y, zy, w, Ax, As (m each), x, s, zx (n each), all of type T.
+// With T = float the sums of every update are formed in FP32 and serve the inner
+// test and as a screen; whenever they pass a Sec. 4.1 test with a factor-4 margin
+// the sums are recomputed with FP64 accumulation and the FP64 values decide.
+template <typename T>
+__device__ void dense_solve_one(DenseInst& I, const DenseParams& P, T* sm, double* red) {
+  const DView<T> V = view(I, T(0));
   const int m = I.m, n = I.n;
-  double* y = sm;
-  double* zy = y + m;
-  double* w = zy + m;
-  double* Ax = w + m;
-  double* As = Ax + m;
-  double* x = As + m;
-  double* s = x + n;
-  double* zx = s + n;
+  T* y = sm;
+  T* zy = y + m;
+  T* w = zy + m;
+  T* Ax = w + m;
+  T* As = Ax + m;
+  T* x = As + m;
+  T* s = x + n;
+  T* zx = s + n;
+  const bool mixed = sizeof(T) == 4;
   const double alpha = P.alpha, beta = P.beta, gamma = P.gamma, eps = P.eps;
   const double zbar = I.zbar, xi = -(double)n - 1.0, nb = I.nb, nc = I.nc;
   const double Ki0 = I.Kinv[0], Ki1 = I.Kinv[1], Ki2 = I.Kinv[2], Ki3 = I.Kinv[3];
-  const double* b = I.b;
-  const double* c = I.c;
-  // start of Algorithm 2
-  for (int i = threadIdx.x; i < m; i += kThreads) y[i] = 0.0;
-  for (int j = threadIdx.x; j < n; j += kThreads) { x[j] = 1.0; s[j] = 1.0; }
-  __syncthreads();
+  // start of Algorithm 2, or a state loaded by abip_set_state
   double tau = 1.0, kappa = 1.0, theta = 1.0, mu = beta;
-  int64_t total = 0;
+  if (I.resume) {
+    for (int i = threadIdx.x; i < m; i += kThreads) y[i] = (T)I.y[i];
+    for (int j = threadIdx.x; j < n; j += kThreads) { x[j] = (T)I.x[j]; s[j] = (T)I.s[j]; }
+    tau = I.r_tau; kappa = I.r_kappa; theta = I.r_theta; mu = I.r_mu;
+  } else {
+    for (int i = threadIdx.x; i < m; i += kThreads) y[i] = T(0);
+    for (int j = threadIdx.x; j < n; j += kThreads) { x[j] = T(1); s[j] = T(1); }
+  }
+  __syncthreads();
+  int64_t total = 0, next_confirm = 0;
   int outer = 0, status = 0;
   double inner2 = 0, pres = 0, dres = 0, dgap = 0, ctx = 0, bty = 0;
 
-  auto evaluate = [&](bool final_test) {
-    gemv_rows<true>(I.A, I.ld, m, n, x, s, Ax, As);
-    double acc[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
-    __syncthreads();
-    for (int i = threadIdx.x; i < m; i += kThreads) {
-      const double ry = Ax[i] - b[i] * tau + I.bbar[i] * theta;
-      const double pr = Ax[i] / tau - b[i];
-      acc[0] += ry * ry; acc[1] += pr * pr; acc[3] += Ax[i] * Ax[i];
-      acc[5] += b[i] * y[i]; acc[6] += I.bbar[i] * y[i];
-    }
-    // A^T y column by column
-    for (int j = threadIdx.x; j < n; j += kThreads) {
-      double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
-      int i = 0;
-      for (; i + 4 <= m; i += 4) {
-        a0 += I.A[(size_t)i * I.ld + j] * y[i];
-        a1 += I.A[(size_t)(i + 1) * I.ld + j] * y[i + 1];
-        a2 += I.A[(size_t)(i + 2) * I.ld + j] * y[i + 2];
-        a3 += I.A[(size_t)(i + 3) * I.ld + j] * y[i + 3];
-      }
-      for (; i < m; ++i) a0 += I.A[(size_t)i * I.ld + j] * y[i];
-      const double aty = (a0 + a1) + (a2 + a3);
-      const double rx = -aty + c[j] * tau - I.cbar[j] * theta - s[j];
-      const double dr = (aty + s[j]) / tau - c[j];
-      acc[0] += rx * rx; acc[2] += dr * dr; acc[4] += (aty + s[j]) * (aty + s[j]);
-      acc[7] += c[j] * x[j]; acc[8] += I.cbar[j] * x[j];
-    }
-    block_allsum<9>(acc, red);
-    bty = acc[5];
-    ctx = acc[7];
-    const double rt = acc[5] - acc[7] + zbar * theta - kappa;
-    const double rth = -acc[6] + acc[8] - zbar * tau - xi;
-    inner2 = acc[0] + rt * rt + rth * rth;
-    pres = sqrt(acc[1]) / (1.0 + nb);
-    dres = sqrt(acc[2]) / (1.0 + nc);
+  // Sec. 4.1 tests on the sums; returns the status they give (0 = continue)
+  auto tests = [&](const double (&a)[9], double margin) -> int {
+    const double ps = sqrt(a[1]) / (1.0 + nb), ds = sqrt(a[2]) / (1.0 + nc);
+    const double gp = fabs(a[7] / tau - a[5] / tau) / (1.0 + fabs(a[7] / tau) + fabs(a[5] / tau));
+    if (ps <= margin * eps && ds <= margin * eps && gp <= margin * eps) return ABIP_OPTIMAL;
+    if (a[5] > 0 && sqrt(a[4]) <= margin * eps * a[5] / nb) return ABIP_PRIMAL_INFEASIBLE;
+    if (a[7] < 0 && sqrt(a[3]) <= margin * eps * (-a[7]) / nc) return ABIP_DUAL_INFEASIBLE;
+    return 0;
+  };
+  auto absorb = [&](const double (&a)[9]) {
+    bty = a[5];
+    ctx = a[7];
+    const double rt = a[5] - a[7] + zbar * theta - kappa;
+    const double rth = -a[6] + a[8] - zbar * tau - xi;
+    inner2 = a[0] + rt * rt + rth * rth;
+    pres = sqrt(a[1]) / (1.0 + nb);
+    dres = sqrt(a[2]) / (1.0 + nc);
     dgap = fabs(ctx / tau - bty / tau) / (1.0 + fabs(ctx / tau) + fabs(bty / tau));
+  };
+  auto evaluate = [&](bool final_test) -> bool {
+    double a[9];
+    residual_sums<T>(V, m, n, I.ld, x, s, y, tau, theta, Ax, As, a, red);
+    absorb(a);
     if (!isfinite(inner2)) return false;
-    if (final_test && P.stop_rule == 0) {
-      if (pres <= eps && dres <= eps && dgap <= eps) status = ABIP_OPTIMAL;
-      else if (bty > 0 && sqrt(acc[4]) <= eps * bty / nb) status = ABIP_PRIMAL_INFEASIBLE;
-      else if (ctx < 0 && sqrt(acc[3]) <= eps * (-ctx) / nc) status = ABIP_DUAL_INFEASIBLE;
+    if (!final_test || P.stop_rule != 0) return true;
+    if (!mixed) {
+      status = tests(a, 1.0);
+    } else if (tests(a, 4.0) != 0 && total >= next_confirm) {
+      double d[9];
+      residual_sums<double>(V, m, n, I.ld, x, s, y, tau, theta, Ax, As, d, red);
+      const double keep = inner2;
+      absorb(d);
+      inner2 = keep;
+      status = tests(d, 1.0);
+      if (status == 0) next_confirm = total + P.check_every;
     }
     return true;
   };
@@ -346,18 +414,18 @@ __device__ void dense_solve_one(DenseInst& I, const DenseParams& P, double* sm, 
       ++outer;
       if (P.stop_rule == 1 && mu < eps) { status = ABIP_OPTIMAL; break; }
       if (outer >= kMaxOuter) { status = ABIP_MAX_ITER; break; }   // mu has underflowed
-      const double sg = sqrt(gamma);
+      const T g = (T)gamma, sg = (T)sqrt(gamma);
       if (P.warmstart == 1) {
         for (int j = threadIdx.x; j < n; j += kThreads) { x[j] *= sg; s[j] *= sg; }
-        tau *= sg; kappa *= sg;
+        tau *= sqrt(gamma); kappa *= sqrt(gamma);
       } else {
         for (int j = threadIdx.x; j < n; j += kThreads) {
-          if (x[j] >= s[j]) s[j] *= gamma; else x[j] *= gamma;
+          if (x[j] >= s[j]) s[j] *= g; else x[j] *= g;
         }
         if (tau >= kappa) kappa *= gamma; else tau *= gamma;
       }
       for (int i = threadIdx.x; i < m; i += kThreads) y[i] *= sg;
-      theta *= sg;
+      theta *= sqrt(gamma);
       __syncthreads();
       ok = evaluate(false);
       continue;
@@ -366,49 +434,50 @@ __device__ void dense_solve_one(DenseInst& I, const DenseParams& P, double* sm, 
     for (int i = threadIdx.x; i < m; i += kThreads) zy[i] = y[i] - (Ax[i] + As[i]);
     for (int j = threadIdx.x; j < n; j += kThreads) zx[j] = x[j] + s[j];
     __syncthreads();
-    trsv_lower(I.L, m, zy);
-    trsv_lower_t(I.L, m, zy);
+    trsv_lower<T>(V.L, m, zy);
+    trsv_lower_t<T>(V.L, m, zy);
     // zx = w_x + A^T zy, and H^T z
-    double hz[2] = {0.0, 0.0};
+    T hz0 = T(0), hz1 = T(0);
     for (int j = threadIdx.x; j < n; j += kThreads) {
-      double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+      T a0 = T(0), a1 = T(0), a2 = T(0), a3 = T(0);
       int i = 0;
       for (; i + 4 <= m; i += 4) {
-        a0 += I.A[(size_t)i * I.ld + j] * zy[i];
-        a1 += I.A[(size_t)(i + 1) * I.ld + j] * zy[i + 1];
-        a2 += I.A[(size_t)(i + 2) * I.ld + j] * zy[i + 2];
-        a3 += I.A[(size_t)(i + 3) * I.ld + j] * zy[i + 3];
+        a0 += V.A[(size_t)i * I.ld + j] * zy[i];
+        a1 += V.A[(size_t)(i + 1) * I.ld + j] * zy[i + 1];
+        a2 += V.A[(size_t)(i + 2) * I.ld + j] * zy[i + 2];
+        a3 += V.A[(size_t)(i + 3) * I.ld + j] * zy[i + 3];
       }
-      for (; i < m; ++i) a0 += I.A[(size_t)i * I.ld + j] * zy[i];
-      const double z = zx[j] + ((a0 + a1) + (a2 + a3));
+      for (; i < m; ++i) a0 += V.A[(size_t)i * I.ld + j] * zy[i];
+      const T z = zx[j] + ((a0 + a1) + (a2 + a3));
       zx[j] = z;
-      hz[0] += c[j] * z;
-      hz[1] -= I.cbar[j] * z;
+      hz0 += V.c[j] * z;
+      hz1 -= V.cbar[j] * z;
     }
     for (int i = threadIdx.x; i < m; i += kThreads) {
-      hz[0] -= b[i] * zy[i];
-      hz[1] += I.bbar[i] * zy[i];
+      hz0 -= V.b[i] * zy[i];
+      hz1 += V.bbar[i] * zy[i];
     }
+    double hz[2] = {(double)hz0, (double)hz1};
     block_allsum<2>(hz, red);
     const double v1 = tau + kappa + hz[0], v2 = theta + xi + hz[1];
     const double t1 = Ki0 * v1 + Ki1 * v2, t2 = Ki2 * v1 + Ki3 * v2;
-    const double cmu = mu / beta;
+    const T a = (T)alpha, a1 = (T)(1.0 - alpha), t1T = (T)t1, t2T = (T)t2, cmu = (T)(mu / beta);
     for (int i = threadIdx.x; i < m; i += kThreads) {
-      const double uy = zy[i] - I.g1[i] * t1 - I.g2[i] * t2;
-      y[i] = alpha * uy + (1.0 - alpha) * y[i];
+      const T uy = zy[i] - V.g1[i] * t1T - V.g2[i] * t2T;
+      y[i] = a * uy + a1 * y[i];
     }
     for (int j = threadIdx.x; j < n; j += kThreads) {
-      const double ux = zx[j] - I.g1[m + j] * t1 - I.g2[m + j] * t2;
-      const double xh = alpha * ux + (1.0 - alpha) * x[j];
-      double xn, sn;
-      barrier_step<double>(xh - s[j], cmu, xn, sn);
+      const T ux = zx[j] - V.g1[m + j] * t1T - V.g2[m + j] * t2T;
+      const T xh = a * ux + a1 * x[j];
+      T xn, sn;
+      barrier_step<T>(xh - s[j], cmu, xn, sn);
       x[j] = xn;
       s[j] = sn;
     }
     {
       const double th_ = alpha * t1 + (1.0 - alpha) * tau;
       double tn, kn;
-      barrier_step<double>(th_ - kappa, cmu, tn, kn);
+      barrier_step<double>(th_ - kappa, mu / beta, tn, kn);
       tau = tn;
       kappa = kn;
       theta = alpha * t2 + (1.0 - alpha) * theta;
@@ -424,17 +493,18 @@ __device__ void dense_solve_one(DenseInst& I, const DenseParams& P, double* sm, 
   if (status == ABIP_PRIMAL_INFEASIBLE) { sx = 1.0; sy = 1.0 / bty; }
   if (status == ABIP_DUAL_INFEASIBLE) { sx = -1.0 / ctx; sy = 1.0; }
   for (int i = threadIdx.x; i < m; i += kThreads) {
-    I.y[i] = y[i];
-    if (I.out_y) I.out_y[i] = y[i] * sy;
+    I.y[i] = (double)y[i];
+    if (I.out_y) I.out_y[i] = (double)y[i] * sy;
   }
   for (int j = threadIdx.x; j < n; j += kThreads) {
-    I.x[j] = x[j];
-    I.s[j] = s[j];
-    if (I.out_x) I.out_x[j] = x[j] * sx;
-    if (I.out_s) I.out_s[j] = s[j] * sy;
+    I.x[j] = (double)x[j];
+    I.s[j] = (double)s[j];
+    if (I.out_x) I.out_x[j] = (double)x[j] * sx;
+    if (I.out_s) I.out_s[j] = (double)s[j] * sy;
   }
   if (threadIdx.x == 0) {
     I.tau = tau; I.kappa = kappa; I.theta = theta; I.mu = mu;
+    I.resume = 0;
     I.pres = pres; I.dres = dres; I.dgap = dgap; I.ctx = ctx; I.bty = bty; I.obj = ctx / tau;
     I.admm_iters = total; I.outer_iters = outer; I.status = status;
     if (!ok) I.err = DEV_ERR_NONFINITE;
@@ -442,16 +512,18 @@ __device__ void dense_solve_one(DenseInst& I, const DenseParams& P, double* sm, 
   __syncthreads();
 }
 
+template <typename T>
 __global__ void __launch_bounds__(kThreads) dense_solve_kernel(DenseInst* insts, int count, DenseParams P,
                                                                int* queue) {
-  extern __shared__ double sm[];
+  extern __shared__ double sm_raw[];
   __shared__ double red[32 * 9];
+  T* sm = reinterpret_cast<T*>(sm_raw);
   for (;;) {
     const int id = next_instance(queue, count);
     if (id < 0) return;
     DenseInst& I = insts[id];
     if (I.err != 0) continue;
-    dense_solve_one(I, P, sm, red);
+    dense_solve_one<T>(I, P, sm, red);
   }
 }
 
@@ -470,11 +542,29 @@ cudaError_t launch_dense_setup(DenseInst* inst, int count, int* queue, int grid,
 
 cudaError_t launch_dense_solve(DenseInst* inst, int count, DenseParams prm, int* queue, int grid,
                                size_t smem, cudaStream_t st) {
-  // the caller sizes smem for the largest instance: 5m + 3n doubles
-  cudaError_t e = cudaFuncSetAttribute(dense_solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDenseSmemMax);
-  if (e != cudaSuccess) return e;
-  dense_solve_kernel<<<grid, kThreads, smem, st>>>(inst, count, prm, queue);
+  // the caller sizes smem for the largest instance: (5m + 3n) elements of the iteration type
+  if (prm.mixed) {
+    cudaError_t e = cudaFuncSetAttribute(dense_solve_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDenseSmemMax);
+    if (e != cudaSuccess) return e;
+    dense_solve_kernel<float><<<grid, kThreads, smem, st>>>(inst, count, prm, queue);
+  } else {
+    cudaError_t e = cudaFuncSetAttribute(dense_solve_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDenseSmemMax);
+    if (e != cudaSuccess) return e;
+    dense_solve_kernel<double><<<grid, kThreads, smem, st>>>(inst, count, prm, queue);
+  }
   return cudaGetLastError();
+}
+
+int dense_solve_ctas_per_sm(bool mixed, size_t smem) {
+  int per = 0;
+  if (mixed) {
+    cudaFuncSetAttribute(dense_solve_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDenseSmemMax);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, dense_solve_kernel<float>, kThreads, smem);
+  } else {
+    cudaFuncSetAttribute(dense_solve_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDenseSmemMax);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, dense_solve_kernel<double>, kThreads, smem);
+  }
+  return per;
 }
 
 int dense_max_ctas(int device) {

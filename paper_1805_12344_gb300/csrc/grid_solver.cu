@@ -46,17 +46,20 @@ struct Thr {
   }
 };
 
-// Row products for every row of a SELL-32 matrix: dot0 = sum_k A_ik g0(k),
-// dot1 = sum_k A_ik g1(k) (NV = 2), accumulated in Acc; epi(row, dot0, dot1)
-// runs on the row's thread.  g0/g1 map a column index to the gathered value.
-template <int U, int NV, typename Acc, typename V, typename G0, typename G1, typename Epi>
-__device__ __forceinline__ void sell_rows_g(const SellMat& S, G0& g0, G1& g1, Epi& epi) {
+// Row products for every row of a SELL matrix with L lanes per row:
+// dot0 = sum_k A_ik g0(k), dot1 = sum_k A_ik g1(k) (NV = 2), accumulated in Acc;
+// epi(row, dot0, dot1) runs on the first lane of the row.  g0/g1 map a column
+// index to the gathered value.  Each lane keeps U gathers in flight.
+template <int L, int U, int NV, typename Acc, typename V, typename G0, typename G1, typename Epi>
+__device__ __forceinline__ void sell_rows_L(const SellMat& S, G0& g0, G1& g1, Epi& epi) {
   const Thr th;
+  constexpr int C = 32 / L;
   const V* __restrict__ val = static_cast<const V*>(S.val);
-  for (int sl = th.gw; sl < S.nslices; sl += th.nwarp) {
+  const int s1 = __ldg(S.wsl + th.gw + 1);
+  for (int sl = __ldg(S.wsl + th.gw); sl < s1; ++sl) {
     const int64_t base = __ldg(S.sp + sl);
     const int w = (int)((__ldg(S.sp + sl + 1) - base) >> 5);
-    const int row = __ldg(S.perm + sl * 32 + th.lane);
+    const int row = __ldg(S.perm + sl * C + th.lane / L);
     const int32_t* __restrict__ ci = S.ci + base + th.lane;
     const V* __restrict__ va = val + base + th.lane;
     Acc a0 = Acc(0), a1 = Acc(0);
@@ -81,26 +84,60 @@ __device__ __forceinline__ void sell_rows_g(const SellMat& S, G0& g0, G1& g1, Ep
       a0 += a * static_cast<Acc>(g0(j));
       if (NV == 2) a1 += a * static_cast<Acc>(g1(j));
     }
-    if (row >= 0) epi(row, a0, a1);
+    if (L > 1) {
+      a0 = group_sum<L>(a0);
+      if (NV == 2) a1 = group_sum<L>(a1);
+    }
+    if (row >= 0 && (th.lane % L) == 0) epi(row, a0, a1);
   }
 }
 
-// Per-row sum and sum of squares of a SELL-32 matrix (setup only).
-template <typename T, typename V, typename Epi>
-__device__ void sell_rowstats(const SellMat& S, Epi& epi) {
+template <int U, int NV, typename Acc, typename V, typename G0, typename G1, typename Epi>
+__device__ __forceinline__ void sell_rows_g(const SellMat& S, G0& g0, G1& g1, Epi& epi) {
+  switch (S.lanes) {
+    case 1: sell_rows_L<1, U, NV, Acc, V>(S, g0, g1, epi); break;
+    case 2: sell_rows_L<2, U, NV, Acc, V>(S, g0, g1, epi); break;
+    case 4: sell_rows_L<4, U, NV, Acc, V>(S, g0, g1, epi); break;
+    case 8: sell_rows_L<8, U, NV, Acc, V>(S, g0, g1, epi); break;
+    case 16: sell_rows_L<16, U, NV, Acc, V>(S, g0, g1, epi); break;
+    default: sell_rows_L<32, U, NV, Acc, V>(S, g0, g1, epi); break;
+  }
+}
+
+// Per-row sum and sum of squares of a SELL matrix with L lanes per row (setup only).
+template <int L, typename T, typename V, typename Epi>
+__device__ void sell_rowstats_L(const SellMat& S, Epi& epi) {
   const Thr th;
+  constexpr int C = 32 / L;
   const V* val = static_cast<const V*>(S.val);
-  for (int sl = th.gw; sl < S.nslices; sl += th.nwarp) {
+  const int s1 = S.wsl[th.gw + 1];
+  for (int sl = S.wsl[th.gw]; sl < s1; ++sl) {
     const int64_t base = S.sp[sl];
     const int w = (int)((S.sp[sl + 1] - base) >> 5);
-    const int row = S.perm[sl * 32 + th.lane];
+    const int row = S.perm[sl * C + th.lane / L];
     T sum = T(0), sq = T(0);
     for (int k = 0; k < w; ++k) {
       const T a = static_cast<T>(val[base + k * 32 + th.lane]);
       sum += a;
       sq += a * a;
     }
-    if (row >= 0) epi(row, sum, sq);
+    if (L > 1) {
+      sum = group_sum<L>(sum);
+      sq = group_sum<L>(sq);
+    }
+    if (row >= 0 && (th.lane % L) == 0) epi(row, sum, sq);
+  }
+}
+
+template <typename T, typename V, typename Epi>
+__device__ void sell_rowstats(const SellMat& S, Epi& epi) {
+  switch (S.lanes) {
+    case 1: sell_rowstats_L<1, T, V>(S, epi); break;
+    case 2: sell_rowstats_L<2, T, V>(S, epi); break;
+    case 4: sell_rowstats_L<4, T, V>(S, epi); break;
+    case 8: sell_rowstats_L<8, T, V>(S, epi); break;
+    case 16: sell_rowstats_L<16, T, V>(S, epi); break;
+    default: sell_rowstats_L<32, T, V>(S, epi); break;
   }
 }
 
@@ -183,17 +220,21 @@ struct Solver {
   // pass and stored by each row's owner in the first A pass.
   template <typename QF>
   __device__ int pcg(T* z, QF qf, double tol, int maxit, bool extrap = false, T* zp2 = nullptr) {
-    T* r = D.r; T* p = D.p; T* t = D.t; T* u = D.u; T* Gp = D.Gp; T* dGp = D.dGp;
-    T* zr_cur = D.zr;
-    T* zr_nxt = D.zr2;
+    using T2 = typename Vec2<T>::type;
+    T* r = D.r; T* p = D.p; T* Gp = D.Gp;
+    T2* ut = D.ut;                 // (u, t)
+    T2* zd_cur = D.zd;             // (zr, D^{-1} Gp)
+    T2* zd_nxt = D.zd2;
     {
+      // A^T z0 into ut[].x
       auto g = [&](int i) -> T { return extrap ? T(2) * z[i] - zp2[i] : z[i]; };
-      auto e = [&](int j, T v, T) { t[j] = v; };
+      auto e = [&](int j, T v, T) { ut[j].x = v; };
       sell_rows_g<8, 1, T, V>(D.AT, g, g, e);
     }
     if (!sync(P_PCG_INIT)) return -1;
-    double acc[3] = {0.0, 0.0, 0.0};
+    T acc[3] = {T(0), T(0), T(0)};
     {
+      auto g = [&](int j) -> T { return ut[j].x; };
       auto e = [&](int i, T v, T) {
         const T qi = qf(i);
         const T zi = extrap ? T(2) * z[i] - zp2[i] : z[i];
@@ -201,14 +242,17 @@ struct Solver {
         z[i] = zi;
         const T ri = qi - (zi + v);
         const T zri = D.dinv[i] * ri;
-        r[i] = ri; zr_cur[i] = zri;
-        acc[0] += (double)ri * (double)zri;
-        acc[1] += (double)ri * (double)ri;
-        acc[2] += (double)qi * (double)qi;
+        r[i] = ri; zd_cur[i].x = zri;
+        acc[0] += ri * zri;
+        acc[1] += ri * ri;
+        acc[2] += qi * qi;
       };
-      rowsA(t, e);
+      sell_rows_g<8, 1, T, V>(D.A, g, g, e);
     }
-    grid_partial<3>(acc, D.partials, S_PCG0, red);
+    {
+      double accd[3] = {(double)acc[0], (double)acc[1], (double)acc[2]};
+      grid_partial<3>(accd, D.partials, S_PCG0, red);
+    }
     if (!sync(P_PCG_INIT)) return -1;
     double tot[3];
     totals<3>(tot, S_PCG0);
@@ -217,8 +261,9 @@ struct Solver {
     if (!(sqrt(rr) > bound)) return 0;
     // u = A^T zr (so that A^T p_0 = u with p_0 = zr)
     {
-      auto e = [&](int j, T v, T) { u[j] = v; };
-      rowsAT(zr_cur, e);
+      auto g = [&](int i) -> T { return zd_cur[i].x; };
+      auto e = [&](int j, T v, T) { ut[j].x = v; };
+      sell_rows_g<8, 1, T, V>(D.AT, g, g, e);
     }
     if (!sync(P_PCG_INIT)) return -1;
     T be = T(0);
@@ -226,50 +271,68 @@ struct Solver {
     for (;;) {
       if (k >= maxit) return -2;
       const bool first = k == 0;
-      double a1[1] = {0.0};
+      T a1 = T(0);
       {
-        auto g = [&](int j) -> T { return first ? u[j] : u[j] + be * t[j]; };
+        // gather A^T p = u + be * t (one pair load per nonzero)
+        auto g = [&](int j) -> T {
+          const T2 w = ut[j];
+          return first ? w.x : w.x + be * w.y;
+        };
         auto e = [&](int i, T v, T) {
-          const T pi = first ? zr_cur[i] : zr_cur[i] + be * p[i];
+          const T zri = zd_cur[i].x;
+          const T pi = first ? zri : zri + be * p[i];
           const T gp = pi + v;
           p[i] = pi;
           Gp[i] = gp;
-          dGp[i] = D.dinv[i] * gp;
-          a1[0] += (double)pi * (double)gp;
+          zd_cur[i].y = D.dinv[i] * gp;
+          a1 += pi * gp;
         };
         sell_rows_g<8, 1, T, V>(D.A, g, g, e);
       }
-      grid_partial<1>(a1, D.partials, S_PGP, red);
+      {
+        double a1d[1] = {(double)a1};
+        grid_partial<1>(a1d, D.partials, S_PGP, red);
+      }
       if (!sync(P_CG_A)) return -1;
       double pgp[1];
       totals<1>(pgp, S_PGP);
       const T al = (T)(rz / pgp[0]);
       {
-        auto g = [&](int i) -> T { return zr_cur[i] - al * dGp[i]; };
+        // gather zr_new = zr - al * D^{-1} Gp (one pair load per nonzero)
+        auto g = [&](int i) -> T {
+          const T2 w = zd_cur[i];
+          return w.x - al * w.y;
+        };
         auto e = [&](int j, T v, T) {
-          t[j] = first ? u[j] : u[j] + be * t[j];
-          u[j] = v;
+          const T2 w = ut[j];
+          T2 o;
+          o.x = v;
+          o.y = first ? w.x : w.x + be * w.y;
+          ut[j] = o;
         };
         sell_rows_g<8, 1, T, V>(D.AT, g, g, e);
       }
       mark(P_CG_AT);
-      double a2[2] = {0.0, 0.0};
+      T a2[2] = {T(0), T(0)};
       for (int i = th.gtid; i < D.m; i += th.nthr) {
         z[i] += al * p[i];
         const T ri = r[i] - al * Gp[i];
         const T zri = D.dinv[i] * ri;
-        r[i] = ri; zr_nxt[i] = zri;
-        a2[0] += (double)ri * (double)zri;
-        a2[1] += (double)ri * (double)ri;
+        r[i] = ri; zd_nxt[i].x = zri;
+        a2[0] += ri * zri;
+        a2[1] += ri * ri;
       }
-      grid_partial<2>(a2, D.partials, S_RZ, red);
+      {
+        double a2d[2] = {(double)a2[0], (double)a2[1]};
+        grid_partial<2>(a2d, D.partials, S_RZ, red);
+      }
       if (!sync(P_CG_UPD)) return -1;
       double t2[2];
       totals<2>(t2, S_RZ);
       be = (T)(t2[0] / rz);
       rz = t2[0];
       rr = t2[1];
-      T* sw = zr_cur; zr_cur = zr_nxt; zr_nxt = sw;
+      T2* sw = zd_cur; zd_cur = zd_nxt; zd_nxt = sw;
       ++k;
       if (!(sqrt(rr) > bound)) break;
     }

@@ -216,3 +216,39 @@ def dense_to_csr(A: np.ndarray, dtype=np.float64) -> CSR:
     np.cumsum(mask.sum(axis=1), out=row_ptr[1:])
     rows, cols = np.nonzero(mask)
     return CSR(m=m, n=n, row_ptr=row_ptr, col_idx=cols.astype(np.int32), val=A[rows, cols].astype(dtype))
+
+
+def planted_dense_f32(m: int, n: int, seed: int) -> LP:
+    """Dense planted LP whose A is iid N(0,1) drawn in float32 (exactly representable in
+    both precisions); b and c are formed in float64 from the exact values."""
+    rng = np.random.default_rng(seed)
+    A = rng.standard_normal((m, n), dtype=np.float32).astype(np.float64)
+    x0, y0, s0 = _planted_pair(rng, n, m)
+    return LP(A=A, b=A @ x0, c=A.T @ y0 + s0, x0=x0, y0=y0, s0=s0, expect="optimal",
+              meta=dict(kind="planted_dense_f32", m=m, n=n))
+
+
+def batch_uneven(count: int = 4096, infeasible_frac: float = 0.1, m_lo: int = 16, m_hi: int = 256,
+                 seed: int | None = None) -> list:
+    """Batch of independent dense planted LPs of uneven size: m ~ U{m_lo..m_hi},
+    n = round(m * U[2, 4]); a seeded choice of round(infeasible_frac * count) instances
+    gets the infeasible-twin treatment (row 1 of A <- |N(0,1)|, b_1 = -1)."""
+    rng = np.random.default_rng(seed_for(BATCH_UNEVEN) if seed is None else seed)
+    ms = rng.integers(m_lo, m_hi + 1, size=count)
+    ratio = rng.uniform(2.0, 4.0, size=count)
+    bad = set(rng.permutation(count)[:int(round(infeasible_frac * count))].tolist())
+    out = []
+    for k in range(count):
+        m = int(ms[k])
+        n = int(round(m * ratio[k]))
+        lp = planted_dense_f32(m, n, seed=seed_for(BATCH_UNEVEN, 100000 + k) if seed is None else seed + 1 + k)
+        if k in bad:
+            r2 = np.random.default_rng((seed_for(BATCH_UNEVEN, 200000 + k) if seed is None else seed + 10**6 + k))
+            lp.A[0, :] = np.abs(r2.standard_normal(n, dtype=np.float32)).astype(np.float64)
+            lp.b = lp.b.copy()
+            lp.b[0] = -1.0
+            lp.x0 = lp.y0 = lp.s0 = None
+            lp.expect = "primal_infeasible"
+        lp.meta.update(batch_index=k)
+        out.append(lp)
+    return out

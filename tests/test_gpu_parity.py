@@ -176,3 +176,50 @@ def test_batch_uneven_matches_single(abip):
     for lp, info, x in zip(lps, infos, xs):
         ref = O.solve(lp.A, lp.b, lp.c)
         _check_end(info, ref)
+
+
+def test_batch_mixed_precision_matches_oracle(abip):
+    """FP32 iterates with FP64 termination decisions: same status as the FP64 oracle and
+    final relative residuals within 1e-6 (recomputed in FP64 on the device), objective
+    within 1e-5."""
+    lps = W.batch_uneven(count=24, m_lo=16, m_hi=96, seed=W.seed_for(W.BATCH_UNEVEN, 7))
+    prm = abip.default_params(precision=abip.ABIP_PREC_MIXED)
+    infos, xs, ys, ss = abip.abip_solve_batch([l.A for l in lps], [l.b for l in lps], [l.c for l in lps], prm)
+    for lp, info, x in zip(lps, infos, xs):
+        ref = O.solve(lp.A, lp.b, lp.c)
+        assert info["status"] == ref.status, (lp.meta, info["status"], ref.status)
+        if ref.status == O.OPTIMAL:
+            assert max(info["pres"], info["dres"], info["dgap"]) <= 1e-6
+            assert abs(info["obj"] - ref.obj) <= OBJ_TOL * max(1.0, abs(ref.obj))
+            # independent FP64 residual of the returned candidate on the host
+            assert np.linalg.norm(lp.A @ x - lp.b) <= 2e-6 * (1 + np.linalg.norm(lp.b))
+
+
+def test_batch_fp64_and_mixed_agree_with_single(abip):
+    lp = W.planted_dense_f32(40, 110, seed=W.seed_for(W.BATCH_UNEVEN, 11))
+    s = abip.Solver(lp.A, lp.b, lp.c, precision=abip.ABIP_PREC_MIXED)
+    info, *_ = s.solve()
+    ref = O.solve(lp.A, lp.b, lp.c)
+    assert info["status"] == ref.status == O.OPTIMAL
+    assert abs(info["obj"] - ref.obj) <= OBJ_TOL * max(1.0, abs(ref.obj))
+
+
+def test_set_state_resumes_the_iteration(abip):
+    """get_state after k updates, set_state on a fresh handle and k more updates give the
+    state after 2k updates (dense path: the projection has no PCG warm start)."""
+    lp = W.planted_dense()
+    a = abip.Solver(lp.A, lp.b, lp.c, max_admm_iters=30)
+    a.solve()
+    s30 = a.state()
+    b = abip.Solver(lp.A, lp.b, lp.c, max_admm_iters=60)
+    b.solve()
+    c = abip.Solver(lp.A, lp.b, lp.c, max_admm_iters=30)
+    c.set_state(s30)
+    c.solve()
+    assert _rel(c.state(), b.state()) <= 1e-13
+    ref = O.solve(lp.A, lp.b, lp.c, O.Params(max_admm_iters=60), trace_iters=60)
+    assert _rel(c.stacked_state(), ref.trace[-1]) <= ITER_TOL
+    bad = s30.copy()
+    bad[lp.m] = -1.0                       # x_0 < 0 is rejected
+    with pytest.raises(abip.AbipError):
+        c.set_state(bad)
