@@ -118,6 +118,7 @@ typedef struct {
     double setup_s, solve_s;/* wall-clock seconds of abip_setup and of the last solve */
     double kernel_s;        /* device time of the solve kernel, from CUDA events on the solve stream */
     int64_t launches;       /* kernels the solve call launched */
+    int64_t fp32_iters;     /* ADMM updates done with FP32 iterates (mixed precision) */
 } abip_info;
 
 typedef struct abip_handle abip_handle;

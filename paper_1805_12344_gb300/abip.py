@@ -72,7 +72,7 @@ class abip_info(C.Structure):
                 ("cg_iters", C.c_int64), ("tau", C.c_double), ("kappa", C.c_double), ("theta", C.c_double),
                 ("mu", C.c_double), ("obj", C.c_double), ("pres", C.c_double), ("dres", C.c_double),
                 ("dgap", C.c_double), ("setup_s", C.c_double), ("solve_s", C.c_double),
-                ("kernel_s", C.c_double), ("launches", C.c_int64)]
+                ("kernel_s", C.c_double), ("launches", C.c_int64), ("fp32_iters", C.c_int64)]
 
     def as_dict(self) -> dict:
         d = {k: getattr(self, k) for k, _ in self._fields_}

@@ -450,8 +450,11 @@ struct DenseHostInst {
 
 constexpr size_t kDenseSmemLimit = 200 * 1024;
 
+// shared memory of the dense solve: 5m + 3n elements; the mixed path also needs the
+// FP64 size because an instance may finish in FP64 after escalation
 size_t dense_solve_smem(int m, int n, bool mixed = false) {
-  return (size_t)(5 * m + 3 * n) * (mixed ? sizeof(float) : sizeof(double));
+  (void)mixed;
+  return (size_t)(5 * m + 3 * n) * sizeof(double);
 }
 size_t dense_setup_smem(int m, int n) {
   return std::max((size_t)(2 * 32 * 33), (size_t)(2 * m + n)) * sizeof(double);
@@ -765,6 +768,7 @@ int abip_solve(abip_handle* h, double* x, double* y, double* s, abip_info* info,
     inf.status = hc.status; inf.outer_iters = hc.outer_iters; inf.admm_iters = hc.admm_iters; inf.cg_iters = hc.cg_iters;
     inf.tau = hc.tau; inf.kappa = hc.kappa; inf.theta = hc.theta; inf.mu = hc.mu;
     inf.obj = hc.ctx / hc.tau; inf.pres = hc.pres; inf.dres = hc.dres; inf.dgap = hc.dgap;
+    inf.fp32_iters = h->mixed ? hc.admm_iters : 0;
     double sx = 1.0 / hc.tau, sy = 1.0 / hc.tau;
     if (hc.status == ABIP_PRIMAL_INFEASIBLE) { sx = 1.0; sy = 1.0 / hc.bty; }
     if (hc.status == ABIP_DUAL_INFEASIBLE) { sx = -1.0 / hc.ctx; sy = 1.0; }
@@ -802,6 +806,8 @@ int abip_solve(abip_handle* h, double* x, double* y, double* s, abip_info* info,
     const DenseInst& I = h->hinst;
     if (I.err != 0) return fail(h, device_error_code(I.err), std::string("solve: ") + device_error_str(I.err));
     inf.status = I.status; inf.outer_iters = I.outer_iters; inf.admm_iters = I.admm_iters; inf.cg_iters = 0;
+    inf.fp32_iters = h->mixed ? (((int64_t)I.fp32_iters_hi << 31) | I.fp32_iters_lo) : 0;
+    if (h->mixed && !I.fp32_iters_lo && !I.fp32_iters_hi) inf.fp32_iters = I.admm_iters;
     inf.tau = I.tau; inf.kappa = I.kappa; inf.theta = I.theta; inf.mu = I.mu;
     inf.obj = I.obj; inf.pres = I.pres; inf.dres = I.dres; inf.dgap = I.dgap;
     rc = copy_out(h, x, I.out_x, n, st);
@@ -879,6 +885,8 @@ int abip_solve_batch(int32_t count, const abip_matrix* A, const double* const* b
         abip_info& f = infos[k];
         std::memset(&f, 0, sizeof(f));
         f.status = I.status; f.outer_iters = I.outer_iters; f.admm_iters = I.admm_iters;
+        f.fp32_iters = mixed ? (((int64_t)I.fp32_iters_hi << 31) | I.fp32_iters_lo) : 0;
+        if (mixed && !I.fp32_iters_lo && !I.fp32_iters_hi) f.fp32_iters = I.admm_iters;
         f.tau = I.tau; f.kappa = I.kappa; f.theta = I.theta; f.mu = I.mu;
         f.obj = I.obj; f.pres = I.pres; f.dres = I.dres; f.dgap = I.dgap;
         f.solve_s = el;

@@ -123,6 +123,11 @@ struct DenseInst {
   int32_t err;
   int32_t resume;              // 1: start from y, x, s and the scalars below instead of Algorithm 2's start
   double r_tau, r_kappa, r_theta, r_mu;
+  int64_t r_iters;             // counters carried into a resumed solve
+  int32_t r_outer;
+  int32_t fp32_iters_hi;       // mixed path: ADMM updates done in FP32 (low and high 31 bits)
+  int32_t fp32_iters_lo;
+  int32_t pad3;
 };
 
 struct DenseParams {

@@ -347,41 +347,48 @@ struct Solver {
   // Returns false on barrier failure.  tot[] receives
   //   0 ||Qu-v||^2 (vector blocks), 1 ||Ax/tau - b||^2, 2 ||(A^T y + s)/tau - c||^2,
   //   3 ||Ax||^2, 4 ||A^T y + s||^2, 5 b^T y, 6 bbar^T y, 7 c^T x, 8 cbar^T x.
-  __device__ bool residuals(double tau, double theta, double (&tot)[9]) {
-    double acc[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+  template <typename Acc>
+  __device__ bool residuals(double tau, double theta, double (&tot)[9], int phase = P_RES) {
+    Acc acc[9] = {Acc(0), Acc(0), Acc(0), Acc(0), Acc(0), Acc(0), Acc(0), Acc(0), Acc(0)};
+    const Acc ta = (Acc)tau, th_ = (Acc)theta;
     {
-      auto e = [&](int i, double ax, double as) {
+      auto g0 = [&](int j) { return D.x[j]; };
+      auto g1 = [&](int j) { return D.s[j]; };
+      auto e = [&](int i, Acc ax, Acc as) {
         D.Ax[i] = (T)ax; D.As[i] = (T)as;
-        const double axd = ax;
-        const double bi = (double)D.b[i];
-        const double ry = axd - bi * tau + (double)D.bbar[i] * theta;
-        const double pr = axd / tau - bi;
-        const double yi = (double)D.y[i];
+        const Acc bi = (Acc)D.b[i];
+        const Acc ry = ax - bi * ta + (Acc)D.bbar[i] * th_;
+        const Acc pr = ax / ta - bi;
+        const Acc yi = (Acc)D.y[i];
         acc[0] += ry * ry;
         acc[1] += pr * pr;
-        acc[3] += axd * axd;
+        acc[3] += ax * ax;
         acc[5] += bi * yi;
-        acc[6] += (double)D.bbar[i] * yi;
+        acc[6] += (Acc)D.bbar[i] * yi;
       };
-      rowsA2_d(D.x, D.s, e);
+      sell_rows_g<8, 2, Acc, V>(D.A, g0, g1, e);
     }
     {
-      auto e = [&](int j, double aty, double) {
+      auto g = [&](int i) { return D.y[i]; };
+      auto e = [&](int j, Acc aty, Acc) {
         D.ATy[j] = (T)aty;
-        const double atyd = aty, sj = (double)D.s[j], cj = (double)D.c[j];
-        const double rx = -atyd + cj * tau - (double)D.cbar[j] * theta - sj;
-        const double dr = (atyd + sj) / tau - cj;
-        const double xj = (double)D.x[j];
+        const Acc sj = (Acc)D.s[j], cj = (Acc)D.c[j];
+        const Acc rx = -aty + cj * ta - (Acc)D.cbar[j] * th_ - sj;
+        const Acc dr = (aty + sj) / ta - cj;
+        const Acc xj = (Acc)D.x[j];
         acc[0] += rx * rx;
         acc[2] += dr * dr;
-        acc[4] += (atyd + sj) * (atyd + sj);
+        acc[4] += (aty + sj) * (aty + sj);
         acc[7] += cj * xj;
-        acc[8] += (double)D.cbar[j] * xj;
+        acc[8] += (Acc)D.cbar[j] * xj;
       };
-      rowsAT_d(D.y, e);
+      sell_rows_g<8, 1, Acc, V>(D.AT, g, g, e);
     }
-    grid_partial<9>(acc, D.partials, S_RES, red);
-    if (!sync(P_RES)) return false;
+    double accd[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) accd[k] = (double)acc[k];
+    grid_partial<9>(accd, D.partials, S_RES, red);
+    if (!sync(phase)) return false;
     totals<9>(tot, S_RES);
     return true;
   }
@@ -470,25 +477,52 @@ struct Solver {
     double tot[9];
     double inner2 = 0, pres = 0, dres = 0, dgap = 0, ctx = 0, bty = 0;
 
-    auto evaluate = [&](bool final_test) -> bool {
-      if (!residuals(tau, theta, tot)) return false;
-      bty = tot[5];
-      ctx = tot[7];
-      const double rt = tot[5] - tot[7] + zbar * theta - kappa;
-      const double rth = -tot[6] + tot[8] - zbar * tau - xi;
-      inner2 = tot[0] + rt * rt + rth * rth;
-      pres = sqrt(tot[1]) / (1.0 + nb);
-      dres = sqrt(tot[2]) / (1.0 + nc);
+    // Sec. 4.1 tests on the sums, with a margin factor (1 = the tests themselves)
+    auto tests = [&](const double (&a)[9], double margin) -> int {
+      const double ps = sqrt(a[1]) / (1.0 + nb), ds = sqrt(a[2]) / (1.0 + nc);
+      const double gp = fabs(a[7] / tau - a[5] / tau) / (1.0 + fabs(a[7] / tau) + fabs(a[5] / tau));
+      if (ps <= margin * eps && ds <= margin * eps && gp <= margin * eps) return ABIP_OPTIMAL;
+      if (a[5] > 0 && sqrt(a[4]) <= margin * eps * a[5] / nb) return ABIP_PRIMAL_INFEASIBLE;
+      if (a[7] < 0 && sqrt(a[3]) <= margin * eps * (-a[7]) / nc) return ABIP_DUAL_INFEASIBLE;
+      return 0;
+    };
+    auto absorb = [&](const double (&a)[9], bool with_inner) {
+      bty = a[5];
+      ctx = a[7];
+      if (with_inner) {
+        const double rt = a[5] - a[7] + zbar * theta - kappa;
+        const double rth = -a[6] + a[8] - zbar * tau - xi;
+        inner2 = a[0] + rt * rt + rth * rth;
+      }
+      pres = sqrt(a[1]) / (1.0 + nb);
+      dres = sqrt(a[2]) / (1.0 + nc);
       const double gap = fabs(ctx / tau - bty / tau);
       dgap = gap / (1.0 + fabs(ctx / tau) + fabs(bty / tau));
+    };
+    // Residual sums of the current iterate.  FP64 path: FP64 accumulation, tests
+    // decided on them.  FP32 path: FP32 sums every update (inner test and screen);
+    // when they pass a Sec. 4.1 test within a factor 4, the sums are recomputed with
+    // FP64 accumulation (exact products of the FP32 data) and those decide.
+    auto evaluate = [&](bool final_test) -> bool {
+      if (sizeof(T) == 8) {
+        if (!residuals<double>(tau, theta, tot)) return false;
+      } else {
+        if (!residuals<T>(tau, theta, tot)) return false;
+      }
+      absorb(tot, true);
       if (!isfinite(inner2) || !isfinite(pres) || !isfinite(dres)) {
         flag(DEV_ERR_NONFINITE);
         return false;
       }
       if (final_test && C->stop_rule == 0) {
-        if (pres <= eps && dres <= eps && dgap <= eps) status = ABIP_OPTIMAL;
-        else if (bty > 0 && sqrt(tot[4]) <= eps * bty / nb) status = ABIP_PRIMAL_INFEASIBLE;
-        else if (ctx < 0 && sqrt(tot[3]) <= eps * (-ctx) / nc) status = ABIP_DUAL_INFEASIBLE;
+        if (sizeof(T) == 8) {
+          status = tests(tot, 1.0);
+        } else if (tests(tot, 4.0) != 0) {
+          double d[9];
+          if (!residuals<double>(tau, theta, d)) return false;
+          absorb(d, false);
+          status = tests(d, 1.0);
+        }
       }
       return true;
     };

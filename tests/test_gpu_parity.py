@@ -182,7 +182,7 @@ def test_batch_mixed_precision_matches_oracle(abip):
     """FP32 iterates with FP64 termination decisions: same status as the FP64 oracle and
     final relative residuals within 1e-6 (recomputed in FP64 on the device), objective
     within 1e-5."""
-    lps = W.batch_uneven(count=24, m_lo=16, m_hi=96, seed=W.seed_for(W.BATCH_UNEVEN, 7))
+    lps = W.batch_uneven(count=10, infeasible_frac=0.3, m_lo=16, m_hi=48, seed=W.seed_for(W.BATCH_UNEVEN, 7))
     prm = abip.default_params(precision=abip.ABIP_PREC_MIXED)
     infos, xs, ys, ss = abip.abip_solve_batch([l.A for l in lps], [l.b for l in lps], [l.c for l in lps], prm)
     for lp, info, x in zip(lps, infos, xs):
