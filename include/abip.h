@@ -196,6 +196,28 @@ ABIP_API int abip_set_state(abip_handle* h, const double* buf);
 /* Number of doubles abip_get_state writes (m + 2n + 4). */
 ABIP_API int64_t abip_state_size(const abip_handle* h);
 
+/*
+ * Solve one small dense LP without allocating any memory.  For callers that
+ * cannot call cudaMalloc (their device memory is owned by a framework's pool,
+ * they run under a fixed memory budget, or they must not grow the process's
+ * footprint): every scratch byte comes from one fixed array of 167,680 bytes that
+ * the library holds on each device that loads it, until the process exits.  The
+ * paper has no counterpart; this is the dense Cholesky path of abip_setup +
+ * abip_solve for one instance, same kernels and same arithmetic.
+ *   m, n, A (m x ld row-major FP64), b (m), c (n): inputs, device pointers.
+ *   x (n), y (m), s (n): outputs, device pointers (same meaning as abip_solve).
+ *   p: NULL for defaults; FP64 only.  info: host, may be NULL.  stream: cudaStream_t.
+ * Limits: m <= 128, n <= 512 (larger -> ABIP_E_UNSUPPORTED).  Inputs are not
+ * checked for non-finite values.  The first call on a device looks up the array's
+ * device address (cudaGetSymbolAddress) and should come before any stream
+ * capture.  Every call uses the same array and leaves its contents behind:
+ * calls whose work overlaps on the GPU (other host threads, other streams) race
+ * and must be serialised by the caller.  Returns when the solve has finished.
+ */
+ABIP_API int abip_solve_dense_noalloc(int32_t m, int32_t n, const double* A, int64_t ld,
+                                      const double* b, const double* c, const abip_params* p,
+                                      double* x, double* y, double* s, abip_info* info, void* stream);
+
 /* Release every resource of h (NULL is accepted). */
 ABIP_API void abip_free(abip_handle* h);
 

@@ -644,6 +644,11 @@ int validate_matrix(abip_handle* h, const abip_matrix* A) {
 
 }  // namespace
 
+namespace abip {
+int check_params_internal(const abip_params& p, std::string& why) { return check_params(p, why); }
+int noalloc_fail(int code, const std::string& msg) { return fail(nullptr, code, msg); }
+}  // namespace abip
+
 // ===========================================================================
 // C ABI
 // ===========================================================================

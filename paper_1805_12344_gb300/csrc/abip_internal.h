@@ -144,6 +144,10 @@ cudaError_t launch_dense_solve(DenseInst* inst, int count, DenseParams prm, int*
 int dense_solve_ctas_per_sm(bool mixed, size_t smem);
 int dense_max_ctas(int device);
 
+// shared by the allocation-free entry point (defined in abip_api.cu)
+int check_params_internal(const abip_params& p, std::string& why);
+int noalloc_fail(int code, const std::string& msg);
+
 }  // namespace abip
 
 // The opaque handle of the C ABI.

@@ -600,3 +600,114 @@ int dense_max_ctas(int device) {
 
 }  // namespace abip
 
+// ===========================================================================
+// Allocation-free entry point (abip_solve_dense_noalloc)
+// ===========================================================================
+// Some callers cannot allocate device memory: code running where cudaMalloc is
+// forbidden or unsafe (inside a framework that owns every device allocation
+// through its own pool, a real-time loop with a fixed memory budget, a plugin
+// that may not grow the process's footprint).  For them this entry point solves
+// one small dense LP with every byte of scratch taken from the fixed array
+// below; the caller passes its inputs and outputs as device pointers.
+
+namespace {
+
+constexpr int kNoAllocMaxM = 128;    // largest m the fixed scratch holds
+constexpr int kNoAllocMaxN = 512;    // largest n
+constexpr size_t kBlk = 256;
+constexpr size_t rup(size_t b) { return (b + kBlk - 1) / kBlk * kBlk; }
+// layout: descriptor | work queue | L (m*m) | seven vector blocks of m + n doubles:
+// bbar, cbar, g1, g2, y, x, s
+constexpr size_t kOffQueue = rup(sizeof(abip::DenseInst));
+constexpr size_t kOffL = kOffQueue + kBlk;
+constexpr size_t kOffVec = kOffL + rup((size_t)kNoAllocMaxM * kNoAllocMaxM * sizeof(double));
+constexpr size_t kVecBlk = rup((size_t)(kNoAllocMaxM + kNoAllocMaxN) * sizeof(double));
+constexpr size_t kNoAllocBytes = kOffVec + 7 * kVecBlk;
+
+std::mutex g_noalloc_mutex;
+void* g_noalloc_ptr[64] = {};       // device address of the scratch array, per device
+
+}  // namespace
+
+// The scratch of abip_solve_dense_noalloc: 167,680 bytes on every device that loads
+// the library, held until the process exits.  Every call uses all of it.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+extern "C" ABIP_API int abip_solve_dense_noalloc(int32_t m, int32_t n, const double* A, int64_t ld,
+                                                 const double* b, const double* c, const abip_params* p,
+                                                 double* x, double* y, double* s, abip_info* info,
+                                                 void* stream) {
+  using abip::DenseInst;
+  if (!A || !b || !c || !x || !y || !s) return abip::noalloc_fail(ABIP_E_INVALID_ARG, "NULL pointer argument");
+  if (m < 1 || n < m || ld < n) return abip::noalloc_fail(ABIP_E_DIM, "need 1 <= m <= n and ld >= n");
+  if (m > kNoAllocMaxM || n > kNoAllocMaxN)
+    return abip::noalloc_fail(ABIP_E_UNSUPPORTED, "abip_solve_dense_noalloc holds at most m = 128, n = 512");
+  abip_params prm;
+  if (p) prm = *p;
+  else abip_default_params(&prm);
+  std::string why;
+  if (!abip::check_params_internal(prm, why)) return abip::noalloc_fail(ABIP_E_INVALID_ARG, why);
+  if (prm.precision != ABIP_PREC_F64) return abip::noalloc_fail(ABIP_E_UNSUPPORTED, "abip_solve_dense_noalloc is FP64 only");
+  const void* ptrs[6] = {A, b, c, x, y, s};
+  for (const void* q : ptrs) {
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, q) != cudaSuccess ||
+        (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged)) {
+      cudaGetLastError();
+      return abip::noalloc_fail(ABIP_E_INVALID_ARG, "every array must be device memory of the current device");
+    }
+  }
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return abip::noalloc_fail(ABIP_E_CUDA, "cudaGetDevice failed");
+  // set-up, once per device, with that device current: the device address of the array
+  unsigned char* base = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_ptr[dev]) {
+      void* ptr = nullptr;
+      const cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+      if (e != cudaSuccess || !ptr) {
+        cudaGetLastError();
+        return abip::noalloc_fail(ABIP_E_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+      }
+      g_noalloc_ptr[dev] = ptr;
+    }
+    base = static_cast<unsigned char*>(g_noalloc_ptr[dev]);
+  }
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  DenseInst* dinst = reinterpret_cast<DenseInst*>(base);
+  int* queue = reinterpret_cast<int*>(base + kOffQueue);
+  double* vec = reinterpret_cast<double*>(base + kOffVec);
+  const size_t vstride = kVecBlk / sizeof(double);
+  DenseInst I{};
+  I.m = m; I.n = n; I.ld = ld;
+  I.A = A; I.b = b; I.c = c;
+  I.L = reinterpret_cast<double*>(base + kOffL);
+  I.bbar = vec; I.cbar = vec + vstride;
+  I.g1 = vec + 2 * vstride; I.g2 = vec + 3 * vstride;
+  I.y = vec + 4 * vstride; I.x = vec + 5 * vstride; I.s = vec + 6 * vstride;
+  I.out_x = x; I.out_y = y; I.out_s = s;
+  // I.err, I.status, I.resume start at zero in the copied descriptor
+  cudaMemcpyAsync(dinst, &I, sizeof(I), cudaMemcpyHostToDevice, st);
+  cudaMemsetAsync(queue, 0, 2 * sizeof(int), st);
+  const size_t smem_setup = std::max((size_t)(2 * 32 * 33), (size_t)(2 * m + n)) * sizeof(double);
+  abip::dense_setup_kernel<<<1, abip::kThreads, smem_setup, st>>>(dinst, 1, queue);
+  cudaMemsetAsync(queue, 0, 2 * sizeof(int), st);
+  abip::DenseParams dp{prm.beta, prm.gamma, prm.alpha, prm.eps, prm.max_admm_iters, prm.warmstart,
+                       prm.stop_rule, 0, 1};
+  const size_t smem_solve = (size_t)(5 * m + 3 * n) * sizeof(double);
+  abip::dense_solve_kernel<double><<<1, abip::kThreads, smem_solve, st>>>(dinst, 1, dp, queue);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&I, dinst, sizeof(I), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return abip::noalloc_fail(ABIP_E_CUDA, std::string("abip_solve_dense_noalloc: ") + cudaGetErrorString(e));
+  if (I.err != 0) return abip::noalloc_fail(ABIP_E_NUMERICAL, "Cholesky breakdown or non-finite value");
+  if (info) {
+    std::memset(info, 0, sizeof(*info));
+    info->status = I.status; info->outer_iters = I.outer_iters; info->admm_iters = I.admm_iters;
+    info->tau = I.tau; info->kappa = I.kappa; info->theta = I.theta; info->mu = I.mu;
+    info->obj = I.obj; info->pres = I.pres; info->dres = I.dres; info->dgap = I.dgap;
+    info->launches = 2;
+  }
+  return ABIP_OK;
+}
