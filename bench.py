@@ -87,6 +87,25 @@ def algorithmic_bytes(m, n, nnz, admm_iters, cg_iters, outer_iters, vec_bytes, v
     return cg_iters * per_cg + admm_iters * per_admm + (outer_iters + 1) * per_outer
 
 
+# DRAM traffic of the solve kernel from the committed ncu summary (fixed fill + per-update
+# part, measured at two update counts); None when the summary does not match this build.
+TRAFFIC_KERNEL_VERSION = "grid_kernel fp32-screen"
+
+
+def traffic_from_profile(precision, admm_updates):
+    path = os.path.join(ROOT, "profiles", "grid_kernel_solve_sparse_m100000.md")
+    try:
+        for line in open(path):
+            if line.startswith("traffic_model:"):
+                tm = json.loads(line.split(":", 1)[1])
+                if tm.get("kernel_version") != TRAFFIC_KERNEL_VERSION or tm.get("precision") != precision:
+                    return None
+                return tm["dram_bytes_fixed"] + tm["dram_bytes_per_admm_update"] * admm_updates
+    except Exception:
+        return None
+    return None
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -343,15 +362,7 @@ def main():
     alg = algorithmic_bytes(m, n, nnz, last["admm_iters"], last["cg_iters"], last["outer_iters"], vec_bytes)
     achieved = alg / last["kernel_s"] / 1e9
     peak, peak_kind = measured_peaks()
-    traffic = None
-    tpath = os.path.join(ROOT, "profiles", "solve_kernel_traffic.json")
-    if os.path.exists(tpath):
-        try:
-            tj = json.load(open(tpath))
-            if tj.get("precision") == args.precision:
-                traffic = tj["dram_bytes_per_admm_iter"] * last["admm_iters"]
-        except Exception:
-            traffic = None
+    traffic = traffic_from_profile(args.precision, last["admm_iters"])
 
     # end to end through the public API with host buffers
     e2e = None
