@@ -97,7 +97,8 @@ typedef struct {
     int32_t cg_max_iter;    /* PCG iteration cap per solve (exceeding it -> ABIP_E_NUMERICAL); default 1000 */
     double cg_rel;          /* > 0: PCG tolerance max(cg_tol, cg_rel * relative KKT residual of the
                                current iterate) instead of cg_tol alone; default 0 (fixed) */
-    int32_t cg_warm;        /* PCG start: 0 previous solution, 1 linear extrapolation 2 z_k - z_{k-1}; default 1 */
+    int32_t cg_warm;        /* PCG start: 0 previous solution, 1 linear extrapolation 2 z_k - z_{k-1},
+                               2 quadratic extrapolation 3 z_k - 3 z_{k-1} + z_{k-2}; default 2 */
     int32_t precision;      /* ABIP_PREC_*; default ABIP_PREC_F64 */
     int32_t warmstart;      /* 0: keep-larger rescale of (x,s), (tau,kappa) and sqrt(gamma) on y, theta
                                (Sec. 5); 1: sqrt(gamma) on every component (Eq. update-next-iterate) */

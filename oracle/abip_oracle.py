@@ -73,7 +73,8 @@ class Params:
     linsys: int = 0              # 0 dense Cholesky of G, 1 Jacobi-PCG on G
     cg_tol: float = 1e-13        # reading A10: ||r|| <= cg_tol * max(1, ||rhs||)
     cg_max_iter: int = 10000
-    cg_warm: int = 1             # PCG start: 0 previous z_y, 1 linear extrapolation 2 z_k - z_{k-1} (reading A10)
+    cg_warm: int = 2             # PCG start (reading A10): 0 previous z_y, 1 linear extrapolation
+                                 # 2 z_k - z_{k-1}, 2 quadratic extrapolation 3 z_k - 3 z_{k-1} + z_{k-2}
     warmstart: int = 0           # 0 keep-larger heuristic (Sec. 5), 1 sqrt(gamma) (Eq. update-next-iterate)
     stop_rule: int = 0           # 0 Sec. 4.1 tests, 1 stop once mu < eps (outer-count check of Thm 3.6)
 
@@ -291,18 +292,23 @@ class Projection:
         self.K = np.eye(2) + S + HtG
         self.zy_prev = np.zeros(P.m)
         self.zy_prev2 = np.zeros(P.m)
+        self.zy_prev3 = np.zeros(P.m)
         self.solves = 0
         self.cg_warm = 0
 
     def start_point(self):
-        """Initial guess of the iterative M-solve (reading A10): the previous z_y, or with
-        cg_warm = 1 and two previous solves the linear extrapolation 2 z_k - z_{k-1}."""
-        if self.cg_warm == 1 and self.solves >= 2:
+        """Initial guess of the iterative M-solve (reading A10): the previous z_y; with
+        cg_warm = 1 (and two previous solves) the linear extrapolation 2 z_k - z_{k-1};
+        with cg_warm = 2 (and three) the quadratic one 3 z_k - 3 z_{k-1} + z_{k-2}."""
+        if self.cg_warm == 2 and self.solves >= 3:
+            return 3.0 * self.zy_prev - 3.0 * self.zy_prev2 + self.zy_prev3
+        if self.cg_warm >= 1 and self.solves >= 2:
             return 2.0 * self.zy_prev - self.zy_prev2
         return self.zy_prev
 
     def __call__(self, wy, wx, wt, wth):
         zy, zx = solve_M(self.P, self.lin, wy, wx, self.start_point())
+        self.zy_prev3 = self.zy_prev2
         self.zy_prev2 = self.zy_prev
         self.zy_prev = zy
         self.solves += 1

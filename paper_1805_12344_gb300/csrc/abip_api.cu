@@ -124,7 +124,7 @@ int check_params(const abip_params& p, std::string& why) {
   if (p.precision != ABIP_PREC_F64 && p.precision != ABIP_PREC_MIXED) { why = "unknown precision"; return 0; }
   if (p.linsys != ABIP_LINSYS_DENSE_CHOL && p.linsys != ABIP_LINSYS_PCG && p.linsys != -1) { why = "unknown linsys"; return 0; }
   if (p.warmstart != 0 && p.warmstart != 1) { why = "warmstart must be 0 or 1"; return 0; }
-  if (p.cg_warm != 0 && p.cg_warm != 1) { why = "cg_warm must be 0 or 1"; return 0; }
+  if (p.cg_warm < 0 || p.cg_warm > 2) { why = "cg_warm must be 0, 1 or 2"; return 0; }
   if (p.stop_rule != 0 && p.stop_rule != 1) { why = "stop_rule must be 0 or 1"; return 0; }
   return 1;
 }
@@ -253,7 +253,7 @@ void assign_vectors(GridData<T>& g, Arena& ar, int m, int n) {
   g.g1y = ar.take<T>(m); g.g1x = ar.take<T>(n); g.g2y = ar.take<T>(m); g.g2x = ar.take<T>(n);
   g.y = ar.take<T>(m); g.x = ar.take<T>(n); g.s = ar.take<T>(n);
   g.Ax = ar.take<T>(m); g.As = ar.take<T>(m); g.ATy = ar.take<T>(n);
-  g.zy = ar.take<T>(m); g.zx = ar.take<T>(n); g.zp2 = ar.take<T>(m);
+  g.zy = ar.take<T>(m); g.zx = ar.take<T>(n); g.zp2 = ar.take<T>(m); g.zp3 = ar.take<T>(m);
   g.r = ar.take<T>(m); g.p = ar.take<T>(m); g.Gp = ar.take<T>(m);
   using T2 = typename abip::Vec2<T>::type;
   g.ut = ar.take<T2>(n); g.zd = ar.take<T2>(m); g.zd2 = ar.take<T2>(m);
@@ -388,6 +388,7 @@ int solve_grid_path(abip_handle* h, cudaStream_t st) {
   }
   fill_kernel<T><<<64, 256, 0, st>>>(g.zy, m, T(0));
   fill_kernel<T><<<64, 256, 0, st>>>(g.zp2, m, T(0));
+  fill_kernel<T><<<64, 256, 0, st>>>(g.zp3, m, T(0));
   SolveCtl hc;
   cudaMemcpyAsync(&hc, h->ctl, sizeof(hc), cudaMemcpyDeviceToHost, st);
   cudaStreamSynchronize(st);
@@ -423,7 +424,7 @@ int solve_grid_path(abip_handle* h, cudaStream_t st) {
   float ms = 0.f;
   cudaEventElapsedTime(&ms, h->ev0, h->ev1);
   h->kernel_s = ms * 1e-3;
-  h->launches = resume ? 3 : 6;   // fills and the persistent solve kernel
+  h->launches = resume ? 4 : 7;   // fills and the persistent solve kernel
   if (prof) {
     unsigned long long pv[abip::kProfBuckets];
     cudaMemcpy(pv, prof, sizeof(pv), cudaMemcpyDeviceToHost);
@@ -666,7 +667,7 @@ int abip_default_params(abip_params* p) {
   p->linsys = -1;   // automatic
   p->cg_tol = 1e-10;
   p->cg_rel = 0.0;
-  p->cg_warm = 1;
+  p->cg_warm = 2;
   p->cg_max_iter = 1000;
   p->precision = ABIP_PREC_F64;
   p->warmstart = 0;

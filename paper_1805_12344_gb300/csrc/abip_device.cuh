@@ -164,6 +164,30 @@ constexpr int kGridTotalPer = 8;   // partials per lane of warp 0 in grid_total
 // Warp 0 loads every slot's partials at once (kGridTotalPer per lane, one L2
 // round trip), sums them in a fixed order and broadcasts the K totals through
 // shared memory, so every CTA gets the same totals.  Needs gridDim.x <= 32 * kGridTotalPer.
+// Same as grid_partial for per-thread values of type T: warp sums in T (FP32 in the
+// mixed-precision path, where FP64 shuffle-adds would occupy the 1/64-rate FP64 pipe),
+// the per-warp results summed in double.  The caller's next step is a grid barrier.
+template <int K, typename T>
+__device__ __forceinline__ void grid_partial_t(T (&v)[K], double* partials, int slot0, double* scratch) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int k = 0; k < K; ++k) v[k] = warp_sum(v[k]);
+  __syncthreads();
+  if (lane == 0) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) scratch[k * 32 + wid] = (double)v[k];
+  }
+  __syncthreads();
+  if (wid == 0) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      double t = lane < nw ? scratch[k * 32 + lane] : 0.0;
+      t = warp_sum(t);
+      if (lane == 0) partials[(size_t)(slot0 + k) * gridDim.x + blockIdx.x] = t;
+    }
+  }
+}
+
 template <int K>
 __device__ __forceinline__ void grid_total(double (&out)[K], const double* partials, int slot0,
                                            double* scratch) {

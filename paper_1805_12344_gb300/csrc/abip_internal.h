@@ -80,7 +80,7 @@ struct GridData {
   T* y; T* x; T* s;                                           // iterate (r = 0, xi = -n-1 implicit)
   T* Ax; T* As; T* ATy;                                       // products for the residuals
   T* zy; T* zx;                                               // M^{-1} w (zy warm-starts PCG)
-  T* zp2;                                                     // previous zy (extrapolated start)
+  T* zp2; T* zp3;                                             // the two zy before the last (extrapolated start)
   T* r; T* p; T* Gp;                                          // PCG work vectors
   typename Vec2<T>::type* ut;                                 // (u, t) per column: A^T zr and A^T p
   typename Vec2<T>::type* zd;                                 // (zr, D^{-1} Gp) per row, double-buffered

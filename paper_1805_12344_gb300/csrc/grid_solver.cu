@@ -204,6 +204,14 @@ struct Solver {
     if (threadIdx.x == 0) atomicCAS(&C->err, 0, code);
   }
 
+  // PCG start (reading A10): 0 the previous solution, 1 the linear extrapolation
+  // 2 z - zp2, 2 the quadratic one 3 z - 3 zp2 + zp3 (zp2, zp3: the two solutions before)
+  __device__ __forceinline__ static T start(const T* z, const T* zp2, const T* zp3, int extrap, int i) {
+    if (extrap == 2) return T(3) * (z[i] - zp2[i]) + zp3[i];
+    if (extrap == 1) return T(2) * z[i] - zp2[i];
+    return z[i];
+  }
+
   // Jacobi-PCG on G = I + A A^T (Sec. 4.4): z (in: warm start, out: solution),
   // right-hand side q_i = qf(i).  Stop when ||r|| <= tol * max(1, ||q||) (reading
   // A10).  Two phases and two grid barriers per iteration:
@@ -219,25 +227,26 @@ struct Solver {
   // previous z.  The extrapolated start is gathered on the fly in the first A^T
   // pass and stored by each row's owner in the first A pass.
   template <typename QF>
-  __device__ int pcg(T* z, QF qf, double tol, int maxit, bool extrap = false, T* zp2 = nullptr) {
+  __device__ int pcg(T* z, QF qf, double tol, int maxit, int extrap = 0, T* zp2 = nullptr, T* zp3 = nullptr) {
     using T2 = typename Vec2<T>::type;
     T* r = D.r; T* p = D.p; T* Gp = D.Gp;
     T2* ut = D.ut;                 // (u, t)
     T2* zd_cur = D.zd;             // (zr, D^{-1} Gp)
     T2* zd_nxt = D.zd2;
+    T acc[3] = {T(0), T(0), T(0)};
     {
       // A^T z0 into ut[].x
-      auto g = [&](int i) -> T { return extrap ? T(2) * z[i] - zp2[i] : z[i]; };
+      auto g = [&](int i) -> T { return start(z, zp2, zp3, extrap, i); };
       auto e = [&](int j, T v, T) { ut[j].x = v; };
       sell_rows_g<8, 1, T, V>(D.AT, g, g, e);
     }
     if (!sync(P_PCG_INIT)) return -1;
-    T acc[3] = {T(0), T(0), T(0)};
     {
       auto g = [&](int j) -> T { return ut[j].x; };
       auto e = [&](int i, T v, T) {
         const T qi = qf(i);
-        const T zi = extrap ? T(2) * z[i] - zp2[i] : z[i];
+        const T zi = start(z, zp2, zp3, extrap, i);
+        if (zp3) zp3[i] = zp2[i];
         if (zp2) zp2[i] = z[i];
         z[i] = zi;
         const T ri = qi - (zi + v);
@@ -249,10 +258,7 @@ struct Solver {
       };
       sell_rows_g<8, 1, T, V>(D.A, g, g, e);
     }
-    {
-      double accd[3] = {(double)acc[0], (double)acc[1], (double)acc[2]};
-      grid_partial<3>(accd, D.partials, S_PCG0, red);
-    }
+    grid_partial_t<3, T>(acc, D.partials, S_PCG0, red);
     if (!sync(P_PCG_INIT)) return -1;
     double tot[3];
     totals<3>(tot, S_PCG0);
@@ -290,8 +296,8 @@ struct Solver {
         sell_rows_g<8, 1, T, V>(D.A, g, g, e);
       }
       {
-        double a1d[1] = {(double)a1};
-        grid_partial<1>(a1d, D.partials, S_PGP, red);
+        T a1v[1] = {a1};
+        grid_partial_t<1, T>(a1v, D.partials, S_PGP, red);
       }
       if (!sync(P_CG_A)) return -1;
       double pgp[1];
@@ -322,10 +328,7 @@ struct Solver {
         a2[0] += ri * zri;
         a2[1] += ri * ri;
       }
-      {
-        double a2d[2] = {(double)a2[0], (double)a2[1]};
-        grid_partial<2>(a2d, D.partials, S_RZ, red);
-      }
+      grid_partial_t<2, T>(a2, D.partials, S_RZ, red);
       if (!sync(P_CG_UPD)) return -1;
       double t2[2];
       totals<2>(t2, S_RZ);
@@ -384,10 +387,7 @@ struct Solver {
       };
       sell_rows_g<8, 1, Acc, V>(D.AT, g, g, e);
     }
-    double accd[9];
-#pragma unroll
-    for (int k = 0; k < 9; ++k) accd[k] = (double)acc[k];
-    grid_partial<9>(accd, D.partials, S_RES, red);
+    grid_partial_t<9, Acc>(acc, D.partials, S_RES, red);
     if (!sync(phase)) return false;
     totals<9>(tot, S_RES);
     return true;
@@ -562,26 +562,27 @@ struct Solver {
       // relative KKT residual, never below cg_tol (reading A10, performance mode)
       const double kkt = fmax(pres, fmax(dres, dgap));
       const double tol = cg_rel > 0.0 ? fmax(C->cg_tol, cg_rel * kkt) : C->cg_tol;
-      const int it = pcg(D.zy, qf, tol, C->cg_max, C->cg_warm == 1 && total >= 2, D.zp2);
+      const int extrap = (C->cg_warm == 2 && total >= 3) ? 2 : (C->cg_warm >= 1 && total >= 2) ? 1 : 0;
+      const int it = pcg(D.zy, qf, tol, C->cg_max, extrap, D.zp2, D.zp3);
       if (it == -1) return;
       if (it == -2) { flag(DEV_ERR_PCG); sync(P_CG_UPD); return; }
       cgtot += it;
-      double hz[2] = {0.0, 0.0};
+      T hz[2] = {T(0), T(0)};
       {
         auto e = [&](int j, T v, T) {
           const T zxj = (D.x[j] + D.s[j]) + v;
           D.zx[j] = zxj;
-          hz[0] += (double)D.c[j] * (double)zxj;
-          hz[1] -= (double)D.cbar[j] * (double)zxj;
+          hz[0] += D.c[j] * zxj;
+          hz[1] -= D.cbar[j] * zxj;
         };
         rowsAT(D.zy, e);
       }
       for (int i = t.gtid; i < D.m; i += t.nthr) {
-        const double zyi = D.zy[i];
-        hz[0] -= (double)D.b[i] * zyi;
-        hz[1] += (double)D.bbar[i] * zyi;
+        const T zyi = D.zy[i];
+        hz[0] -= D.b[i] * zyi;
+        hz[1] += D.bbar[i] * zyi;
       }
-      grid_partial<2>(hz, D.partials, S_HZ, red);
+      grid_partial_t<2, T>(hz, D.partials, S_HZ, red);
       if (!sync(P_ZX)) return;
       double h[2];
       totals<2>(h, S_HZ);
