@@ -641,3 +641,65 @@ def central_point(A, b, c, mu: float, beta: float = 1.0, start: Optional[dict] =
         z = z + step * dz
     return dict(y=z[iy].copy(), x=z[ix].copy(), tau=float(z[it]), theta=float(z[ith]),
                 s=z[isl].copy(), kappa=float(z[ik]), residual=float(np.linalg.norm(F(z))))
+
+
+# ---------------------------------------------------------------------------
+# Differentiation of the central point (system HSD-log-kkt) with respect to (A, b, c)
+# ---------------------------------------------------------------------------
+
+def kkt_residual(P: Problem, z: np.ndarray, cmu: float) -> np.ndarray:
+    """F(z) of system HSD-log-kkt for z = (y, x, tau, theta, s, kappa): Q u - v with r = 0
+    and xi = -n-1, then x o s - cmu e and tau kappa - cmu."""
+    m, n = P.m, P.n
+    y, x = z[:m], z[m:m + n]
+    tau, theta = z[m + n], z[m + n + 1]
+    s, kap = z[m + n + 2:m + 2 * n + 2], z[m + 2 * n + 2]
+    ry, rx, rt, rth = residual_Qu_v(P, y, x, tau, theta, np.zeros(m), s, kap, P.xi)
+    return np.concatenate([ry, rx, [rt, rth], x * s - cmu, [tau * kap - cmu]])
+
+
+def kkt_jacobian(P: Problem, z: np.ndarray) -> np.ndarray:
+    """dF/dz of `kkt_residual` (dense): Q in the (y, x, tau, theta) columns, -I for s in
+    the x rows, -1 for kappa in the tau row, diag(s), diag(x) and (kappa, tau) below."""
+    m, n = P.m, P.n
+    N = m + 2 * n + 3
+    J = np.zeros((N, N))
+    J[:m + n + 2, :m + n + 2] = dense_Q(P)
+    J[m:m + n, m + n + 2:m + 2 * n + 2] = -np.eye(n)
+    J[m + n, N - 1] = -1.0
+    x, s = z[m:m + n], z[m + n + 2:m + 2 * n + 2]
+    J[m + n + 2:m + 2 * n + 2, m:m + n] = np.diag(s)
+    J[m + n + 2:m + 2 * n + 2, m + n + 2:m + 2 * n + 2] = np.diag(x)
+    J[N - 1, m + n] = z[N - 1]
+    J[N - 1, N - 1] = z[m + n]
+    return J
+
+
+def central_point_grad(A, b, c, mu: float, dl_dxstar: Callable, beta: float = 1.0,
+                       start: Optional[dict] = None) -> dict:
+    """Gradient of L(x*) with x* = x / tau at the central point of system HSD-log-kkt
+    (the barrier-smoothed solution at mu) with respect to A, b and c, by implicit
+    differentiation: solve J^T lam = dL/dz at the central point, then
+    dL/dp = -lam^T dF/dp.  F is affine in (A, b, c) for fixed z, including through
+    bbar = b - A e, cbar = c - e, zbar = c^T e + 1 (Eq. bar-b-c-z-re), which gives
+      dL/dA_ij = -(lam1_i (x_j - theta) - lam2_j y_i + lam4 y_i)
+      dL/db_i  = -(lam1_i (theta - tau) + (lam3 - lam4) y_i)
+      dL/dc_j  = -(lam2_j (tau - theta) + lam3 (theta - x_j) + lam4 (x_j - tau))
+    with lam = (lam1 (m), lam2 (n), lam3, lam4, lam5 (n), lam6) in the order of F's rows.
+    dl_dxstar(xstar) returns dL/dx*.  Dense: small and medium sizes."""
+    P = Problem(A, b, c)
+    m, n = P.m, P.n
+    cp = central_point(A, b, c, mu, beta, start=start)
+    z = np.concatenate([cp["y"], cp["x"], [cp["tau"], cp["theta"]], cp["s"], [cp["kappa"]]])
+    y, x, tau, theta = cp["y"], cp["x"], cp["tau"], cp["theta"]
+    xstar = x / tau
+    g = np.asarray(dl_dxstar(xstar), dtype=np.float64)
+    dz = np.zeros_like(z)
+    dz[m:m + n] = g / tau
+    dz[m + n] = -(g @ x) / tau ** 2
+    lam = np.linalg.solve(kkt_jacobian(P, z).T, dz)
+    l1, l2, l3, l4 = lam[:m], lam[m:m + n], lam[m + n], lam[m + n + 1]
+    dA = -(np.outer(l1, x - theta) - np.outer(y, l2) + l4 * np.outer(y, np.ones(n)))
+    db = -(l1 * (theta - tau) + (l3 - l4) * y)
+    dc = -(l2 * (tau - theta) + l3 * (theta - x) + l4 * (x - tau))
+    return dict(xstar=xstar, dA=dA, db=db, dc=dc, lam=lam, point=cp, residual=cp["residual"])

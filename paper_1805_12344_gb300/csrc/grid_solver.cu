@@ -48,10 +48,12 @@ struct Thr {
 
 // Row products for every row of a SELL matrix with L lanes per row:
 // dot0 = sum_k A_ik g0(k), dot1 = sum_k A_ik g1(k) (NV = 2), accumulated in Acc;
-// epi(row, dot0, dot1) runs on the first lane of the row.  g0/g1 map a column
-// index to the gathered value.  Each lane keeps U gathers in flight.
-template <int L, int U, int NV, typename Acc, typename V, typename G0, typename G1, typename Epi>
-__device__ __forceinline__ void sell_rows_L(const SellMat& S, G0& g0, G1& g1, Epi& epi) {
+// epi(row, dot0, dot1, pv) runs on the first lane of the row with pv = pre(row),
+// which is loaded when the slice starts so the row's own operands arrive while
+// the gathers are in flight.  g0/g1 map a column index to the gathered value.
+// Each lane keeps U gathers in flight.
+template <int L, int U, int NV, typename Acc, typename V, typename G0, typename G1, typename Pre, typename Epi>
+__device__ __forceinline__ void sell_rows_L(const SellMat& S, G0& g0, G1& g1, Pre& pre, Epi& epi) {
   const Thr th;
   constexpr int C = 32 / L;
   const V* __restrict__ val = static_cast<const V*>(S.val);
@@ -60,6 +62,8 @@ __device__ __forceinline__ void sell_rows_L(const SellMat& S, G0& g0, G1& g1, Ep
     const int64_t base = __ldg(S.sp + sl);
     const int w = (int)((__ldg(S.sp + sl + 1) - base) >> 5);
     const int row = __ldg(S.perm + sl * C + th.lane / L);
+    const bool owner = row >= 0 && (th.lane % L) == 0;
+    const auto pv = pre(owner ? row : -1);
     const int32_t* __restrict__ ci = S.ci + base + th.lane;
     const V* __restrict__ va = val + base + th.lane;
     Acc a0 = Acc(0), a1 = Acc(0);
@@ -88,20 +92,30 @@ __device__ __forceinline__ void sell_rows_L(const SellMat& S, G0& g0, G1& g1, Ep
       a0 = group_sum<L>(a0);
       if (NV == 2) a1 = group_sum<L>(a1);
     }
-    if (row >= 0 && (th.lane % L) == 0) epi(row, a0, a1);
+    if (owner) epi(row, a0, a1, pv);
   }
 }
 
+struct NoPre {};
+
+template <int U, int NV, typename Acc, typename V, typename G0, typename G1, typename Pre, typename Epi>
+__device__ __forceinline__ void sell_rows_gp(const SellMat& S, G0& g0, G1& g1, Pre& pre, Epi& epi) {
+  switch (S.lanes) {
+    case 1: sell_rows_L<1, U, NV, Acc, V>(S, g0, g1, pre, epi); break;
+    case 2: sell_rows_L<2, U, NV, Acc, V>(S, g0, g1, pre, epi); break;
+    case 4: sell_rows_L<4, U, NV, Acc, V>(S, g0, g1, pre, epi); break;
+    case 8: sell_rows_L<8, U, NV, Acc, V>(S, g0, g1, pre, epi); break;
+    case 16: sell_rows_L<16, U, NV, Acc, V>(S, g0, g1, pre, epi); break;
+    default: sell_rows_L<32, U, NV, Acc, V>(S, g0, g1, pre, epi); break;
+  }
+}
+
+// Row products without prefetched row operands: epi(row, dot0, dot1).
 template <int U, int NV, typename Acc, typename V, typename G0, typename G1, typename Epi>
 __device__ __forceinline__ void sell_rows_g(const SellMat& S, G0& g0, G1& g1, Epi& epi) {
-  switch (S.lanes) {
-    case 1: sell_rows_L<1, U, NV, Acc, V>(S, g0, g1, epi); break;
-    case 2: sell_rows_L<2, U, NV, Acc, V>(S, g0, g1, epi); break;
-    case 4: sell_rows_L<4, U, NV, Acc, V>(S, g0, g1, epi); break;
-    case 8: sell_rows_L<8, U, NV, Acc, V>(S, g0, g1, epi); break;
-    case 16: sell_rows_L<16, U, NV, Acc, V>(S, g0, g1, epi); break;
-    default: sell_rows_L<32, U, NV, Acc, V>(S, g0, g1, epi); break;
-  }
+  auto pre = [](int) { return NoPre{}; };
+  auto e = [&](int row, Acc a0, Acc a1, NoPre) { epi(row, a0, a1); };
+  sell_rows_gp<U, NV, Acc, V>(S, g0, g1, pre, e);
 }
 
 // Per-row sum and sum of squares of a SELL matrix with L lanes per row (setup only).
@@ -173,6 +187,45 @@ struct Solver {
   template <int K>
   __device__ void totals(double (&out)[K], int slot) {
     grid_total<K>(out, D.partials, slot, red);
+    mark(P_TOTALS);
+  }
+
+  // Grid totals of K slots plus E scalars derived from them by f(totals, extra),
+  // which runs on thread 0 only and is broadcast with the totals.  Every scalar
+  // that steers the iteration (CG step lengths, stop tests, the Sec. 4.1 tests,
+  // the tau/kappa step) is formed this way: once per CTA, not once per thread,
+  // which matters on a part whose FP64 rate is 1/64 of FP32.
+  template <int K, int E, typename F>
+  __device__ void totals_x(double (&out)[K], double (&ext)[E], int slot, F f) {
+    const int nb = gridDim.x;
+    if (threadIdx.x < 32) {
+      double v[K];
+#pragma unroll
+      for (int k = 0; k < K; ++k) {
+        const double* pp = D.partials + (size_t)(slot + k) * nb;
+        double acc = 0.0;
+#pragma unroll
+        for (int q = 0; q < kGridTotalPer; ++q) {
+          const int i = threadIdx.x + q * 32;
+          acc += i < nb ? __ldcg(pp + i) : 0.0;
+        }
+        v[k] = warp_sum(acc);
+      }
+      if (threadIdx.x == 0) {
+        double e[E];
+        f(v, e);
+#pragma unroll
+        for (int k = 0; k < K; ++k) red[k] = v[k];
+#pragma unroll
+        for (int i = 0; i < E; ++i) red[K + i] = e[i];
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < K; ++k) out[k] = red[k];
+#pragma unroll
+    for (int i = 0; i < E; ++i) ext[i] = red[K + i];
+    __syncthreads();
     mark(P_TOTALS);
   }
 
@@ -260,11 +313,15 @@ struct Solver {
     }
     grid_partial_t<3, T>(acc, D.partials, S_PCG0, red);
     if (!sync(P_PCG_INIT)) return -1;
-    double tot[3];
-    totals<3>(tot, S_PCG0);
-    double rz = tot[0], rr = tot[1];
-    const double bound = tol * fmax(1.0, sqrt(tot[2]));
-    if (!(sqrt(rr) > bound)) return 0;
+    double tot[3], ex0[2];
+    totals_x<3, 2>(tot, ex0, S_PCG0, [&](const double* v, double* e) {
+      const double bnd = tol * fmax(1.0, sqrt(v[2]));
+      e[0] = bnd * bnd;                       // stop when ||r||^2 <= bound^2
+      e[1] = v[1] > e[0] ? 1.0 : 0.0;
+    });
+    double rz = tot[0];
+    const double bound2 = ex0[0];
+    if (ex0[1] == 0.0) return 0;
     // u = A^T zr (so that A^T p_0 = u with p_0 = zr)
     {
       auto g = [&](int i) -> T { return zd_cur[i].x; };
@@ -284,39 +341,49 @@ struct Solver {
           const T2 w = ut[j];
           return first ? w.x : w.x + be * w.y;
         };
-        auto e = [&](int i, T v, T) {
-          const T zri = zd_cur[i].x;
-          const T pi = first ? zri : zri + be * p[i];
+        struct RowOps { T zr, p, dinv; };
+        auto pre = [&](int i) -> RowOps {
+          RowOps o{T(0), T(0), T(0)};
+          if (i >= 0) { o.zr = zd_cur[i].x; o.p = p[i]; o.dinv = D.dinv[i]; }
+          return o;
+        };
+        auto e = [&](int i, T v, T, RowOps o) {
+          const T pi = first ? o.zr : o.zr + be * o.p;
           const T gp = pi + v;
           p[i] = pi;
           Gp[i] = gp;
-          zd_cur[i].y = D.dinv[i] * gp;
+          zd_cur[i].y = o.dinv * gp;
           a1 += pi * gp;
         };
-        sell_rows_g<8, 1, T, V>(D.A, g, g, e);
+        sell_rows_gp<8, 1, T, V>(D.A, g, g, pre, e);
       }
       {
         T a1v[1] = {a1};
         grid_partial_t<1, T>(a1v, D.partials, S_PGP, red);
       }
       if (!sync(P_CG_A)) return -1;
-      double pgp[1];
-      totals<1>(pgp, S_PGP);
-      const T al = (T)(rz / pgp[0]);
+      double pgp[1], exa[1];
+      totals_x<1, 1>(pgp, exa, S_PGP, [&](const double* v, double* e) { e[0] = rz / v[0]; });
+      const T al = (T)exa[0];
       {
         // gather zr_new = zr - al * D^{-1} Gp (one pair load per nonzero)
         auto g = [&](int i) -> T {
           const T2 w = zd_cur[i];
           return w.x - al * w.y;
         };
-        auto e = [&](int j, T v, T) {
-          const T2 w = ut[j];
+        auto pre = [&](int j) -> T2 {
+          T2 w;
+          w.x = T(0); w.y = T(0);
+          if (j >= 0) w = ut[j];
+          return w;
+        };
+        auto e = [&](int j, T v, T, T2 w) {
           T2 o;
           o.x = v;
           o.y = first ? w.x : w.x + be * w.y;
           ut[j] = o;
         };
-        sell_rows_g<8, 1, T, V>(D.AT, g, g, e);
+        sell_rows_gp<8, 1, T, V>(D.AT, g, g, pre, e);
       }
       mark(P_CG_AT);
       T a2[2] = {T(0), T(0)};
@@ -330,14 +397,16 @@ struct Solver {
       }
       grid_partial_t<2, T>(a2, D.partials, S_RZ, red);
       if (!sync(P_CG_UPD)) return -1;
-      double t2[2];
-      totals<2>(t2, S_RZ);
-      be = (T)(t2[0] / rz);
+      double t2[2], exb[2];
+      totals_x<2, 2>(t2, exb, S_RZ, [&](const double* v, double* e) {
+        e[0] = v[0] / rz;
+        e[1] = v[1] > bound2 ? 1.0 : 0.0;
+      });
+      be = (T)exb[0];
       rz = t2[0];
-      rr = t2[1];
       T2* sw = zd_cur; zd_cur = zd_nxt; zd_nxt = sw;
       ++k;
-      if (!(sqrt(rr) > bound)) break;
+      if (exb[1] == 0.0) break;
     }
     return k;
   }
@@ -350,8 +419,9 @@ struct Solver {
   // Returns false on barrier failure.  tot[] receives
   //   0 ||Qu-v||^2 (vector blocks), 1 ||Ax/tau - b||^2, 2 ||(A^T y + s)/tau - c||^2,
   //   3 ||Ax||^2, 4 ||A^T y + s||^2, 5 b^T y, 6 bbar^T y, 7 c^T x, 8 cbar^T x.
-  template <typename Acc>
-  __device__ bool residuals(double tau, double theta, double (&tot)[9], int phase = P_RES) {
+  template <typename Acc, int E, typename F>
+  __device__ bool residuals(double tau, double theta, double (&tot)[9], double (&ext)[E], F f,
+                            int phase = P_RES) {
     Acc acc[9] = {Acc(0), Acc(0), Acc(0), Acc(0), Acc(0), Acc(0), Acc(0), Acc(0), Acc(0)};
     const Acc ta = (Acc)tau, th_ = (Acc)theta;
     {
@@ -389,7 +459,7 @@ struct Solver {
     }
     grid_partial_t<9, Acc>(acc, D.partials, S_RES, red);
     if (!sync(phase)) return false;
-    totals<9>(tot, S_RES);
+    totals_x<9, E>(tot, ext, S_RES, f);
     return true;
   }
 
@@ -462,13 +532,51 @@ struct Solver {
     }
   }
 
+  // Thread 0 only: the nine residual sums -> e = (inner2 = ||Qu - v||^2, pres, dres,
+  // dgap, c^T x, b^T y, finite flag, Sec. 4.1 test result with the given margin or 0).
+  __device__ __noinline__ void derive_sums(const double* a, double* e, bool with_tests, double margin,
+                                           double tau, double kappa, double theta) {
+    const double zbar = C->zbar, xi = C->xi, nb = C->nb, nc = C->nc, eps = C->eps;
+    const double rt = a[5] - a[7] + zbar * theta - kappa;
+    const double rth = -a[6] + a[8] - zbar * tau - xi;
+    e[0] = a[0] + rt * rt + rth * rth;
+    e[1] = sqrt(a[1]) / (1.0 + nb);
+    e[2] = sqrt(a[2]) / (1.0 + nc);
+    e[3] = fabs(a[7] / tau - a[5] / tau) / (1.0 + fabs(a[7] / tau) + fabs(a[5] / tau));
+    e[4] = a[7];
+    e[5] = a[5];
+    e[6] = (isfinite(e[0]) && isfinite(e[1]) && isfinite(e[2])) ? 1.0 : 0.0;
+    int st = 0;
+    if (with_tests) {
+      if (e[1] <= margin * eps && e[2] <= margin * eps && e[3] <= margin * eps) st = ABIP_OPTIMAL;
+      else if (a[5] > 0 && sqrt(a[4]) <= margin * eps * a[5] / nb) st = ABIP_PRIMAL_INFEASIBLE;
+      else if (a[7] < 0 && sqrt(a[3]) <= margin * eps * (-a[7]) / nc) st = ABIP_DUAL_INFEASIBLE;
+    }
+    e[7] = (double)st;
+  }
+
+  // Thread 0 only: t = K^{-1} (w_{tau,theta} + H^T z) from v = H^T z, and the
+  // relaxed barrier and dual steps of (tau, kappa) and theta (Sec. 4.2):
+  // e = (t1, t2, tau, kappa, theta, mu/beta).
+  __device__ __noinline__ void scalar_step(const double* v, double* e, double tau, double kappa,
+                                           double theta, double mu) {
+    const double alpha = C->alpha, beta = C->beta, xi = C->xi;
+    const double v1 = tau + kappa + v[0], v2 = theta + xi + v[1];
+    const double t1 = C->Kinv[0] * v1 + C->Kinv[1] * v2, t2 = C->Kinv[2] * v1 + C->Kinv[3] * v2;
+    const double th_ = alpha * t1 + (1.0 - alpha) * tau;
+    double tn, kn;
+    barrier_step<double>(th_ - kappa, mu / beta, tn, kn);
+    e[0] = t1; e[1] = t2; e[2] = tn; e[3] = kn;
+    e[4] = alpha * t2 + (1.0 - alpha) * theta;
+    e[5] = mu / beta;
+  }
+
   // MODE_SOLVE: Algorithm 2 from the state in D / C.
   __device__ void solve() {
     const Thr t = th;
     const double alpha = C->alpha, beta = C->beta, gamma = C->gamma, eps = C->eps;
-    const double zbar = C->zbar, xi = C->xi, nb = C->nb, nc = C->nc;
-    const double Ki0 = C->Kinv[0], Ki1 = C->Kinv[1], Ki2 = C->Kinv[2], Ki3 = C->Kinv[3];
     const double cg_rel = C->cg_rel;
+    const double sqrt_gamma = sqrt(gamma);
     double tau = C->tau, kappa = C->kappa, theta = C->theta, mu = C->mu;
     int64_t total = C->admm_iters;
     int64_t cgtot = C->cg_iters;
@@ -477,51 +585,36 @@ struct Solver {
     double tot[9];
     double inner2 = 0, pres = 0, dres = 0, dgap = 0, ctx = 0, bty = 0;
 
-    // Sec. 4.1 tests on the sums, with a margin factor (1 = the tests themselves)
-    auto tests = [&](const double (&a)[9], double margin) -> int {
-      const double ps = sqrt(a[1]) / (1.0 + nb), ds = sqrt(a[2]) / (1.0 + nc);
-      const double gp = fabs(a[7] / tau - a[5] / tau) / (1.0 + fabs(a[7] / tau) + fabs(a[5] / tau));
-      if (ps <= margin * eps && ds <= margin * eps && gp <= margin * eps) return ABIP_OPTIMAL;
-      if (a[5] > 0 && sqrt(a[4]) <= margin * eps * a[5] / nb) return ABIP_PRIMAL_INFEASIBLE;
-      if (a[7] < 0 && sqrt(a[3]) <= margin * eps * (-a[7]) / nc) return ABIP_DUAL_INFEASIBLE;
-      return 0;
-    };
-    auto absorb = [&](const double (&a)[9], bool with_inner) {
-      bty = a[5];
-      ctx = a[7];
-      if (with_inner) {
-        const double rt = a[5] - a[7] + zbar * theta - kappa;
-        const double rth = -a[6] + a[8] - zbar * tau - xi;
-        inner2 = a[0] + rt * rt + rth * rth;
-      }
-      pres = sqrt(a[1]) / (1.0 + nb);
-      dres = sqrt(a[2]) / (1.0 + nc);
-      const double gap = fabs(ctx / tau - bty / tau);
-      dgap = gap / (1.0 + fabs(ctx / tau) + fabs(bty / tau));
+    auto derive = [&](const double* a, double* e, bool with_tests, double margin) {
+      derive_sums(a, e, with_tests, margin, tau, kappa, theta);
     };
     // Residual sums of the current iterate.  FP64 path: FP64 accumulation, tests
     // decided on them.  FP32 path: FP32 sums every update (inner test and screen);
     // when they pass a Sec. 4.1 test within a factor 4, the sums are recomputed with
     // FP64 accumulation (exact products of the FP32 data) and those decide.
     auto evaluate = [&](bool final_test) -> bool {
-      if (sizeof(T) == 8) {
-        if (!residuals<double>(tau, theta, tot)) return false;
-      } else {
-        if (!residuals<T>(tau, theta, tot)) return false;
-      }
-      absorb(tot, true);
-      if (!isfinite(inner2) || !isfinite(pres) || !isfinite(dres)) {
+      const bool want = final_test && C->stop_rule == 0;
+      double e[8];
+      const double margin = sizeof(T) == 8 ? 1.0 : 4.0;
+      auto f = [&](const double* a, double* ee) { derive(a, ee, want, margin); };
+      bool ok;
+      if (sizeof(T) == 8) ok = residuals<double>(tau, theta, tot, e, f);
+      else ok = residuals<T>(tau, theta, tot, e, f);
+      if (!ok) return false;
+      inner2 = e[0]; pres = e[1]; dres = e[2]; dgap = e[3]; ctx = e[4]; bty = e[5];
+      if (e[6] == 0.0) {
         flag(DEV_ERR_NONFINITE);
         return false;
       }
-      if (final_test && C->stop_rule == 0) {
+      if (want) {
         if (sizeof(T) == 8) {
-          status = tests(tot, 1.0);
-        } else if (tests(tot, 4.0) != 0) {
-          double d[9];
-          if (!residuals<double>(tau, theta, d)) return false;
-          absorb(d, false);
-          status = tests(d, 1.0);
+          status = (int)e[7];
+        } else if (e[7] != 0.0) {
+          double d[9], e2[8];
+          auto f2 = [&](const double* a, double* ee) { derive(a, ee, true, 1.0); };
+          if (!residuals<double>(tau, theta, d, e2, f2)) return false;
+          pres = e2[1]; dres = e2[2]; dgap = e2[3]; ctx = e2[4]; bty = e2[5];
+          status = (int)e2[7];
         }
       }
       return true;
@@ -536,10 +629,10 @@ struct Solver {
         if (C->stop_rule == 1 && mu < eps) { status = ABIP_OPTIMAL; break; }
         if (outer >= kMaxOuter) { status = ABIP_MAX_ITER; break; }   // mu has underflowed
         // warm start (Sec. 5 heuristic, or Eq. update-next-iterate)
-        const T g = (T)gamma, sg = (T)sqrt(gamma);
+        const T g = (T)gamma, sg = (T)sqrt_gamma;
         if (C->warmstart == 1) {
           for (int j = t.gtid; j < D.n; j += t.nthr) { D.x[j] *= sg; D.s[j] *= sg; }
-          tau *= sqrt(gamma); kappa *= sqrt(gamma);
+          tau *= sqrt_gamma; kappa *= sqrt_gamma;
         } else {
           for (int j = t.gtid; j < D.n; j += t.nthr) {
             const T xj = D.x[j], sj = D.s[j];
@@ -548,7 +641,7 @@ struct Solver {
           if (tau >= kappa) kappa *= gamma; else tau *= gamma;
         }
         for (int i = t.gtid; i < D.m; i += t.nthr) D.y[i] *= sg;
-        theta *= sqrt(gamma);
+        theta *= sqrt_gamma;
         if (!sync(P_WARM)) return;
         if (!evaluate(false)) return;
         continue;
@@ -584,13 +677,12 @@ struct Solver {
       }
       grid_partial_t<2, T>(hz, D.partials, S_HZ, red);
       if (!sync(P_ZX)) return;
-      double h[2];
-      totals<2>(h, S_HZ);
-      // t = K^{-1} (w_{tau,theta} + H^T z)
-      const double v1 = tau + kappa + h[0], v2 = theta + xi + h[1];
-      const double t1 = Ki0 * v1 + Ki1 * v2, t2 = Ki2 * v1 + Ki3 * v2;
+      double h[2], sc[6];
+      // thread 0: t = K^{-1} (w_{tau,theta} + H^T z), and the relaxed barrier and dual
+      // steps of the scalar pair (tau, kappa) and of theta (Sec. 4.2)
+      totals_x<2, 6>(h, sc, S_HZ, [&](const double* v, double* e) { scalar_step(v, e, tau, kappa, theta, mu); });
       // u~_yx = z - [g1 g2] t; relaxation (Sec. 4.2); barrier and dual steps
-      const T a = (T)alpha, a1 = (T)(1.0 - alpha), t1T = (T)t1, t2T = (T)t2, cmu = (T)(mu / beta);
+      const T a = (T)alpha, a1 = (T)(1.0 - alpha), t1T = (T)sc[0], t2T = (T)sc[1], cmu = (T)sc[5];
       for (int i = t.gtid; i < D.m; i += t.nthr) {
         const T uy = D.zy[i] - D.g1y[i] * t1T - D.g2y[i] * t2T;
         D.y[i] = a * uy + a1 * D.y[i];
@@ -602,13 +694,7 @@ struct Solver {
         barrier_step<T>(xh - D.s[j], cmu, xn, sn);
         D.x[j] = xn; D.s[j] = sn;
       }
-      {
-        const double th_ = alpha * t1 + (1.0 - alpha) * tau;
-        double tn, kn;
-        barrier_step<double>(th_ - kappa, mu / beta, tn, kn);
-        tau = tn; kappa = kn;
-        theta = alpha * t2 + (1.0 - alpha) * theta;
-      }
+      tau = sc[2]; kappa = sc[3]; theta = sc[4];
       if (!sync(P_UPD)) return;
       ++total;
       if (!evaluate(true)) return;

@@ -252,3 +252,29 @@ def batch_uneven(count: int = 4096, infeasible_frac: float = 0.1, m_lo: int = 16
         lp.meta.update(batch_index=k)
         out.append(lp)
     return out
+
+
+def l1_svm(d: int = 64, N: int = 512, C: float = 1.0, seed: int | None = None) -> LP:
+    """L1-regularised SVM  min ||w||_1 + C sum(xi)  s.t.  y_i (w^T a_i + b0) >= 1 - xi_i,
+    xi >= 0, in standard form.  Variables x = [w+ (d), w- (d), b+, b-, xi (N), t (N)],
+    n = 2d + 2 + 2N; row i reads  y_i a_i^T (w+ - w-) + y_i (b+ - b-) + xi_i - t_i = 1.
+    Labels: N/2 of each sign in a seeded order; a_i ~ N(0.5 y_i e, I).  meta["x_target"]
+    is an N(0,1) vector of length n (the target of the differentiation loss)."""
+    rng = np.random.default_rng(seed_for(L1_SVM) if seed is None else seed)
+    labels = np.concatenate([np.ones(N // 2), -np.ones(N - N // 2)])
+    labels = labels[rng.permutation(N)]
+    feats = rng.standard_normal((N, d)) + 0.5 * labels[:, None]
+    n = 2 * d + 2 + 2 * N
+    A = np.zeros((N, n))
+    ya = labels[:, None] * feats
+    A[:, :d] = ya
+    A[:, d:2 * d] = -ya
+    A[:, 2 * d] = labels
+    A[:, 2 * d + 1] = -labels
+    A[np.arange(N), 2 * d + 2 + np.arange(N)] = 1.0
+    A[np.arange(N), 2 * d + 2 + N + np.arange(N)] = -1.0
+    b = np.ones(N)
+    c = np.concatenate([np.ones(2 * d), [0.0, 0.0], C * np.ones(N), np.zeros(N)])
+    x_target = rng.standard_normal(n)
+    return LP(A=A, b=b, c=c, expect="optimal",
+              meta=dict(kind="l1_svm", m=N, n=n, d=d, C=C, x_target=x_target))
