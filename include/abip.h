@@ -169,14 +169,41 @@ ABIP_API int abip_solve_batch(int32_t count, const abip_matrix* A, const double*
                      abip_info* infos, void* stream);
 
 /*
- * Gradient of a loss L(x) with respect to (c, b, A) at the solution returned by
- * the last abip_solve, by implicit differentiation of the ADMM fixed point at the
- * final mu.  dl_dx: n entries.  Outputs (host or device, may be NULL):
- * dl_dc (n), dl_db (m), dl_dA (m*n dense row-major; nnz for CSR).
- * Not provided by this build: returns ABIP_E_UNSUPPORTED.
+ * Gradient of a loss L(x*) of the returned primal solution x* = x / tau with respect
+ * to (c, b, A), by implicit differentiation of the central point of the HSD
+ * embedding at the final mu of the last abip_solve (the fixed point of the ADMM
+ * inner loop at that mu, system HSD-log-kkt of Sec. 3.2: Q u = v with r = 0 and
+ * xi = -n-1, x o s = tau kappa = mu / beta).  The final ADMM iterate is first
+ * polished onto that point by damped Newton steps; then J^T lam = dL/dz is solved
+ * through the m x m matrix A X S^-1 A^T (FP64 Cholesky) and a 2 x 2 system, and
+ * dL/dp = -lam^T dF/dp, counting the dependence of bbar, cbar, zbar on (A, b, c)
+ * (Eq. bar-b-c-z-re).  The handle's state is left unchanged.
+ *   dl_dx: n entries, dL/dx* (host or device).
+ *   dl_dc (n), dl_db (m), dl_dA (m*n dense row-major, every entry, also for CSR
+ *   input): caller-allocated outputs, host or device, each may be NULL.
+ * Needs a dense handle (linsys = dense, or the automatic choice for dense input):
+ * ABIP_E_UNSUPPORTED otherwise.  ABIP_E_NOT_SOLVED before the first solve;
+ * ABIP_E_INVALID_ARG for an infeasibility result (no tau > 0) or non-finite dl_dx;
+ * ABIP_E_NUMERICAL if A X S^-1 A^T is not numerically positive definite.
  */
 ABIP_API int abip_backward(abip_handle* h, const double* dl_dx,
-                  double* dl_dc, double* dl_db, double* dl_dA);
+                           double* dl_dc, double* dl_db, double* dl_dA);
+
+/*
+ * abip_backward for the instances of one abip_solve_batch call, one CTA per
+ * instance in one launch.  A, b, c, p: as given to abip_solve_batch.  x, y, s,
+ * infos: what that call returned (the outputs are x/tau, y/tau, s/tau; the raw
+ * iterate is rebuilt from them and infos[k].tau, theta, kappa, mu).  dl_dx[k]
+ * (n_k), outputs dl_dc[k] (n_k), dl_db[k] (m_k), dl_dA[k] (m_k*n_k): per-instance
+ * pointers, host or device; the output arrays and their entries may be NULL.
+ * Every instance needs status OPTIMAL or MAX_ITER.  Errors as abip_backward.
+ */
+ABIP_API int abip_backward_batch(int32_t count, const abip_matrix* A, const double* const* b,
+                                 const double* const* c, const abip_params* p,
+                                 const double* const* x, const double* const* y,
+                                 const double* const* s, const abip_info* infos,
+                                 const double* const* dl_dx, double* const* dl_dc,
+                                 double* const* dl_db, double* const* dl_dA, void* stream);
 
 /*
  * Copy the raw iterate after the last solve into buf (host or device, m + 2n + 4

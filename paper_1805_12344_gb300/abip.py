@@ -93,6 +93,11 @@ _SIGS = {
                                    C.POINTER(C.c_void_p), C.POINTER(C.c_void_p), C.POINTER(abip_info),
                                    C.c_void_p]),
     "abip_backward": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "abip_backward_batch": (C.c_int, [C.c_int32, C.POINTER(abip_matrix), C.POINTER(C.c_void_p),
+                                      C.POINTER(C.c_void_p), C.POINTER(abip_params), C.POINTER(C.c_void_p),
+                                      C.POINTER(C.c_void_p), C.POINTER(C.c_void_p), C.POINTER(abip_info),
+                                      C.POINTER(C.c_void_p), C.POINTER(C.c_void_p), C.POINTER(C.c_void_p),
+                                      C.POINTER(C.c_void_p), C.c_void_p]),
     "abip_get_state": (C.c_int, [C.c_void_p, C.c_void_p]),
     "abip_set_state": (C.c_int, [C.c_void_p, C.c_void_p]),
     "abip_state_size": (C.c_int64, [C.c_void_p]),
@@ -230,13 +235,74 @@ def abip_free(h):
 
 
 def abip_backward(h, dl_dx, dl_dc=None, dl_db=None, dl_dA=None):
-    gp, _, _ = _ptr(dl_dx)
+    """Gradients of L(x*) w.r.t. c, b, A at the central point of the last solve's final mu,
+    written into the caller's arrays (numpy or CUDA tensors, float64; None to skip)."""
+    gp, _kg, _ = _ptr(dl_dx if _is_torch(dl_dx) else np.ascontiguousarray(dl_dx, dtype=np.float64))
     _check(lib().abip_backward(h, gp, _ptr(dl_dc)[0], _ptr(dl_db)[0], _ptr(dl_dA)[0]), h)
 
 
+def _stream_arg(stream):
+    if stream is None:
+        return None
+    return stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+
+
+def _vec(a):
+    return a if _is_torch(a) else np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _info_struct(d: dict) -> abip_info:
+    f = abip_info()
+    for k, _ in abip_info._fields_:
+        if k in d:
+            setattr(f, k, d[k])
+    return f
+
+
+def abip_backward_batch(As: Sequence, bs: Sequence, cs: Sequence, xs: Sequence, ys: Sequence, ss: Sequence,
+                        infos: Sequence[dict], dl_dxs: Sequence, params: Optional[abip_params] = None,
+                        want=("c", "b", "A"), device: bool = False, stream=None):
+    """Gradients for the instances of one `abip_solve_batch` call (one launch).  xs, ys, ss,
+    infos: what that call returned.  Returns lists (dcs, dbs, dAs) with None where not wanted;
+    numpy arrays, or CUDA float64 tensors when `device`."""
+    count = len(As)
+    mats = (abip_matrix * count)()
+    keep = []
+    ptrs = {k: (C.c_void_p * count)() for k in ("b", "c", "x", "y", "s", "g", "dc", "db", "dA")}
+    outs = {"c": [], "b": [], "A": []}
+    finfo = (abip_info * count)()
+    if device:
+        import torch
+    for k in range(count):
+        M, kk = _matrix(As[k])
+        keep += kk
+        mats[k] = M
+        for name, arr in (("b", bs[k]), ("c", cs[k]), ("x", xs[k]), ("y", ys[k]), ("s", ss[k]), ("g", dl_dxs[k])):
+            a = _vec(arr)
+            keep.append(a)
+            ptrs[name][k] = _ptr(a)[0]
+        finfo[k] = _info_struct(infos[k])
+        for name, shape in (("c", (M.n,)), ("b", (M.m,)), ("A", (M.m, M.n))):
+            if name in want:
+                o = torch.empty(shape, dtype=torch.float64, device="cuda") if device else np.zeros(shape)
+                outs[name].append(o)
+                ptrs["d" + name][k] = _ptr(o)[0]
+            else:
+                outs[name].append(None)
+    rc = lib().abip_backward_batch(count, mats, ptrs["b"], ptrs["c"],
+                                   C.byref(params) if params is not None else None,
+                                   ptrs["x"], ptrs["y"], ptrs["s"], finfo, ptrs["g"],
+                                   ptrs["dc"] if "c" in want else None, ptrs["db"] if "b" in want else None,
+                                   ptrs["dA"] if "A" in want else None, _stream_arg(stream))
+    _check(rc)
+    return outs["c"], outs["b"], outs["A"]
+
+
 def abip_solve_batch(As: Sequence, bs: Sequence, cs: Sequence, params: Optional[abip_params] = None,
-                     want_solution: bool = True, stream=None):
-    """Solve dense LPs (numpy arrays) in one persistent launch.  Returns (infos, xs, ys, ss)."""
+                     want_solution: bool = True, stream=None, device_out: bool = False):
+    """Solve dense LPs (numpy arrays or torch tensors) in one persistent launch.
+    Returns (infos, xs, ys, ss); the solutions are numpy arrays, or CUDA float64 tensors
+    when `device_out`."""
     count = len(As)
     mats = (abip_matrix * count)()
     keep = []
@@ -250,15 +316,18 @@ def abip_solve_batch(As: Sequence, bs: Sequence, cs: Sequence, params: Optional[
         M, kk = _matrix(As[k])
         keep += kk
         mats[k] = M
-        b = np.ascontiguousarray(bs[k], dtype=np.float64)
-        c = np.ascontiguousarray(cs[k], dtype=np.float64)
+        b, c = _vec(bs[k]), _vec(cs[k])
         keep += [b, c]
-        bptr[k] = b.ctypes.data
-        cptr[k] = c.ctypes.data
+        bptr[k] = _ptr(b)[0]
+        cptr[k] = _ptr(c)[0]
         if want_solution:
-            x = np.zeros(M.n); y = np.zeros(M.m); s = np.zeros(M.n)
+            if device_out:
+                import torch
+                x, y, s = (torch.empty(k_, dtype=torch.float64, device="cuda") for k_ in (M.n, M.m, M.n))
+            else:
+                x, y, s = np.zeros(M.n), np.zeros(M.m), np.zeros(M.n)
             xs.append(x); ys.append(y); ss.append(s)
-            xptr[k], yptr[k], sptr[k] = x.ctypes.data, y.ctypes.data, s.ctypes.data
+            xptr[k], yptr[k], sptr[k] = _ptr(x)[0], _ptr(y)[0], _ptr(s)[0]
     infos = (abip_info * count)()
     st = None
     if stream is not None:
@@ -288,6 +357,14 @@ class Solver:
             x, y, s = np.zeros(self.n), np.zeros(self.m), np.zeros(self.n)
         info = abip_solve(self.h, x, y, s, stream=stream)
         return info, x, y, s
+
+    def backward(self, dl_dx, want=("c", "b", "A")) -> dict:
+        """dL/dc, dL/db, dL/dA (numpy) at the central point of the last solve's final mu."""
+        out = {"c": np.zeros(self.n) if "c" in want else None,
+               "b": np.zeros(self.m) if "b" in want else None,
+               "A": np.zeros((self.m, self.n)) if "A" in want else None}
+        abip_backward(self.h, dl_dx, out["c"], out["b"], out["A"])
+        return out
 
     def state(self) -> np.ndarray:
         return abip_get_state(self.h)

@@ -12,6 +12,7 @@
 #include "abip_device.cuh"
 #include "abip_internal.h"
 
+using abip::BackwardInst;
 using abip::DenseInst;
 using abip::DenseParams;
 using abip::GridData;
@@ -643,6 +644,107 @@ int validate_matrix(abip_handle* h, const abip_matrix* A) {
   return ABIP_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Differentiation at the central point: host staging shared by the single-handle and
+// batch entry points.  Each item carries its data on the host (A only when not already
+// on the device), the raw final iterate and the caller's output pointers.
+// ---------------------------------------------------------------------------
+constexpr int kNewtonMax = 40;
+constexpr double kNewtonTol = 1e-15;   // relative to 1 + tau + kappa; the floor test usually ends it first
+
+struct BwdItem {
+  int m = 0, n = 0;
+  int64_t ld = 0;
+  const double* A_dev = nullptr;          // device A (ld) when resident, else A_host (ld = n)
+  const double* b_dev = nullptr;
+  const double* c_dev = nullptr;
+  std::vector<double> A_host, b_host, c_host;
+  std::vector<double> y, x, s, g;         // raw iterate and dL/dx*
+  double tau = 0, theta = 0, kappa = 0, cmu = 0;
+  double* out_dA = nullptr;
+  double* out_db = nullptr;
+  double* out_dc = nullptr;
+};
+
+int run_backward(abip_handle* h, std::vector<BwdItem>& items, cudaStream_t st) {
+  const int count = (int)items.size();
+  Arena ar;
+  auto plan = [&](std::vector<BackwardInst>* hb) {
+    ar.take<BackwardInst>(count);
+    for (int k = 0; k < count; ++k) {
+      BwdItem& it = items[k];
+      const size_t m = it.m, n = it.n;
+      BackwardInst q{};
+      q.m = it.m; q.n = it.n; q.ld = it.ld;
+      q.A = it.A_dev ? it.A_dev : ar.take<double>(m * n);
+      q.b = it.b_dev ? it.b_dev : ar.take<double>(m);
+      q.c = it.c_dev ? it.c_dev : ar.take<double>(n);
+      q.y = ar.take<double>(m); q.x = ar.take<double>(n); q.s = ar.take<double>(n);
+      q.dl_dx = ar.take<double>(n);
+      q.dA = it.out_dA ? ar.take<double>(m * n) : nullptr;
+      q.db = it.out_db ? ar.take<double>(m) : nullptr;
+      q.dc = it.out_dc ? ar.take<double>(n) : nullptr;
+      q.K = ar.take<double>((m + n + 2) * (m + n + 2));
+      q.work = ar.take<double>(abip::backward_work_doubles(it.m, it.n));
+      q.tau = it.tau; q.theta = it.theta; q.kappa = it.kappa; q.cmu = it.cmu;
+      q.newton_max = kNewtonMax;
+      q.newton_tol = kNewtonTol;
+      if (hb) (*hb)[k] = q;
+    }
+  };
+  plan(nullptr);
+  const size_t bytes = ar.off;
+  void* arena = nullptr;
+  if (cudaMalloc(&arena, bytes) != cudaSuccess) return fail(h, ABIP_E_OOM, "backward scratch: " + std::to_string(bytes) + " bytes");
+  ar.off = 0;
+  ar.base = static_cast<char*>(arena);
+  BackwardInst* dinsts = reinterpret_cast<BackwardInst*>(arena);   // first block of the plan
+  std::vector<BackwardInst> hb(count);
+  plan(&hb);
+  int rc = ABIP_OK;
+  auto up = [&](const double* dst, const std::vector<double>& v) {
+    if (rc == ABIP_OK && !v.empty() &&
+        cudaMemcpyAsync(const_cast<double*>(dst), v.data(), v.size() * 8, cudaMemcpyHostToDevice, st) != cudaSuccess)
+      rc = fail(h, ABIP_E_CUDA, "backward upload");
+  };
+  for (int k = 0; k < count; ++k) {
+    BwdItem& it = items[k];
+    if (!it.A_dev) up(hb[k].A, it.A_host);
+    if (!it.b_dev) up(hb[k].b, it.b_host);
+    if (!it.c_dev) up(hb[k].c, it.c_host);
+    up(hb[k].y, it.y); up(hb[k].x, it.x); up(hb[k].s, it.s); up(hb[k].dl_dx, it.g);
+  }
+  if (rc == ABIP_OK && cudaMemcpyAsync(dinsts, hb.data(), sizeof(BackwardInst) * count, cudaMemcpyHostToDevice, st) != cudaSuccess)
+    rc = fail(h, ABIP_E_CUDA, "backward descriptors");
+  if (rc == ABIP_OK) {
+    const int grid = std::min(count, abip::dense_max_ctas(h ? h->device : 0));
+    cudaError_t e = abip::launch_dense_backward(dinsts, count, std::max(grid, 1), st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) rc = fail(h, ABIP_E_CUDA, std::string("backward kernel: ") + cudaGetErrorString(e));
+    if (h) h->launches = 1;
+  }
+  std::vector<BackwardInst> res(count);
+  if (rc == ABIP_OK && cudaMemcpy(res.data(), dinsts, sizeof(BackwardInst) * count, cudaMemcpyDeviceToHost) != cudaSuccess)
+    rc = fail(h, ABIP_E_CUDA, "backward results");
+  for (int k = 0; k < count && rc == ABIP_OK; ++k) {
+    if (res[k].err) {
+      rc = fail(h, ABIP_E_NUMERICAL, "instance " + std::to_string(k) + ": the KKT matrix at the central point is singular");
+      break;
+    }
+    const BwdItem& it = items[k];
+    const size_t m = it.m, n = it.n;
+    auto down = [&](double* dst, const double* src, size_t len) {
+      if (rc == ABIP_OK && dst && cudaMemcpy(dst, src, len * 8, cudaMemcpyDefault) != cudaSuccess)
+        rc = fail(h, ABIP_E_CUDA, "backward output copy");
+    };
+    down(it.out_dA, res[k].dA, m * n);
+    down(it.out_db, res[k].db, m);
+    down(it.out_dc, res[k].dc, n);
+  }
+  cudaFree(arena);
+  return rc;
+}
+
 }  // namespace
 
 namespace abip {
@@ -913,8 +1015,80 @@ int abip_solve_batch(int32_t count, const abip_matrix* A, const double* const* b
 }
 
 int abip_backward(abip_handle* h, const double* dl_dx, double* dl_dc, double* dl_db, double* dl_dA) {
-  (void)dl_dx; (void)dl_dc; (void)dl_db; (void)dl_dA;
-  return fail(h, ABIP_E_UNSUPPORTED, "abip_backward is not provided by this build");
+  if (!h || !dl_dx) return fail(h, ABIP_E_INVALID_ARG, "NULL argument");
+  if (!h->solved) return fail(h, ABIP_E_NOT_SOLVED, "no solve has run on this handle");
+  if (h->path != 1)
+    return fail(h, ABIP_E_UNSUPPORTED, "abip_backward needs a dense handle (linsys = dense): the adjoint factors the m x m matrix A D A^T");
+  const DenseInst& I = h->hinst;
+  if (I.status != ABIP_OPTIMAL && I.status != ABIP_MAX_ITER)
+    return fail(h, ABIP_E_INVALID_ARG, std::string("no gradient at a ") + abip_status_str(I.status) + " result (needs tau > 0)");
+  const int m = h->m, n = h->n;
+  std::vector<BwdItem> items(1);
+  BwdItem& it = items[0];
+  it.m = m; it.n = n; it.ld = I.ld;
+  it.A_dev = I.A; it.b_dev = I.b; it.c_dev = I.c;
+  if (fetch(I.y, m, true, it.y) != cudaSuccess || fetch(I.x, n, true, it.x) != cudaSuccess ||
+      fetch(I.s, n, true, it.s) != cudaSuccess || fetch(dl_dx, n, is_device_ptr(dl_dx), it.g) != cudaSuccess)
+    return fail(h, ABIP_E_CUDA, "reading the state or dl_dx");
+  if (!finite_all(it.g.data(), n)) return fail(h, ABIP_E_INVALID_ARG, "dl_dx has non-finite entries");
+  it.tau = I.tau; it.theta = I.theta; it.kappa = I.kappa; it.cmu = I.mu / h->prm.beta;
+  it.out_dA = dl_dA; it.out_db = dl_db; it.out_dc = dl_dc;
+  return run_backward(h, items, nullptr);
+}
+
+int abip_backward_batch(int32_t count, const abip_matrix* A, const double* const* b, const double* const* c,
+                        const abip_params* p, const double* const* x, const double* const* y,
+                        const double* const* s, const abip_info* infos, const double* const* dl_dx,
+                        double* const* dl_dc, double* const* dl_db, double* const* dl_dA, void* stream) {
+  if (count < 0) return fail(nullptr, ABIP_E_INVALID_ARG, "count < 0");
+  if (count == 0) return ABIP_OK;
+  if (!A || !b || !c || !x || !y || !s || !infos || !dl_dx)
+    return fail(nullptr, ABIP_E_INVALID_ARG, "A, b, c, x, y, s, infos or dl_dx is NULL");
+  abip_params prm;
+  if (p) prm = *p;
+  else abip_default_params(&prm);
+  std::string why;
+  if (!check_params(prm, why)) return fail(nullptr, ABIP_E_INVALID_ARG, why);
+  abip_handle tmp;
+  cudaGetDevice(&tmp.device);
+  std::vector<BwdItem> items(count);
+  for (int k = 0; k < count; ++k) {
+    const std::string at = "instance " + std::to_string(k) + ": ";
+    int rc = validate_matrix(&tmp, &A[k]);
+    if (rc) return fail(nullptr, rc, at + tmp.err);
+    if (!b[k] || !c[k] || !x[k] || !y[k] || !s[k] || !dl_dx[k]) return fail(nullptr, ABIP_E_INVALID_ARG, at + "NULL vector");
+    const abip_info& f = infos[k];
+    if (f.status != ABIP_OPTIMAL && f.status != ABIP_MAX_ITER)
+      return fail(nullptr, ABIP_E_INVALID_ARG, at + "no gradient at a " + abip_status_str(f.status) + " result (needs tau > 0)");
+    if (!(f.tau > 0) || !(f.kappa > 0) || !(f.mu > 0)) return fail(nullptr, ABIP_E_INVALID_ARG, at + "tau, kappa and mu must be > 0");
+    BwdItem& it = items[k];
+    const int m = A[k].m, n = A[k].n;
+    it.m = m; it.n = n; it.ld = n;
+    rc = read_matrix_dense(&tmp, &A[k], it.A_host);
+    if (rc) return fail(nullptr, rc, at + tmp.err);
+    if (fetch(b[k], m, is_device_ptr(b[k]), it.b_host) != cudaSuccess ||
+        fetch(c[k], n, is_device_ptr(c[k]), it.c_host) != cudaSuccess ||
+        fetch(y[k], m, is_device_ptr(y[k]), it.y) != cudaSuccess ||
+        fetch(x[k], n, is_device_ptr(x[k]), it.x) != cudaSuccess ||
+        fetch(s[k], n, is_device_ptr(s[k]), it.s) != cudaSuccess ||
+        fetch(dl_dx[k], n, is_device_ptr(dl_dx[k]), it.g) != cudaSuccess)
+      return fail(nullptr, ABIP_E_CUDA, at + "reading the inputs");
+    // the solve returned (y, x, s) / tau: undo the scaling to get the raw iterate
+    for (auto* v : {&it.y, &it.x, &it.s})
+      for (double& e : *v) e *= f.tau;
+    for (int j = 0; j < n; ++j)
+      if (!(it.x[j] > 0) || !(it.s[j] > 0)) return fail(nullptr, ABIP_E_INVALID_ARG, at + "x and s must be > 0");
+    if (!finite_all(it.b_host.data(), m) || !finite_all(it.c_host.data(), n) || !finite_all(it.y.data(), m) ||
+        !finite_all(it.g.data(), n))
+      return fail(nullptr, ABIP_E_INVALID_ARG, at + "non-finite input");
+    it.tau = f.tau; it.theta = f.theta; it.kappa = f.kappa; it.cmu = f.mu / prm.beta;
+    it.out_dA = dl_dA ? dl_dA[k] : nullptr;
+    it.out_db = dl_db ? dl_db[k] : nullptr;
+    it.out_dc = dl_dc ? dl_dc[k] : nullptr;
+  }
+  const int rc = run_backward(&tmp, items, static_cast<cudaStream_t>(stream));
+  if (rc) g_err = tmp.err;
+  return rc;
 }
 
 int64_t abip_state_size(const abip_handle* h) {

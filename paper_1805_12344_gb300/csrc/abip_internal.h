@@ -130,6 +130,25 @@ struct DenseInst {
   int32_t pad3;
 };
 
+// One instance of the central-point differentiation (dense A, FP64, device pointers).
+struct BackwardInst {
+  int32_t m, n;
+  int64_t ld;
+  const double* A; const double* b; const double* c;
+  double* y; double* x; double* s;  // in: final ADMM iterate (raw); out: Newton-polished point
+  double tau, theta, kappa;         // in/out like y, x, s
+  double cmu;                       // mu / beta of the central point
+  const double* dl_dx;              // dL/dx*, x* = x / tau (n)
+  double* dA; double* db; double* dc;   // outputs (each may be null); dA m x n row-major
+  double* K;                        // (m + n + 2)^2 scratch: the reduced Jacobian and its LU
+  double* work;                     // backward_work_doubles(m, n) doubles scratch
+  int32_t newton_max;
+  int32_t pad;
+  double newton_tol;
+  double fnorm;                     // out: ||F|| at the point differentiated
+  int32_t steps, err;               // out: Newton steps taken; 1 if a factorisation broke down
+};
+
 struct DenseParams {
   double beta, gamma, alpha, eps;
   int64_t max_admm;
@@ -143,6 +162,8 @@ cudaError_t launch_dense_solve(DenseInst* inst, int count, DenseParams prm, int*
                                size_t smem, cudaStream_t st);
 int dense_solve_ctas_per_sm(bool mixed, size_t smem);
 int dense_max_ctas(int device);
+cudaError_t launch_dense_backward(BackwardInst* insts, int count, int grid, cudaStream_t st);
+inline size_t backward_work_doubles(int m, int n) { return 2 * (size_t)m + 4 * (size_t)n + 5 * ((size_t)m + n + 2); }
 
 // shared by the allocation-free entry point (defined in abip_api.cu)
 int check_params_internal(const abip_params& p, std::string& why);

@@ -552,6 +552,501 @@ __global__ void __launch_bounds__(kThreads) dense_solve_kernel(DenseInst* insts,
   }
 }
 
+// ---------------------------------------------------------------------------
+// Differentiation at the central point (system HSD-log-kkt), one CTA per instance
+// ---------------------------------------------------------------------------
+// Unknowns z = (y, x, tau, theta, s, kappa); F(z) = (Q u - v with r = 0 and xi = -n-1;
+// x o s - cm e; tau kappa - cm), cm = mu / beta.  Eliminating ds = (r5 - S dx) / X and
+// dkappa = (r6 - kappa dtau) / tau from J dz = r leaves K (dy, dx, dtau, dtheta) =
+// (r1, r2 + r5 / x, r3 + r6 / tau, r4) with
+//   K = Q + diag(0, S X^{-1}, kappa / tau, 0)      (order m + n + 2),
+// and the adjoint J^T lam = g reduces to K^T (lam1, lam2, lam3, lam4) =
+// (g1, g2 - S X^{-1} g5, g3 - kappa g6 / tau, g4).  K is factored by LU with partial
+// pivoting in FP64: unlike the normal equations A X S^{-1} A^T, whose condition number
+// grows like 1/mu^2 on degenerate LPs, K's grows like that of J itself.
+
+// Block argmax of |v| over this thread's candidates (ties: smaller index); broadcast.
+__device__ int block_argmax(double v, int idx, double* red, int* redi) {
+  for (int o = 16; o > 0; o >>= 1) {
+    const double ov = __shfl_xor_sync(0xffffffffu, v, o);
+    const int oi = __shfl_xor_sync(0xffffffffu, idx, o);
+    if (ov > v || (ov == v && oi < idx)) { v = ov; idx = oi; }
+  }
+  if ((threadIdx.x & 31) == 0) { red[threadIdx.x >> 5] = v; redi[threadIdx.x >> 5] = idx; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double bv = red[0];
+    int bi = redi[0];
+    for (int k = 1; k < kWarps; ++k)
+      if (red[k] > bv || (red[k] == bv && redi[k] < bi)) { bv = red[k]; bi = redi[k]; }
+    red[32] = bv;
+    redi[32] = bi;
+  }
+  __syncthreads();
+  const int r = redi[32];
+  __syncthreads();
+  return r;
+}
+
+// In-place LU with partial pivoting of the N x N row-major K (P K = L U, L unit lower),
+// right-looking with 32-column panels; the trailing update runs as 64 x 64 tiles through
+// shared memory (16 x 16 threads, 4 x 4 outputs each).  ipiv[k] = row swapped with k.
+// Returns false on an exactly zero pivot.
+__device__ bool lu_factor(double* K, int N, int* ipiv, double* sm, double* red, int* redi) {
+  const int tid = threadIdx.x;
+  for (int j0 = 0; j0 < N; j0 += 32) {
+    const int jb = min(32, N - j0);
+    for (int k = j0; k < j0 + jb; ++k) {
+      double best = -1.0;
+      int bi = N;
+      for (int i = k + tid; i < N; i += kThreads) {
+        const double v = fabs(K[(size_t)i * N + k]);
+        if (v > best) { best = v; bi = i; }
+      }
+      const int piv = block_argmax(best, bi, red, redi);
+      if (tid == 0) ipiv[k] = piv;
+      if (piv != k)
+        for (int j = tid; j < N; j += kThreads) {
+          const double t = K[(size_t)k * N + j];
+          K[(size_t)k * N + j] = K[(size_t)piv * N + j];
+          K[(size_t)piv * N + j] = t;
+        }
+      __syncthreads();
+      const double p = K[(size_t)k * N + k];
+      if (p == 0.0 || !isfinite(p)) return false;
+      for (int i = k + 1 + tid; i < N; i += kThreads) K[(size_t)i * N + k] /= p;
+      __syncthreads();
+      const int nc = j0 + jb - (k + 1);
+      if (nc > 0) {
+        const int rows = N - k - 1;
+        for (int e = tid; e < rows * nc; e += kThreads) {
+          const int i = k + 1 + e / nc, j = k + 1 + e % nc;
+          K[(size_t)i * N + j] -= K[(size_t)i * N + k] * K[(size_t)k * N + j];
+        }
+      }
+      __syncthreads();
+    }
+    const int c0 = j0 + jb;
+    if (c0 >= N) break;
+    // U12 = L11^{-1} K12: one thread per column, L11 from shared memory
+    double* L11 = sm;   // 32 x 33
+    for (int e = tid; e < jb * jb; e += kThreads) {
+      const int r = e / jb, q = e % jb;
+      L11[r * 33 + q] = K[(size_t)(j0 + r) * N + j0 + q];
+    }
+    __syncthreads();
+    for (int j = c0 + tid; j < N; j += kThreads) {
+      double col[32];
+#pragma unroll
+      for (int r = 0; r < 32; ++r) col[r] = r < jb ? K[(size_t)(j0 + r) * N + j] : 0.0;
+#pragma unroll
+      for (int r = 1; r < 32; ++r) {
+        double acc = col[r];
+#pragma unroll
+        for (int q = 0; q < r; ++q) acc -= L11[r * 33 + q] * col[q];
+        col[r] = acc;
+      }
+      for (int r = 1; r < jb; ++r) K[(size_t)(j0 + r) * N + j] = col[r];
+    }
+    __syncthreads();
+    // trailing update K22 -= L21 U12
+    double* Lt = sm;             // 64 x 33
+    double* Ut = sm + 64 * 33;   // 32 x 65
+    const int tr = tid / 16, tc = tid % 16;
+    for (int i0 = c0; i0 < N; i0 += 64) {
+      for (int k0 = c0; k0 < N; k0 += 64) {
+        for (int e = tid; e < 64 * 32; e += kThreads) {
+          const int r = e / 32, q = e % 32;
+          const int gi = i0 + r;
+          Lt[r * 33 + q] = (gi < N && q < jb) ? K[(size_t)gi * N + j0 + q] : 0.0;
+        }
+        for (int e = tid; e < 32 * 64; e += kThreads) {
+          const int q = e / 64, cc = e % 64;
+          const int gk = k0 + cc;
+          Ut[q * 65 + cc] = (gk < N && q < jb) ? K[(size_t)(j0 + q) * N + gk] : 0.0;
+        }
+        __syncthreads();
+        double acc[4][4] = {};
+        for (int q = 0; q < 32; ++q) {
+          double lv[4], uv[4];
+#pragma unroll
+          for (int a = 0; a < 4; ++a) lv[a] = Lt[(tr * 4 + a) * 33 + q];
+#pragma unroll
+          for (int bq = 0; bq < 4; ++bq) uv[bq] = Ut[q * 65 + tc * 4 + bq];
+#pragma unroll
+          for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int bq = 0; bq < 4; ++bq) acc[a][bq] += lv[a] * uv[bq];
+        }
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+          const int gi = i0 + tr * 4 + a;
+          if (gi >= N) continue;
+#pragma unroll
+          for (int bq = 0; bq < 4; ++bq) {
+            const int gk = k0 + tc * 4 + bq;
+            if (gk < N) K[(size_t)gi * N + gk] -= acc[a][bq];
+          }
+        }
+        __syncthreads();
+      }
+    }
+  }
+  return true;
+}
+
+// w <- K^{-1} w from the factors of lu_factor.
+__device__ void lu_solve(const double* K, int N, const int* ipiv, double* w) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (threadIdx.x == 0)
+    for (int k = 0; k < N; ++k) {
+      const int p = ipiv[k];
+      if (p != k) { const double t = w[k]; w[k] = w[p]; w[p] = t; }
+    }
+  __syncthreads();
+  for (int kb = 0; kb < N; kb += 32) {   // L (unit diagonal)
+    const int nb = min(32, N - kb);
+    if (wid == 0) {
+      double wl = lane < nb ? w[kb + lane] : 0.0;
+      for (int j = 0; j < nb; ++j) {
+        const double wj = __shfl_sync(0xffffffffu, wl, j);
+        if (lane > j && lane < nb) wl -= K[(size_t)(kb + lane) * N + kb + j] * wj;
+      }
+      if (lane < nb) w[kb + lane] = wl;
+    }
+    __syncthreads();
+    const double wb = lane < nb ? w[kb + lane] : 0.0;
+    for (int i = kb + nb + wid; i < N; i += kWarps) {
+      double a = lane < nb ? K[(size_t)i * N + kb + lane] * wb : 0.0;
+      a = warp_sum(a);
+      if (lane == 0) w[i] -= a;
+    }
+    __syncthreads();
+  }
+  const int nblk = (N + 31) / 32;
+  for (int bk = nblk - 1; bk >= 0; --bk) {   // U
+    const int kb = bk * 32, nb = min(32, N - kb);
+    if (wid == 0) {
+      double wl = lane < nb ? w[kb + lane] : 0.0;
+      for (int j = nb - 1; j >= 0; --j) {
+        if (lane == j) wl = wl / K[(size_t)(kb + j) * N + kb + j];
+        const double zj = __shfl_sync(0xffffffffu, wl, j);
+        if (lane < j) wl -= K[(size_t)(kb + lane) * N + kb + j] * zj;
+      }
+      if (lane < nb) w[kb + lane] = wl;
+    }
+    __syncthreads();
+    const double wb = lane < nb ? w[kb + lane] : 0.0;
+    for (int i = wid; i < kb; i += kWarps) {
+      double a = lane < nb ? K[(size_t)i * N + kb + lane] * wb : 0.0;
+      a = warp_sum(a);
+      if (lane == 0) w[i] -= a;
+    }
+    __syncthreads();
+  }
+}
+
+// w <- K^{-T} w from the same factors (K^T = U^T L^T P).
+__device__ void lu_solve_t(const double* K, int N, const int* ipiv, double* w) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int kb = 0; kb < N; kb += 32) {   // U^T (lower, diagonal of U)
+    const int nb = min(32, N - kb);
+    if (wid == 0) {
+      double wl = lane < nb ? w[kb + lane] : 0.0;
+      for (int j = 0; j < nb; ++j) {
+        if (lane == j) wl = wl / K[(size_t)(kb + j) * N + kb + j];
+        const double zj = __shfl_sync(0xffffffffu, wl, j);
+        if (lane > j && lane < nb) wl -= K[(size_t)(kb + j) * N + kb + lane] * zj;
+      }
+      if (lane < nb) w[kb + lane] = wl;
+    }
+    __syncthreads();
+    for (int k = kb + nb + threadIdx.x; k < N; k += kThreads) {
+      double a = 0.0;
+      for (int j = 0; j < nb; ++j) a += K[(size_t)(kb + j) * N + k] * w[kb + j];
+      w[k] -= a;
+    }
+    __syncthreads();
+  }
+  const int nblk = (N + 31) / 32;
+  for (int bk = nblk - 1; bk >= 0; --bk) {   // L^T (upper, unit diagonal)
+    const int kb = bk * 32, nb = min(32, N - kb);
+    if (wid == 0) {
+      double wl = lane < nb ? w[kb + lane] : 0.0;
+      for (int j = nb - 1; j >= 0; --j) {
+        const double zj = __shfl_sync(0xffffffffu, wl, j);
+        if (lane < j) wl -= K[(size_t)(kb + j) * N + kb + lane] * zj;
+      }
+      if (lane < nb) w[kb + lane] = wl;
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < kb; k += kThreads) {
+      double a = 0.0;
+      for (int j = 0; j < nb; ++j) a += K[(size_t)(kb + j) * N + k] * w[kb + j];
+      w[k] -= a;
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0)
+    for (int k = N - 1; k >= 0; --k) {
+      const int p = ipiv[k];
+      if (p != k) { const double t = w[k]; w[k] = w[p]; w[p] = t; }
+    }
+  __syncthreads();
+}
+
+__device__ double block_dot(const double* a, const double* b, int len, double* red) {
+  double v[1] = {0.0};
+  for (int i = threadIdx.x; i < len; i += kThreads) v[0] += a[i] * b[i];
+  block_allsum<1>(v, red);
+  return v[0];
+}
+
+// Block minimum of one value per thread (result broadcast).
+__device__ double block_min(double a, double* red) {
+  for (int o = 16; o > 0; o >>= 1) a = fmin(a, __shfl_xor_sync(0xffffffffu, a, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = a;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double r = red[0];
+    for (int k = 1; k < kWarps; ++k) r = fmin(r, red[k]);
+    red[32] = r;
+  }
+  __syncthreads();
+  const double r = red[32];
+  __syncthreads();
+  return r;
+}
+
+__device__ void backward_one(BackwardInst& P, double* sm, double* red, int* redi) {
+  const int m = P.m, n = P.n, N = m + n + 2;
+  const int64_t ld = P.ld;
+  const double* A = P.A;
+  const double* b = P.b;
+  const double* c = P.c;
+  const double cm = P.cmu, xi = -(double)n - 1.0;
+  double* y = P.y;
+  double* x = P.x;
+  double* s = P.s;
+  double* K = P.K;
+  double* bbar = P.work;         // m
+  double* F1 = bbar + m;         // m
+  double* cbar = F1 + m;         // n
+  double* F2 = cbar + n;         // n
+  double* F5 = F2 + n;           // n
+  double* sig = F5 + n;          // n: S X^{-1}
+  double* rhs = sig + n;         // N
+  double* sol = rhs + N;         // N
+  double* res = sol + N;         // N
+  double* tmp = res + N;         // N
+  int* ipiv = reinterpret_cast<int*>(tmp + N);   // N
+  double tau = P.tau, kappa = P.kappa, theta = P.theta;
+
+  // embedding constants of Eq. bar-b-c-z-re: bbar = b - A e, cbar = c - e, zbar = c^T e + 1
+  for (int j = threadIdx.x; j < n; j += kThreads) cbar[j] = c[j] - 1.0;
+  for (int j = threadIdx.x; j < n; j += kThreads) tmp[j] = 1.0;
+  __syncthreads();
+  gemv_rows<false, double>(A, ld, m, n, tmp, tmp, bbar, bbar);
+  __syncthreads();
+  for (int i = threadIdx.x; i < m; i += kThreads) bbar[i] = b[i] - bbar[i];
+  double zs[1] = {0.0};
+  for (int j = threadIdx.x; j < n; j += kThreads) zs[0] += c[j];
+  block_allsum<1>(zs, red);
+  const double zbar = zs[0] + 1.0;
+
+  // F at the current point: F1, F2, F5 kept; the tau, theta and tau-kappa rows in Fs;
+  // returns ||F||^2
+  auto residual = [&](double (&Fs)[3]) -> double {
+    gemv_rows<false, double>(A, ld, m, n, x, x, F1, F1);
+    __syncthreads();
+    double acc[5] = {0, 0, 0, 0, 0};
+    for (int i = threadIdx.x; i < m; i += kThreads) {
+      F1[i] = F1[i] - b[i] * tau + bbar[i] * theta;
+      acc[0] += F1[i] * F1[i];
+      acc[1] += b[i] * y[i];
+      acc[2] += bbar[i] * y[i];
+    }
+    for (int j = threadIdx.x; j < n; j += kThreads) {
+      double aty = 0.0;
+      for (int i = 0; i < m; ++i) aty += A[(size_t)i * ld + j] * y[i];
+      F2[j] = -aty + c[j] * tau - cbar[j] * theta - s[j];
+      F5[j] = x[j] * s[j] - cm;
+      acc[0] += F2[j] * F2[j] + F5[j] * F5[j];
+      acc[3] += c[j] * x[j];
+      acc[4] += cbar[j] * x[j];
+    }
+    block_allsum<5>(acc, red);
+    Fs[0] = acc[1] - acc[3] + zbar * theta - kappa;
+    Fs[1] = -acc[2] + acc[4] - zbar * tau - xi;
+    Fs[2] = tau * kappa - cm;
+    return acc[0] + Fs[0] * Fs[0] + Fs[1] * Fs[1] + Fs[2] * Fs[2];
+  };
+  // K at the current point, then its LU factors
+  auto factor = [&]() -> bool {
+    for (int j = threadIdx.x; j < n; j += kThreads) sig[j] = s[j] / x[j];
+    const double kt = kappa / tau;
+    for (size_t e = threadIdx.x; e < (size_t)N * N; e += kThreads) {
+      const int r = (int)(e / N), q = (int)(e % N);
+      double v = 0.0;
+      if (r < m) {                      // y rows: [0, A, -b, bbar]
+        if (q >= m && q < m + n) v = A[(size_t)r * ld + (q - m)];
+        else if (q == m + n) v = -b[r];
+        else if (q == m + n + 1) v = bbar[r];
+      } else if (r < m + n) {           // x rows: [-A^T, S X^{-1}, c, -cbar]
+        const int j = r - m;
+        if (q < m) v = -A[(size_t)q * ld + j];
+        else if (q == r) v = s[j] / x[j];
+        else if (q == m + n) v = c[j];
+        else if (q == m + n + 1) v = -cbar[j];
+      } else if (r == m + n) {          // tau row: [b^T, -c^T, kappa/tau, zbar]
+        if (q < m) v = b[q];
+        else if (q < m + n) v = -c[q - m];
+        else if (q == m + n) v = kt;
+        else v = zbar;
+      } else {                          // theta row: [-bbar^T, cbar^T, -zbar, 0]
+        if (q < m) v = -bbar[q];
+        else if (q < m + n) v = cbar[q - m];
+        else if (q == m + n) v = -zbar;
+      }
+      K[e] = v;
+    }
+    __syncthreads();
+    return lu_factor(K, N, ipiv, sm, red, redi);
+  };
+  // out = K v (sgn = 1) or K^T v (sgn = -1): the skew part Q flips sign, the diagonal stays
+  auto kmul = [&](const double* v, double* out, double sgn) {
+    const double vt = v[m + n], vth = v[m + n + 1];
+    gemv_rows<false, double>(A, ld, m, n, v + m, v + m, out, out);
+    __syncthreads();
+    for (int i = threadIdx.x; i < m; i += kThreads) out[i] = sgn * (out[i] - b[i] * vt + bbar[i] * vth);
+    double dd[4] = {0, 0, 0, 0};
+    for (int i = threadIdx.x; i < m; i += kThreads) { dd[0] += b[i] * v[i]; dd[1] += bbar[i] * v[i]; }
+    for (int j = threadIdx.x; j < n; j += kThreads) {
+      double aty = 0.0;
+      for (int i = 0; i < m; ++i) aty += A[(size_t)i * ld + j] * v[i];
+      out[m + j] = sgn * (-aty + c[j] * vt - cbar[j] * vth) + sig[j] * v[m + j];
+      dd[2] += c[j] * v[m + j];
+      dd[3] += cbar[j] * v[m + j];
+    }
+    block_allsum<4>(dd, red);
+    if (threadIdx.x == 0) {
+      out[m + n] = sgn * (dd[0] - dd[2] + zbar * vth) + (kappa / tau) * vt;
+      out[m + n + 1] = sgn * (-dd[1] + dd[3] - zbar * vt);
+    }
+    __syncthreads();
+  };
+  // sol = K^{-1} rhs (or K^{-T}) with one step of iterative refinement
+  auto refined = [&](double sgn) {
+    for (int e = threadIdx.x; e < N; e += kThreads) sol[e] = rhs[e];
+    __syncthreads();
+    if (sgn > 0) lu_solve(K, N, ipiv, sol);
+    else lu_solve_t(K, N, ipiv, sol);
+    kmul(sol, tmp, sgn);
+    for (int e = threadIdx.x; e < N; e += kThreads) res[e] = rhs[e] - tmp[e];
+    __syncthreads();
+    if (sgn > 0) lu_solve(K, N, ipiv, res);
+    else lu_solve_t(K, N, ipiv, res);
+    for (int e = threadIdx.x; e < N; e += kThreads) sol[e] += res[e];
+    __syncthreads();
+  };
+
+  bool ok = true;
+  int steps = 0;
+  double Fs[3];
+  double fn2 = residual(Fs);
+  // Newton to the rounding floor: stop once ||F|| is small and no longer halves
+  const double scale2 = (1.0 + tau + kappa) * (1.0 + tau + kappa);
+  double prev = INFINITY;
+  for (; steps < P.newton_max; ++steps) {
+    if (fn2 <= P.newton_tol * P.newton_tol * scale2) break;
+    if (fn2 > 0.25 * prev && fn2 <= 1e-20 * scale2) break;
+    prev = fn2;
+    if (!factor()) { ok = false; break; }
+    for (int i = threadIdx.x; i < m; i += kThreads) rhs[i] = -F1[i];
+    for (int j = threadIdx.x; j < n; j += kThreads) rhs[m + j] = -F2[j] - F5[j] / x[j];
+    if (threadIdx.x == 0) {
+      rhs[m + n] = -Fs[0] - Fs[2] / tau;
+      rhs[m + n + 1] = -Fs[1];
+    }
+    __syncthreads();
+    refined(1.0);
+    const double dtau = sol[m + n], dth = sol[m + n + 1];
+    if (!isfinite(dtau) || !isfinite(dth)) { ok = false; break; }
+    const double dkap = (-Fs[2] - kappa * dtau) / tau;
+    // largest step in (0, 1] keeping x, s, tau, kappa at least 1 % inside the orthant
+    double amax = 1.0;
+    for (int j = threadIdx.x; j < n; j += kThreads) {
+      const double dx = sol[m + j];
+      const double ds = (-F5[j] - s[j] * dx) / x[j];
+      if (dx < 0) amax = fmin(amax, -0.99 * x[j] / dx);
+      if (ds < 0) amax = fmin(amax, -0.99 * s[j] / ds);
+    }
+    if (threadIdx.x == 0) {
+      if (dtau < 0) amax = fmin(amax, -0.99 * tau / dtau);
+      if (dkap < 0) amax = fmin(amax, -0.99 * kappa / dkap);
+    }
+    const double step = block_min(amax, red);
+    for (int j = threadIdx.x; j < n; j += kThreads) {
+      const double dx = sol[m + j];
+      const double ds = (-F5[j] - s[j] * dx) / x[j];
+      x[j] += step * dx;
+      s[j] += step * ds;
+    }
+    for (int i = threadIdx.x; i < m; i += kThreads) y[i] += step * sol[i];
+    tau += step * dtau;
+    theta += step * dth;
+    kappa += step * dkap;
+    __syncthreads();
+    fn2 = residual(Fs);
+  }
+  if (ok && !factor()) ok = false;
+  if (ok) {
+    // Adjoint: g = (0, g_x, g_tau, 0, 0, 0) with g_x = dL/dx* / tau and
+    // g_tau = -(dL/dx*)^T x / tau^2, so K^T (lam1, lam2, lam3, lam4) = (0, g_x, g_tau, 0)
+    for (int i = threadIdx.x; i < m; i += kThreads) rhs[i] = 0.0;
+    for (int j = threadIdx.x; j < n; j += kThreads) rhs[m + j] = P.dl_dx[j] / tau;
+    const double gtau = -block_dot(P.dl_dx, x, n, red) / (tau * tau);
+    if (threadIdx.x == 0) {
+      rhs[m + n] = gtau;
+      rhs[m + n + 1] = 0.0;
+    }
+    __syncthreads();
+    refined(-1.0);
+    const double* l1 = sol;
+    const double* l2 = sol + m;
+    const double lam3 = sol[m + n], lam4 = sol[m + n + 1];
+    if (!isfinite(lam3) || !isfinite(lam4)) ok = false;
+    // dL/dp = -lam^T dF/dp (F is affine in A, b, c through bbar, cbar, zbar too)
+    if (ok && P.db)
+      for (int i = threadIdx.x; i < m; i += kThreads) P.db[i] = -(l1[i] * (theta - tau) + (lam3 - lam4) * y[i]);
+    if (ok && P.dc)
+      for (int j = threadIdx.x; j < n; j += kThreads)
+        P.dc[j] = -(l2[j] * (tau - theta) + lam3 * (theta - x[j]) + lam4 * (x[j] - tau));
+    if (ok && P.dA)
+      for (int i = 0; i < m; ++i) {
+        const double li = l1[i], yi = y[i];
+        for (int j = threadIdx.x; j < n; j += kThreads)
+          P.dA[(size_t)i * n + j] = -(li * (x[j] - theta) - l2[j] * yi + lam4 * yi);
+      }
+  }
+  if (threadIdx.x == 0) {
+    P.fnorm = sqrt(fn2);
+    P.steps = steps;
+    P.err = ok ? 0 : 1;
+    P.tau = tau;
+    P.theta = theta;
+    P.kappa = kappa;
+  }
+  __syncthreads();
+}
+
+__global__ void __launch_bounds__(kThreads) dense_backward_kernel(BackwardInst* insts, int count) {
+  __shared__ double sm[64 * 33 + 32 * 65];
+  __shared__ double red[32 * 5];   // block_allsum<K> needs 32 K doubles; K <= 5 here
+  __shared__ int redi[40];
+  for (int k = blockIdx.x; k < count; k += gridDim.x) backward_one(insts[k], sm, red, redi);
+}
+
 }  // namespace
 
 // dynamic shared memory of the solve kernel: 5m + 3n doubles, at most this many bytes
@@ -590,6 +1085,11 @@ int dense_solve_ctas_per_sm(bool mixed, size_t smem) {
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, dense_solve_kernel<double>, kThreads, smem);
   }
   return per;
+}
+
+cudaError_t launch_dense_backward(BackwardInst* insts, int count, int grid, cudaStream_t st) {
+  dense_backward_kernel<<<grid, kThreads, 0, st>>>(insts, count);
+  return cudaGetLastError();
 }
 
 int dense_max_ctas(int device) {

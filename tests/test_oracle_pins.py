@@ -296,3 +296,57 @@ def test_tiny_lps_against_basis_enumeration(seed):
         assert r.status in (O.PRIMAL_INFEASIBLE, O.DUAL_INFEASIBLE)
     else:
         assert r.status == O.DUAL_INFEASIBLE
+
+
+# --- Differentiation of the central point (system HSD-log-kkt, Sec. 3.2) -------------
+
+def test_central_point_gradient_matches_central_differences():
+    """The adjoint gradient of L(x*) = ||x* - x_t||^2 agrees with FP64 central differences
+    (step 1e-6 max(1, |p|)) of the Newton-polished solution map, for every entry of b, c, A."""
+    lp = W.l1_svm(d=3, N=8, seed=5)
+    mu = 1e-3
+    xt = lp.meta["x_target"]
+    g = O.central_point_grad(lp.A, lp.b, lp.c, mu, lambda xs: 2.0 * (xs - xt))
+    start = {k: g["point"][k] for k in ("y", "x", "tau", "theta", "s", "kappa")}
+
+    def loss(A, b, c):
+        cp = O.central_point(A, b, c, mu, start=start, tol=1e-15)
+        return float(np.sum((cp["x"] / cp["tau"] - xt) ** 2))
+
+    base = {"A": lp.A, "b": lp.b, "c": lp.c}
+    for which, key in (("b", "db"), ("c", "dc"), ("A", "dA")):
+        P = base[which]
+        fd = np.zeros_like(P)
+        for idx in np.ndindex(P.shape):
+            h = 1e-6 * max(1.0, abs(P[idx]))
+            args = {}
+            for sgn in (1, -1):
+                Pp = P.copy()
+                Pp[idx] += sgn * h
+                args[sgn] = dict(base, **{which: Pp})
+            fd[idx] = (loss(**args[1]) - loss(**args[-1])) / (2 * h)
+        err = np.abs(fd - g[key]).max() / np.abs(g[key]).max()
+        assert err <= 1e-5, (which, err)
+
+
+def test_central_point_gradient_vertex_limit():
+    """At a nondegenerate vertex x0 (basis B, strictly complementary) the central point tends
+    to x0 with x0_B = B^{-1} b, so as mu -> 0 the gradient tends to dL/db = B^{-T} g_B,
+    dL/dA = -(B^{-T} g_B) x0^T and dL/dc = 0 (g = dL/dx at x0); the gap is O(mu)."""
+    m, n = 6, 14
+    rng = np.random.default_rng(7)
+    A = rng.standard_normal((m, n))
+    basic = np.zeros(n, dtype=bool)
+    basic[rng.permutation(n)[:m]] = True
+    x0 = np.where(basic, rng.uniform(0.5, 2.0, n), 0.0)
+    s0 = np.where(basic, 0.0, rng.uniform(0.5, 2.0, n))
+    y0 = rng.standard_normal(m)
+    b, c = A @ x0, A.T @ y0 + s0
+    xt = rng.standard_normal(n)
+    g = O.central_point_grad(A, b, c, 1e-8, lambda xs: 2.0 * (xs - xt))
+    w = np.linalg.solve(A[:, basic].T, 2.0 * (x0 - xt)[basic])
+    scale = np.abs(w).max()
+    assert np.abs(g["db"] - w).max() <= 1e-6 * scale
+    assert np.abs(g["dc"]).max() <= 1e-6 * scale
+    dA = -np.outer(w, x0)
+    assert np.abs(g["dA"] - dA).max() <= 1e-6 * np.abs(dA).max()
