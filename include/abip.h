@@ -169,6 +169,26 @@ ABIP_API int abip_solve_batch(int32_t count, const abip_matrix* A, const double*
                      abip_info* infos, void* stream);
 
 /*
+ * Solve `count` LPs  min c_k^T x  s.t.  A x = b_k,  x >= 0  that share one dense A
+ * (e.g. basis pursuit with one dictionary and many measurements).  Algorithm 2 runs
+ * for all instances in lockstep with per-instance convergence control; each update's
+ * products are GEMMs over the instances (A [X S], A^T Y, G^{-1} Q, A^T Z_y with
+ * G = I + A A^T of Sec. 4.4 inverted once from its FP64 Cholesky factor).
+ *   A: one dense row-major matrix (host or device, F32 or F64), 1 <= m <= n.
+ *   b[k] (m), c[k] (n): host or device.  x, y, s: arrays of `count` caller-allocated
+ *   output pointers (host or device; entries may be NULL), scaled as abip_solve's.
+ *   infos: `count` entries or NULL.  p->precision: ABIP_PREC_F64 (FP64 throughout) or
+ *   ABIP_PREC_MIXED (FP32 iterates and products; the Sec. 4.1 tests are screened in
+ *   FP32 with margin 4 and decided on FP64 products of the same state).
+ * Instances are processed in chunks of 64.  Needs m <= 25600.  Errors: as
+ * abip_solve_batch; ABIP_E_UNSUPPORTED for a CSR A.
+ */
+ABIP_API int abip_solve_batch_shared(int32_t count, const abip_matrix* A, const double* const* b,
+                                     const double* const* c, const abip_params* p,
+                                     double* const* x, double* const* y, double* const* s,
+                                     abip_info* infos, void* stream);
+
+/*
  * Gradient of a loss L(x*) of the returned primal solution x* = x / tau with respect
  * to (c, b, A), by implicit differentiation of the central point of the HSD
  * embedding at the final mu of the last abip_solve (the fixed point of the ADMM

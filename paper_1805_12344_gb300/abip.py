@@ -92,6 +92,10 @@ _SIGS = {
                                    C.POINTER(C.c_void_p), C.POINTER(abip_params), C.POINTER(C.c_void_p),
                                    C.POINTER(C.c_void_p), C.POINTER(C.c_void_p), C.POINTER(abip_info),
                                    C.c_void_p]),
+    "abip_solve_batch_shared": (C.c_int, [C.c_int32, C.POINTER(abip_matrix), C.POINTER(C.c_void_p),
+                                          C.POINTER(C.c_void_p), C.POINTER(abip_params), C.POINTER(C.c_void_p),
+                                          C.POINTER(C.c_void_p), C.POINTER(C.c_void_p), C.POINTER(abip_info),
+                                          C.c_void_p]),
     "abip_backward": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "abip_backward_batch": (C.c_int, [C.c_int32, C.POINTER(abip_matrix), C.POINTER(C.c_void_p),
                                       C.POINTER(C.c_void_p), C.POINTER(abip_params), C.POINTER(C.c_void_p),
@@ -335,6 +339,40 @@ def abip_solve_batch(As: Sequence, bs: Sequence, cs: Sequence, params: Optional[
     rc = lib().abip_solve_batch(count, mats, bptr, cptr, C.byref(params) if params is not None else None,
                                 xptr if want_solution else None, yptr if want_solution else None,
                                 sptr if want_solution else None, infos, st)
+    _check(rc)
+    return [infos[k].as_dict() for k in range(count)], xs, ys, ss
+
+
+def abip_solve_batch_shared(A, bs: Sequence, cs: Sequence, params: Optional[abip_params] = None,
+                            want_solution: bool = True, stream=None, device_out: bool = False):
+    """Solve LPs that share the dense matrix A (numpy array or CUDA tensor) in lockstep.
+    Returns (infos, xs, ys, ss) like `abip_solve_batch`."""
+    count = len(bs)
+    M, keep = _matrix(A)
+    bptr = (C.c_void_p * count)()
+    cptr = (C.c_void_p * count)()
+    xptr = (C.c_void_p * count)()
+    yptr = (C.c_void_p * count)()
+    sptr = (C.c_void_p * count)()
+    xs, ys, ss = [], [], []
+    for k in range(count):
+        b, c = _vec(bs[k]), _vec(cs[k])
+        keep += [b, c]
+        bptr[k] = _ptr(b)[0]
+        cptr[k] = _ptr(c)[0]
+        if want_solution:
+            if device_out:
+                import torch
+                x, y, s = (torch.empty(k_, dtype=torch.float64, device="cuda") for k_ in (M.n, M.m, M.n))
+            else:
+                x, y, s = np.zeros(M.n), np.zeros(M.m), np.zeros(M.n)
+            xs.append(x); ys.append(y); ss.append(s)
+            xptr[k], yptr[k], sptr[k] = _ptr(x)[0], _ptr(y)[0], _ptr(s)[0]
+    infos = (abip_info * count)()
+    rc = lib().abip_solve_batch_shared(count, C.byref(M), bptr, cptr,
+                                       C.byref(params) if params is not None else None,
+                                       xptr if want_solution else None, yptr if want_solution else None,
+                                       sptr if want_solution else None, infos, _stream_arg(stream))
     _check(rc)
     return [infos[k].as_dict() for k in range(count)], xs, ys, ss
 

@@ -1014,6 +1014,77 @@ int abip_solve_batch(int32_t count, const abip_matrix* A, const double* const* b
   return rc;
 }
 
+int abip_solve_batch_shared(int32_t count, const abip_matrix* A, const double* const* b, const double* const* c,
+                            const abip_params* p, double* const* x, double* const* y, double* const* s,
+                            abip_info* infos, void* stream) {
+  const double t0 = now_s();
+  if (count < 0) return fail(nullptr, ABIP_E_INVALID_ARG, "count < 0");
+  if (count == 0) return ABIP_OK;
+  if (!A || !b || !c) return fail(nullptr, ABIP_E_INVALID_ARG, "A, b or c is NULL");
+  if (A->fmt != ABIP_DENSE_ROWMAJOR) return fail(nullptr, ABIP_E_UNSUPPORTED, "the shared-A batch takes a dense A");
+  abip_params prm;
+  if (p) prm = *p;
+  else abip_default_params(&prm);
+  std::string why;
+  if (!check_params(prm, why)) return fail(nullptr, ABIP_E_INVALID_ARG, why);
+  abip_handle tmp;
+  cudaGetDevice(&tmp.device);
+  int rc = validate_matrix(&tmp, A);
+  if (rc) return fail(nullptr, rc, tmp.err);
+  const int m = A->m, n = A->n;
+  std::vector<double> Ah;
+  rc = read_matrix_dense(&tmp, A, Ah);
+  if (rc) return fail(nullptr, rc, tmp.err);
+  std::vector<std::vector<double>> hb(count), hc(count);
+  for (int k = 0; k < count; ++k) {
+    if (!b[k] || !c[k]) return fail(nullptr, ABIP_E_INVALID_ARG, "instance " + std::to_string(k) + ": b or c is NULL");
+    if (fetch(b[k], m, is_device_ptr(b[k]), hb[k]) != cudaSuccess || fetch(c[k], n, is_device_ptr(c[k]), hc[k]) != cudaSuccess)
+      return fail(nullptr, ABIP_E_CUDA, "reading b, c");
+    if (!finite_all(hb[k].data(), m) || !finite_all(hc[k].data(), n))
+      return fail(nullptr, ABIP_E_INVALID_ARG, "instance " + std::to_string(k) + ": non-finite b or c");
+  }
+  abip::ShParams sp{};
+  sp.beta = prm.beta; sp.gamma = prm.gamma; sp.alpha = prm.alpha; sp.eps = prm.eps;
+  sp.max_admm = prm.max_admm_iters; sp.warmstart = prm.warmstart; sp.stop_rule = prm.stop_rule;
+  sp.mixed = prm.precision == ABIP_PREC_MIXED ? 1 : 0;
+  sp.n = n;
+  sp.confirm_gap = std::max<int64_t>(prm.check_every, 20);
+  sp.refresh = 200;
+  for (int k0 = 0; k0 < count; k0 += 64) {
+    const int cnt = std::min(64, count - k0);
+    std::vector<const double*> bp(cnt), cp(cnt);
+    for (int k = 0; k < cnt; ++k) { bp[k] = hb[k0 + k].data(); cp[k] = hc[k0 + k].data(); }
+    abip::SharedBatchArgs args{m, n, cnt, Ah.data(), bp.data(), cp.data(), sp, static_cast<cudaStream_t>(stream)};
+    std::vector<abip::SharedBatchResult> res;
+    std::string err;
+    rc = abip::shared_batch_run(args, res, err);
+    if (rc) return fail(nullptr, rc, err);
+    const double el = now_s() - t0;
+    for (int k = 0; k < cnt; ++k) {
+      const abip::ShInst& I = res[k].inst;
+      const int id = k0 + k;
+      if (infos) {
+        abip_info& f = infos[id];
+        std::memset(&f, 0, sizeof(f));
+        f.status = I.status; f.outer_iters = I.outer; f.admm_iters = I.total;
+        f.fp32_iters = sp.mixed ? I.total : 0;
+        f.tau = I.tau; f.kappa = I.kappa; f.theta = I.theta; f.mu = I.mu;
+        f.obj = I.ctx / I.tau; f.pres = I.pres; f.dres = I.dres; f.dgap = I.dgap;
+        f.setup_s = res[k].setup_s; f.solve_s = el; f.kernel_s = res[k].kernel_s; f.launches = res[k].launches;
+      }
+      auto put = [&](double* dst, const std::vector<double>& v) {
+        if (rc == ABIP_OK && dst && cudaMemcpy(dst, v.data(), v.size() * 8, cudaMemcpyDefault) != cudaSuccess)
+          rc = fail(nullptr, ABIP_E_CUDA, "output copy");
+      };
+      if (x) put(x[id], res[k].x);
+      if (y) put(y[id], res[k].y);
+      if (s) put(s[id], res[k].s);
+    }
+    if (rc) return rc;
+  }
+  return ABIP_OK;
+}
+
 int abip_backward(abip_handle* h, const double* dl_dx, double* dl_dc, double* dl_db, double* dl_dA) {
   if (!h || !dl_dx) return fail(h, ABIP_E_INVALID_ARG, "NULL argument");
   if (!h->solved) return fail(h, ABIP_E_NOT_SOLVED, "no solve has run on this handle");

@@ -169,6 +169,60 @@ inline size_t backward_work_doubles(int m, int n) { return 2 * (size_t)m + 4 * (
 int check_params_internal(const abip_params& p, std::string& why);
 int noalloc_fail(int code, const std::string& msg);
 
+
+// ---------------------------------------------------------------------------
+// Batch of LPs sharing one dense A (shared_solver.cu)
+// ---------------------------------------------------------------------------
+enum ShAction : int32_t { SH_INIT = 0, SH_STEP = 1, SH_WARM = 2, SH_CONFIRM = 3, SH_DONE = 4 };
+
+// Per-instance scalars of the shared-A batch.
+struct ShInst {
+  double tau, kappa, theta, mu, cmu;
+  double zbar, nb, nc, Kinv[4];
+  double inner2, pres, dres, dgap, ctx, bty;
+  double t1, t2;
+  int64_t total, level_start, next_confirm;
+  int32_t outer, status, action, last, err, pad;
+};
+
+struct ShParams {
+  double beta, gamma, alpha, eps;
+  int64_t max_admm;
+  int32_t warmstart, stop_rule, mixed, n;
+  int64_t confirm_gap;
+  int32_t refresh;                 // mixed: FP64 recomputation of the maintained products every `refresh` cycles
+  int32_t pad;
+};
+
+// Device arrays of one iteration type; every vector is [length x B], instance fastest.
+// XS = [X | S] (n x 2B), AXS = [AX | AS] (m x 2B), G1 / G2 = M^{-1} h1 / h2 ((m+n) x B).
+template <typename T>
+struct ShView {
+  int m, n, B;
+  const T* A; const T* Ginv;
+  T* b; T* bbar; T* c; T* cbar; T* G1; T* G2;
+  T* Y; T* XS; T* AXS; T* ATY; T* Q; T* ZY; T* ZX;
+};
+
+struct SharedBatchArgs {
+  int m, n, count;                 // count <= 64
+  const double* A;                 // host, m x n row-major FP64
+  const double* const* b;          // host, count vectors of m
+  const double* const* c;          // host, count vectors of n
+  ShParams prm;
+  cudaStream_t stream;
+};
+
+struct SharedBatchResult {
+  ShInst inst;
+  std::vector<double> x, y, s;     // scaled outputs (Sec. 4.1)
+  double setup_s;                  // device time of the setup (Gram, Cholesky, inverse, M^{-1} H)
+  double kernel_s;                 // device time of the iterations
+  int64_t launches;
+};
+
+int shared_batch_run(const SharedBatchArgs& a, std::vector<SharedBatchResult>& out, std::string& err);
+
 }  // namespace abip
 
 // The opaque handle of the C ABI.

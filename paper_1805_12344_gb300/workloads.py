@@ -278,3 +278,43 @@ def l1_svm(d: int = 64, N: int = 512, C: float = 1.0, seed: int | None = None) -
     x_target = rng.standard_normal(n)
     return LP(A=A, b=b, c=c, expect="optimal",
               meta=dict(kind="l1_svm", m=N, n=n, d=d, C=C, x_target=x_target))
+
+
+def bf16_exact(a: np.ndarray) -> np.ndarray:
+    """Round float values to the nearest bfloat16 (ties to even) and return them as float64:
+    numbers exactly representable in bfloat16, float32 and float64 alike."""
+    u = np.ascontiguousarray(a, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    u = (u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000
+    return u.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+@dataclass
+class SharedBatch:
+    """Independent LPs  min c_k^T x  s.t.  A x = b_k,  x >= 0  sharing one dense A."""
+    A: np.ndarray
+    bs: list
+    cs: list
+    meta: dict = field(default_factory=dict)
+
+
+def basis_pursuit(m: int = 2048, n_d: int = 8192, batch: int = 64, density: float = 0.05,
+                  seed: Optional[int] = None) -> SharedBatch:
+    """Basis pursuit  min ||x||_1  s.t.  D x = b_k  as the standard-form LP with x = x+ - x-:
+    A = [D, -D] (m x 2 n_d), c = e, b_k = D x_true_k.  D iid N(0, 1/m) rounded to
+    bfloat16-representable values; x_true_k has round(density * n_d) nonzeros N(0, 1).
+    meta["x_true"]: the planted sparse vectors (x_true is feasible, so the optimum is at most
+    ||x_true||_1, with equality when l1 recovery succeeds)."""
+    rng = np.random.default_rng(seed_for(BASIS_PURSUIT) if seed is None else seed)
+    D = bf16_exact(rng.standard_normal((m, n_d)) / np.sqrt(m))
+    A = np.concatenate([D, -D], axis=1)
+    k = int(round(density * n_d))
+    xs, bs = [], []
+    for _ in range(batch):
+        xt = np.zeros(n_d)
+        idx = rng.choice(n_d, k, replace=False)
+        xt[idx] = rng.standard_normal(k)
+        xs.append(xt)
+        bs.append(D @ xt)
+    cs = [np.ones(2 * n_d) for _ in range(batch)]
+    return SharedBatch(A=A, bs=bs, cs=cs, meta=dict(kind="basis_pursuit", m=m, n=2 * n_d, n_d=n_d,
+                                                    density=density, x_true=xs))
