@@ -455,7 +455,13 @@ constexpr size_t kDenseSmemLimit = 200 * 1024;
 // shared memory of the dense solve: 5m + 3n elements; the mixed path also needs the
 // FP64 size because an instance may finish in FP64 after escalation
 size_t dense_solve_smem(int m, int n, bool mixed = false) {
-  (void)mixed;
+  // FP64: y, zy, w, Ax, As (m) and x, s, zx (n) doubles.  Mixed (FP64 state, FP32
+  // changes): y, Ax, As, zy, q_prev (m) and x, s, A^T y, A^T zy (n) doubles, plus
+  // dy, dq, dz (m, padded to 4) and dx, ds (n, padded to 4) floats, 16-byte aligned.
+  if (mixed) {
+    const size_t mp = (m + 3) / 4 * 4, np = (n + 3) / 4 * 4;
+    return (size_t)(5 * m + 4 * n + 2) * sizeof(double) + (3 * mp + 2 * np) * sizeof(float);
+  }
   return (size_t)(5 * m + 3 * n) * sizeof(double);
 }
 size_t dense_setup_smem(int m, int n) {
@@ -483,15 +489,14 @@ int dense_alloc(abip_handle* h, const std::vector<DenseHostInst>& hi, void** are
       I.y = ar.take<double>(m); I.x = ar.take<double>(n); I.s = ar.take<double>(n);
       I.out_y = ar.take<double>(m); I.out_x = ar.take<double>(n); I.out_s = ar.take<double>(n);
       I.work = nullptr;
+      I.ldf = (n + 3) / 4 * 4;
+      I.ldtf = (m + 3) / 4 * 4;
       if (mixed) {
-        I.Af = ar.take<float>((size_t)m * n);
-        I.Lf = ar.take<float>((size_t)m * m);
-        I.g1f = ar.take<float>(m + n); I.g2f = ar.take<float>(m + n);
-        I.bf = ar.take<float>(m); I.cf = ar.take<float>(n);
-        I.bbarf = ar.take<float>(m); I.cbarf = ar.take<float>(n);
+        I.Af = ar.take<float>((size_t)m * I.ldf);
+        I.ATf = ar.take<float>((size_t)n * I.ldtf);
+        I.Ginvf = ar.take<float>((size_t)m * I.ldtf);
       } else {
-        I.Af = nullptr; I.Lf = nullptr; I.g1f = I.g2f = nullptr;
-        I.bf = I.cf = I.bbarf = I.cbarf = nullptr;
+        I.Af = nullptr; I.ATf = nullptr; I.Ginvf = nullptr;
       }
     }
   };
@@ -512,9 +517,17 @@ int dense_alloc(abip_handle* h, const std::vector<DenseHostInst>& hi, void** are
     cudaMemcpy((void*)I.A, hi[k].A.data(), hi[k].A.size() * 8, cudaMemcpyHostToDevice);
     cudaMemcpy((void*)I.b, hi[k].b.data(), hi[k].m * 8, cudaMemcpyHostToDevice);
     cudaMemcpy((void*)I.c, hi[k].c.data(), hi[k].n * 8, cudaMemcpyHostToDevice);
-    if (mixed) {
-      std::vector<float> f(hi[k].A.begin(), hi[k].A.end());
+    if (mixed) {   // padded FP32 copies of A and A^T (padding stays 0 from the memset)
+      const int m = hi[k].m, n = hi[k].n;
+      std::vector<float> f((size_t)m * I.ldf, 0.f), ft((size_t)n * I.ldtf, 0.f);
+      for (int i = 0; i < m; ++i)
+        for (int j = 0; j < n; ++j) {
+          const float v = (float)hi[k].A[(size_t)i * n + j];
+          f[(size_t)i * I.ldf + j] = v;
+          ft[(size_t)j * I.ldtf + i] = v;
+        }
       cudaMemcpy((void*)I.Af, f.data(), f.size() * 4, cudaMemcpyHostToDevice);
+      cudaMemcpy((void*)I.ATf, ft.data(), ft.size() * 4, cudaMemcpyHostToDevice);
     }
   }
   cudaMemcpy(*dinst, hdesc.data(), sizeof(DenseInst) * count, cudaMemcpyHostToDevice);
@@ -826,7 +839,7 @@ int abip_setup(const abip_matrix* A, const double* b, const double* c, const abi
   } else {
     h->path = 1;
     if (dense_solve_smem(m, n, h->mixed) > kDenseSmemLimit)
-      rc = fail(h, ABIP_E_UNSUPPORTED, "dense Cholesky path needs (5m + 3n) elements in 200 KB of shared memory; use linsys = PCG");
+      rc = fail(h, ABIP_E_UNSUPPORTED, "dense Cholesky path needs 40m + 24n bytes (FP64) or 48m + 40n bytes (mixed) of shared memory, at most 200 KB; use linsys = PCG");
     else {
       std::vector<DenseHostInst> hi(1);
       hi[0].m = m; hi[0].n = n; hi[0].b = hb; hi[0].c = hc;
@@ -958,8 +971,8 @@ int abip_solve_batch(int32_t count, const abip_matrix* A, const double* const* b
     if (!b[k] || !c[k]) return fail(nullptr, ABIP_E_INVALID_ARG, "instance " + std::to_string(k) + ": b or c is NULL");
     const int m = A[k].m, n = A[k].n;
     if (dense_solve_smem(m, n, mixed) > kDenseSmemLimit)
-      return fail(nullptr, ABIP_E_UNSUPPORTED, "instance " + std::to_string(k) + ": needs 5m + 3n <= " +
-                                                  std::to_string(kDenseSmemLimit / (mixed ? 4 : 8)));
+      return fail(nullptr, ABIP_E_UNSUPPORTED, "instance " + std::to_string(k) + ": needs 40m + 24n bytes (FP64) or "
+                                                  "48m + 40n bytes (mixed) of shared memory, at most 200 KB");
     hi[k].m = m; hi[k].n = n;
     rc = read_matrix_dense(&tmp, &A[k], hi[k].A);
     if (rc) return fail(nullptr, rc, "instance " + std::to_string(k) + ": " + tmp.err);

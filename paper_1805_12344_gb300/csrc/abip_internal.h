@@ -111,8 +111,9 @@ struct DenseInst {
   double* y; double* x; double* s;   // iterate
   double* work;                // 3*(m + n) doubles
   double* out_x; double* out_y; double* out_s;   // device outputs (may be null)
-  // FP32 copies for the mixed-precision solve (null on the FP64 path)
-  const float* Af; float* Lf; float* g1f; float* g2f; float* bf; float* cf; float* bbarf; float* cbarf;
+  // mixed precision (null on the FP64 path): FP32 A (rows padded to ldf), FP32 A^T
+  // (rows padded to ldtf) and the FP32 explicit inverse of G = I + A A^T (m x ldtf)
+  const float* Af; const float* ATf; float* Ginvf;
   double zbar, nb, nc;
   double Kinv[4];
   // results
@@ -127,6 +128,7 @@ struct DenseInst {
   int32_t r_outer;
   int32_t fp32_iters_hi;       // mixed path: ADMM updates done in FP32 (low and high 31 bits)
   int32_t fp32_iters_lo;
+  int32_t ldf, ldtf;           // padded row lengths of Af (n) and of ATf / Ginvf (m), multiples of 4
   int32_t pad3;
 };
 

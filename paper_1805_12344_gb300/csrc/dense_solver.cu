@@ -270,15 +270,16 @@ __global__ void __launch_bounds__(kThreads) dense_setup_kernel(DenseInst* insts,
       I.err = isfinite(det) && det != 0.0 ? 0 : DEV_ERR_NONFINITE;
     }
     __syncthreads();
-    if (I.Lf) {   // FP32 copies for the mixed-precision solve
-      for (int idx = threadIdx.x; idx < m * m; idx += kThreads) I.Lf[idx] = (float)I.L[idx];
-      for (int k = threadIdx.x; k < m + n; k += kThreads) {
-        I.g1f[k] = (float)I.g1[k];
-        I.g2f[k] = (float)I.g2[k];
+    if (I.Ginvf) {   // mixed precision: the FP32 explicit inverse of G, column by column
+      double* w = sm;   // m
+      for (int col = 0; col < m; ++col) {
+        for (int i = threadIdx.x; i < m; i += kThreads) w[i] = i == col ? 1.0 : 0.0;
+        __syncthreads();
+        trsv_lower<double>(I.L, m, w);
+        trsv_lower_t<double>(I.L, m, w);
+        for (int i = threadIdx.x; i < m; i += kThreads) I.Ginvf[(size_t)col * I.ldtf + i] = (float)w[i];
+        __syncthreads();
       }
-      for (int i = threadIdx.x; i < m; i += kThreads) { I.bf[i] = (float)I.b[i]; I.bbarf[i] = (float)I.bbar[i]; }
-      for (int j = threadIdx.x; j < n; j += kThreads) { I.cf[j] = (float)I.c[j]; I.cbarf[j] = (float)I.cbar[j]; }
-      __syncthreads();
     }
   }
 }
@@ -290,9 +291,6 @@ struct DView {
 };
 __device__ __forceinline__ DView<double> view(const DenseInst& I, double) {
   return {I.A, I.L, I.g1, I.g2, I.b, I.c, I.bbar, I.cbar};
-}
-__device__ __forceinline__ DView<float> view(const DenseInst& I, float) {
-  return {I.Af, I.Lf, I.g1f, I.g2f, I.bf, I.cf, I.bbarf, I.cbarf};
 }
 
 // Residual products Ax, As, A^T y and the nine sums of the Sec. 4.1 tests and
@@ -335,15 +333,10 @@ __device__ void residual_sums(const DView<T>& V, int m, int n, int64_t ld, const
   block_allsum<9>(out, red);
 }
 
-// Algorithm 2 for one instance with the CTA, iterates of type T.  Shared layout:
-// y, zy, w, Ax, As (m each), x, s, zx (n each), all of type T.
-// With T = float the sums of every update are formed in FP32 and serve the inner
-// test and as a screen; whenever they pass a Sec. 4.1 test with a factor-4 margin
-// the sums are recomputed with FP64 accumulation and the FP64 values decide.
-// Returns 1 when a mixed (T = float) solve hands its state to FP64 (escalation),
-// 0 when the instance is finished.
+// Algorithm 2 for one instance with the CTA, FP64 iterates (T = double).  Shared
+// layout: y, zy, w, Ax, As (m each), x, s, zx (n each).
 template <typename T>
-__device__ int dense_solve_one(DenseInst& I, const DenseParams& P, T* sm, double* red) {
+__device__ void dense_solve_one(DenseInst& I, const DenseParams& P, T* sm, double* red) {
   const DView<T> V = view(I, T(0));
   const int m = I.m, n = I.n;
   T* y = sm;
@@ -354,13 +347,12 @@ __device__ int dense_solve_one(DenseInst& I, const DenseParams& P, T* sm, double
   T* x = As + m;
   T* s = x + n;
   T* zx = s + n;
-  const bool mixed = sizeof(T) == 4;
   const double alpha = P.alpha, beta = P.beta, gamma = P.gamma, eps = P.eps;
   const double zbar = I.zbar, xi = -(double)n - 1.0, nb = I.nb, nc = I.nc;
   const double Ki0 = I.Kinv[0], Ki1 = I.Kinv[1], Ki2 = I.Kinv[2], Ki3 = I.Kinv[3];
   // start of Algorithm 2, or a state loaded by abip_set_state
   double tau = 1.0, kappa = 1.0, theta = 1.0, mu = beta;
-  int64_t total = 0, next_confirm = 0;
+  int64_t total = 0;
   int outer = 0, status = 0;
   if (I.resume) {
     for (int i = threadIdx.x; i < m; i += kThreads) y[i] = (T)I.y[i];
@@ -373,8 +365,6 @@ __device__ int dense_solve_one(DenseInst& I, const DenseParams& P, T* sm, double
     for (int j = threadIdx.x; j < n; j += kThreads) { x[j] = T(1); s[j] = T(1); }
   }
   __syncthreads();
-  bool escalate = false;
-  int64_t level_start = total;   // update count when the current mu level began
   double inner2 = 0, pres = 0, dres = 0, dgap = 0, ctx = 0, bty = 0;
 
   // Sec. 4.1 tests on the sums; returns the status they give (0 = continue)
@@ -402,14 +392,7 @@ __device__ int dense_solve_one(DenseInst& I, const DenseParams& P, T* sm, double
     absorb(a);
     if (!isfinite(inner2)) return false;
     if (!final_test || P.stop_rule != 0) return true;
-    if (!mixed) {
-      status = tests(a, 1.0);
-    } else if (tests(a, 100.0) != 0 || mu / beta <= 1e-6 || total - level_start > 20000) {
-      // within two decades of a Sec. 4.1 test, mu small, or an inner loop that
-      // FP32 sums cannot close: FP32 iterates cannot certify 1e-6 reliably, so
-      // hand the state to FP64
-      escalate = true;
-    }
+    status = tests(a, 1.0);
     return true;
   };
 
@@ -418,7 +401,6 @@ __device__ int dense_solve_one(DenseInst& I, const DenseParams& P, T* sm, double
     if (inner2 <= mu) {
       mu *= gamma;
       ++outer;
-      level_start = total;
       if (P.stop_rule == 1 && mu < eps) { status = ABIP_OPTIMAL; break; }
       if (outer >= kMaxOuter) { status = ABIP_MAX_ITER; break; }   // mu has underflowed
       const T g = (T)gamma, sg = (T)sqrt(gamma);
@@ -494,20 +476,6 @@ __device__ int dense_solve_one(DenseInst& I, const DenseParams& P, T* sm, double
     ok = evaluate(true);
     if (status != 0) break;
     if (total >= P.max_admm) { status = ABIP_MAX_ITER; break; }
-    if (escalate) break;
-  }
-  if (escalate && ok) {
-    for (int i = threadIdx.x; i < m; i += kThreads) I.y[i] = (double)y[i];
-    for (int j = threadIdx.x; j < n; j += kThreads) { I.x[j] = (double)x[j]; I.s[j] = (double)s[j]; }
-    if (threadIdx.x == 0) {
-      I.resume = 1;
-      I.r_tau = tau; I.r_kappa = kappa; I.r_theta = theta; I.r_mu = mu;
-      I.r_iters = total; I.r_outer = outer;
-      I.fp32_iters_lo = (int32_t)(total & 0x7fffffff);
-      I.fp32_iters_hi = (int32_t)(total >> 31);
-    }
-    __syncthreads();
-    return 1;
   }
   // outputs: raw state and the scaled candidate or certificate (Sec. 4.1)
   double sx = 1.0 / tau, sy = 1.0 / tau;
@@ -531,7 +499,310 @@ __device__ int dense_solve_one(DenseInst& I, const DenseParams& P, T* sm, double
     if (!ok) I.err = DEV_ERR_NONFINITE;
   }
   __syncthreads();
-  return 0;
+}
+
+// ---------------------------------------------------------------------------
+// Mixed precision: FP64 state, FP32 products of changes
+// ---------------------------------------------------------------------------
+// The iterate (y, x, s, tau, kappa, theta) and the products the update needs
+// (Ax, As, A^T y, z_y = G^{-1} q with q = y - Ax - As, A^T z_y) are kept in FP64.  Each
+// update changes them by FP32 products of the change of the iterate:
+//   z_y += G^{-1} (q - q_prev)            (FP32, with the explicit inverse formed at setup)
+//   A^T z_y += A^T (G^{-1} (q - q_prev))   (FP32)
+//   Ax += A dx, As += A ds, A^T y += A^T dy (FP32, after the update)
+// so FP32 rounding scales with the step, not with the iterate, and there is no FP32
+// accuracy floor.  Every kDeltaRefresh updates, and whenever the Sec. 4.1 tests pass on
+// the maintained sums with a factor-4 margin, the products are recomputed exactly in
+// FP64; the tests are decided on the exact sums.
+constexpr int kDeltaRefresh = 100;
+
+// o0[i] += sum_j M[i][j] v0[j] (and o1 with v1) for rows i < rows: warp per row, float4
+// loads, FP32 accumulation.  M rows are ldm floats (a multiple of 4, zero padded); v0,
+// v1 hold ldm floats, 16-byte aligned.  f0 (optional) receives the FP32 row sums.
+template <bool TWO>
+__device__ void rows_f32(const float* __restrict__ M, int ldm, int rows, const float* v0, const float* v1,
+                         double* o0, double* o1, float* f0) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int nq = ldm / 4;
+  const float4* p0 = reinterpret_cast<const float4*>(v0);
+  const float4* p1 = reinterpret_cast<const float4*>(v1);
+  for (int i = wid; i < rows; i += kWarps) {
+    const float4* r = reinterpret_cast<const float4*>(M + (size_t)i * ldm);
+    float a0 = 0.f, a1 = 0.f;
+#pragma unroll 8
+    for (int t = lane; t < nq; t += 32) {
+      const float4 a = r[t];
+      const float4 x = p0[t];
+      a0 += a.x * x.x + a.y * x.y + a.z * x.z + a.w * x.w;
+      if (TWO) {
+        const float4 z = p1[t];
+        a1 += a.x * z.x + a.y * z.y + a.z * z.z + a.w * z.w;
+      }
+    }
+    a0 = warp_sum(a0);
+    if (TWO) a1 = warp_sum(a1);
+    if (lane == 0) {
+      o0[i] += (double)a0;
+      if (TWO) o1[i] += (double)a1;
+      if (f0) f0[i] = a0;
+    }
+  }
+}
+
+__device__ void dense_solve_delta(DenseInst& I, const DenseParams& P, unsigned char* smraw, double* red) {
+  const int m = I.m, n = I.n;
+  const int64_t ld = I.ld;
+  double* y = reinterpret_cast<double*>(smraw);
+  double* Ax = y + m;
+  double* As = Ax + m;
+  double* zy = As + m;
+  double* qp = zy + m;
+  double* x = qp + m;
+  double* s = x + n;
+  double* ATy = s + n;
+  double* ATz = ATy + n;
+  const int mp = I.ldtf, np = I.ldf;
+  float* dy = reinterpret_cast<float*>(smraw + (((size_t)(5 * m + 4 * n) * 8 + 15) / 16) * 16);
+  float* dq = dy + mp;
+  float* dz = dq + mp;
+  float* dx = dz + mp;
+  float* ds = dx + np;
+  const double alpha = P.alpha, beta = P.beta, gamma = P.gamma, eps = P.eps;
+  const double zbar = I.zbar, xi = -(double)n - 1.0, nb = I.nb, nc = I.nc;
+  const double Ki0 = I.Kinv[0], Ki1 = I.Kinv[1], Ki2 = I.Kinv[2], Ki3 = I.Kinv[3];
+  double tau = 1.0, kappa = 1.0, theta = 1.0, mu = beta;
+  int64_t total = 0;
+  int outer = 0, status = 0;
+  if (I.resume) {
+    for (int i = threadIdx.x; i < m; i += kThreads) y[i] = I.y[i];
+    for (int j = threadIdx.x; j < n; j += kThreads) { x[j] = I.x[j]; s[j] = I.s[j]; }
+    tau = I.r_tau; kappa = I.r_kappa; theta = I.r_theta; mu = I.r_mu;
+    total = I.r_iters;
+    outer = I.r_outer;
+  } else {
+    for (int i = threadIdx.x; i < m; i += kThreads) y[i] = 0.0;
+    for (int j = threadIdx.x; j < n; j += kThreads) { x[j] = 1.0; s[j] = 1.0; }
+  }
+  // the padding of the FP32 vectors meets zero padding of the FP32 matrices
+  for (int i = threadIdx.x; i < 3 * mp + 2 * np; i += kThreads) dy[i] = 0.f;
+  __syncthreads();
+  int64_t since_refresh = 0, next_confirm = 0;
+  double inner2 = 0, pres = 0, dres = 0, dgap = 0, ctx = 0, bty = 0;
+
+  // exact FP64 products of the current state
+  auto refresh = [&]() {
+    gemv_rows<true, double>(I.A, ld, m, n, x, s, Ax, As);
+    __syncthreads();
+    for (int i = threadIdx.x; i < m; i += kThreads) {
+      const double q = y[i] - (Ax[i] + As[i]);
+      qp[i] = q;
+      zy[i] = q;
+    }
+    __syncthreads();
+    trsv_lower<double>(I.L, m, zy);
+    trsv_lower_t<double>(I.L, m, zy);
+    for (int j = threadIdx.x; j < n; j += kThreads) {
+      double a0 = 0.0, a1 = 0.0;
+      for (int i = 0; i < m; ++i) {
+        const double aij = I.A[(size_t)i * ld + j];
+        a0 += aij * y[i];
+        a1 += aij * zy[i];
+      }
+      ATy[j] = a0;
+      ATz[j] = a1;
+    }
+    __syncthreads();
+    since_refresh = 0;
+  };
+  // the nine sums from the maintained products (as residual_sums)
+  auto sums = [&](double (&out)[9]) {
+    double acc[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    for (int i = threadIdx.x; i < m; i += kThreads) {
+      const double ax = Ax[i], bi = I.b[i], yi = y[i], bb = I.bbar[i];
+      const double ry = ax - bi * tau + bb * theta;
+      const double pr = ax / tau - bi;
+      acc[0] += ry * ry; acc[1] += pr * pr; acc[3] += ax * ax;
+      acc[5] += bi * yi; acc[6] += bb * yi;
+    }
+    for (int j = threadIdx.x; j < n; j += kThreads) {
+      const double aty = ATy[j], sj = s[j], cj = I.c[j], cb = I.cbar[j], xj = x[j];
+      const double rx = -aty + cj * tau - cb * theta - sj;
+      const double dr = (aty + sj) / tau - cj;
+      acc[0] += rx * rx; acc[2] += dr * dr; acc[4] += (aty + sj) * (aty + sj);
+      acc[7] += cj * xj; acc[8] += cb * xj;
+    }
+#pragma unroll
+    for (int k = 0; k < 9; ++k) out[k] = acc[k];
+    block_allsum<9>(out, red);
+  };
+  auto tests = [&](const double (&a)[9], double margin) -> int {
+    const double ps = sqrt(a[1]) / (1.0 + nb), dsn = sqrt(a[2]) / (1.0 + nc);
+    const double gp = fabs(a[7] / tau - a[5] / tau) / (1.0 + fabs(a[7] / tau) + fabs(a[5] / tau));
+    if (ps <= margin * eps && dsn <= margin * eps && gp <= margin * eps) return ABIP_OPTIMAL;
+    if (a[5] > 0 && sqrt(a[4]) <= margin * eps * a[5] / nb) return ABIP_PRIMAL_INFEASIBLE;
+    if (a[7] < 0 && sqrt(a[3]) <= margin * eps * (-a[7]) / nc) return ABIP_DUAL_INFEASIBLE;
+    return 0;
+  };
+  auto absorb = [&](const double (&a)[9]) {
+    bty = a[5];
+    ctx = a[7];
+    const double rt = a[5] - a[7] + zbar * theta - kappa;
+    const double rth = -a[6] + a[8] - zbar * tau - xi;
+    inner2 = a[0] + rt * rt + rth * rth;
+    pres = sqrt(a[1]) / (1.0 + nb);
+    dres = sqrt(a[2]) / (1.0 + nc);
+    dgap = fabs(ctx / tau - bty / tau) / (1.0 + fabs(ctx / tau) + fabs(bty / tau));
+  };
+  auto evaluate = [&](bool final_test) -> bool {
+    double a[9];
+    sums(a);
+    absorb(a);
+    if (!isfinite(inner2)) return false;
+    if (!final_test || P.stop_rule != 0) return true;
+    if (total >= next_confirm && tests(a, 4.0) != 0) {
+      refresh();
+      sums(a);
+      absorb(a);
+      status = tests(a, 1.0);
+      next_confirm = total + P.check_every;
+    }
+    return true;
+  };
+  // maintained products after a change (dy, dx, ds) of the iterate
+  auto maintain = [&]() {
+    rows_f32<true>(I.Af, np, m, dx, ds, Ax, As, nullptr);
+    rows_f32<false>(I.ATf, mp, n, dy, dy, ATy, ATy, nullptr);
+    __syncthreads();
+  };
+
+  refresh();
+  bool ok = evaluate(false);
+  while (ok) {
+    if (inner2 <= mu) {
+      mu *= gamma;
+      ++outer;
+      if (P.stop_rule == 1 && mu < eps) { status = ABIP_OPTIMAL; break; }
+      if (outer >= kMaxOuter) { status = ABIP_MAX_ITER; break; }
+      const double sg = sqrt(gamma);
+      for (int j = threadIdx.x; j < n; j += kThreads) {
+        const double x0 = x[j], s0 = s[j];
+        if (P.warmstart == 1) { x[j] = x0 * sg; s[j] = s0 * sg; }
+        else if (x0 >= s0) s[j] = s0 * gamma;
+        else x[j] = x0 * gamma;
+        dx[j] = (float)(x[j] - x0);
+        ds[j] = (float)(s[j] - s0);
+      }
+      if (P.warmstart == 1) { tau *= sg; kappa *= sg; }
+      else if (tau >= kappa) kappa *= gamma;
+      else tau *= gamma;
+      for (int i = threadIdx.x; i < m; i += kThreads) {
+        const double y0 = y[i];
+        y[i] = y0 * sg;
+        dy[i] = (float)(y[i] - y0);
+      }
+      theta *= sg;
+      __syncthreads();
+      maintain();
+      ok = evaluate(false);
+      continue;
+    }
+    // projection on the change of q = y - A(x + s)
+    for (int i = threadIdx.x; i < m; i += kThreads) {
+      const double q = y[i] - (Ax[i] + As[i]);
+      dq[i] = (float)(q - qp[i]);
+      qp[i] = q;
+    }
+    __syncthreads();
+    // zy += G^{-1} dq (dz keeps the FP32 change), A^T zy += A^T dz
+    rows_f32<false>(I.Ginvf, mp, m, dq, dq, zy, zy, dz);
+    __syncthreads();
+    rows_f32<false>(I.ATf, mp, n, dz, dz, ATz, ATz, nullptr);
+    __syncthreads();
+    double hz[2] = {0.0, 0.0};
+    for (int j = threadIdx.x; j < n; j += kThreads) {
+      const double z = x[j] + s[j] + ATz[j];
+      hz[0] += I.c[j] * z;
+      hz[1] -= I.cbar[j] * z;
+    }
+    for (int i = threadIdx.x; i < m; i += kThreads) {
+      hz[0] -= I.b[i] * zy[i];
+      hz[1] += I.bbar[i] * zy[i];
+    }
+    block_allsum<2>(hz, red);
+    const double v1 = tau + kappa + hz[0], v2 = theta + xi + hz[1];
+    const double t1 = Ki0 * v1 + Ki1 * v2, t2 = Ki2 * v1 + Ki3 * v2;
+    const double cmu = mu / beta;
+    for (int i = threadIdx.x; i < m; i += kThreads) {
+      const double uy = zy[i] - I.g1[i] * t1 - I.g2[i] * t2;
+      const double y0 = y[i];
+      y[i] = alpha * uy + (1.0 - alpha) * y0;
+      dy[i] = (float)(y[i] - y0);
+    }
+    for (int j = threadIdx.x; j < n; j += kThreads) {
+      const double z = x[j] + s[j] + ATz[j];
+      const double ux = z - I.g1[m + j] * t1 - I.g2[m + j] * t2;
+      const double x0 = x[j], s0 = s[j];
+      const double xh = alpha * ux + (1.0 - alpha) * x0;
+      double xn, sn;
+      barrier_step<double>(xh - s0, cmu, xn, sn);
+      x[j] = xn;
+      s[j] = sn;
+      dx[j] = (float)(xn - x0);
+      ds[j] = (float)(sn - s0);
+    }
+    {
+      const double th_ = alpha * t1 + (1.0 - alpha) * tau;
+      double tn, kn;
+      barrier_step<double>(th_ - kappa, mu / beta, tn, kn);
+      tau = tn;
+      kappa = kn;
+      theta = alpha * t2 + (1.0 - alpha) * theta;
+    }
+    __syncthreads();
+    maintain();
+    ++total;
+    if (++since_refresh >= kDeltaRefresh) refresh();
+    ok = evaluate(true);
+    if (status != 0) break;
+    if (total >= P.max_admm) { status = ABIP_MAX_ITER; break; }
+  }
+  // outputs: raw state and the scaled candidate or certificate (Sec. 4.1)
+  double sx = 1.0 / tau, sy = 1.0 / tau;
+  if (status == ABIP_PRIMAL_INFEASIBLE) { sx = 1.0; sy = 1.0 / bty; }
+  if (status == ABIP_DUAL_INFEASIBLE) { sx = -1.0 / ctx; sy = 1.0; }
+  for (int i = threadIdx.x; i < m; i += kThreads) {
+    I.y[i] = y[i];
+    if (I.out_y) I.out_y[i] = y[i] * sy;
+  }
+  for (int j = threadIdx.x; j < n; j += kThreads) {
+    I.x[j] = x[j];
+    I.s[j] = s[j];
+    if (I.out_x) I.out_x[j] = x[j] * sx;
+    if (I.out_s) I.out_s[j] = s[j] * sy;
+  }
+  if (threadIdx.x == 0) {
+    I.tau = tau; I.kappa = kappa; I.theta = theta; I.mu = mu;
+    I.resume = 0;
+    I.pres = pres; I.dres = dres; I.dgap = dgap; I.ctx = ctx; I.bty = bty; I.obj = ctx / tau;
+    I.admm_iters = total; I.outer_iters = outer; I.status = status;
+    I.fp32_iters_lo = (int32_t)(total & 0x7fffffff);
+    I.fp32_iters_hi = (int32_t)(total >> 31);
+    if (!ok) I.err = DEV_ERR_NONFINITE;
+  }
+  __syncthreads();
+}
+
+__global__ void __launch_bounds__(kThreads) dense_solve_mixed_kernel(DenseInst* insts, int count, DenseParams P,
+                                                                     int* queue) {
+  extern __shared__ double sm_raw[];
+  __shared__ double red[32 * 9];
+  for (;;) {
+    const int id = next_instance(queue, count);
+    if (id < 0) return;
+    DenseInst& I = insts[id];
+    if (I.err != 0) continue;
+    dense_solve_delta(I, P, reinterpret_cast<unsigned char*>(sm_raw), red);
+  }
 }
 
 template <typename T>
@@ -545,10 +816,7 @@ __global__ void __launch_bounds__(kThreads) dense_solve_kernel(DenseInst* insts,
     if (id < 0) return;
     DenseInst& I = insts[id];
     if (I.err != 0) continue;
-    if (dense_solve_one<T>(I, P, sm, red) == 1) {
-      // escalation: finish the instance with FP64 iterates (shared memory is sized for FP64)
-      dense_solve_one<double>(I, P, reinterpret_cast<double*>(sm_raw), red);
-    }
+    dense_solve_one<T>(I, P, sm, red);
   }
 }
 
@@ -1062,11 +1330,11 @@ cudaError_t launch_dense_setup(DenseInst* inst, int count, int* queue, int grid,
 
 cudaError_t launch_dense_solve(DenseInst* inst, int count, DenseParams prm, int* queue, int grid,
                                size_t smem, cudaStream_t st) {
-  // the caller sizes smem for the largest instance: (5m + 3n) elements of the iteration type
+  // the caller sizes smem for the largest instance: (5m + 3n) doubles (FP64), 48m + 40n bytes (mixed)
   if (prm.mixed) {
-    cudaError_t e = cudaFuncSetAttribute(dense_solve_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDenseSmemMax);
+    cudaError_t e = cudaFuncSetAttribute(dense_solve_mixed_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDenseSmemMax);
     if (e != cudaSuccess) return e;
-    dense_solve_kernel<float><<<grid, kThreads, smem, st>>>(inst, count, prm, queue);
+    dense_solve_mixed_kernel<<<grid, kThreads, smem, st>>>(inst, count, prm, queue);
   } else {
     cudaError_t e = cudaFuncSetAttribute(dense_solve_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDenseSmemMax);
     if (e != cudaSuccess) return e;
@@ -1078,8 +1346,8 @@ cudaError_t launch_dense_solve(DenseInst* inst, int count, DenseParams prm, int*
 int dense_solve_ctas_per_sm(bool mixed, size_t smem) {
   int per = 0;
   if (mixed) {
-    cudaFuncSetAttribute(dense_solve_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDenseSmemMax);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, dense_solve_kernel<float>, kThreads, smem);
+    cudaFuncSetAttribute(dense_solve_mixed_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDenseSmemMax);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, dense_solve_mixed_kernel, kThreads, smem);
   } else {
     cudaFuncSetAttribute(dense_solve_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDenseSmemMax);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, dense_solve_kernel<double>, kThreads, smem);

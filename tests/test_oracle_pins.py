@@ -350,3 +350,17 @@ def test_central_point_gradient_vertex_limit():
     assert np.abs(g["dc"]).max() <= 1e-6 * scale
     dA = -np.outer(w, x0)
     assert np.abs(g["dA"] - dA).max() <= 1e-6 * np.abs(dA).max()
+
+
+def test_basis_pursuit_recovers_sparse_vector():
+    """Basis pursuit LP (min ||x||_1, D x = b as [D, -D] in standard form): x_true is feasible,
+    so the optimum is at most ||x_true||_1; with 5 % nonzeros and m = n_d / 4 Gaussian
+    measurements l1 recovery succeeds, so the oracle's solution is x_true itself."""
+    sb = W.basis_pursuit(32, 128, batch=1, density=0.05, seed=7)
+    r = O.solve(sb.A, sb.bs[0], sb.cs[0])
+    assert r.status == O.OPTIMAL
+    xt = sb.meta["x_true"][0]
+    nd = sb.meta["n_d"]
+    assert r.obj <= np.abs(xt).sum() * (1 + 1e-6) + 1e-9
+    assert np.abs((r.x[:nd] - r.x[nd:]) - xt).max() <= 1e-4
+    assert abs(r.obj - np.abs(xt).sum()) <= 1e-5 * np.abs(xt).sum()
