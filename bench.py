@@ -106,6 +106,20 @@ def traffic_from_profile(precision, admm_updates):
     return None
 
 
+def aggregate_ranks(total_s, solved, admm, dist_mod=None, device="cpu"):
+    """Whole-job totals over the ranks: the timed region is the slowest rank's, the work
+    (LPs solved, ADMM updates) is summed.  dist_mod: torch.distributed or None (one rank)."""
+    if dist_mod is None:
+        return float(total_s), float(solved), float(admm)
+    import torch
+    t = torch.tensor([total_s, float(solved), float(admm)], dtype=torch.float64, device=device)
+    tmax = t[0:1].clone()
+    work = t[1:3].clone()
+    dist_mod.all_reduce(tmax, op=dist_mod.ReduceOp.MAX)
+    dist_mod.all_reduce(work, op=dist_mod.ReduceOp.SUM)
+    return float(tmax[0]), float(work[0]), float(work[1])
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -348,12 +362,7 @@ def main():
     total_s = sum(step_ms) * 1e-3
     solved = sum(1 for i in infos if i["status"] == abip.ABIP_OPTIMAL)
     admm = sum(i["admm_iters"] for i in infos)
-    if dist:
-        t = torch.tensor([total_s, float(solved), float(admm)], dtype=torch.float64, device=dev)
-        tmax = t.clone()
-        dist.all_reduce(tmax[0:1], op=dist.ReduceOp.MAX)
-        dist.all_reduce(t[1:3], op=dist.ReduceOp.SUM)
-        total_s, solved, admm = float(tmax[0]), float(t[1]), float(t[2])
+    total_s, solved, admm = aggregate_ranks(total_s, solved, admm, dist, dev)
     value = admm / total_s
 
     # roofline of the persistent solve kernel (one launch per step)
