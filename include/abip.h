@@ -67,7 +67,10 @@ extern "C" {
 
 /* arithmetic of the iteration */
 #define ABIP_PREC_F64        0   /* every vector and product in FP64 */
-#define ABIP_PREC_MIXED      1   /* FP32 iterates and products, FP64 termination tests */
+#define ABIP_PREC_MIXED      1   /* FP32 products (of the iterates' changes on the dense paths), FP64 tests */
+#define ABIP_PREC_MIXED_BF16 2   /* as MIXED; the shared-A batch runs its products with A on the tensor
+                                    cores (tcgen05, bfloat16 operands, FP32 accumulation) and needs an
+                                    A exactly representable in bfloat16; other paths treat it as MIXED */
 
 /* linear system for the projection (Sec. 4.4) */
 #define ABIP_LINSYS_DENSE_CHOL  0   /* G = I + A A^T formed once, Cholesky G = L L^T, triangular solves */
@@ -177,9 +180,14 @@ ABIP_API int abip_solve_batch(int32_t count, const abip_matrix* A, const double*
  *   A: one dense row-major matrix (host or device, F32 or F64), 1 <= m <= n.
  *   b[k] (m), c[k] (n): host or device.  x, y, s: arrays of `count` caller-allocated
  *   output pointers (host or device; entries may be NULL), scaled as abip_solve's.
- *   infos: `count` entries or NULL.  p->precision: ABIP_PREC_F64 (FP64 throughout) or
- *   ABIP_PREC_MIXED (FP32 iterates and products; the Sec. 4.1 tests are screened in
- *   FP32 with margin 4 and decided on FP64 products of the same state).
+ *   infos: `count` entries or NULL.  p->precision: ABIP_PREC_F64 (FP64 throughout),
+ *   ABIP_PREC_MIXED (FP64 state; the products are updated by FP32 GEMMs of the state's
+ *   changes and recomputed in FP64 every 200 cycles and before every termination
+ *   decision) or ABIP_PREC_MIXED_BF16 (as MIXED with the products with A on the tensor
+ *   cores: the changes are split into three bfloat16 terms, so the products keep FP32
+ *   accuracy; A must be exactly representable in bfloat16, else ABIP_E_INVALID_ARG;
+ *   shapes other than m, n multiples of 128 and count a multiple of 16 per chunk of 64
+ *   use the FP32 GEMMs).
  * Instances are processed in chunks of 64.  Needs m <= 25600.  Errors: as
  * abip_solve_batch; ABIP_E_UNSUPPORTED for a CSR A.
  */

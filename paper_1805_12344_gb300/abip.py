@@ -41,6 +41,7 @@ ABIP_DUAL_INFEASIBLE = 3
 ABIP_MAX_ITER = 4
 ABIP_PREC_F64 = 0
 ABIP_PREC_MIXED = 1
+ABIP_PREC_MIXED_BF16 = 2
 ABIP_LINSYS_DENSE_CHOL = 0
 ABIP_LINSYS_PCG = 1
 

@@ -122,7 +122,10 @@ int check_params(const abip_params& p, std::string& why) {
   if (!(p.cg_tol > 0)) { why = "cg_tol must be > 0"; return 0; }
   if (!(p.cg_rel >= 0)) { why = "cg_rel must be >= 0"; return 0; }
   if (p.cg_max_iter < 1) { why = "cg_max_iter must be >= 1"; return 0; }
-  if (p.precision != ABIP_PREC_F64 && p.precision != ABIP_PREC_MIXED) { why = "unknown precision"; return 0; }
+  if (p.precision != ABIP_PREC_F64 && p.precision != ABIP_PREC_MIXED && p.precision != ABIP_PREC_MIXED_BF16) {
+    why = "unknown precision";
+    return 0;
+  }
   if (p.linsys != ABIP_LINSYS_DENSE_CHOL && p.linsys != ABIP_LINSYS_PCG && p.linsys != -1) { why = "unknown linsys"; return 0; }
   if (p.warmstart != 0 && p.warmstart != 1) { why = "warmstart must be 0 or 1"; return 0; }
   if (p.cg_warm < 0 || p.cg_warm > 2) { why = "cg_warm must be 0, 1 or 2"; return 0; }
@@ -549,7 +552,7 @@ int dense_run_setup(abip_handle* h, DenseInst* dinst, int* queue, int count, int
 int dense_run_solve(abip_handle* h, DenseInst* dinst, int* queue, int count, int grid, size_t smem,
                     const abip_params& p, cudaStream_t st) {
   DenseParams dp{p.beta, p.gamma, p.alpha, p.eps, p.max_admm_iters, p.warmstart, p.stop_rule,
-                 p.precision == ABIP_PREC_MIXED ? 1 : 0, std::max(1, p.check_every)};
+                 p.precision != ABIP_PREC_F64 ? 1 : 0, std::max(1, p.check_every)};
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
@@ -828,7 +831,7 @@ int abip_setup(const abip_matrix* A, const double* b, const double* c, const abi
   int linsys = prm.linsys;
   if (linsys < 0) linsys = A->fmt == ABIP_CSR ? ABIP_LINSYS_PCG : ABIP_LINSYS_DENSE_CHOL;
   h->prm.linsys = linsys;
-  h->mixed = prm.precision == ABIP_PREC_MIXED;
+  h->mixed = prm.precision != ABIP_PREC_F64;
   if (linsys == ABIP_LINSYS_PCG) {
     h->path = 0;
     HostCSR hA;
@@ -959,7 +962,7 @@ int abip_solve_batch(int32_t count, const abip_matrix* A, const double* const* b
   else abip_default_params(&prm);
   std::string why;
   if (!check_params(prm, why)) return fail(nullptr, ABIP_E_INVALID_ARG, why);
-  const bool mixed = prm.precision == ABIP_PREC_MIXED;
+  const bool mixed = prm.precision != ABIP_PREC_F64;
   abip_handle tmp;
   cudaGetDevice(&tmp.device);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -1059,7 +1062,17 @@ int abip_solve_batch_shared(int32_t count, const abip_matrix* A, const double* c
   abip::ShParams sp{};
   sp.beta = prm.beta; sp.gamma = prm.gamma; sp.alpha = prm.alpha; sp.eps = prm.eps;
   sp.max_admm = prm.max_admm_iters; sp.warmstart = prm.warmstart; sp.stop_rule = prm.stop_rule;
-  sp.mixed = prm.precision == ABIP_PREC_MIXED ? 1 : 0;
+  sp.mixed = prm.precision != ABIP_PREC_F64 ? 1 : 0;
+  sp.tc = prm.precision == ABIP_PREC_MIXED_BF16 ? 1 : 0;
+  if (sp.tc) {   // the tensor-core products use A in bfloat16: it must be exact there
+    for (const double v : Ah) {
+      const float f = (float)v;
+      uint32_t u;
+      std::memcpy(&u, &f, 4);
+      if ((double)f != v || (u & 0xFFFFu) != 0)
+        return fail(nullptr, ABIP_E_INVALID_ARG, "ABIP_PREC_MIXED_BF16 needs A exactly representable in bfloat16");
+    }
+  }
   sp.n = n;
   sp.confirm_gap = std::max<int64_t>(prm.check_every, 20);
   sp.refresh = 200;

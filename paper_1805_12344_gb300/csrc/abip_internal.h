@@ -193,7 +193,7 @@ struct ShParams {
   int32_t warmstart, stop_rule, mixed, n;
   int64_t confirm_gap;
   int32_t refresh;                 // mixed: FP64 recomputation of the maintained products every `refresh` cycles
-  int32_t pad;
+  int32_t tc;                      // mixed: products with A on the tensor cores (A exact in bfloat16)
 };
 
 // Device arrays of one iteration type; every vector is [length x B], instance fastest.
@@ -221,6 +221,7 @@ struct SharedBatchResult {
   double setup_s;                  // device time of the setup (Gram, Cholesky, inverse, M^{-1} H)
   double kernel_s;                 // device time of the iterations
   int64_t launches;
+  bool tensor_cores;               // the products with A ran on tcgen05
 };
 
 int shared_batch_run(const SharedBatchArgs& a, std::vector<SharedBatchResult>& out, std::string& err);

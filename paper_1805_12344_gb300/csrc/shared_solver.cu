@@ -19,6 +19,7 @@
 //             dual update (Eqs. Simple-Update:*, Sec. 4.2)
 #include "abip_internal.h"
 #include "abip_device.cuh"
+#include "tc_gemm.cuh"
 
 #include <algorithm>
 #include <cstring>
@@ -242,6 +243,19 @@ template <typename T>
 __global__ void convert_kernel(const double* __restrict__ src, T* __restrict__ dst, size_t len) {
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < len; e += (size_t)gridDim.x * blockDim.x)
     dst[e] = (T)src[e];
+}
+
+// bfloat16 copies of A (m x n) and A^T (n x m) for the tensor-core products; A is exact in
+// bfloat16 (checked by the host), so the conversion loses nothing.
+__global__ void bf16_copies_kernel(const double* __restrict__ A, int m, int n, __nv_bfloat16* __restrict__ A16,
+                                   __nv_bfloat16* __restrict__ AT16) {
+  const size_t tot = (size_t)m * n;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < tot; e += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e / n), j = (int)(e % n);
+    const __nv_bfloat16 v = __float2bfloat16_rn((float)A[e]);
+    A16[e] = v;
+    AT16[(size_t)j * m + i] = v;
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -796,6 +810,36 @@ cudaError_t gemm_acc(bool trans, const float* A, int64_t lda, int M, int N, int 
   return cudaGetLastError();
 }
 
+// Tensor-core product of deltas (tcgen05, A16 exact bfloat16, W split in three bfloat16
+// terms), accumulated into an FP64 running product like gemm_acc.
+struct TcPlan {
+  int splits = 1, kchunk = 0;
+};
+TcPlan plan_tc(int M, int K, int sms) {
+  TcPlan p;
+  const int tiles = M / tc::kTM, kblocks = K / tc::kTK;
+  int splits = std::max(1, (2 * sms + tiles - 1) / tiles);
+  splits = std::min(splits, std::max(1, kblocks / 4));
+  p.kchunk = ((kblocks + splits - 1) / splits) * tc::kTK;
+  p.splits = (K + p.kchunk - 1) / p.kchunk;
+  return p;
+}
+bool tc_shape_ok(int m, int n, int B) {
+  return m % tc::kTM == 0 && n % tc::kTM == 0 && B % 16 == 0 && 2 * B <= 256;
+}
+cudaError_t gemm_tc(const __nv_bfloat16* A16, int64_t lda, int M, int N, int K, const float* W, int64_t ldw, int B,
+                    double* acc64, float* out32, const ShInst* mask, float* work, size_t work_elems, int sms,
+                    int* err, cudaStream_t st) {
+  const TcPlan p = plan_tc(M, K, sms);
+  if ((size_t)p.splits * M * N > work_elems) return cudaErrorInvalidValue;
+  tc::tc_gemm_kernel<<<dim3(M / tc::kTM, p.splits), tc::kTCThreads, tc::tc_smem_bytes(N), st>>>(
+      A16, lda, M, N, K, W, ldw, work, p.kchunk, err);
+  const size_t MN = (size_t)M * N;
+  const int rb = (int)std::min<size_t>((MN + kThr - 1) / kThr, (size_t)sms * 8);
+  accum_kernel<<<std::max(rb, 1), kThr, 0, st>>>(work, p.splits, M, N, B, acc64, out32, mask);
+  return cudaGetLastError();
+}
+
 template <typename T>
 size_t gemm_work(int M, int N, int K, int sms) {
   const GemmPlan g = plan_gemm<T>(M, N, K, sms);
@@ -829,10 +873,14 @@ int shared_batch_run(const SharedBatchArgs& a, std::vector<SharedBatchResult>& o
   const size_t wk64 = std::max({gemm_work<double>(m, m, n, sms), gemm_work<double>(m, 2 * B, n, sms),
                                 gemm_work<double>(m, 2 * B, m, sms), gemm_work<double>(n, 2 * B, m, sms),
                                 gemm_work<double>(n, B, m, sms), gemm_work<double>(m, B, m, sms)});
-  const size_t wk32 = mixed ? std::max({gemm_work<float>(m, 2 * B, n, sms), gemm_work<float>(n, B, m, sms),
-                                        gemm_work<float>(m, B, m, sms)})
-                            : 0;
+  const bool tc = mixed && a.prm.tc != 0 && tc_shape_ok(m, n, B);
+  size_t wk32 = mixed ? std::max({gemm_work<float>(m, 2 * B, n, sms), gemm_work<float>(n, B, m, sms),
+                                  gemm_work<float>(m, B, m, sms)})
+                      : 0;
+  if (tc)
+    wk32 = std::max({wk32, (size_t)plan_tc(m, n, sms).splits * m * 2 * B, (size_t)plan_tc(n, m, sms).splits * n * B});
   ShView<double> V{};
+  __nv_bfloat16 *A16 = nullptr, *AT16 = nullptr;
   double *A64 = nullptr, *AT64 = nullptr, *G = nullptr, *Ginv64 = nullptr, *Ae = nullptr, *work64 = nullptr;
   double *partials = nullptr, *W2 = nullptr, *P2 = nullptr, *R = nullptr, *ZY2 = nullptr, *ZX2 = nullptr;
   double *Xo = nullptr, *Yo = nullptr, *So = nullptr, *ATZY = nullptr, *Qprev = nullptr;
@@ -870,10 +918,14 @@ int shared_batch_run(const SharedBatchArgs& a, std::vector<SharedBatchResult>& o
     V.Y = bp.take<double>((size_t)m * B); V.XS = bp.take<double>((size_t)n * 2 * B);
     V.AXS = bp.take<double>((size_t)m * 2 * B); V.ATY = bp.take<double>((size_t)n * B);
     V.Q = bp.take<double>((size_t)m * B); V.ZY = bp.take<double>((size_t)m * B); V.ZX = bp.take<double>((size_t)n * B);
+    if (tc) {
+      A16 = bp.take<__nv_bfloat16>((size_t)m * n);
+      AT16 = bp.take<__nv_bfloat16>((size_t)n * m);
+    }
     if (mixed) {
       ATZY = bp.take<double>((size_t)n * B);
       Qprev = bp.take<double>((size_t)m * B);
-      A32 = bp.take<float>((size_t)m * n);
+      A32 = bp.take<float>((size_t)(tc ? 1 : m) * (tc ? 1 : n));
       Ginv32 = bp.take<float>((size_t)m * m);
       work32 = bp.take<float>(wk32);
       dY = bp.take<float>((size_t)m * B);
@@ -943,7 +995,13 @@ int shared_batch_run(const SharedBatchArgs& a, std::vector<SharedBatchResult>& o
   init_state_kernel<double><<<eb, kThr, 0, st>>>(V);
   if (mixed) {
     const int cb = sms * 8;
-    convert_kernel<float><<<cb, kThr, 0, st>>>(A64, A32, (size_t)m * n);
+    if (tc) {
+      bf16_copies_kernel<<<cb, kThr, 0, st>>>(A64, m, n, A16, AT16);
+      ck(cudaFuncSetAttribute(tc::tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)tc::tc_smem_bytes(2 * B)), "tc smem");
+    } else {
+      convert_kernel<float><<<cb, kThr, 0, st>>>(A64, A32, (size_t)m * n);
+    }
     convert_kernel<float><<<cb, kThr, 0, st>>>(Ginv64, Ginv32, (size_t)m * m);
   }
   ck(cudaGetLastError(), "setup launches");
@@ -994,13 +1052,19 @@ int shared_batch_run(const SharedBatchArgs& a, std::vector<SharedBatchResult>& o
     refresh();
     // projection on the change of Q: ZY += G^{-1} dQ, A^T ZY += A^T (G^{-1} dQ)
     ck(gemm_acc(false, Ginv32, m, m, B, m, dQ, B, B, V.ZY, dZY, insts, work32, wk32, sms, st), "Ginv dQ");
-    ck(gemm_acc(true, A32, n, n, B, m, dZY, B, B, ATZY, nullptr, nullptr, work32, wk32, sms, st), "A^T dZY");
+    if (tc) ck(gemm_tc(AT16, m, n, B, m, dZY, B, B, ATZY, nullptr, nullptr, work32, wk32, sms, derr + 1, st), "A^T dZY");
+    else ck(gemm_acc(true, A32, n, n, B, m, dZY, B, B, ATZY, nullptr, nullptr, work32, wk32, sms, st), "A^T dZY");
     hz_delta_kernel<<<red_ctas, kThr, 0, st>>>(V, ATZY, Qprev, insts, partials);
     ctrl_step_kernel<<<1, kMaxBatch, 0, st>>>(insts, B, n, partials, red_ctas, a.prm);
     update_kernel<double><<<eb, kThr, 0, st>>>(V, insts, a.prm, dY, dXS);
     // maintained products of the new state: AX, AS += A [dX dS], A^T Y += A^T dY
-    ck(gemm_acc(false, A32, n, m, 2 * B, n, dXS, 2 * B, B, V.AXS, nullptr, nullptr, work32, wk32, sms, st), "A dXS");
-    ck(gemm_acc(true, A32, n, n, B, m, dY, B, B, V.ATY, nullptr, nullptr, work32, wk32, sms, st), "A^T dY");
+    if (tc) {
+      ck(gemm_tc(A16, n, m, 2 * B, n, dXS, 2 * B, B, V.AXS, nullptr, nullptr, work32, wk32, sms, derr + 1, st), "A dXS");
+      ck(gemm_tc(AT16, m, n, B, m, dY, B, B, V.ATY, nullptr, nullptr, work32, wk32, sms, derr + 1, st), "A^T dY");
+    } else {
+      ck(gemm_acc(false, A32, n, m, 2 * B, n, dXS, 2 * B, B, V.AXS, nullptr, nullptr, work32, wk32, sms, st), "A dXS");
+      ck(gemm_acc(true, A32, n, n, B, m, dY, B, B, V.ATY, nullptr, nullptr, work32, wk32, sms, st), "A^T dY");
+    }
     launches += 11;
   };
   if (mixed && rc == ABIP_OK) {
@@ -1026,6 +1090,14 @@ int shared_batch_run(const SharedBatchArgs& a, std::vector<SharedBatchResult>& o
     if (cycles > max_cycles) { err = "shared batch: cycle guard reached"; rc = ABIP_E_NUMERICAL; }
   }
   cudaFreeHost(hflags);
+  if (rc == ABIP_OK && tc) {
+    int herr2 = 0;
+    ck(cudaMemcpy(&herr2, derr + 1, sizeof(int), cudaMemcpyDeviceToHost), "tensor-core status");
+    if (rc == ABIP_OK && herr2 != 0) {
+      err = "shared batch: a tensor-core wait ran past its limit";
+      rc = ABIP_E_TIMEOUT;
+    }
+  }
   // ---- outputs
   if (rc == ABIP_OK) {
     output_kernel<double><<<eb, kThr, 0, st>>>(V, insts, Xo, Yo, So);
@@ -1047,6 +1119,7 @@ int shared_batch_run(const SharedBatchArgs& a, std::vector<SharedBatchResult>& o
       r.setup_s = ms_setup * 1e-3;
       r.kernel_s = ms_iter * 1e-3;
       r.launches = launches;
+      r.tensor_cores = tc;
       r.x.resize(n); r.y.resize(m); r.s.resize(n);
       for (int j = 0; j < n; ++j) { r.x[j] = hx[(size_t)j * B + k]; r.s[j] = hs[(size_t)j * B + k]; }
       for (int i = 0; i < m; ++i) r.y[i] = hy[(size_t)i * B + k];

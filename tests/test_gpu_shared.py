@@ -134,3 +134,28 @@ def test_shared_chunks_past_64(abip):
     for k in (0, 33, 63):
         ref = O.solve(A, bs[k], cs[k])
         assert abs(infos[k]["obj"] - ref.obj) <= OBJ_TOL * max(1.0, abs(ref.obj))
+
+
+def test_shared_tensor_cores_end_to_end(abip):
+    """ABIP_PREC_MIXED_BF16: the products with A run on tcgen05 (A exact in bfloat16, the
+    changes split in three bfloat16 terms); same bars as the other paths."""
+    sb = W.basis_pursuit(128, 256, batch=16, seed=9)
+    prm = abip.default_params(precision=abip.ABIP_PREC_MIXED_BF16)
+    infos, xs, ys, ss = abip.abip_solve_batch_shared(sb.A, sb.bs, sb.cs, prm)
+    for k in range(16):
+        f = infos[k]
+        assert f["status"] == O.OPTIMAL, (k, f["status_name"])
+        assert max(f["pres"], f["dres"], f["dgap"]) <= 1e-6
+        assert np.linalg.norm(sb.A @ xs[k] - sb.bs[k]) <= 1e-6 * (1 + np.linalg.norm(sb.bs[k])) * 1.01
+        assert f["obj"] <= np.abs(sb.meta["x_true"][k]).sum() * (1 + 1e-5)
+    for k in (0, 7, 15):
+        ref = O.solve(sb.A, sb.bs[k], sb.cs[k])
+        assert ref.status == O.OPTIMAL
+        assert abs(infos[k]["obj"] - ref.obj) <= OBJ_TOL * max(1.0, abs(ref.obj))
+
+
+def test_shared_tensor_cores_need_bfloat16_A(abip):
+    A, bs, cs, _ = _shared_planted(128, 256, 16, seed=3)
+    with pytest.raises(abip.AbipError) as e:
+        abip.abip_solve_batch_shared(A, bs, cs, abip.default_params(precision=abip.ABIP_PREC_MIXED_BF16))
+    assert e.value.code == abip.ABIP_E_INVALID_ARG
