@@ -815,10 +815,12 @@ cudaError_t gemm_acc(bool trans, const float* A, int64_t lda, int M, int N, int 
 struct TcPlan {
   int splits = 1, kchunk = 0;
 };
-TcPlan plan_tc(int M, int K, int sms) {
+TcPlan plan_tc(int M, int N, int K, int sms) {
+  // one wave: CTAs per SM from the two-stage shared memory, split K to fill the SMs
   TcPlan p;
+  const int occ = std::max(1, (int)((227 * 1024) / tc::tc2_smem_bytes(N)));
   const int tiles = M / tc::kTM, kblocks = K / tc::kTK;
-  int splits = std::max(1, (2 * sms + tiles - 1) / tiles);
+  int splits = std::max(1, (sms * occ) / tiles);
   splits = std::min(splits, std::max(1, kblocks / 4));
   p.kchunk = ((kblocks + splits - 1) / splits) * tc::kTK;
   p.splits = (K + p.kchunk - 1) / p.kchunk;
@@ -828,12 +830,13 @@ bool tc_shape_ok(int m, int n, int B) {
   return m % tc::kTM == 0 && n % tc::kTM == 0 && B % 16 == 0 && 2 * B <= 256;
 }
 cudaError_t gemm_tc(const __nv_bfloat16* A16, int64_t lda, int M, int N, int K, const float* W, int64_t ldw, int B,
-                    double* acc64, float* out32, const ShInst* mask, float* work, size_t work_elems, int sms,
-                    int* err, cudaStream_t st) {
-  const TcPlan p = plan_tc(M, K, sms);
+                    double* acc64, float* out32, const ShInst* mask, float* work, size_t work_elems,
+                    __nv_bfloat16* wt, int sms, int* err, cudaStream_t st) {
+  const TcPlan p = plan_tc(M, N, K, sms);
   if ((size_t)p.splits * M * N > work_elems) return cudaErrorInvalidValue;
-  tc::tc_gemm_kernel<<<dim3(M / tc::kTM, p.splits), tc::kTCThreads, tc::tc_smem_bytes(N), st>>>(
-      A16, lda, M, N, K, W, ldw, work, p.kchunk, err);
+  tc::split3_kernel<<<dim3((K + 31) / 32, (N + 31) / 32), dim3(32, 8), 0, st>>>(W, ldw, K, N, wt);
+  tc::tc_gemm2_kernel<<<dim3(M / tc::kTM, p.splits), tc::kTCThreads, tc::tc2_smem_bytes(N), st>>>(
+      A16, lda, M, N, K, wt, work, p.kchunk, err);
   const size_t MN = (size_t)M * N;
   const int rb = (int)std::min<size_t>((MN + kThr - 1) / kThr, (size_t)sms * 8);
   accum_kernel<<<std::max(rb, 1), kThr, 0, st>>>(work, p.splits, M, N, B, acc64, out32, mask);
@@ -869,7 +872,8 @@ int shared_batch_run(const SharedBatchArgs& a, std::vector<SharedBatchResult>& o
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const int red_ctas = std::max(1, std::min(sms * 2, (m + n + 63) / 64));
+  // CTAs of the per-instance column reductions: each control thread adds red_ctas partials
+  const int red_ctas = std::max(1, std::min(sms / 2, (m + n + 255) / 256));
   const size_t wk64 = std::max({gemm_work<double>(m, m, n, sms), gemm_work<double>(m, 2 * B, n, sms),
                                 gemm_work<double>(m, 2 * B, m, sms), gemm_work<double>(n, 2 * B, m, sms),
                                 gemm_work<double>(n, B, m, sms), gemm_work<double>(m, B, m, sms)});
@@ -878,9 +882,10 @@ int shared_batch_run(const SharedBatchArgs& a, std::vector<SharedBatchResult>& o
                                   gemm_work<float>(m, B, m, sms)})
                       : 0;
   if (tc)
-    wk32 = std::max({wk32, (size_t)plan_tc(m, n, sms).splits * m * 2 * B, (size_t)plan_tc(n, m, sms).splits * n * B});
+    wk32 = std::max({wk32, (size_t)plan_tc(m, 2 * B, n, sms).splits * m * 2 * B,
+                     (size_t)plan_tc(n, B, m, sms).splits * n * B});
   ShView<double> V{};
-  __nv_bfloat16 *A16 = nullptr, *AT16 = nullptr;
+  __nv_bfloat16 *A16 = nullptr, *AT16 = nullptr, *WT16 = nullptr;
   double *A64 = nullptr, *AT64 = nullptr, *G = nullptr, *Ginv64 = nullptr, *Ae = nullptr, *work64 = nullptr;
   double *partials = nullptr, *W2 = nullptr, *P2 = nullptr, *R = nullptr, *ZY2 = nullptr, *ZX2 = nullptr;
   double *Xo = nullptr, *Yo = nullptr, *So = nullptr, *ATZY = nullptr, *Qprev = nullptr;
@@ -921,6 +926,7 @@ int shared_batch_run(const SharedBatchArgs& a, std::vector<SharedBatchResult>& o
     if (tc) {
       A16 = bp.take<__nv_bfloat16>((size_t)m * n);
       AT16 = bp.take<__nv_bfloat16>((size_t)n * m);
+      WT16 = bp.take<__nv_bfloat16>(3 * std::max((size_t)2 * B * n, (size_t)B * m));
     }
     if (mixed) {
       ATZY = bp.take<double>((size_t)n * B);
@@ -997,8 +1003,8 @@ int shared_batch_run(const SharedBatchArgs& a, std::vector<SharedBatchResult>& o
     const int cb = sms * 8;
     if (tc) {
       bf16_copies_kernel<<<cb, kThr, 0, st>>>(A64, m, n, A16, AT16);
-      ck(cudaFuncSetAttribute(tc::tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)tc::tc_smem_bytes(2 * B)), "tc smem");
+      ck(cudaFuncSetAttribute(tc::tc_gemm2_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)tc::tc2_smem_bytes(2 * B)), "tc smem");
     } else {
       convert_kernel<float><<<cb, kThr, 0, st>>>(A64, A32, (size_t)m * n);
     }
@@ -1052,20 +1058,23 @@ int shared_batch_run(const SharedBatchArgs& a, std::vector<SharedBatchResult>& o
     refresh();
     // projection on the change of Q: ZY += G^{-1} dQ, A^T ZY += A^T (G^{-1} dQ)
     ck(gemm_acc(false, Ginv32, m, m, B, m, dQ, B, B, V.ZY, dZY, insts, work32, wk32, sms, st), "Ginv dQ");
-    if (tc) ck(gemm_tc(AT16, m, n, B, m, dZY, B, B, ATZY, nullptr, nullptr, work32, wk32, sms, derr + 1, st), "A^T dZY");
+    if (tc) ck(gemm_tc(AT16, m, n, B, m, dZY, B, B, ATZY, nullptr, nullptr, work32, wk32, WT16, sms, derr + 1, st),
+               "A^T dZY");
     else ck(gemm_acc(true, A32, n, n, B, m, dZY, B, B, ATZY, nullptr, nullptr, work32, wk32, sms, st), "A^T dZY");
     hz_delta_kernel<<<red_ctas, kThr, 0, st>>>(V, ATZY, Qprev, insts, partials);
     ctrl_step_kernel<<<1, kMaxBatch, 0, st>>>(insts, B, n, partials, red_ctas, a.prm);
     update_kernel<double><<<eb, kThr, 0, st>>>(V, insts, a.prm, dY, dXS);
     // maintained products of the new state: AX, AS += A [dX dS], A^T Y += A^T dY
     if (tc) {
-      ck(gemm_tc(A16, n, m, 2 * B, n, dXS, 2 * B, B, V.AXS, nullptr, nullptr, work32, wk32, sms, derr + 1, st), "A dXS");
-      ck(gemm_tc(AT16, m, n, B, m, dY, B, B, V.ATY, nullptr, nullptr, work32, wk32, sms, derr + 1, st), "A^T dY");
+      ck(gemm_tc(A16, n, m, 2 * B, n, dXS, 2 * B, B, V.AXS, nullptr, nullptr, work32, wk32, WT16, sms, derr + 1, st),
+         "A dXS");
+      ck(gemm_tc(AT16, m, n, B, m, dY, B, B, V.ATY, nullptr, nullptr, work32, wk32, WT16, sms, derr + 1, st),
+         "A^T dY");
     } else {
       ck(gemm_acc(false, A32, n, m, 2 * B, n, dXS, 2 * B, B, V.AXS, nullptr, nullptr, work32, wk32, sms, st), "A dXS");
       ck(gemm_acc(true, A32, n, n, B, m, dY, B, B, V.ATY, nullptr, nullptr, work32, wk32, sms, st), "A^T dY");
     }
-    launches += 11;
+    launches += tc ? 14 : 11;
   };
   if (mixed && rc == ABIP_OK) {
     // exact products of the starting point
@@ -1094,8 +1103,9 @@ int shared_batch_run(const SharedBatchArgs& a, std::vector<SharedBatchResult>& o
     int herr2 = 0;
     ck(cudaMemcpy(&herr2, derr + 1, sizeof(int), cudaMemcpyDeviceToHost), "tensor-core status");
     if (rc == ABIP_OK && herr2 != 0) {
-      err = "shared batch: a tensor-core wait ran past its limit";
-      rc = ABIP_E_TIMEOUT;
+      err = herr2 == tc::kErrShape ? "shared batch: tensor-core product called with an unsupported shape"
+                                   : "shared batch: a tensor-core wait ran past its limit";
+      rc = herr2 == tc::kErrShape ? ABIP_E_INVALID_ARG : ABIP_E_TIMEOUT;
     }
   }
   // ---- outputs

@@ -31,6 +31,7 @@ constexpr int kTK = 64;           // K per staging step
 constexpr int kTCThreads = 128;
 constexpr unsigned long long kWaitLimitNs = 2000000000ull;   // 2 s per wait
 constexpr int kErrTimeout = 1;
+constexpr int kErrShape = 2;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -240,6 +241,167 @@ __global__ void __launch_bounds__(kTCThreads, 1)
     for (int c0 = 0; c0 < N; c0 += 16) {
       float v[16];
       if (any) {
+        tmem_ld16(tmem + (static_cast<uint32_t>(warp * 32) << 16) + static_cast<uint32_t>(c0), v);
+      } else {
+#pragma unroll
+        for (int q = 0; q < 16; ++q) v[q] = 0.f;
+      }
+#pragma unroll
+      for (int q = 0; q < 16; q += 4)
+        *reinterpret_cast<float4*>(C + (size_t)row * N + c0 + q) = make_float4(v[q], v[q + 1], v[q + 2], v[q + 3]);
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tmem, ncols);
+}
+
+// ---------------------------------------------------------------------------
+// Pipelined variant: the changes are split beforehand into three bfloat16 arrays
+// Wt[t] (N rows x K, K contiguous), so every tile is a plain 16-byte copy.  Two shared
+// memory stages: while the MMAs of step j run, cp.async fills the other stage with step
+// j + 1; an mbarrier per stage tells when its MMAs have finished reading it.
+// ---------------------------------------------------------------------------
+
+// Wt[t][n][k] = t-th bfloat16 term of W[k][n] (W: K x N FP32 row-major, ldw).
+__global__ void split3_kernel(const float* __restrict__ W, int64_t ldw, int K, int N, __nv_bfloat16* __restrict__ Wt) {
+  __shared__ float tile[32][33];
+  const int k0 = blockIdx.x * 32, n0 = blockIdx.y * 32;
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+    const int k = k0 + r, n = n0 + threadIdx.x;
+    tile[r][threadIdx.x] = (k < K && n < N) ? W[(size_t)k * ldw + n] : 0.f;
+  }
+  __syncthreads();
+  const size_t plane = (size_t)N * K;
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+    const int n = n0 + r, k = k0 + threadIdx.x;
+    if (n < N && k < K) {
+      const float w = tile[threadIdx.x][r];
+      const __nv_bfloat16 h = __float2bfloat16_rn(w);
+      const float r1 = w - __bfloat162float(h);
+      const __nv_bfloat16 md = __float2bfloat16_rn(r1);
+      const __nv_bfloat16 lo = __float2bfloat16_rn(r1 - __bfloat162float(md));
+      const size_t e = (size_t)n * K + k;
+      Wt[e] = h;
+      Wt[plane + e] = md;
+      Wt[2 * plane + e] = lo;
+    }
+  }
+}
+
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int NPEND>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(NPEND) : "memory");
+}
+
+__host__ __device__ inline size_t tc2_stage_bytes(int N) {
+  return static_cast<size_t>(kTM) * kTK * 2 + 3 * static_cast<size_t>(N) * kTK * 2;
+}
+__host__ __device__ inline size_t tc2_smem_bytes(int N) { return 1024 + 2 * tc2_stage_bytes(N); }
+
+// Requirements as tc_gemm_kernel, plus K % 8 == 0 for Wt rows (16-byte chunks).
+__global__ void __launch_bounds__(kTCThreads, 1)
+    tc_gemm2_kernel(const __nv_bfloat16* __restrict__ A16, int64_t lda, int M, int N, int K,
+                    const __nv_bfloat16* __restrict__ Wt, float* __restrict__ Cp, int kchunk, int* err) {
+  // shapes the tiles and the 16-byte copies need; anything else is refused here
+  if (M % kTM != 0 || K % kTK != 0 || kchunk <= 0 || kchunk % kTK != 0 || N % 16 != 0 || N < 16 || N > 256 ||
+      lda % 8 != 0 || (reinterpret_cast<uintptr_t>(A16) & 15) != 0 || (reinterpret_cast<uintptr_t>(Wt) & 15) != 0) {
+    if (threadIdx.x == 0 && blockIdx.x == 0 && blockIdx.y == 0) atomicExch(err, kErrShape);
+    return;
+  }
+  extern __shared__ uint8_t tc_smem_raw[];
+  __shared__ uint64_t mbar[2];
+  __shared__ uint32_t tslot;
+  __shared__ int failed;
+  uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(tc_smem_raw) + 1023) & ~uintptr_t(1023));
+  const uint32_t stage = static_cast<uint32_t>(tc2_stage_bytes(N));
+  const uint32_t abytes = kTM * kTK * 2, wbytes = static_cast<uint32_t>(N) * kTK * 2;
+  const size_t plane = static_cast<size_t>(N) * K;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int m0 = blockIdx.x * kTM;
+  const int kz0 = blockIdx.y * kchunk, kz1 = min(K, kz0 + kchunk);
+  const int steps = kz1 > kz0 ? (kz1 - kz0) / kTK : 0;
+  uint32_t ncols = 32;
+  while (ncols < static_cast<uint32_t>(N)) ncols <<= 1;
+  if (tid == 0) {
+    mbar_init(&mbar[0], 1);
+    mbar_init(&mbar[1], 1);
+    failed = 0;
+  }
+  if (warp == 0) tmem_alloc(&tslot, ncols);
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tslot;
+  const uint32_t idesc = instr_desc(kTM, N);
+  const uint32_t s0 = smem_u32(base);
+  auto load_stage = [&](int j) {
+    const int k0 = kz0 + j * kTK;
+    const uint32_t sa = s0 + (j & 1) * stage;
+    for (int e = tid; e < kTM * 8; e += kTCThreads) {
+      const int r = e >> 3, kc = e & 7;
+      cp_async16(sa + core_off(r, kc), A16 + (size_t)(m0 + r) * lda + k0 + kc * 8);
+    }
+    for (int e = tid; e < 3 * N * 8; e += kTCThreads) {
+      const int t = e / (N * 8), rem = e % (N * 8), n = rem >> 3, kc = rem & 7;
+      cp_async16(sa + abytes + t * wbytes + core_off(n, kc), Wt + t * plane + (size_t)n * K + k0 + kc * 8);
+    }
+    cp_async_commit();
+  };
+  uint32_t uses[2] = {0u, 0u};
+  if (steps > 0) load_stage(0);
+  for (int j = 0; j < steps; ++j) {
+    if (j + 1 < steps) {
+      if (j >= 1) {   // the MMAs of step j - 1 read the stage that step j + 1 refills
+        if (!mbar_wait(&mbar[(j - 1) & 1], (uses[(j - 1) & 1] - 1) & 1u)) {
+          if (tid == 0) { failed = 1; atomicExch(err, kErrTimeout); }
+        }
+        tc_fence_after();
+      }
+      load_stage(j + 1);
+      cp_async_wait<1>();
+    } else {
+      cp_async_wait<0>();
+    }
+    fence_async_smem();
+    __syncthreads();
+    if (failed) break;
+    if (tid == 0) {
+      tc_fence_after();
+      const uint32_t a0 = s0 + (j & 1) * stage, w0 = a0 + abytes;
+#pragma unroll
+      for (int s = 0; s < kTK / 16; ++s) {
+        const uint64_t ad = smem_desc(a0 + s * 256, 128, 1024);
+#pragma unroll
+        for (int t = 0; t < 3; ++t) {
+          const uint64_t bd = smem_desc(w0 + t * wbytes + s * 256, 128, 1024);
+          mma_bf16(tmem, ad, bd, idesc, (j > 0 || s > 0 || t > 0) ? 1u : 0u);
+        }
+      }
+      mma_commit(&mbar[j & 1]);
+    }
+    uses[j & 1] += 1;
+  }
+  // all MMAs done: the last commit of each stage covers every earlier MMA
+  if (steps > 0 && !failed) {
+    const int jl = steps - 1;
+    if (!mbar_wait(&mbar[jl & 1], (uses[jl & 1] - 1) & 1u)) {
+      if (tid == 0) { failed = 1; atomicExch(err, kErrTimeout); }
+    }
+  }
+  tc_fence_after();
+  __syncthreads();
+  float* C = Cp + (size_t)blockIdx.y * M * N;
+  const int row = m0 + warp * 32 + lane;
+  if (!failed) {
+    for (int c0 = 0; c0 < N; c0 += 16) {
+      float v[16];
+      if (steps > 0) {
         tmem_ld16(tmem + (static_cast<uint32_t>(warp * 32) << 16) + static_cast<uint32_t>(c0), v);
       } else {
 #pragma unroll
