@@ -516,35 +516,50 @@ __device__ void dense_solve_one(DenseInst& I, const DenseParams& P, T* sm, doubl
 // FP64; the tests are decided on the exact sums.
 constexpr int kDeltaRefresh = 100;
 
-// o0[i] += sum_j M[i][j] v0[j] (and o1 with v1) for rows i < rows: warp per row, float4
-// loads, FP32 accumulation.  M rows are ldm floats (a multiple of 4, zero padded); v0,
-// v1 hold ldm floats, 16-byte aligned.  f0 (optional) receives the FP32 row sums.
+// o0[i] += sum_j M[i][j] v0[j] (and o1 with v1) for rows i < rows: each warp takes four
+// rows at a time (rows w, w + 8, w + 16, w + 24 of a group of 32), float4 loads, FP32
+// accumulation, so that four rows' loads are in flight per warp.  M rows are ldm floats
+// (a multiple of 4, zero padded); v0, v1 hold ldm floats, 16-byte aligned.  f0
+// (optional) receives the FP32 row sums.
 template <bool TWO>
 __device__ void rows_f32(const float* __restrict__ M, int ldm, int rows, const float* v0, const float* v1,
                          double* o0, double* o1, float* f0) {
+  constexpr int R = 4;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int nq = ldm / 4;
   const float4* p0 = reinterpret_cast<const float4*>(v0);
   const float4* p1 = reinterpret_cast<const float4*>(v1);
-  for (int i = wid; i < rows; i += kWarps) {
-    const float4* r = reinterpret_cast<const float4*>(M + (size_t)i * ldm);
-    float a0 = 0.f, a1 = 0.f;
-#pragma unroll 8
+  for (int g = 0; g < rows; g += R * kWarps) {
+    float a0[R], a1[R];
+    const float4* r[R];
+#pragma unroll
+    for (int q = 0; q < R; ++q) {
+      a0[q] = 0.f;
+      a1[q] = 0.f;
+      const int i = g + wid + q * kWarps;
+      r[q] = reinterpret_cast<const float4*>(M + (size_t)min(i, rows - 1) * ldm);
+    }
     for (int t = lane; t < nq; t += 32) {
-      const float4 a = r[t];
       const float4 x = p0[t];
-      a0 += a.x * x.x + a.y * x.y + a.z * x.z + a.w * x.w;
-      if (TWO) {
-        const float4 z = p1[t];
-        a1 += a.x * z.x + a.y * z.y + a.z * z.z + a.w * z.w;
+      float4 z = x;
+      if (TWO) z = p1[t];
+#pragma unroll
+      for (int q = 0; q < R; ++q) {
+        const float4 a = r[q][t];
+        a0[q] += a.x * x.x + a.y * x.y + a.z * x.z + a.w * x.w;
+        if (TWO) a1[q] += a.x * z.x + a.y * z.y + a.z * z.z + a.w * z.w;
       }
     }
-    a0 = warp_sum(a0);
-    if (TWO) a1 = warp_sum(a1);
-    if (lane == 0) {
-      o0[i] += (double)a0;
-      if (TWO) o1[i] += (double)a1;
-      if (f0) f0[i] = a0;
+#pragma unroll
+    for (int q = 0; q < R; ++q) {
+      const int i = g + wid + q * kWarps;
+      const float s0 = warp_sum(a0[q]);
+      const float s1 = TWO ? warp_sum(a1[q]) : 0.f;
+      if (lane == 0 && i < rows) {
+        o0[i] += (double)s0;
+        if (TWO) o1[i] += (double)s1;
+        if (f0) f0[i] = s0;
+      }
     }
   }
 }
@@ -617,17 +632,18 @@ __device__ void dense_solve_delta(DenseInst& I, const DenseParams& P, unsigned c
   // the nine sums from the maintained products (as residual_sums)
   auto sums = [&](double (&out)[9]) {
     double acc[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    const double itau = 1.0 / tau;
     for (int i = threadIdx.x; i < m; i += kThreads) {
       const double ax = Ax[i], bi = I.b[i], yi = y[i], bb = I.bbar[i];
       const double ry = ax - bi * tau + bb * theta;
-      const double pr = ax / tau - bi;
+      const double pr = ax * itau - bi;
       acc[0] += ry * ry; acc[1] += pr * pr; acc[3] += ax * ax;
       acc[5] += bi * yi; acc[6] += bb * yi;
     }
     for (int j = threadIdx.x; j < n; j += kThreads) {
       const double aty = ATy[j], sj = s[j], cj = I.c[j], cb = I.cbar[j], xj = x[j];
       const double rx = -aty + cj * tau - cb * theta - sj;
-      const double dr = (aty + sj) / tau - cj;
+      const double dr = (aty + sj) * itau - cj;
       acc[0] += rx * rx; acc[2] += dr * dr; acc[4] += (aty + sj) * (aty + sj);
       acc[7] += cj * xj; acc[8] += cb * xj;
     }

@@ -408,6 +408,25 @@ __device__ void total_partials(const double* partials, int nparts, int k, double
     for (int q = 0; q < NS; ++q) out[q] += partials[((size_t)p * kMaxBatch + k) * NS + q];
 }
 
+// totals[k][q] = sum over the reduction CTAs of partials[cta][k][q]: one CTA per instance,
+// fixed assignment of partials to threads and a fixed-order block reduction.
+template <int NS>
+__global__ void __launch_bounds__(kThr) partials_total_kernel(const double* __restrict__ partials, int nparts,
+                                                              double* __restrict__ totals) {
+  __shared__ double red[32 * NS];
+  const int k = blockIdx.x;
+  double v[NS];
+#pragma unroll
+  for (int q = 0; q < NS; ++q) v[q] = 0.0;
+  for (int p = threadIdx.x; p < nparts; p += kThr)
+#pragma unroll
+    for (int q = 0; q < NS; ++q) v[q] += partials[((size_t)p * kMaxBatch + k) * NS + q];
+  block_sum<NS>(v, red);
+  if (threadIdx.x == 0)
+#pragma unroll
+    for (int q = 0; q < NS; ++q) totals[k * NS + q] = v[q];
+}
+
 // Sec. 4.1 tests on the nine sums; 0 = none passes.
 __device__ int sh_tests(const ShInst& I, const double (&a)[9], double margin, double eps) {
   const double tau = I.tau;
@@ -872,8 +891,9 @@ int shared_batch_run(const SharedBatchArgs& a, std::vector<SharedBatchResult>& o
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  // CTAs of the per-instance column reductions: each control thread adds red_ctas partials
-  const int red_ctas = std::max(1, std::min(sms / 2, (m + n + 255) / 256));
+  // CTAs of the per-instance column reductions (their partials are totalled per instance
+  // by partials_total_kernel before the control kernels read them)
+  const int red_ctas = std::max(1, std::min(sms * 2, (m + n + 63) / 64));
   const size_t wk64 = std::max({gemm_work<double>(m, m, n, sms), gemm_work<double>(m, 2 * B, n, sms),
                                 gemm_work<double>(m, 2 * B, m, sms), gemm_work<double>(n, 2 * B, m, sms),
                                 gemm_work<double>(n, B, m, sms), gemm_work<double>(m, B, m, sms)});
@@ -887,6 +907,7 @@ int shared_batch_run(const SharedBatchArgs& a, std::vector<SharedBatchResult>& o
   ShView<double> V{};
   __nv_bfloat16 *A16 = nullptr, *AT16 = nullptr, *WT16 = nullptr;
   double *A64 = nullptr, *AT64 = nullptr, *G = nullptr, *Ginv64 = nullptr, *Ae = nullptr, *work64 = nullptr;
+  double* totals = nullptr;
   double *partials = nullptr, *W2 = nullptr, *P2 = nullptr, *R = nullptr, *ZY2 = nullptr, *ZX2 = nullptr;
   double *Xo = nullptr, *Yo = nullptr, *So = nullptr, *ATZY = nullptr, *Qprev = nullptr;
   float *A32 = nullptr, *Ginv32 = nullptr, *work32 = nullptr, *dY = nullptr, *dXS = nullptr, *dQ = nullptr,
@@ -903,6 +924,7 @@ int shared_batch_run(const SharedBatchArgs& a, std::vector<SharedBatchResult>& o
     Ae = bp.take<double>(m);
     work64 = bp.take<double>(wk64);
     partials = bp.take<double>((size_t)red_ctas * kMaxBatch * 9);
+    totals = bp.take<double>((size_t)kMaxBatch * 9);
     insts = bp.take<ShInst>(kMaxBatch);
     flags = bp.take<int>(8);
     derr = bp.take<int>(8);
@@ -1029,32 +1051,36 @@ int shared_batch_run(const SharedBatchArgs& a, std::vector<SharedBatchResult>& o
     ck(gemm<double>(true, A64, n, n, B, m, V.Y, B, V.ATY, work64, wk64, sms, st, 0.0, nullptr, nullptr, 0, gate),
        "refresh A^T Y");
     sums_kernel<double><<<red_ctas, kThr, 0, st>>>(V, insts, partials, V.Q, gate, nullptr, nullptr);
-    ctrl_confirm_kernel<<<1, kMaxBatch, 0, st>>>(insts, B, partials, red_ctas, a.prm, flags);
+    partials_total_kernel<9><<<B, kThr, 0, st>>>(partials, red_ctas, totals);
+    ctrl_confirm_kernel<<<1, kMaxBatch, 0, st>>>(insts, B, totals, 1, a.prm, flags);
     ck(gemm<double>(false, Ginv64, m, m, B, m, V.Q, B, V.ZY, work64, wk64, sms, st, 0.0, nullptr, nullptr, 0, gate),
        "refresh Ginv Q");
     ck(gemm<double>(true, A64, n, n, B, m, V.ZY, B, ATZY, work64, wk64, sms, st, 0.0, nullptr, nullptr, 0, gate),
        "refresh A^T ZY");
     refresh_finish_kernel<<<eb, kThr, 0, st>>>(V.Q, Qprev, dQ, (size_t)m * B, gate);
-    launches += 11;
+    launches += 12;
   };
   // ---- Algorithm 2, all instances in lockstep
   auto cycle64 = [&]() {
     ck(gemm<double>(false, A64, n, m, 2 * B, n, V.XS, 2 * B, V.AXS, work64, wk64, sms, st), "A [X S]");
     ck(gemm<double>(true, A64, n, n, B, m, V.Y, B, V.ATY, work64, wk64, sms, st), "A^T Y");
     sums_kernel<double><<<red_ctas, kThr, 0, st>>>(V, insts, partials, V.Q, nullptr, nullptr, nullptr);
-    ctrl_eval_kernel<<<1, kMaxBatch, 0, st>>>(insts, B, n, partials, red_ctas, a.prm, flags);
+    partials_total_kernel<9><<<B, kThr, 0, st>>>(partials, red_ctas, totals);
+    ctrl_eval_kernel<<<1, kMaxBatch, 0, st>>>(insts, B, n, totals, 1, a.prm, flags);
     ck(gemm<double>(false, Ginv64, m, m, B, m, V.Q, B, V.ZY, work64, wk64, sms, st), "Ginv Q");
     ck(gemm<double>(true, A64, n, n, B, m, V.ZY, B, V.ZX, work64, wk64, sms, st, 0.0, V.XS, V.XS + B, 2 * B),
        "A^T ZY");
     hz_kernel<double><<<red_ctas, kThr, 0, st>>>(V, partials);
-    ctrl_step_kernel<<<1, kMaxBatch, 0, st>>>(insts, B, n, partials, red_ctas, a.prm);
+    partials_total_kernel<2><<<B, kThr, 0, st>>>(partials, red_ctas, totals);
+    ctrl_step_kernel<<<1, kMaxBatch, 0, st>>>(insts, B, n, totals, 1, a.prm);
     update_kernel<double><<<eb, kThr, 0, st>>>(V, insts, a.prm, nullptr, nullptr);
-    launches += 13;
+    launches += 15;
   };
   auto cycle_mixed = [&]() {
     sums_kernel<double><<<red_ctas, kThr, 0, st>>>(V, insts, partials, V.Q, nullptr, Qprev, dQ);
-    ctrl_eval_kernel<<<1, kMaxBatch, 0, st>>>(insts, B, n, partials, red_ctas, a.prm, flags);
-    launches += 2;
+    partials_total_kernel<9><<<B, kThr, 0, st>>>(partials, red_ctas, totals);
+    ctrl_eval_kernel<<<1, kMaxBatch, 0, st>>>(insts, B, n, totals, 1, a.prm, flags);
+    launches += 3;
     refresh();
     // projection on the change of Q: ZY += G^{-1} dQ, A^T ZY += A^T (G^{-1} dQ)
     ck(gemm_acc(false, Ginv32, m, m, B, m, dQ, B, B, V.ZY, dZY, insts, work32, wk32, sms, st), "Ginv dQ");
@@ -1062,7 +1088,8 @@ int shared_batch_run(const SharedBatchArgs& a, std::vector<SharedBatchResult>& o
                "A^T dZY");
     else ck(gemm_acc(true, A32, n, n, B, m, dZY, B, B, ATZY, nullptr, nullptr, work32, wk32, sms, st), "A^T dZY");
     hz_delta_kernel<<<red_ctas, kThr, 0, st>>>(V, ATZY, Qprev, insts, partials);
-    ctrl_step_kernel<<<1, kMaxBatch, 0, st>>>(insts, B, n, partials, red_ctas, a.prm);
+    partials_total_kernel<2><<<B, kThr, 0, st>>>(partials, red_ctas, totals);
+    ctrl_step_kernel<<<1, kMaxBatch, 0, st>>>(insts, B, n, totals, 1, a.prm);
     update_kernel<double><<<eb, kThr, 0, st>>>(V, insts, a.prm, dY, dXS);
     // maintained products of the new state: AX, AS += A [dX dS], A^T Y += A^T dY
     if (tc) {
@@ -1074,7 +1101,7 @@ int shared_batch_run(const SharedBatchArgs& a, std::vector<SharedBatchResult>& o
       ck(gemm_acc(false, A32, n, m, 2 * B, n, dXS, 2 * B, B, V.AXS, nullptr, nullptr, work32, wk32, sms, st), "A dXS");
       ck(gemm_acc(true, A32, n, n, B, m, dY, B, B, V.ATY, nullptr, nullptr, work32, wk32, sms, st), "A^T dY");
     }
-    launches += tc ? 14 : 11;
+    launches += tc ? 15 : 12;
   };
   if (mixed && rc == ABIP_OK) {
     // exact products of the starting point
