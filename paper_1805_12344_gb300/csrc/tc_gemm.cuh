@@ -4,19 +4,18 @@
 //
 // A16: BF16, row-major (K contiguous), exactly the shared matrix (the batch uses this
 // path only when A is representable in bfloat16).  W: FP32 row-major (N contiguous), the
-// changes of the batched iterates; each element is split on the fly into three bfloat16
-// terms w = hi + mid + lo (each the bfloat16 rounding of the remainder), so the three
+// changes of the batched iterates; each element is split into three bfloat16 terms
+// w = hi + mid + lo (each the bfloat16 rounding of the remainder), so the three
 // accumulated MMAs reproduce an FP32-accurate product: every BF16 x BF16 product is exact
 // and the accumulation is FP32 in tensor memory.
 //
 // One CTA (128 threads) owns a 128-row tile of C and one K range (split-K over
-// gridDim.y).  Per 64-wide K step the CTA stages the A tile and the three W tiles in
-// shared memory in the no-swizzle K-major core-matrix layout (8 rows x 16 bytes per core
-// matrix; core matrices adjacent in K are 128 bytes apart, adjacent in M/N 1024 bytes),
-// one thread issues 4 x 3 tcgen05.mma (K = 16 each) into the TMEM accumulator and commits
-// them to an mbarrier, and all threads wait on it (bounded) before the buffers are reused.
-// The epilogue reads the accumulator with tcgen05.ld (warp w owns TMEM lanes 32w..32w+31,
-// one lane per row) and writes the FP32 partial tile.
+// gridDim.y).  Per 64-wide K step the A tile and the three W tiles sit in shared memory in
+// the no-swizzle K-major core-matrix layout (8 rows x 16 bytes per core matrix; core
+// matrices adjacent in K are 128 bytes apart, adjacent in M/N 1024 bytes); one thread
+// issues 4 x 3 tcgen05.mma (K = 16 each) into the TMEM accumulator and commits them to an
+// mbarrier.  The epilogue reads the accumulator with tcgen05.ld (warp w owns TMEM lanes
+// 32w..32w+31, one lane per row) and writes the FP32 partial tile.
 #pragma once
 
 #include <cstdint>
@@ -142,125 +141,11 @@ __device__ __forceinline__ uint32_t core_off(int r, int kc) {
   return static_cast<uint32_t>(((r >> 3) * 8 + kc) * 128 + (r & 7) * 16);
 }
 
-__device__ __forceinline__ uint32_t pack2(__nv_bfloat16 a, __nv_bfloat16 b) {
-  return static_cast<uint32_t>(__bfloat16_as_ushort(a)) | (static_cast<uint32_t>(__bfloat16_as_ushort(b)) << 16);
-}
-
-// Requirements (checked by the host): M % 128 == 0, K % 64 == 0, kchunk % 64 == 0,
-// N % 16 == 0 and 16 <= N <= 256, lda % 8 == 0, A16 16-byte aligned.
-// Dynamic shared memory: 1024 (alignment) + 16 KB (A) + 3 * N * 128 bytes (W terms).
-__global__ void __launch_bounds__(kTCThreads, 1)
-    tc_gemm_kernel(const __nv_bfloat16* __restrict__ A16, int64_t lda, int M, int N, int K,
-                   const float* __restrict__ W, int64_t ldw, float* __restrict__ Cp, int kchunk, int* err) {
-  extern __shared__ uint8_t tc_smem_raw[];
-  __shared__ uint64_t mbar;
-  __shared__ uint32_t tslot;
-  __shared__ int failed;
-  uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(tc_smem_raw) + 1023) & ~uintptr_t(1023));
-  uint8_t* sA = base;                         // 128 rows x 64 K, BF16: 16 KB
-  uint8_t* sW = base + kTM * kTK * 2;         // three N x 64 tiles, BF16
-  const uint32_t wbytes = static_cast<uint32_t>(N) * kTK * 2;
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int m0 = blockIdx.x * kTM;
-  const int kz0 = blockIdx.y * kchunk, kz1 = min(K, kz0 + kchunk);
-  uint32_t ncols = 32;
-  while (ncols < static_cast<uint32_t>(N)) ncols <<= 1;
-  if (tid == 0) {
-    mbar_init(&mbar, 1);
-    failed = 0;
-  }
-  if (warp == 0) tmem_alloc(&tslot, ncols);
-  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  tc_fence_before();
-  __syncthreads();
-  tc_fence_after();
-  const uint32_t tmem = tslot;
-  const uint32_t idesc = instr_desc(kTM, N);
-  uint32_t phase = 0;
-  bool any = false;
-  for (int k0 = kz0; k0 < kz1; k0 += kTK) {
-    // A tile: 128 rows x 8 chunks of 8 BF16 (16 bytes), straight copies
-    for (int e = tid; e < kTM * 8; e += kTCThreads) {
-      const int r = e >> 3, kc = e & 7;
-      const uint4 v = *reinterpret_cast<const uint4*>(A16 + (size_t)(m0 + r) * lda + k0 + kc * 8);
-      *reinterpret_cast<uint4*>(sA + core_off(r, kc)) = v;
-    }
-    // W tiles: element (k, n) goes to row n, K chunk k / 8 of the B operand; split in three
-    for (int e = tid; e < N * 8; e += kTCThreads) {
-      const int n = e % N, kc = e / N;
-      uint32_t h[4], md[4], lo[4];
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        __nv_bfloat16 hb[2], mb[2], lb[2];
-#pragma unroll
-        for (int u = 0; u < 2; ++u) {
-          const float w = W[(size_t)(k0 + kc * 8 + 2 * q + u) * ldw + n];
-          hb[u] = __float2bfloat16_rn(w);
-          const float r1 = w - __bfloat162float(hb[u]);
-          mb[u] = __float2bfloat16_rn(r1);
-          lb[u] = __float2bfloat16_rn(r1 - __bfloat162float(mb[u]));
-        }
-        h[q] = pack2(hb[0], hb[1]);
-        md[q] = pack2(mb[0], mb[1]);
-        lo[q] = pack2(lb[0], lb[1]);
-      }
-      const uint32_t off = core_off(n, kc);
-      *reinterpret_cast<uint4*>(sW + off) = make_uint4(h[0], h[1], h[2], h[3]);
-      *reinterpret_cast<uint4*>(sW + wbytes + off) = make_uint4(md[0], md[1], md[2], md[3]);
-      *reinterpret_cast<uint4*>(sW + 2 * wbytes + off) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
-    }
-    fence_async_smem();
-    __syncthreads();
-    if (tid == 0) {
-      tc_fence_after();
-      const uint32_t a0 = smem_u32(sA), w0 = smem_u32(sW);
-#pragma unroll
-      for (int s = 0; s < kTK / 16; ++s) {
-        const uint64_t ad = smem_desc(a0 + s * 256, 128, 1024);
-#pragma unroll
-        for (int t = 0; t < 3; ++t) {
-          const uint64_t bd = smem_desc(w0 + t * wbytes + s * 256, 128, 1024);
-          mma_bf16(tmem, ad, bd, idesc, (any || s > 0 || t > 0) ? 1u : 0u);
-        }
-      }
-      mma_commit(&mbar);
-    }
-    if (!mbar_wait(&mbar, phase)) {
-      if (tid == 0) { failed = 1; atomicExch(err, kErrTimeout); }
-    }
-    phase ^= 1u;
-    any = true;
-    tc_fence_after();
-    __syncthreads();
-    if (failed) break;
-  }
-  // epilogue: row m0 + 32 warp + lane, N columns
-  float* C = Cp + (size_t)blockIdx.y * M * N;
-  const int row = m0 + warp * 32 + lane;
-  if (!failed) {
-    for (int c0 = 0; c0 < N; c0 += 16) {
-      float v[16];
-      if (any) {
-        tmem_ld16(tmem + (static_cast<uint32_t>(warp * 32) << 16) + static_cast<uint32_t>(c0), v);
-      } else {
-#pragma unroll
-        for (int q = 0; q < 16; ++q) v[q] = 0.f;
-      }
-#pragma unroll
-      for (int q = 0; q < 16; q += 4)
-        *reinterpret_cast<float4*>(C + (size_t)row * N + c0 + q) = make_float4(v[q], v[q + 1], v[q + 2], v[q + 3]);
-    }
-  }
-  tc_fence_before();
-  __syncthreads();
-  if (warp == 0) tmem_dealloc(tmem, ncols);
-}
-
 // ---------------------------------------------------------------------------
-// Pipelined variant: the changes are split beforehand into three bfloat16 arrays
-// Wt[t] (N rows x K, K contiguous), so every tile is a plain 16-byte copy.  Two shared
-// memory stages: while the MMAs of step j run, cp.async fills the other stage with step
-// j + 1; an mbarrier per stage tells when its MMAs have finished reading it.
+// The changes are split beforehand into three bfloat16 arrays Wt[t] (N rows x K, K
+// contiguous), so every tile is a plain 16-byte copy.  Two shared-memory stages: while
+// the MMAs of step j run, cp.async fills the other stage with step j + 1; an mbarrier per
+// stage tells when its MMAs have finished reading it.
 // ---------------------------------------------------------------------------
 
 // Wt[t][n][k] = t-th bfloat16 term of W[k][n] (W: K x N FP32 row-major, ldw).
@@ -303,7 +188,9 @@ __host__ __device__ inline size_t tc2_stage_bytes(int N) {
 }
 __host__ __device__ inline size_t tc2_smem_bytes(int N) { return 1024 + 2 * tc2_stage_bytes(N); }
 
-// Requirements as tc_gemm_kernel, plus K % 8 == 0 for Wt rows (16-byte chunks).
+// Requirements (refused on the device with kErrShape): M % 128 == 0, K % 64 == 0,
+// kchunk % 64 == 0, N % 16 == 0 and 16 <= N <= 256, lda % 8 == 0, A16 and Wt 16-byte
+// aligned.  Dynamic shared memory: tc2_smem_bytes(N).
 __global__ void __launch_bounds__(kTCThreads, 1)
     tc_gemm2_kernel(const __nv_bfloat16* __restrict__ A16, int64_t lda, int M, int N, int K,
                     const __nv_bfloat16* __restrict__ Wt, float* __restrict__ Cp, int kchunk, int* err) {
@@ -416,8 +303,6 @@ __global__ void __launch_bounds__(kTCThreads, 1)
   __syncthreads();
   if (warp == 0) tmem_dealloc(tmem, ncols);
 }
-
-inline size_t tc_smem_bytes(int N) { return 1024 + static_cast<size_t>(kTM) * kTK * 2 + 3 * static_cast<size_t>(N) * kTK * 2; }
 
 }  // namespace tc
 }  // namespace abip
