@@ -106,7 +106,9 @@ typedef struct {
     int32_t warmstart;      /* 0: keep-larger rescale of (x,s), (tau,kappa) and sqrt(gamma) on y, theta
                                (Sec. 5); 1: sqrt(gamma) on every component (Eq. update-next-iterate) */
     int32_t stop_rule;      /* 0: Sec. 4.1 tests; 1: stop once mu < eps (outer-count mode) */
-    int32_t check_every;    /* FP64 termination test every k ADMM updates (mixed precision); 1 = every update */
+    int32_t check_every;    /* mixed precision: minimum number of ADMM updates between two exact FP64
+                               confirmations of the Sec. 4.1 tests (each screen pass that comes
+                               sooner waits); 1 = confirm whenever the screen passes */
     int32_t grid_ctas;      /* 0: automatic; else the persistent grid size (tests) */
     int32_t reserved[8];
 } abip_params;
@@ -122,7 +124,9 @@ typedef struct {
     double setup_s, solve_s;/* wall-clock seconds of abip_setup and of the last solve */
     double kernel_s;        /* device time of the solve kernel, from CUDA events on the solve stream */
     int64_t launches;       /* kernels the solve call launched */
-    int64_t fp32_iters;     /* ADMM updates done with FP32 iterates (mixed precision) */
+    int64_t fp32_iters;     /* ADMM updates whose products were FP32 (mixed precision; the dense and
+                               shared-A paths update FP64 products with FP32 products of the
+                               changes, the sparse path iterates in FP32) */
 } abip_info;
 
 typedef struct abip_handle abip_handle;
