@@ -854,8 +854,13 @@ cudaError_t gemm_tc(const __nv_bfloat16* A16, int64_t lda, int M, int N, int K, 
   const TcPlan p = plan_tc(M, N, K, sms);
   if ((size_t)p.splits * M * N > work_elems) return cudaErrorInvalidValue;
   tc::split3_kernel<<<dim3((K + 31) / 32, (N + 31) / 32), dim3(32, 8), 0, st>>>(W, ldw, K, N, wt);
-  tc::tc_gemm2_kernel<<<dim3(M / tc::kTM, p.splits), tc::kTCThreads, tc::tc2_smem_bytes(N), st>>>(
-      A16, lda, M, N, K, wt, work, p.kchunk, err);
+  const dim3 grid(M / tc::kTM, p.splits);
+  const size_t smem = tc::tc2_smem_bytes(N);
+  switch (tc::tc2_stages(N)) {
+    case 4: tc::tc_gemm2_kernel<4><<<grid, tc::kTCThreads, smem, st>>>(A16, lda, M, N, K, wt, work, p.kchunk, err); break;
+    case 3: tc::tc_gemm2_kernel<3><<<grid, tc::kTCThreads, smem, st>>>(A16, lda, M, N, K, wt, work, p.kchunk, err); break;
+    default: tc::tc_gemm2_kernel<2><<<grid, tc::kTCThreads, smem, st>>>(A16, lda, M, N, K, wt, work, p.kchunk, err); break;
+  }
   const size_t MN = (size_t)M * N;
   const int rb = (int)std::min<size_t>((MN + kThr - 1) / kThr, (size_t)sms * 8);
   accum_kernel<<<std::max(rb, 1), kThr, 0, st>>>(work, p.splits, M, N, B, acc64, out32, mask);
@@ -1025,8 +1030,14 @@ int shared_batch_run(const SharedBatchArgs& a, std::vector<SharedBatchResult>& o
     const int cb = sms * 8;
     if (tc) {
       bf16_copies_kernel<<<cb, kThr, 0, st>>>(A64, m, n, A16, AT16);
-      ck(cudaFuncSetAttribute(tc::tc_gemm2_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)tc::tc2_smem_bytes(2 * B)), "tc smem");
+      for (int N : {B, 2 * B}) {
+        const int smem = (int)tc::tc2_smem_bytes(N);
+        switch (tc::tc2_stages(N)) {
+          case 4: ck(cudaFuncSetAttribute(tc::tc_gemm2_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem), "tc smem"); break;
+          case 3: ck(cudaFuncSetAttribute(tc::tc_gemm2_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem), "tc smem"); break;
+          default: ck(cudaFuncSetAttribute(tc::tc_gemm2_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem), "tc smem"); break;
+        }
+      }
     } else {
       convert_kernel<float><<<cb, kThr, 0, st>>>(A64, A32, (size_t)m * n);
     }

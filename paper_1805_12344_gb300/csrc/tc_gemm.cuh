@@ -143,9 +143,9 @@ __device__ __forceinline__ uint32_t core_off(int r, int kc) {
 
 // ---------------------------------------------------------------------------
 // The changes are split beforehand into three bfloat16 arrays Wt[t] (N rows x K, K
-// contiguous), so every tile is a plain 16-byte copy.  Two shared-memory stages: while
-// the MMAs of step j run, cp.async fills the other stage with step j + 1; an mbarrier per
-// stage tells when its MMAs have finished reading it.
+// contiguous), so every tile is a plain 16-byte copy.  S shared-memory stages: while the
+// MMAs of step j run, cp.async fills the stages of steps j + 1 .. j + S - 1; an mbarrier
+// per stage tells when its MMAs have finished reading it.
 // ---------------------------------------------------------------------------
 
 // Wt[t][n][k] = t-th bfloat16 term of W[k][n] (W: K x N FP32 row-major, ldw).
@@ -186,22 +186,26 @@ __device__ __forceinline__ void cp_async_wait() {
 __host__ __device__ inline size_t tc2_stage_bytes(int N) {
   return static_cast<size_t>(kTM) * kTK * 2 + 3 * static_cast<size_t>(N) * kTK * 2;
 }
-__host__ __device__ inline size_t tc2_smem_bytes(int N) { return 1024 + 2 * tc2_stage_bytes(N); }
+// shared-memory stages: as many as fit in about 200 KB (4 for N <= 64, 3 up to N = 128)
+__host__ __device__ inline int tc2_stages(int N) { return N <= 64 ? 4 : (N <= 128 ? 3 : 2); }
+__host__ __device__ inline size_t tc2_smem_bytes(int N) { return 1024 + tc2_stages(N) * tc2_stage_bytes(N); }
 
 // Requirements (refused on the device with kErrShape): M % 128 == 0, K % 64 == 0,
 // kchunk % 64 == 0, N % 16 == 0 and 16 <= N <= 256, lda % 8 == 0, A16 and Wt 16-byte
 // aligned.  Dynamic shared memory: tc2_smem_bytes(N).
+template <int S>
 __global__ void __launch_bounds__(kTCThreads, 1)
     tc_gemm2_kernel(const __nv_bfloat16* __restrict__ A16, int64_t lda, int M, int N, int K,
                     const __nv_bfloat16* __restrict__ Wt, float* __restrict__ Cp, int kchunk, int* err) {
   // shapes the tiles and the 16-byte copies need; anything else is refused here
   if (M % kTM != 0 || K % kTK != 0 || kchunk <= 0 || kchunk % kTK != 0 || N % 16 != 0 || N < 16 || N > 256 ||
-      lda % 8 != 0 || (reinterpret_cast<uintptr_t>(A16) & 15) != 0 || (reinterpret_cast<uintptr_t>(Wt) & 15) != 0) {
+      lda % 8 != 0 || (reinterpret_cast<uintptr_t>(A16) & 15) != 0 || (reinterpret_cast<uintptr_t>(Wt) & 15) != 0 ||
+      tc2_stages(N) != S) {
     if (threadIdx.x == 0 && blockIdx.x == 0 && blockIdx.y == 0) atomicExch(err, kErrShape);
     return;
   }
   extern __shared__ uint8_t tc_smem_raw[];
-  __shared__ uint64_t mbar[2];
+  __shared__ uint64_t mbar[S];
   __shared__ uint32_t tslot;
   __shared__ int failed;
   uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(tc_smem_raw) + 1023) & ~uintptr_t(1023));
@@ -215,8 +219,8 @@ __global__ void __launch_bounds__(kTCThreads, 1)
   uint32_t ncols = 32;
   while (ncols < static_cast<uint32_t>(N)) ncols <<= 1;
   if (tid == 0) {
-    mbar_init(&mbar[0], 1);
-    mbar_init(&mbar[1], 1);
+#pragma unroll
+    for (int b = 0; b < S; ++b) mbar_init(&mbar[b], 1);
     failed = 0;
   }
   if (warp == 0) tmem_alloc(&tslot, ncols);
@@ -229,7 +233,7 @@ __global__ void __launch_bounds__(kTCThreads, 1)
   const uint32_t s0 = smem_u32(base);
   auto load_stage = [&](int j) {
     const int k0 = kz0 + j * kTK;
-    const uint32_t sa = s0 + (j & 1) * stage;
+    const uint32_t sa = s0 + (j % S) * stage;
     for (int e = tid; e < kTM * 8; e += kTCThreads) {
       const int r = e >> 3, kc = e & 7;
       cp_async16(sa + core_off(r, kc), A16 + (size_t)(m0 + r) * lda + k0 + kc * 8);
@@ -238,29 +242,36 @@ __global__ void __launch_bounds__(kTCThreads, 1)
       const int t = e / (N * 8), rem = e % (N * 8), n = rem >> 3, kc = rem & 7;
       cp_async16(sa + abytes + t * wbytes + core_off(n, kc), Wt + t * plane + (size_t)n * K + k0 + kc * 8);
     }
-    cp_async_commit();
   };
-  uint32_t uses[2] = {0u, 0u};
-  if (steps > 0) load_stage(0);
+  // cp.async groups: one per step (empty past the last), so that after the commit of
+  // iteration j, wait_group<S - 1> means the group of step j has landed
+  uint32_t uses[S];
+#pragma unroll
+  for (int b = 0; b < S; ++b) uses[b] = 0u;
+  for (int q = 0; q < S - 1; ++q) {
+    if (q < steps) load_stage(q);
+    cp_async_commit();
+  }
   for (int j = 0; j < steps; ++j) {
-    if (j + 1 < steps) {
-      if (j >= 1) {   // the MMAs of step j - 1 read the stage that step j + 1 refills
-        if (!mbar_wait(&mbar[(j - 1) & 1], (uses[(j - 1) & 1] - 1) & 1u)) {
+    const int nxt = j + S - 1;
+    if (nxt < steps) {
+      if (j >= 1) {   // the MMAs of step j - 1 read the stage that step nxt refills
+        const int b = (j - 1) % S;
+        if (!mbar_wait(&mbar[b], (uses[b] - 1) & 1u)) {
           if (tid == 0) { failed = 1; atomicExch(err, kErrTimeout); }
         }
         tc_fence_after();
       }
-      load_stage(j + 1);
-      cp_async_wait<1>();
-    } else {
-      cp_async_wait<0>();
+      load_stage(nxt);
     }
+    cp_async_commit();
+    cp_async_wait<S - 1>();
     fence_async_smem();
     __syncthreads();
     if (failed) break;
     if (tid == 0) {
       tc_fence_after();
-      const uint32_t a0 = s0 + (j & 1) * stage, w0 = a0 + abytes;
+      const uint32_t a0 = s0 + (j % S) * stage, w0 = a0 + abytes;
 #pragma unroll
       for (int s = 0; s < kTK / 16; ++s) {
         const uint64_t ad = smem_desc(a0 + s * 256, 128, 1024);
@@ -270,17 +281,18 @@ __global__ void __launch_bounds__(kTCThreads, 1)
           mma_bf16(tmem, ad, bd, idesc, (j > 0 || s > 0 || t > 0) ? 1u : 0u);
         }
       }
-      mma_commit(&mbar[j & 1]);
+      mma_commit(&mbar[j % S]);
     }
-    uses[j & 1] += 1;
+    uses[j % S] += 1;
   }
-  // all MMAs done: the last commit of each stage covers every earlier MMA
+  // all MMAs done: the last commit covers every earlier MMA of this thread
   if (steps > 0 && !failed) {
-    const int jl = steps - 1;
-    if (!mbar_wait(&mbar[jl & 1], (uses[jl & 1] - 1) & 1u)) {
+    const int b = (steps - 1) % S;
+    if (!mbar_wait(&mbar[b], (uses[b] - 1) & 1u)) {
       if (tid == 0) { failed = 1; atomicExch(err, kErrTimeout); }
     }
   }
+  cp_async_wait<0>();
   tc_fence_after();
   __syncthreads();
   float* C = Cp + (size_t)blockIdx.y * M * N;
