@@ -35,9 +35,10 @@ def main(argv=None):
     sh.add_argument("--batch", type=int, default=64)
     bt = sub.add_parser("batch", help="uneven batch of dense planted LPs")
     bt.add_argument("--count", type=int, default=64)
-    sv = sub.add_parser("svm", help="one L1-SVM LP")
+    sv = sub.add_parser("svm", help="L1-SVM LPs: one through abip_setup/abip_solve, or a batch")
     sv.add_argument("--d", type=int, default=64)
     sv.add_argument("--N", type=int, default=512)
+    sv.add_argument("--batch", type=int, default=0, help="solve this many instances (seeds seed..seed+batch-1) in one batch")
     for p in (sh, bt, sv):
         p.add_argument("--precision", choices=sorted(PRECISION), default="mixed")
         p.add_argument("--max-admm", type=int, default=1000000)
@@ -51,15 +52,27 @@ def main(argv=None):
         sb = W.basis_pursuit(a.m, a.nd, batch=a.batch, seed=a.seed)
         t0 = time.time()
         infos, *_ = abip.abip_solve_batch_shared(sb.A, sb.bs, sb.cs, prm, want_solution=False)
+        solved = sum(1 for f in infos if f["status"] == abip.ABIP_OPTIMAL)
         out = _summary("basis_pursuit_shared", infos, time.time() - t0,
                        dict(m=a.m, n=2 * a.nd, precision=a.precision,
-                            ms_per_cycle=1e3 * infos[0]["kernel_s"] / max(1, infos[0]["admm_iters"])))
+                            ms_per_cycle=1e3 * infos[0]["kernel_s"] / max(1, max(f["admm_iters"] for f in infos)),
+                            lps_solved_per_s=solved / (infos[0]["kernel_s"] + infos[0]["setup_s"])))
     elif a.cmd == "batch":
         lps = W.batch_uneven(count=a.count, seed=a.seed)
         t0 = time.time()
         infos, *_ = abip.abip_solve_batch([l.A for l in lps], [l.b for l in lps], [l.c for l in lps], prm,
                                           want_solution=False)
         out = _summary("batch_uneven", infos, time.time() - t0, dict(precision=a.precision))
+    elif a.batch > 0:
+        base = W.seed_for(W.L1_SVM) if a.seed is None else a.seed
+        lps = [W.l1_svm(d=a.d, N=a.N, seed=base + k) for k in range(a.batch)]
+        t0 = time.time()
+        infos, *_ = abip.abip_solve_batch([l.A for l in lps], [l.b for l in lps], [l.c for l in lps], prm,
+                                          want_solution=False)
+        wall = time.time() - t0
+        solved = sum(1 for f in infos if f["status"] == abip.ABIP_OPTIMAL)
+        out = _summary("l1_svm_batch", infos, wall, dict(m=a.N, n=2 * a.d + 2 + 2 * a.N, precision=a.precision,
+                                                         lps_solved_per_s=solved / infos[0]["kernel_s"]))
     else:
         lp = W.l1_svm(d=a.d, N=a.N, seed=a.seed)
         s = abip.Solver(lp.A, lp.b, lp.c, linsys=0, precision=PRECISION[a.precision], max_admm_iters=a.max_admm,

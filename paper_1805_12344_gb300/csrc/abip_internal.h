@@ -184,7 +184,8 @@ struct ShInst {
   double inner2, pres, dres, dgap, ctx, bty;
   double t1, t2;
   int64_t total, level_start, next_confirm;
-  int32_t outer, status, action, last, err, pad;
+  int32_t outer, status, action, last, err;
+  int32_t pending;                 // mixed: the FP32-maintained screen passed; decide at the next refresh
 };
 
 struct ShParams {

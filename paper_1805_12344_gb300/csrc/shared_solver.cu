@@ -478,11 +478,10 @@ __global__ void ctrl_eval_kernel(ShInst* insts, int B, int n, const double* part
       if (!P.mixed) {
         status = sh_tests(I, a, 1.0, P.eps);
       } else if (I.total >= I.next_confirm && sh_tests(I, a, 4.0, P.eps) != 0) {
-        I.action = SH_CONFIRM;   // decided after the FP64 sums
+        // decided on exact FP64 sums at the next scheduled refresh; the instance keeps
+        // iterating meanwhile, so a refresh serves every instance that asked since the last
+        I.pending = 1;
         I.next_confirm = I.total + P.confirm_gap;
-        flags[1] = 1;
-        atomicAdd(&flags[0], 1);
-        return;
       }
     }
     if (status != 0) { I.status = status; I.action = SH_DONE; return; }
@@ -511,42 +510,24 @@ __global__ void ctrl_eval_kernel(ShInst* insts, int B, int n, const double* part
   }
 }
 
-// FP64 confirmation of the instances the FP32 screen flagged (mixed path).
+// At a scheduled FP64 refresh: the instances whose maintained screen passed since the last
+// one are decided on the exact sums of their current state (mixed path).
 __global__ void ctrl_confirm_kernel(ShInst* insts, int B, const double* partials, int nparts, ShParams P,
                                     const int* flags) {
   const int k = threadIdx.x;
   if (flags[1] == 0 || k >= B) return;
   ShInst& I = insts[k];
-  if (I.action != SH_CONFIRM) return;
+  // an instance that warm-starts this cycle already carries the new tau, kappa, theta while
+  // its vectors are rescaled only later in the cycle: it stays pending for the next refresh
+  if (I.action != SH_STEP || !I.pending) return;
+  I.pending = 0;
   double a[9];
   total_partials<9>(partials, nparts, k, a);
   const int status = sh_tests(I, a, 1.0, P.eps);
   if (status != 0) {
-    // the FP64 sums of this very state decide: report them
-    sh_absorb(I, a, P.n);
+    sh_absorb(I, a, P.n);   // report the exact sums of the state that passed
     I.status = status;
     I.action = SH_DONE;
-    return;
-  }
-  if (I.total >= P.max_admm) { I.status = ABIP_MAX_ITER; I.action = SH_DONE; return; }
-  if (I.inner2 <= I.mu) {
-    I.mu *= P.gamma;
-    I.outer += 1;
-    I.level_start = I.total;
-    if (I.outer >= kMaxOuter) { I.status = ABIP_MAX_ITER; I.action = SH_DONE; return; }
-    const double sg = sqrt(P.gamma);
-    if (P.warmstart == 1) {
-      I.tau *= sg;
-      I.kappa *= sg;
-    } else if (I.tau >= I.kappa) {
-      I.kappa *= P.gamma;
-    } else {
-      I.tau *= P.gamma;
-    }
-    I.theta *= sg;
-    I.action = SH_WARM;
-  } else {
-    I.action = SH_STEP;
   }
 }
 
@@ -697,7 +678,7 @@ __global__ void setup_ctrl_kernel(ShInst* insts, int B, const double* partials, 
     I.nc = sqrt(a[2]);
     I.tau = 1.0; I.kappa = 1.0; I.theta = 1.0; I.mu = P.beta;
     I.total = 0; I.level_start = 0; I.next_confirm = 0;
-    I.outer = 0; I.status = 0; I.action = SH_STEP; I.last = SH_INIT; I.err = 0;
+    I.outer = 0; I.status = 0; I.action = SH_STEP; I.last = SH_INIT; I.err = 0; I.pending = 0;
     return;
   }
   const double K0 = 1.0 + a[3], K1 = I.zbar + a[4], K2 = -I.zbar + a[5], K3 = 1.0 + a[6];
