@@ -168,7 +168,9 @@ ABIP_API int abip_solve(abip_handle* h, double* x, double* y, double* s,
  * (on_device = 0) or device pointers (on_device = 1) per instance.  x, y, s:
  * arrays of `count` caller-allocated output pointers (same memory kind as the
  * inputs), entries may be NULL.  infos: `count` entries, may be NULL.
- * Each instance needs m <= 1024 here; larger dense LPs go through abip_setup.
+ * Each instance needs 40m + 24n bytes (FP64) or 48m + 40n bytes (mixed) of shared
+ * memory, at most 200 KB (ABIP_E_UNSUPPORTED otherwise); larger LPs go through
+ * abip_setup with linsys = PCG.
  */
 ABIP_API int abip_solve_batch(int32_t count, const abip_matrix* A, const double* const* b,
                      const double* const* c, const abip_params* p,

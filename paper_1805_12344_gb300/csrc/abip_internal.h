@@ -175,7 +175,7 @@ int noalloc_fail(int code, const std::string& msg);
 // ---------------------------------------------------------------------------
 // Batch of LPs sharing one dense A (shared_solver.cu)
 // ---------------------------------------------------------------------------
-enum ShAction : int32_t { SH_INIT = 0, SH_STEP = 1, SH_WARM = 2, SH_CONFIRM = 3, SH_DONE = 4 };
+enum ShAction : int32_t { SH_INIT = 0, SH_STEP = 1, SH_WARM = 2, SH_DONE = 4 };
 
 // Per-instance scalars of the shared-A batch.
 struct ShInst {

@@ -101,3 +101,33 @@ def test_argument_errors_without_device(lib):
     assert e.value.code in (abip.ABIP_E_DIM, abip.ABIP_E_CUDA)
     # empty batch is a no-op
     assert lib.abip_solve_batch(0, None, None, None, None, None, None, None, None, None) == 0
+
+
+def test_shared_and_backward_argument_errors_without_device(lib):
+    """The shared-A batch and the batch backward refuse bad arguments before any device work."""
+    from paper_1805_12344_gb300 import abip
+    from paper_1805_12344_gb300 import workloads as W
+    assert lib.abip_solve_batch_shared(0, None, None, None, None, None, None, None, None, None) == 0
+    assert lib.abip_solve_batch_shared(1, None, None, None, None, None, None, None, None, None) == \
+        abip.ABIP_E_INVALID_ARG
+    assert lib.abip_backward(None, None, None, None, None) == abip.ABIP_E_INVALID_ARG
+    assert lib.abip_backward_batch(0, None, None, None, None, None, None, None, None, None, None, None, None,
+                                   None) == 0
+    # a CSR matrix is not a shared dense A
+    csr = W.dense_to_csr(np.eye(2, 3))
+    with pytest.raises(abip.AbipError) as e:
+        abip.abip_solve_batch_shared(csr, [np.ones(2)], [np.ones(3)])
+    assert e.value.code == abip.ABIP_E_UNSUPPORTED
+    # the tensor-core products need A exact in bfloat16
+    A = np.full((2, 3), 0.1)
+    with pytest.raises(abip.AbipError) as e:
+        abip.abip_solve_batch_shared(A, [np.ones(2)], [np.ones(3)],
+                                     abip.default_params(precision=abip.ABIP_PREC_MIXED_BF16))
+    assert e.value.code == abip.ABIP_E_INVALID_ARG
+    assert b"bfloat16" in lib.abip_last_error(None)
+    # no gradient at an infeasibility certificate (status from the forward's infos)
+    with pytest.raises(abip.AbipError) as e:
+        abip.abip_backward_batch([np.eye(2, 3)], [np.ones(2)], [np.ones(3)], [np.ones(3)], [np.ones(2)],
+                                 [np.ones(3)], [dict(status=abip.ABIP_PRIMAL_INFEASIBLE, tau=1.0, kappa=1.0,
+                                                     theta=1.0, mu=1e-3)], [np.ones(3)])
+    assert e.value.code == abip.ABIP_E_INVALID_ARG
