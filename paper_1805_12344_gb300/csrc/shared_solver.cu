@@ -871,9 +871,24 @@ struct Bump {
 int shared_batch_run(const SharedBatchArgs& a, std::vector<SharedBatchResult>& out, std::string& err) {
   const int m = a.m, n = a.n, B = a.count;
   const bool mixed = a.prm.mixed != 0;
-  cudaStream_t st = a.stream;
   if (B < 1 || B > kMaxBatch) { err = "shared batch: a chunk holds 1..64 instances"; return ABIP_E_INVALID_ARG; }
-  if ((size_t)m * 8 > 200 * 1024) { err = "shared batch: m <= 25600"; return ABIP_E_UNSUPPORTED; }
+  // the update cycles are captured in a CUDA graph, which the legacy default stream cannot
+  // record: without a caller stream the solve runs on its own (it is synchronous, and its
+  // inputs are staged through host memory first)
+  cudaStream_t st = a.stream;
+  cudaStream_t owned = nullptr;
+  if (!st) {
+    if (cudaStreamCreateWithFlags(&owned, cudaStreamNonBlocking) != cudaSuccess) {
+      err = "shared batch: cannot create a stream";
+      return ABIP_E_CUDA;
+    }
+    st = owned;
+  }
+  if ((size_t)m * 8 > 200 * 1024) {
+    err = "shared batch: m <= 25600";
+    if (owned) cudaStreamDestroy(owned);
+    return ABIP_E_UNSUPPORTED;
+  }
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -953,6 +968,8 @@ int shared_batch_run(const SharedBatchArgs& a, std::vector<SharedBatchResult>& o
   void* arena = nullptr;
   if (cudaMalloc(&arena, bytes) != cudaSuccess) {
     err = "shared batch: cannot allocate " + std::to_string(bytes) + " bytes";
+    cudaGetLastError();
+    if (owned) cudaStreamDestroy(owned);
     return ABIP_E_OOM;
   }
   bp.base = static_cast<char*>(arena);
@@ -1105,10 +1122,42 @@ int shared_batch_run(const SharedBatchArgs& a, std::vector<SharedBatchResult>& o
   const int64_t max_cycles = 2 * a.prm.max_admm + 2 * (int64_t)kMaxOuter + 16;
   int64_t cycles = 0;
   constexpr int kGroup = 16;
+  // one group of cycles as a CUDA graph (every decision in it is taken on the device);
+  // direct launches if the capture or the instantiation fails
+  cudaGraphExec_t gexec = nullptr;
+  int64_t group_launches = 0;
+  if (rc == ABIP_OK) {
+    const int rc0 = rc;
+    const int64_t l0 = launches;
+    cudaGraph_t graph = nullptr;
+    if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+      for (int g = 0; g < kGroup; ++g) {
+        if (mixed) cycle_mixed();
+        else cycle64();
+      }
+      const cudaError_t ec = cudaStreamEndCapture(st, &graph);
+      if (ec == cudaSuccess && graph && rc == ABIP_OK && cudaGraphInstantiate(&gexec, graph, 0) == cudaSuccess)
+        group_launches = launches - l0;
+      else
+        gexec = nullptr;
+      if (graph) cudaGraphDestroy(graph);
+    }
+    launches = l0;
+    if (!gexec) {   // fall back to direct launches
+      rc = rc0;
+      err.clear();
+      cudaGetLastError();
+    }
+  }
   while (rc == ABIP_OK) {
-    for (int g = 0; g < kGroup; ++g) {
-      if (mixed) cycle_mixed();
-      else cycle64();
+    if (gexec) {
+      ck(cudaGraphLaunch(gexec, st), "cycle graph");
+      launches += group_launches;
+    } else {
+      for (int g = 0; g < kGroup; ++g) {
+        if (mixed) cycle_mixed();
+        else cycle64();
+      }
     }
     cycles += kGroup;
     ck(cudaGetLastError(), "cycle launches");
@@ -1118,6 +1167,7 @@ int shared_batch_run(const SharedBatchArgs& a, std::vector<SharedBatchResult>& o
     if (cycles > max_cycles) { err = "shared batch: cycle guard reached"; rc = ABIP_E_NUMERICAL; }
   }
   cudaFreeHost(hflags);
+  if (gexec) cudaGraphExecDestroy(gexec);
   if (rc == ABIP_OK && tc) {
     int herr2 = 0;
     ck(cudaMemcpy(&herr2, derr + 1, sizeof(int), cudaMemcpyDeviceToHost), "tensor-core status");
@@ -1163,6 +1213,7 @@ int shared_batch_run(const SharedBatchArgs& a, std::vector<SharedBatchResult>& o
   cudaEventDestroy(e1);
   cudaStreamSynchronize(st);
   cudaFree(arena);
+  if (owned) cudaStreamDestroy(owned);
   return rc;
 }
 
