@@ -89,7 +89,7 @@ def algorithmic_bytes(m, n, nnz, admm_iters, cg_iters, outer_iters, vec_bytes, v
 
 # DRAM traffic of the solve kernel from the committed ncu summary (fixed fill + per-update
 # part, measured at two update counts); None when the summary does not match this build.
-TRAFFIC_KERNEL_VERSION = "grid_kernel thread0-scalars"
+TRAFFIC_KERNEL_VERSION = "grid_kernel thread0-scalars sell16"
 
 
 def traffic_from_profile(precision, admm_updates):
