@@ -12,7 +12,7 @@ complement) + abip_solve running Algorithm 2 for a fixed budget of ADMM updates
 Jacobi-PCG, A and A^T products, prox, dual update, residual and termination
 reductions, mu decreases), inputs resident in HBM.
 
-Value: ADMM updates per second, whole job (BASELINE's metric lists LPs solved/s,
+Value: ADMM updates per second, whole job (the headline metric lists LPs solved/s,
 ADMM iter/s and HBM GB/s).  LPs solved to 1e-6 per second is reported beside it
 and is 0 on this workload: ABIP with the paper's inner stop rule needs more than
 the paper's 10^6-update cap to reach a 1e-6 gap at n = 400000 (measured: after
@@ -411,7 +411,7 @@ def main():
                        "parallelism": f"replicas{world}"},
             "lps_solved_per_s": solved / total_s,
             "lps_solved_note": ("0 on this workload: the paper's inner stop needs more than its 1e6-update cap "
-                                "to reach a 1e-6 gap at n = 400000; see DESIGN.md"),
+                                "to reach a 1e-6 gap at n = 400000 (the gap falls like n mu / tau^2)"),
             "hbm_gbs_algorithmic": achieved,
             "status": [i["status_name"] for i in infos],
             "admm_iters": last["admm_iters"], "cg_iters": last["cg_iters"], "outer_iters": last["outer_iters"],

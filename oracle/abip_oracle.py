@@ -26,7 +26,7 @@ The algorithm follows the paper's order and notation:
   heuristic that keeps the larger of x_j, s_j), or the sqrt(gamma) rescale of
   Eq. update-next-iterate.
 
-Readings of silent or ambiguous points (documented in the design doc, same labels):
+Readings of silent or ambiguous points (labels shared with the CUDA library's notes):
 A1 4-block Q; A2 fixed gamma; A3 beta = mu0 = 1; A4 heuristic warm start for
 (x,s),(tau,kappa) and sqrt(gamma) for y, theta, ties keep x; A6 dgap normaliser uses
 the tau-scaled candidate; A8 certificate signs and test order; A9 two-root stable
