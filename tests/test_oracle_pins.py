@@ -364,3 +364,44 @@ def test_basis_pursuit_recovers_sparse_vector():
     assert r.obj <= np.abs(xt).sum() * (1 + 1e-6) + 1e-9
     assert np.abs((r.x[:nd] - r.x[nd:]) - xt).max() <= 1e-4
     assert abs(r.obj - np.abs(xt).sum()) <= 1e-5 * np.abs(xt).sum()
+
+
+# --- special cases whose optimum the mathematics fixes ---------------------------------
+
+def test_square_system_has_the_unique_feasible_point():
+    """m = n with A nonsingular: x = A^{-1} b is the only feasible point; when it is
+    positive it is the optimum whatever c is."""
+    rng = np.random.default_rng(41)
+    n = 6
+    A = rng.standard_normal((n, n)) + 3.0 * np.eye(n)
+    x0 = rng.uniform(0.5, 2.0, n)
+    b = A @ x0
+    c = rng.standard_normal(n)
+    r = O.solve(A, b, c)
+    assert r.status == O.OPTIMAL
+    assert np.abs(r.x - x0).max() <= 1e-4 * np.abs(x0).max()
+    assert abs(r.obj - c @ x0) <= 1e-5 * max(1.0, abs(c @ x0))
+
+
+def test_duplicated_row_leaves_the_optimum_unchanged():
+    """Repeating an equality (a redundant row of A, b) changes neither the feasible set nor
+    the optimal value; I + A A^T stays positive definite."""
+    lp = W.planted_dense(8, 20, seed=17)
+    A2 = np.vstack([lp.A, lp.A[2:3]])
+    b2 = np.concatenate([lp.b, lp.b[2:3]])
+    r1 = O.solve(lp.A, lp.b, lp.c)
+    r2 = O.solve(A2, b2, lp.c)
+    assert r1.status == r2.status == O.OPTIMAL
+    p_star = lp.c @ lp.x0
+    for r in (r1, r2):
+        assert abs(r.obj - p_star) <= 1e-5 * max(1.0, abs(p_star))
+
+
+def test_scaling_the_cost_scales_the_optimal_value():
+    """min (2c)^T x has the same solution set as min c^T x and twice its optimal value."""
+    lp = W.planted_dense(8, 20, seed=19)
+    r1 = O.solve(lp.A, lp.b, lp.c)
+    r2 = O.solve(lp.A, lp.b, 2.0 * lp.c)
+    assert r1.status == r2.status == O.OPTIMAL
+    assert abs(r2.obj - 2.0 * r1.obj) <= 1e-5 * max(1.0, abs(r2.obj))
+    assert np.abs(r2.x - r1.x).max() <= 1e-3 * max(1.0, np.abs(r1.x).max())
