@@ -73,8 +73,9 @@ class Params:
     linsys: int = 0              # 0 dense Cholesky of G, 1 Jacobi-PCG on G
     cg_tol: float = 1e-13        # reading A10: ||r|| <= cg_tol * max(1, ||rhs||)
     cg_max_iter: int = 10000
-    cg_warm: int = 2             # PCG start (reading A10): 0 previous z_y, 1 linear extrapolation
-                                 # 2 z_k - z_{k-1}, 2 quadratic extrapolation 3 z_k - 3 z_{k-1} + z_{k-2}
+    cg_warm: int = 2             # PCG start (reading A10): 0 the previous z_y; 1 the linear
+                                 # extrapolation 2 z_k - z_{k-1}; 2 the quadratic one
+                                 # 3 z_k - 3 z_{k-1} + z_{k-2}
     warmstart: int = 0           # 0 keep-larger heuristic (Sec. 5), 1 sqrt(gamma) (Eq. update-next-iterate)
     stop_rule: int = 0           # 0 Sec. 4.1 tests, 1 stop once mu < eps (outer-count check of Thm 3.6)
 
