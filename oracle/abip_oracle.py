@@ -78,6 +78,10 @@ class Params:
                                  # 3 z_k - 3 z_{k-1} + z_{k-2}
     warmstart: int = 0           # 0 keep-larger heuristic (Sec. 5), 1 sqrt(gamma) (Eq. update-next-iterate)
     stop_rule: int = 0           # 0 Sec. 4.1 tests, 1 stop once mu < eps (outer-count check of Thm 3.6)
+    bb_beta: bool = False        # Sec. 4.3: Barzilai-Borwein choice of beta at each outer iteration
+    eps_cor: float = 0.2         # Sec. 4.3 curvature-quality threshold (value from Sec. 5)
+    eps_penalty: float = 0.1     # Sec. 4.3 heuristic threshold (value from Sec. 5)
+    bb_max_redo: int = 5         # reading B5: the paper does not bound the "redo" loop
 
 
 @dataclass
@@ -379,9 +383,11 @@ def make_linsys(P: Problem, prm: Params):
     return JacobiPCG(P, prm.cg_tol, prm.cg_max_iter)
 
 
-def admm_step(P: Problem, proj: Projection, st: dict, mu: float, prm: Params):
+def admm_step(P: Problem, proj: Projection, st: dict, mu: float, prm: Params, beta: Optional[float] = None):
     """One inner iteration of Algorithm 2 with over-relaxation (Sec. 4.2):
-    projection, relaxation, barrier step for u, dual step for v."""
+    projection, relaxation, barrier step for u, dual step for v.  beta: the outer
+    iteration's beta (Sec. 4.3), prm.beta when None.  Returns the projection u_tilde
+    as (y, x, tau, theta)."""
     y, x, s = st["y"], st["x"], st["s"]
     tau, kappa, theta = st["tau"], st["kappa"], st["theta"]
     r = np.zeros(P.m)
@@ -394,7 +400,7 @@ def admm_step(P: Problem, proj: Projection, st: dict, mu: float, prm: Params):
     xh = a * ux + (1 - a) * x
     th = a * ut + (1 - a) * tau
     thh = a * uth + (1 - a) * theta
-    cmu = mu / prm.beta
+    cmu = mu / (prm.beta if beta is None else beta)
     # Eqs. Simple-Update:Barrier-Y/X/tau/theta and Simple-Update:Dual
     x_new, s_new = barrier_prox(xh - s, cmu)
     tau_new, kappa_new = barrier_prox(np.array([th - kappa]), cmu)
@@ -404,6 +410,75 @@ def admm_step(P: Problem, proj: Projection, st: dict, mu: float, prm: Params):
     st["tau"] = float(tau_new[0])
     st["kappa"] = float(kappa_new[0])
     st["theta"] = thh
+    return uy, ux, float(ut), float(uth)
+
+
+# ---------------------------------------------------------------------------
+# Barzilai-Borwein choice of beta (Sec. 4.3)
+# ---------------------------------------------------------------------------
+
+def _u_vec(st: dict) -> np.ndarray:
+    return np.concatenate([st["y"], st["x"], [st["tau"], st["theta"]]])
+
+
+def _v_vec(P: Problem, st: dict) -> np.ndarray:
+    """v = (r, s, kappa, xi) with r = 0 and xi = -n-1 (Algorithm 2)."""
+    return np.concatenate([np.zeros(P.m), st["s"], [st["kappa"], P.xi]])
+
+
+def _hybrid(sd: float, mg: float) -> float:
+    """The hybrid spectral step: the minimum-gradient step when 2 MG > SD, else SD - MG/2."""
+    return mg if 2.0 * mg > sd else sd - mg / 2.0
+
+
+def bb_estimate(dv_hat: np.ndarray, du_tilde: np.ndarray, du: np.ndarray, beta: float, eps_cor: float) -> float:
+    """beta_hat of Sec. 4.3 from the curvature pairs (dv_hat, du_tilde) and (dv_hat, du):
+    steepest-descent and minimum-gradient spectral steps, their hybrid, the correlation
+    safeguards, and the geometric mean when both estimates are reliable."""
+    vv = float(dv_hat @ dv_hat)
+    nv = np.sqrt(vv)
+
+    def pair(d):
+        vd, dd = float(dv_hat @ d), float(d @ d)
+        if vd == 0.0 or dd == 0.0 or nv == 0.0:
+            return 0.0, -1.0
+        return _hybrid(vv / vd, vd / dd), vd / (nv * np.sqrt(dd))
+
+    phi, phi_cor = pair(du_tilde)
+    psi, psi_cor = pair(du)
+    if phi_cor > eps_cor and psi_cor > eps_cor:
+        return float(np.sqrt(phi * psi))
+    if phi_cor > eps_cor:
+        return float(phi)
+    if psi_cor > eps_cor:
+        return float(psi)
+    return float(beta)
+
+
+def bb_select(P: Problem, proj: Projection, st0: dict, mu: float, beta: float, prm: Params):
+    """Sec. 4.3 at the start of an outer iteration: two ADMM updates from st0 with beta give
+    the curvature pairs; then the heuristic selection (reading B5).  Returns (beta for this
+    outer iteration, state to continue from, ADMM updates spent)."""
+    a = prm.alpha
+    spent = 0
+    st = st0
+    for redo in range(prm.bb_max_redo + 1):
+        st = {k: (v.copy() if isinstance(v, np.ndarray) else v) for k, v in st0.items()}
+        u0, v0 = _u_vec(st), _v_vec(P, st)
+        ut1 = np.concatenate(list(map(np.atleast_1d, admm_step(P, proj, st, mu, prm, beta))))
+        u1, v1 = _u_vec(st), _v_vec(P, st)
+        ut2 = np.concatenate(list(map(np.atleast_1d, admm_step(P, proj, st, mu, prm, beta))))
+        u2 = _u_vec(st)
+        spent += 2
+        vh1 = v0 - a * ut1 - (1 - a) * u0 + a * u1
+        vh2 = v1 - a * ut2 - (1 - a) * u1 + a * u2
+        beta_hat = bb_estimate(vh2 - vh1, a * (ut2 - ut1) + (1 - a) * (u1 - u0), -(u2 - u1), beta, prm.eps_cor)
+        if beta_hat == beta:                       # no reliable curvature: keep beta, go on
+            return beta, st, spent
+        if abs(beta_hat - beta) <= prm.eps_penalty:
+            return 0.5 * (beta + beta_hat), st, spent
+        beta = beta_hat                            # redo from the same initial point
+    return beta, st, spent
 
 
 def warm_start(st: dict, gamma: float, rule: int):
@@ -464,17 +539,23 @@ def solve(A, b, c, prm: Optional[Params] = None, trace_iters: int = 0,
     nc = float(np.linalg.norm(P.c))
     st = initial_state(P)
     mu = prm.beta                      # mu0 = beta
+    beta_k = prm.beta
+    betas = []
     total = 0
     outer = 0
     trace = []
     chk = None
     status = 0
     while status == 0:
+        if prm.bb_beta and total + 2 <= prm.max_admm_iters:
+            beta_k, st, spent = bb_select(P, proj, st, mu, beta_k, prm)
+            total += spent
+            betas.append(beta_k)
         # inner loop at fixed mu (Algorithm 2)
         while True:
             if inner_residual_sq(P, st) <= mu:
                 break
-            admm_step(P, proj, st, mu, prm)
+            admm_step(P, proj, st, mu, prm, beta_k)
             total += 1
             if total <= trace_iters:
                 trace.append(stacked(st))
@@ -512,7 +593,8 @@ def solve(A, b, c, prm: Optional[Params] = None, trace_iters: int = 0,
     return Result(status=status, x=xo, y=yo, s=so, tau=tau, kappa=st["kappa"], theta=st["theta"],
                   mu=mu, admm_iters=total, outer_iters=outer, cg_iters=getattr(lin, "iters", 0),
                   pres=chk.pres, dres=chk.dres, dgap=chk.dgap, obj=chk.ctx / tau,
-                  raw=dict(y=y.copy(), x=x.copy(), s=s.copy(), tau=tau, kappa=st["kappa"], theta=st["theta"]),
+                  raw=dict(y=y.copy(), x=x.copy(), s=s.copy(), tau=tau, kappa=st["kappa"], theta=st["theta"],
+                           betas=betas),
                   trace=trace)
 
 

@@ -405,3 +405,31 @@ def test_scaling_the_cost_scales_the_optimal_value():
     assert r1.status == r2.status == O.OPTIMAL
     assert abs(r2.obj - 2.0 * r1.obj) <= 1e-5 * max(1.0, abs(r2.obj))
     assert np.abs(r2.x - r1.x).max() <= 1e-3 * max(1.0, np.abs(r1.x).max())
+
+
+# --- Barzilai-Borwein choice of beta (Sec. 4.3) ----------------------------------------
+
+def test_bb_estimate_collinear_and_orthogonal_cases():
+    """Collinear curvature pairs dv = c1 du_tilde and dv = c2 du (the equality case of
+    Cauchy-Schwarz): both spectral steps equal the scale, the hybrid keeps it, both
+    correlations are 1, so beta_hat = sqrt(c1 c2).  Orthogonal pairs (correlation 0) fail
+    the safeguard and keep beta."""
+    rng = np.random.default_rng(5)
+    d = rng.standard_normal(40)
+    # dv = 3 du_tilde and dv = (3 / 0.75) du
+    assert O.bb_estimate(3.0 * d, d, 0.75 * d, 1.0, 0.2) == pytest.approx(np.sqrt(3.0 * (3.0 / 0.75)), rel=1e-12)
+    e = rng.standard_normal(40)
+    e -= (e @ d) / (d @ d) * d
+    assert O.bb_estimate(d, e, e, 0.7, 0.2) == 0.7
+    # one reliable pair: its own hybrid step
+    assert O.bb_estimate(2.0 * d, d, e, 0.7, 0.2) == pytest.approx(2.0, rel=1e-12)
+
+
+def test_bb_beta_solve_reaches_the_planted_optimum():
+    lp = W.planted_dense(20, 60, seed=23)
+    r = O.solve(lp.A, lp.b, lp.c, O.Params(bb_beta=True))
+    assert r.status == O.OPTIMAL
+    p_star = lp.c @ lp.x0
+    assert abs(r.obj - p_star) <= 1e-5 * max(1.0, abs(p_star))
+    assert len(r.raw["betas"]) == r.outer_iters + 1
+    assert all(b > 0 for b in r.raw["betas"])
