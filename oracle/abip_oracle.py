@@ -30,7 +30,9 @@ Readings of silent or ambiguous points (labels shared with the CUDA library's no
 A1 4-block Q; A2 fixed gamma; A3 beta = mu0 = 1; A4 heuristic warm start for
 (x,s),(tau,kappa) and sqrt(gamma) for y, theta, ties keep x; A6 dgap normaliser uses
 the tau-scaled candidate; A8 certificate signs and test order; A9 two-root stable
-prox; A10 CG stop rule; A13 MAX_ITER status.
+prox; A10 CG stop rule; A13 MAX_ITER status; B5 Barzilai-Borwein beta (Sec. 4.3,
+opt-in): continue from the trial iterates, at most 5 redo rounds; B6 the curvature
+pairs with the printed signs.
 
 Parity status: every function here is pinned by tests in tests/test_oracle_*.py
 except the exact iteration trajectory of `solve` (iteration counts, the iterates
