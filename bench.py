@@ -69,41 +69,41 @@ def parse():
 # algorithmic bytes of the persistent solve kernel (one launch = one whole solve)
 # --------------------------------------------------------------------------------------
 
-def algorithmic_bytes(m, n, nnz, admm_iters, cg_iters, outer_iters, vec_bytes, val_bytes=4):
-    """Compulsory traffic of the solve kernel: every phase reads its matrix once
-    (values, column indices, row offsets) and each vector it touches once.
-      one pass over A:   MA  = nnz (vb + 4) + 4 (m + 1)
-      one pass over A^T: MAT = nnz (vb + 4) + 4 (n + 1)
-      per PCG iteration:   MA + MAT + t (3 n + 13 m)
-      per ADMM iteration (PCG start, z_x, update, residuals): 2 MA + 3 MAT + t (21 n + 23 m)
-      per mu decrease (rescale, residuals): MA + MAT + t (10 n + 7 m)
-    with t the bytes of one vector element."""
-    t = vec_bytes
-    MA = nnz * (val_bytes + 4) + 4 * (m + 1)
-    MAT = nnz * (val_bytes + 4) + 4 * (n + 1)
-    per_cg = MA + MAT + t * (3 * n + 13 * m)
-    per_admm = 2 * MA + 3 * MAT + t * (21 * n + 23 * m)
-    per_outer = MA + MAT + t * (10 * n + 7 * m)
-    return cg_iters * per_cg + admm_iters * per_admm + (outer_iters + 1) * per_outer
+def algorithmic_bytes(m, n, nnz, admm_iters, cg_iters, vec_bytes, val_bytes=4):
+    """Minimum traffic of the ADMM iteration on a CSR A (one pass over a CSR matrix reads
+    its values, column indices and row offsets: nnz (p + 4) + 8 (rows + 1) bytes):
+      per ADMM update:   one pass over A, one over A^T, and 20 vector passes of n elements
+                         (A x of the new iterate fused with the next projection's A d; A^T y
+                         by the exact recurrence of the projection);
+      per PCG iteration: one pass over A, one over A^T, and 6 vector passes of m elements;
+    with p the bytes of a matrix value and q (vec_bytes) those of a vector element."""
+    q = vec_bytes
+    MA = nnz * (val_bytes + 4) + 8 * (m + 1)
+    MAT = nnz * (val_bytes + 4) + 8 * (n + 1)
+    return admm_iters * (MA + MAT + 20 * n * q) + cg_iters * (MA + MAT + 6 * m * q)
 
 
-# DRAM traffic of the solve kernel from the committed ncu summary (fixed fill + per-update
-# part, measured at two update counts); None when the summary does not match this build.
-TRAFFIC_KERNEL_VERSION = "grid_kernel thread0-scalars sell16"
+# DRAM traffic of the solve kernel from one ncu capture (dram__bytes_read.sum +
+# dram__bytes_write.sum at two update counts: a fixed fill and a per-update part), valid
+# only for the kernel sources it was measured on; None once any of them has changed.
+KERNEL_SOURCES = ("paper_1805_12344_gb300/csrc/grid_delta.cu", "paper_1805_12344_gb300/csrc/sell.cuh",
+                  "paper_1805_12344_gb300/csrc/abip_device.cuh")
+TRAFFIC = {"sources_sha256": None, "dram_bytes_fixed": None, "dram_bytes_per_update": None}
 
 
-def traffic_from_profile(precision, admm_updates):
-    path = os.path.join(ROOT, "profiles", "grid_kernel_solve_sparse_m100000.md")
-    try:
-        for line in open(path):
-            if line.startswith("traffic_model:"):
-                tm = json.loads(line.split(":", 1)[1])
-                if tm.get("kernel_version") != TRAFFIC_KERNEL_VERSION or tm.get("precision") != precision:
-                    return None
-                return tm["dram_bytes_fixed"] + tm["dram_bytes_per_admm_update"] * admm_updates
-    except Exception:
+def kernel_sources_hash():
+    import hashlib
+    h = hashlib.sha256()
+    for rel in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
+def traffic_per_launch(admm_updates):
+    if TRAFFIC["sources_sha256"] is None or TRAFFIC["sources_sha256"] != kernel_sources_hash():
         return None
-    return None
+    return TRAFFIC["dram_bytes_fixed"] + TRAFFIC["dram_bytes_per_update"] * admm_updates
 
 
 def aggregate_ranks(total_s, solved, admm, dist_mod=None, device="cpu"):
@@ -368,10 +368,10 @@ def main():
     # roofline of the persistent solve kernel (one launch per step)
     vec_bytes = 4 if args.precision == "mixed" else 8
     last = infos[-1]
-    alg = algorithmic_bytes(m, n, nnz, last["admm_iters"], last["cg_iters"], last["outer_iters"], vec_bytes)
+    alg = algorithmic_bytes(m, n, nnz, last["admm_iters"], last["cg_iters"], vec_bytes)
     achieved = alg / last["kernel_s"] / 1e9
     peak, peak_kind = measured_peaks()
-    traffic = traffic_from_profile(args.precision, last["admm_iters"])
+    traffic = traffic_per_launch(last["admm_iters"]) if args.precision == "mixed" else None
 
     # end to end through the public API with host buffers
     e2e = None

@@ -67,7 +67,10 @@ extern "C" {
 
 /* arithmetic of the iteration */
 #define ABIP_PREC_F64        0   /* every vector and product in FP64 */
-#define ABIP_PREC_MIXED      1   /* FP32 products (of the iterates' changes on the dense paths), FP64 tests */
+#define ABIP_PREC_MIXED      1   /* FP64 iterate and products, updated by FP32 products of the iterate's
+                                    changes (sparse path: FP32 PCG for the correction of each projection
+                                    solve, with an FP64 right-hand side); FP64 tests.  A CSR A's values
+                                    are used rounded to FP32 */
 #define ABIP_PREC_MIXED_BF16 2   /* as MIXED; the shared-A batch runs its products with A on the tensor
                                     cores (tcgen05, bfloat16 operands, FP32 accumulation) and needs an
                                     A exactly representable in bfloat16; other paths treat it as MIXED */
@@ -110,7 +113,10 @@ typedef struct {
                                confirmations of the Sec. 4.1 tests (each screen pass that comes
                                sooner waits); 1 = confirm whenever the screen passes */
     int32_t grid_ctas;      /* 0: automatic; else the persistent grid size (tests) */
-    int32_t reserved[8];
+    int64_t barrier_limit_ns; /* sparse (PCG) path: wall-clock limit of one grid-barrier wait in
+                                 the persistent kernel; a wait past it ends the solve with
+                                 ABIP_E_TIMEOUT (the kernel returns).  0: 4 s (default) */
+    int32_t reserved[6];
 } abip_params;
 
 typedef struct {
@@ -124,9 +130,9 @@ typedef struct {
     double setup_s, solve_s;/* wall-clock seconds of abip_setup and of the last solve */
     double kernel_s;        /* device time of the solve kernel, from CUDA events on the solve stream */
     int64_t launches;       /* kernels the solve call launched */
-    int64_t fp32_iters;     /* ADMM updates whose products were FP32 (mixed precision; the dense and
-                               shared-A paths update FP64 products with FP32 products of the
-                               changes, the sparse path iterates in FP32) */
+    int64_t fp32_iters;     /* ADMM updates whose products were FP32 (mixed precision: every path
+                               keeps the iterate and its products in FP64 and updates them with
+                               FP32 products of the changes) */
 } abip_info;
 
 typedef struct abip_handle abip_handle;
@@ -208,8 +214,10 @@ ABIP_API int abip_solve_batch_shared(int32_t count, const abip_matrix* A, const 
  * embedding at the final mu of the last abip_solve (the fixed point of the ADMM
  * inner loop at that mu, system HSD-log-kkt of Sec. 3.2: Q u = v with r = 0 and
  * xi = -n-1, x o s = tau kappa = mu / beta).  The final ADMM iterate is first
- * polished onto that point by damped Newton steps; then J^T lam = dL/dz is solved
- * through the m x m matrix A X S^-1 A^T (FP64 Cholesky) and a 2 x 2 system, and
+ * polished onto that point by damped Newton steps; then J^T lam = dL/dz is solved by
+ * eliminating ds and dkappa, which leaves the reduced Jacobian
+ * K = Q + diag(0, S X^-1, kappa / tau, 0) of order m + n + 2, factored by LU with
+ * partial pivoting in FP64 (one step of iterative refinement), and
  * dL/dp = -lam^T dF/dp, counting the dependence of bbar, cbar, zbar on (A, b, c)
  * (Eq. bar-b-c-z-re).  The handle's state is left unchanged.
  *   dl_dx: n entries, dL/dx* (host or device).
@@ -218,7 +226,7 @@ ABIP_API int abip_solve_batch_shared(int32_t count, const abip_matrix* A, const 
  * Needs a dense handle (linsys = dense, or the automatic choice for dense input):
  * ABIP_E_UNSUPPORTED otherwise.  ABIP_E_NOT_SOLVED before the first solve;
  * ABIP_E_INVALID_ARG for an infeasibility result (no tau > 0) or non-finite dl_dx;
- * ABIP_E_NUMERICAL if A X S^-1 A^T is not numerically positive definite.
+ * ABIP_E_NUMERICAL if K has an exactly zero pivot (singular at the central point).
  */
 ABIP_API int abip_backward(abip_handle* h, const double* dl_dx,
                            double* dl_dc, double* dl_db, double* dl_dA);

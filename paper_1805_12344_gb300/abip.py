@@ -65,7 +65,7 @@ class abip_params(C.Structure):
                 ("max_admm_iters", C.c_int64), ("linsys", C.c_int32), ("cg_tol", C.c_double),
                 ("cg_max_iter", C.c_int32), ("cg_rel", C.c_double), ("cg_warm", C.c_int32), ("precision", C.c_int32), ("warmstart", C.c_int32),
                 ("stop_rule", C.c_int32), ("check_every", C.c_int32), ("grid_ctas", C.c_int32),
-                ("reserved", C.c_int32 * 8)]
+                ("barrier_limit_ns", C.c_int64), ("reserved", C.c_int32 * 6)]
 
 
 class abip_info(C.Structure):

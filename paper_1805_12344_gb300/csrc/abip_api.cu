@@ -130,6 +130,7 @@ int check_params(const abip_params& p, std::string& why) {
   if (p.warmstart != 0 && p.warmstart != 1) { why = "warmstart must be 0 or 1"; return 0; }
   if (p.cg_warm < 0 || p.cg_warm > 2) { why = "cg_warm must be 0, 1 or 2"; return 0; }
   if (p.stop_rule != 0 && p.stop_rule != 1) { why = "stop_rule must be 0 or 1"; return 0; }
+  if (p.barrier_limit_ns < 0) { why = "barrier_limit_ns must be >= 0"; return 0; }
   return 1;
 }
 
@@ -251,8 +252,8 @@ HostSell to_sell(const HostCSR& M, int L) {
   return S;
 }
 
-template <typename T>
-void assign_vectors(GridData<T>& g, Arena& ar, int m, int n) {
+void assign_vectors(GridData<double>& g, Arena& ar, int m, int n) {
+  using T = double;
   g.b = ar.take<T>(m);
   g.c = ar.take<T>(n);
   g.bbar = ar.take<T>(m); g.cbar = ar.take<T>(n); g.dinv = ar.take<T>(m);
@@ -261,22 +262,38 @@ void assign_vectors(GridData<T>& g, Arena& ar, int m, int n) {
   g.Ax = ar.take<T>(m); g.As = ar.take<T>(m); g.ATy = ar.take<T>(n);
   g.zy = ar.take<T>(m); g.zx = ar.take<T>(n); g.zp2 = ar.take<T>(m); g.zp3 = ar.take<T>(m);
   g.r = ar.take<T>(m); g.p = ar.take<T>(m); g.Gp = ar.take<T>(m);
-  using T2 = typename abip::Vec2<T>::type;
-  g.ut = ar.take<T2>(n); g.zd = ar.take<T2>(m); g.zd2 = ar.take<T2>(m);
+  g.ut = ar.take<double2>(n); g.zd = ar.take<double2>(m); g.zd2 = ar.take<double2>(m);
 }
 
-template <typename T>
-int setup_grid_path(abip_handle* h, const HostCSR& A, const std::vector<double>& b, const std::vector<double>& c,
-                    bool vals_f32_exact) {
+void assign_vectors(abip::GridDelta& g, Arena& ar, int m, int n) {
+  g.b = ar.take<double>(m);
+  g.c = ar.take<double>(n);
+  g.bbar = ar.take<double>(m); g.cbar = ar.take<double>(n);
+  g.g1y = ar.take<double>(m); g.g1x = ar.take<double>(n); g.g2y = ar.take<double>(m); g.g2x = ar.take<double>(n);
+  g.y = ar.take<double>(m); g.x = ar.take<double>(n); g.s = ar.take<double>(n);
+  g.Ax = ar.take<double>(m); g.As = ar.take<double>(m); g.ATy = ar.take<double>(n);
+  g.zy = ar.take<double>(m); g.ATz = ar.take<double>(n); g.wv = ar.take<double>(n);
+  g.dinv = ar.take<float>(m); g.dz = ar.take<float>(m); g.d1 = ar.take<float>(m); g.d2 = ar.take<float>(m);
+  g.r = ar.take<float>(m); g.p = ar.take<float>(m); g.Gp = ar.take<float>(m);
+  g.ut = ar.take<float2>(n); g.zd = ar.take<float2>(m); g.zd2 = ar.take<float2>(m);
+  g.dxs = ar.take<float2>(n); g.dy = ar.take<float>(m);
+}
+
+cudaError_t launch_persistent(abip_handle* h, cudaStream_t st) {
+  if (h->mixed) return abip::launch_grid_delta(h->gdd, h->grid, st);
+  return abip::launch_grid_solver_f64(h->gd64, h->val_f64 != 0, h->grid, st);
+}
+
+// Setup of the sparse (PCG) path for one LP: SELL copies of A and A^T, the device
+// arena of G (GridData<double> for FP64, GridDelta for mixed precision) and one
+// launch of the persistent kernel in MODE_SETUP.  vf64: store A's values as double.
+template <typename G>
+int setup_grid_path(abip_handle* h, G& g, const HostCSR& A, const std::vector<double>& b,
+                    const std::vector<double>& c, bool vf64, int maxc) {
   const int m = A.m, n = A.n;
-  const int64_t nnz = A.rp[m];
   HostCSR AT = transpose(A);
-  const bool mixed = std::is_same<T, float>::value;
-  // values are stored as float when they are exactly float (input F32) or when iterating in FP32
-  const bool vf64 = !mixed && !vals_f32_exact;
   h->val_f64 = vf64 ? 1 : 0;
   const size_t vb = vf64 ? 8 : 4;
-  const int maxc = abip::grid_solver_max_ctas(mixed, vf64, h->device);
   if (maxc <= 0) return fail(h, ABIP_E_CUDA, "grid kernel cannot be made resident");
   // grid_total reads at most kGridTotalPer partials per thread
   const int cap = std::min(maxc, abip::kGridTotalPer * 32);
@@ -294,18 +311,18 @@ int setup_grid_path(abip_handle* h, const HostCSR& A, const std::vector<double>&
     M.perm = ar.take<int32_t>(H.perm.size());
     M.wsl = ar.take<int32_t>((size_t)grid * (abip::kGridThreads / 32) + 1);
   };
-  auto layout = [&](Arena& ar, GridData<T>& g) {
+  auto layout = [&](Arena& ar, G& gg) {
     h->ctl = ar.take<SolveCtl>(1);
-    layout_sell(ar, g.A, SA);
-    layout_sell(ar, g.AT, ST);
-    assign_vectors(g, ar, m, n);
-    g.partials = ar.take<double>((size_t)abip::kNumSlots * grid);
-    g.bar = ar.take<unsigned long long>(1);
+    layout_sell(ar, gg.A, SA);
+    layout_sell(ar, gg.AT, ST);
+    assign_vectors(gg, ar, m, n);
+    gg.partials = ar.take<double>((size_t)abip::kNumSlots * grid);
+    gg.bar = ar.take<unsigned long long>(1);
     h->stage = ar.take<double>((size_t)m + 2 * (size_t)n);
   };
   Arena probe;
-  GridData<T> g{};
-  layout(probe, g);
+  G tmp{};
+  layout(probe, tmp);
   void* mem = nullptr;
   if (cudaMalloc(&mem, probe.off) != cudaSuccess) {
     cudaGetLastError();
@@ -315,7 +332,7 @@ int setup_grid_path(abip_handle* h, const HostCSR& A, const std::vector<double>&
   h->arena_bytes = probe.off;
   Arena ar;
   ar.base = static_cast<char*>(mem);
-  g = GridData<T>{};
+  g = G{};
   layout(ar, g);
   g.m = m; g.n = n;
   g.ctl = h->ctl;
@@ -337,24 +354,19 @@ int setup_grid_path(abip_handle* h, const HostCSR& A, const std::vector<double>&
   };
   upload_sell(g.A, SA);
   upload_sell(g.AT, ST);
-  (void)nnz;
-  {
-    std::vector<T> tb(b.begin(), b.end()), tc(c.begin(), c.end());
-    cudaMemcpy((void*)g.b, tb.data(), m * sizeof(T), cudaMemcpyHostToDevice);
-    cudaMemcpy((void*)g.c, tc.data(), n * sizeof(T), cudaMemcpyHostToDevice);
-  }
+  cudaMemcpy((void*)g.b, b.data(), m * sizeof(double), cudaMemcpyHostToDevice);
+  cudaMemcpy((void*)g.c, c.data(), n * sizeof(double), cudaMemcpyHostToDevice);
   SolveCtl hc{};
   hc.beta = h->prm.beta; hc.gamma = h->prm.gamma; hc.alpha = h->prm.alpha; hc.eps = h->prm.eps;
   hc.cg_tol = h->prm.cg_tol; hc.cg_rel = h->prm.cg_rel; hc.cg_max = h->prm.cg_max_iter; hc.max_admm = h->prm.max_admm_iters;
-  hc.warmstart = h->prm.warmstart; hc.stop_rule = h->prm.stop_rule; hc.check_every = h->prm.check_every;
+  hc.warmstart = h->prm.warmstart; hc.stop_rule = h->prm.stop_rule; hc.check_every = std::max(1, h->prm.check_every);
   hc.cg_warm = h->prm.cg_warm;
+  hc.bar_limit_ns = (unsigned long long)h->prm.barrier_limit_ns;
   hc.mode = abip::MODE_SETUP;
   cudaMemcpy(h->ctl, &hc, sizeof(hc), cudaMemcpyHostToDevice);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return fail(h, ABIP_E_CUDA, std::string("setup copies: ") + cudaGetErrorString(e));
-  if (mixed) h->gd32 = *reinterpret_cast<GridData<float>*>(&g);
-  else h->gd64 = *reinterpret_cast<GridData<double>*>(&g);
-  e = mixed ? abip::launch_grid_solver_f32(h->gd32, grid, 0) : abip::launch_grid_solver_f64(h->gd64, vf64, grid, 0);
+  e = launch_persistent(h, 0);
   if (e != cudaSuccess) return fail(h, ABIP_E_CUDA, std::string("setup launch: ") + cudaGetErrorString(e));
   e = cudaDeviceSynchronize();
   if (e != cudaSuccess) return fail(h, ABIP_E_CUDA, std::string("setup kernel: ") + cudaGetErrorString(e));
@@ -373,28 +385,41 @@ int setup_grid_path(abip_handle* h, const HostCSR& A, const std::vector<double>&
   return ABIP_OK;
 }
 
-template <typename T>
-int solve_grid_path(abip_handle* h, cudaStream_t st) {
-  GridData<T>& g = *reinterpret_cast<GridData<T>*>(std::is_same<T, float>::value ? (void*)&h->gd32 : (void*)&h->gd64);
+// Start vectors of a solve on the sparse path: Algorithm 2's start (or the state set
+// by abip_set_state) and a cold projection (z_y = 0, no previous solutions).
+void init_grid_state(abip_handle* h, cudaStream_t st) {
   const int m = h->m, n = h->n;
-  const bool resume = h->resume;
-  if (resume) {
+  double* y = h->mixed ? h->gdd.y : h->gd64.y;
+  double* x = h->mixed ? h->gdd.x : h->gd64.x;
+  double* s = h->mixed ? h->gdd.s : h->gd64.s;
+  if (h->resume) {
     const std::vector<double>& rs = h->resume_state;
-    std::vector<T> v(rs.begin(), rs.begin() + m);
-    cudaMemcpyAsync(g.y, v.data(), m * sizeof(T), cudaMemcpyHostToDevice, st);
-    std::vector<T> w(rs.begin() + m, rs.begin() + m + n);
-    cudaMemcpyAsync(g.x, w.data(), n * sizeof(T), cudaMemcpyHostToDevice, st);
-    std::vector<T> u(rs.begin() + m + n + 2, rs.begin() + m + 2 * n + 2);
-    cudaMemcpyAsync(g.s, u.data(), n * sizeof(T), cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(y, rs.data(), m * sizeof(double), cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(x, rs.data() + m, n * sizeof(double), cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(s, rs.data() + m + n + 2, n * sizeof(double), cudaMemcpyHostToDevice, st);
     cudaStreamSynchronize(st);
   } else {
-    fill_kernel<T><<<64, 256, 0, st>>>(g.y, m, T(0));
-    fill_kernel<T><<<256, 256, 0, st>>>(g.x, n, T(1));
-    fill_kernel<T><<<256, 256, 0, st>>>(g.s, n, T(1));
+    fill_kernel<double><<<64, 256, 0, st>>>(y, m, 0.0);
+    fill_kernel<double><<<256, 256, 0, st>>>(x, n, 1.0);
+    fill_kernel<double><<<256, 256, 0, st>>>(s, n, 1.0);
   }
-  fill_kernel<T><<<64, 256, 0, st>>>(g.zy, m, T(0));
-  fill_kernel<T><<<64, 256, 0, st>>>(g.zp2, m, T(0));
-  fill_kernel<T><<<64, 256, 0, st>>>(g.zp3, m, T(0));
+  if (h->mixed) {
+    abip::GridDelta& g = h->gdd;
+    fill_kernel<double><<<64, 256, 0, st>>>(g.zy, m, 0.0);
+    fill_kernel<float><<<64, 256, 0, st>>>(g.d1, m, 0.f);
+    fill_kernel<float><<<64, 256, 0, st>>>(g.d2, m, 0.f);
+  } else {
+    GridData<double>& g = h->gd64;
+    fill_kernel<double><<<64, 256, 0, st>>>(g.zy, m, 0.0);
+    fill_kernel<double><<<64, 256, 0, st>>>(g.zp2, m, 0.0);
+    fill_kernel<double><<<64, 256, 0, st>>>(g.zp3, m, 0.0);
+  }
+}
+
+int solve_grid_path(abip_handle* h, cudaStream_t st) {
+  const int m = h->m, n = h->n;
+  const bool resume = h->resume;
+  init_grid_state(h, st);
   SolveCtl hc;
   cudaMemcpyAsync(&hc, h->ctl, sizeof(hc), cudaMemcpyDeviceToHost, st);
   cudaStreamSynchronize(st);
@@ -406,7 +431,7 @@ int solve_grid_path(abip_handle* h, cudaStream_t st) {
     hc.tau = rs[m + n]; hc.theta = rs[m + n + 1]; hc.kappa = rs[m + 2 * n + 2]; hc.mu = rs[m + 2 * n + 3];
     h->resume = false;
   }
-  hc.admm_iters = 0; hc.cg_iters = 0; hc.outer_iters = 0; hc.status = 0; hc.err = 0;
+  hc.admm_iters = 0; hc.cg_iters = 0; hc.outer_iters = 0; hc.status = 0; hc.err = 0; hc.refreshes = 0;
   hc.max_admm = h->prm.max_admm_iters;
   // ABIP_PROFILE=1: phase timers of CTA 0, printed to stderr after the solve
   const char* prof_env = std::getenv("ABIP_PROFILE");
@@ -417,12 +442,11 @@ int solve_grid_path(abip_handle* h, cudaStream_t st) {
     else { cudaGetLastError(); prof = nullptr; }
   }
   hc.prof = prof;
+  unsigned long long* bar = h->mixed ? h->gdd.bar : h->gd64.bar;
   cudaMemcpyAsync(h->ctl, &hc, sizeof(hc), cudaMemcpyHostToDevice, st);
-  cudaMemsetAsync(g.bar, 0, sizeof(unsigned long long), st);
+  cudaMemsetAsync(bar, 0, sizeof(unsigned long long), st);
   cudaEventRecord(h->ev0, st);
-  cudaError_t e = std::is_same<T, float>::value
-                      ? abip::launch_grid_solver_f32(h->gd32, h->grid, st)
-                      : abip::launch_grid_solver_f64(h->gd64, h->val_f64 != 0, h->grid, st);
+  cudaError_t e = launch_persistent(h, st);
   if (e != cudaSuccess) return fail(h, ABIP_E_CUDA, std::string("solve launch: ") + cudaGetErrorString(e));
   cudaEventRecord(h->ev1, st);
   e = cudaStreamSynchronize(st);
@@ -430,7 +454,7 @@ int solve_grid_path(abip_handle* h, cudaStream_t st) {
   float ms = 0.f;
   cudaEventElapsedTime(&ms, h->ev0, h->ev1);
   h->kernel_s = ms * 1e-3;
-  h->launches = resume ? 4 : 7;   // fills and the persistent solve kernel
+  h->launches = (resume ? 0 : 3) + 3 + 1;   // fills and the persistent solve kernel
   if (prof) {
     unsigned long long pv[abip::kProfBuckets];
     cudaMemcpy(pv, prof, sizeof(pv), cudaMemcpyDeviceToHost);
@@ -839,8 +863,12 @@ int abip_setup(const abip_matrix* A, const double* b, const double* c, const abi
     HostCSR hA;
     bool f32 = false;
     rc = read_matrix_csr(h, A, hA, f32);
-    if (rc == ABIP_OK)
-      rc = h->mixed ? setup_grid_path<float>(h, hA, hb, hc, true) : setup_grid_path<double>(h, hA, hb, hc, f32);
+    if (rc == ABIP_OK) {
+      if (h->mixed)   // FP32 values: exact for float input, rounded for double input (FP64 refreshes see them)
+        rc = setup_grid_path(h, h->gdd, hA, hb, hc, false, abip::grid_delta_max_ctas(h->device));
+      else
+        rc = setup_grid_path(h, h->gd64, hA, hb, hc, !f32, abip::grid_solver_max_ctas(!f32, h->device));
+    }
   } else {
     h->path = 1;
     if (dense_solve_smem(m, n, h->mixed) > kDenseSmemLimit)
@@ -886,7 +914,7 @@ int abip_solve(abip_handle* h, double* x, double* y, double* s, abip_info* info,
   int rc;
   abip_info inf{};
   if (h->path == 0) {
-    rc = h->mixed ? solve_grid_path<float>(h, st) : solve_grid_path<double>(h, st);
+    rc = solve_grid_path(h, st);
     if (rc) return rc;
     SolveCtl hc;
     cudaMemcpy(&hc, h->ctl, sizeof(hc), cudaMemcpyDeviceToHost);
@@ -899,15 +927,12 @@ int abip_solve(abip_handle* h, double* x, double* y, double* s, abip_info* info,
     if (hc.status == ABIP_PRIMAL_INFEASIBLE) { sx = 1.0; sy = 1.0 / hc.bty; }
     if (hc.status == ABIP_DUAL_INFEASIBLE) { sx = -1.0 / hc.ctx; sy = 1.0; }
     double* stage = h->stage;
-    if (h->mixed) {
-      output_kernel<float><<<128, 256, 0, st>>>(h->gd32.x, n, sx, stage);
-      output_kernel<float><<<128, 256, 0, st>>>(h->gd32.y, m, sy, stage + n);
-      output_kernel<float><<<128, 256, 0, st>>>(h->gd32.s, n, sy, stage + n + m);
-    } else {
-      output_kernel<double><<<128, 256, 0, st>>>(h->gd64.x, n, sx, stage);
-      output_kernel<double><<<128, 256, 0, st>>>(h->gd64.y, m, sy, stage + n);
-      output_kernel<double><<<128, 256, 0, st>>>(h->gd64.s, n, sy, stage + n + m);
-    }
+    const double* gx = h->mixed ? h->gdd.x : h->gd64.x;
+    const double* gy = h->mixed ? h->gdd.y : h->gd64.y;
+    const double* gs = h->mixed ? h->gdd.s : h->gd64.s;
+    output_kernel<double><<<128, 256, 0, st>>>(gx, n, sx, stage);
+    output_kernel<double><<<128, 256, 0, st>>>(gy, m, sy, stage + n);
+    output_kernel<double><<<128, 256, 0, st>>>(gs, n, sy, stage + n + m);
     h->launches += 3;
     rc = copy_out(h, x, stage, n, st);
     if (!rc) rc = copy_out(h, y, stage + n, m, st);
@@ -1117,7 +1142,7 @@ int abip_backward(abip_handle* h, const double* dl_dx, double* dl_dc, double* dl
   if (!h || !dl_dx) return fail(h, ABIP_E_INVALID_ARG, "NULL argument");
   if (!h->solved) return fail(h, ABIP_E_NOT_SOLVED, "no solve has run on this handle");
   if (h->path != 1)
-    return fail(h, ABIP_E_UNSUPPORTED, "abip_backward needs a dense handle (linsys = dense): the adjoint factors the m x m matrix A D A^T");
+    return fail(h, ABIP_E_UNSUPPORTED, "abip_backward needs a dense handle (linsys = dense): the adjoint factors the dense reduced KKT matrix of order m + n + 2");
   const DenseInst& I = h->hinst;
   if (I.status != ABIP_OPTIMAL && I.status != ABIP_MAX_ITER)
     return fail(h, ABIP_E_INVALID_ARG, std::string("no gradient at a ") + abip_status_str(I.status) + " result (needs tau > 0)");
@@ -1206,19 +1231,9 @@ int abip_get_state(const abip_handle* h, double* buf) {
     SolveCtl hc;
     cudaMemcpy(&hc, h->ctl, sizeof(hc), cudaMemcpyDeviceToHost);
     tau = hc.tau; theta = hc.theta; kappa = hc.kappa; mu = hc.mu;
-    if (h->mixed) {
-      std::vector<float> f(std::max(m, n));
-      cudaMemcpy(f.data(), h->gd32.y, m * 4, cudaMemcpyDeviceToHost);
-      for (int i = 0; i < m; ++i) out[i] = f[i];
-      cudaMemcpy(f.data(), h->gd32.x, n * 4, cudaMemcpyDeviceToHost);
-      for (int j = 0; j < n; ++j) out[m + j] = f[j];
-      cudaMemcpy(f.data(), h->gd32.s, n * 4, cudaMemcpyDeviceToHost);
-      for (int j = 0; j < n; ++j) out[m + n + 2 + j] = f[j];
-    } else {
-      cudaMemcpy(out.data(), h->gd64.y, m * 8, cudaMemcpyDeviceToHost);
-      cudaMemcpy(out.data() + m, h->gd64.x, n * 8, cudaMemcpyDeviceToHost);
-      cudaMemcpy(out.data() + m + n + 2, h->gd64.s, n * 8, cudaMemcpyDeviceToHost);
-    }
+    cudaMemcpy(out.data(), h->mixed ? h->gdd.y : h->gd64.y, m * 8, cudaMemcpyDeviceToHost);
+    cudaMemcpy(out.data() + m, h->mixed ? h->gdd.x : h->gd64.x, n * 8, cudaMemcpyDeviceToHost);
+    cudaMemcpy(out.data() + m + n + 2, h->mixed ? h->gdd.s : h->gd64.s, n * 8, cudaMemcpyDeviceToHost);
   } else {
     const DenseInst& I = h->hinst;
     tau = I.tau; theta = I.theta; kappa = I.kappa; mu = I.mu;

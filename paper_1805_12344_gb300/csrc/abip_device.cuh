@@ -21,8 +21,8 @@ enum DevErr : int {
 // a solve that reaches it stops with ABIP_MAX_ITER instead of looping.
 constexpr int kMaxOuter = 4000;
 
-// Wall-clock limit of one barrier wait (nanoseconds).  A healthy barrier on a
-// co-resident cooperative grid completes in microseconds.
+// Default wall-clock limit of one barrier wait (nanoseconds).  A healthy barrier on
+// a co-resident cooperative grid completes in microseconds.
 constexpr unsigned long long kBarrierLimitNs = 4000000000ull;
 
 __device__ __forceinline__ unsigned long long globaltimer_ns() {
@@ -46,15 +46,16 @@ __device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long
 struct GridBarrier {
   unsigned long long* count;   // total arrivals since the launch (host zeroes it)
   int* err;                    // first device error (0 = none)
+  unsigned long long limit_ns; // wall-clock limit of one wait; 0 = kBarrierLimitNs
 };
 
 // Grid-wide barrier for a cooperative launch (all CTAs co-resident).  The
 // arrival counter only grows: barrier number k of the launch completes when it
 // reaches k * gridDim.x, so no reset is needed.  Thread 0 of each CTA arrives
-// after a release fence and waits with a wall-clock limit, leaving early if any
-// CTA has flagged an error.  `target` is this CTA's running count (all CTAs pass
-// the same barriers).  Returns false (in every thread) on timeout or error; the
-// caller must then leave the kernel.
+// after a release fence and waits with a wall-clock limit (read on the first spin
+// and every 64th after it), leaving early if any CTA has flagged an error.
+// `target` is this CTA's running count (all CTAs pass the same barriers).  Returns
+// false (in every thread) on timeout or error; the caller must then leave the kernel.
 __device__ __forceinline__ bool grid_sync(const GridBarrier& gb, unsigned long long& target) {
   __shared__ int s_ok;
   __syncthreads();
@@ -65,11 +66,12 @@ __device__ __forceinline__ bool grid_sync(const GridBarrier& gb, unsigned long l
     atomicAdd(gb.count, 1ull);
     if (ld_acquire_u64(gb.count) < target) {
       const unsigned long long t0 = globaltimer_ns();
+      const unsigned long long limit = gb.limit_ns ? gb.limit_ns : kBarrierLimitNs;
       unsigned spins = 0;
       while (ld_acquire_u64(gb.count) < target) {
         __nanosleep(32);
         if (ld_relaxed_i32(gb.err) != 0) { ok = 0; break; }
-        if ((++spins & 63u) == 0 && globaltimer_ns() - t0 > kBarrierLimitNs) {
+        if ((spins++ & 63u) == 0 && globaltimer_ns() - t0 > limit) {
           atomicCAS(gb.err, 0, (int)DEV_ERR_BARRIER_TIMEOUT);
           ok = 0;
           break;

@@ -39,6 +39,10 @@ struct SolveCtl {
   int32_t err;                    // DevErr
   int32_t pad1;
   unsigned long long* prof;       // optional phase timers (kProfBuckets ns counters), null = off
+  unsigned long long bar_limit_ns;// wall-clock limit of one grid-barrier wait (0: kBarrierLimitNs)
+  int64_t refreshes;              // mixed path: exact FP64 recomputations of the maintained products
+  int32_t setup_rounds;           // mixed path: refinement rounds of the setup solves
+  int32_t pad4;
 };
 
 // phase timer buckets of the solve kernel (CTA 0's view, nanoseconds)
@@ -90,10 +94,37 @@ struct GridData {
   SolveCtl* ctl;
 };
 
+// Device pointers of the sparse mixed-precision path (grid_delta.cu): the iterate, the
+// products the update needs and the embedding data in FP64; the matrix values, the
+// changes of the iterate and the PCG work vectors of the correction solve in FP32.
+struct GridDelta {
+  int m, n;
+  SellMat A;                                   // rows of A (float values)
+  SellMat AT;                                  // rows of A^T (float values)
+  const double* b; const double* c;
+  double* bbar; double* cbar;                  // embedding constants
+  double* g1y; double* g1x; double* g2y; double* g2x;   // M^{-1} h1, M^{-1} h2
+  double* y; double* x; double* s;             // iterate (r = 0, xi = -n-1 implicit)
+  double* Ax; double* As; double* ATy;         // maintained products for the residuals
+  double* zy; double* ATz;                     // z_y = G^{-1} q and A^T z_y
+  double* wv;                                  // n: A^T z_y + A^T delta_0 (start residual of a solve)
+  float* dinv;                                 // Jacobi diagonal 1 / (1 + sum_j A_ij^2)
+  float* dz;                                   // correction of z_y (PCG iterate)
+  float* d1; float* d2;                        // the last two corrections (extrapolated start)
+  float* r; float* p; float* Gp;               // PCG work vectors
+  float2* ut; float2* zd; float2* zd2;         // (A^T zr, A^T p); (zr, D^{-1} Gp), double-buffered
+  float2* dxs;                                 // (dx, ds) per column: change of the iterate
+  float* dy;                                   // change of y
+  double* partials;                            // kNumSlots * gridDim doubles
+  unsigned long long* bar;                     // barrier arrival counter
+  SolveCtl* ctl;
+};
+
 // Launch the persistent grid kernel (cooperative).  val_f64: whether A's values are double.
 cudaError_t launch_grid_solver_f64(const GridData<double>& d, bool val_f64, int grid, cudaStream_t st);
-cudaError_t launch_grid_solver_f32(const GridData<float>& d, int grid, cudaStream_t st);
-int grid_solver_max_ctas(bool mixed, bool val_f64, int device);
+int grid_solver_max_ctas(bool val_f64, int device);
+cudaError_t launch_grid_delta(const GridDelta& d, int grid, cudaStream_t st);
+int grid_delta_max_ctas(int device);
 
 // ---------------------------------------------------------------------------
 // dense CTA-per-instance path
@@ -245,7 +276,7 @@ struct abip_handle {
   size_t arena_bytes = 0;
   abip::SolveCtl* ctl = nullptr;
   abip::GridData<double> gd64{};
-  abip::GridData<float> gd32{};
+  abip::GridDelta gdd{};
   double* stage = nullptr;            // m + 2n doubles for scaled outputs
   int grid = 0;
   // dense path

@@ -1432,17 +1432,18 @@ extern "C" ABIP_API int abip_solve_dense_noalloc(int32_t m, int32_t n, const dou
   std::string why;
   if (!abip::check_params_internal(prm, why)) return abip::noalloc_fail(ABIP_E_INVALID_ARG, why);
   if (prm.precision != ABIP_PREC_F64) return abip::noalloc_fail(ABIP_E_UNSUPPORTED, "abip_solve_dense_noalloc is FP64 only");
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return abip::noalloc_fail(ABIP_E_CUDA, "cudaGetDevice failed");
   const void* ptrs[6] = {A, b, c, x, y, s};
   for (const void* q : ptrs) {
     cudaPointerAttributes at;
     if (cudaPointerGetAttributes(&at, q) != cudaSuccess ||
-        (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged)) {
+        (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged) ||
+        (at.type == cudaMemoryTypeDevice && at.device != dev)) {
       cudaGetLastError();
       return abip::noalloc_fail(ABIP_E_INVALID_ARG, "every array must be device memory of the current device");
     }
   }
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return abip::noalloc_fail(ABIP_E_CUDA, "cudaGetDevice failed");
   // set-up, once per device, with that device current: the device address of the array
   unsigned char* base = nullptr;
   {

@@ -1,0 +1,648 @@
+// Persistent cooperative kernel running ABIP (Algorithm 2 with the over-relaxation
+// of Sec. 4.2) on one sparse LP in mixed precision: the iterate and every product
+// the update and the Sec. 4.1 tests need are kept in FP64, and each ADMM update
+// changes them by FP32 products of the change of the iterate.
+//
+//   * Residual products: after an update, Ax += A dx, As += A ds, A^T y += A^T dy
+//     (FP32 products of the FP32-rounded changes, added to FP64), recomputed exactly
+//     (FP64 products of the FP64 state) every kDeltaRefresh updates, after each mu
+//     decrease and before any termination decision.
+//   * Projection (Sec. 4.4): G z_y = q with G = I + A A^T and q = y - Ax - As.  z_y and
+//     A^T z_y are kept in FP64; each update solves G delta = e for the correction by
+//     Jacobi-PCG in FP32, where the right-hand side e = q - z_y - A (A^T z_y) is formed
+//     in FP64 (one step of iterative refinement per update), then z_y += delta and
+//     A^T z_y += A^T delta.  The start of the correction solve extrapolates the last two
+//     corrections, the same start point as extrapolating the last three solutions
+//     (reading A10).
+//   * The prox and dual update of x, s, tau, kappa (Eqs. Simple-Update:Barrier-X and
+//     Simple-Update:Dual, two-root form, reading A9) run in FP64 on the FP64 state.
+//
+// FP32 rounding thus scales with the size of each change, not with the iterate, so the
+// Sec. 4.1 tolerances below FP32's unit roundoff times ||A|| ||y|| are reachable.  The
+// setup computes M^{-1} H in FP64 by refining FP32 PCG solves with FP64 residuals.
+#include <cmath>
+
+#include "abip_device.cuh"
+#include "abip_internal.h"
+#include "sell.cuh"
+
+namespace abip {
+
+namespace {
+
+using namespace sell;
+
+// reduction slots (a slot is never rewritten before a barrier separates its previous read)
+enum Slot : int {
+  S_PCG0 = 0,    // 3: r.zr, r.r, q.q
+  S_PGP = 3,     // 1: p.Gp
+  S_RZ = 4,      // 2: r.zr, r.r
+  S_HZ = 6,      // 2: h1.z, h2.z
+  S_RES = 8,     // 9: residual sums
+  S_SETUP = 17,  // 3: sum c, ||b||^2, ||c||^2
+  S_K = 20,      // 4: H^T M^{-1} H
+};
+
+constexpr int kDeltaRefresh = 100;   // updates between exact FP64 recomputations
+constexpr int kSetupRounds = 12;     // refinement rounds of one setup solve, at most
+constexpr double kSetupRoundRed = 1e-5;   // residual reduction asked of one FP32 round
+
+struct DeltaSolver {
+  const GridDelta& D;
+  SolveCtl* C;
+  double* red;   // shared scratch
+  Thr th;
+  unsigned long long bar_target = 0;
+  unsigned long long* prof;
+  unsigned long long t_last = 0;
+  __device__ DeltaSolver(const GridDelta& d, double* r) : D(d), C(d.ctl), red(r) {
+    prof = (blockIdx.x == 0 && threadIdx.x == 0) ? d.ctl->prof : nullptr;
+    if (prof) t_last = globaltimer_ns();
+  }
+
+  __device__ __forceinline__ void mark(int b) {
+    if (prof) {
+      const unsigned long long t = globaltimer_ns();
+      prof[b] += t - t_last;
+      t_last = t;
+    }
+  }
+  __device__ bool sync(int phase) {
+    mark(phase);
+    const bool ok = grid_sync(GridBarrier{D.bar, &C->err, C->bar_limit_ns}, bar_target);
+    mark(P_BARRIER);
+    return ok;
+  }
+  __device__ void flag(int code) {
+    if (threadIdx.x == 0) atomicCAS(&C->err, 0, code);
+  }
+
+  // Grid totals of K slots plus E scalars derived from them by f(totals, extra) on
+  // thread 0, broadcast to the CTA (every CTA computes the same values).
+  template <int K, int E, typename F>
+  __device__ void totals_x(double (&out)[K], double (&ext)[E], int slot, F f) {
+    const int nb = gridDim.x;
+    if (threadIdx.x < 32) {
+      double v[K];
+#pragma unroll
+      for (int k = 0; k < K; ++k) {
+        const double* pp = D.partials + (size_t)(slot + k) * nb;
+        double acc = 0.0;
+#pragma unroll
+        for (int q = 0; q < kGridTotalPer; ++q) {
+          const int i = threadIdx.x + q * 32;
+          acc += i < nb ? __ldcg(pp + i) : 0.0;
+        }
+        v[k] = warp_sum(acc);
+      }
+      if (threadIdx.x == 0) {
+        double e[E];
+        f(v, e);
+#pragma unroll
+        for (int k = 0; k < K; ++k) red[k] = v[k];
+#pragma unroll
+        for (int i = 0; i < E; ++i) red[K + i] = e[i];
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < K; ++k) out[k] = red[k];
+#pragma unroll
+    for (int i = 0; i < E; ++i) ext[i] = red[K + i];
+    __syncthreads();
+    mark(P_TOTALS);
+  }
+
+  // start of the correction solve (reading A10 restated on corrections): 0 none,
+  // 1 the last correction d1 (linear extrapolation of the solutions), 2 2 d1 - d2
+  // (quadratic extrapolation)
+  __device__ __forceinline__ float start(int i, int extrap) const {
+    if (extrap == 2) return 2.f * D.d1[i] - D.d2[i];
+    if (extrap == 1) return D.d1[i];
+    return 0.f;
+  }
+
+  // Jacobi-PCG (Sec. 4.4) on G delta = e, e = q - z_y - A ATz in FP64, from delta_0 =
+  // start(extrap); leaves delta in D.dz.  Stop when ||r|| <= max(tol max(1, ||q||),
+  // rel0 ||r_0||): the first term is the FP64 path's rule for the full system, whose
+  // residual r equals (reading A10); rel0 > 0 ends a setup refinement round early.
+  // The iteration is the FP64 path's two-phase PCG in FP32:
+  //   phase A (rows of A):   p = zr + beta p;  Gp = p + A (u + beta t);  p.Gp
+  //   phase B (rows of A^T): t <- u + beta t (= A^T p);  u <- A^T zr_new, gathering
+  //                          zr_new = zr - alpha D^{-1} Gp;  rows of A: dz += alpha p,
+  //                          r -= alpha Gp, zr_new = D^{-1} r;  r.zr, r.r
+  // Returns iterations, -1 on barrier failure, -2 past the cap.
+  template <typename QF>
+  __device__ int pcg(QF qf, double tol, double rel0, int maxit, int extrap) {
+    float* dz = D.dz; float* r = D.r; float* p = D.p; float* Gp = D.Gp;
+    float2* ut = D.ut;
+    float2* zd_cur = D.zd;
+    float2* zd_nxt = D.zd2;
+    if (extrap > 0) {
+      // wv = A^T z_y + A^T delta_0
+      auto g = [&](int i) -> float { return start(i, extrap); };
+      auto e = [&](int j, float v, float) { D.wv[j] = D.ATz[j] + (double)v; };
+      sell_rows_g<8, 1, float, float>(D.AT, g, g, e);
+      if (!sync(P_PCG_INIT)) return -1;
+    }
+    const double* wsrc = extrap > 0 ? D.wv : D.ATz;
+    double acc[3] = {0.0, 0.0, 0.0};
+    {
+      // r_0 = q - z_y - delta_0 - A wv in FP64
+      auto g = [&](int j) -> double { return wsrc[j]; };
+      auto e = [&](int i, double v, double) {
+        const double qi = qf(i);
+        const float d0 = start(i, extrap);
+        const double ri = qi - D.zy[i] - (double)d0 - v;
+        const float rf = (float)ri;
+        const float zri = D.dinv[i] * rf;
+        dz[i] = d0;
+        r[i] = rf;
+        zd_cur[i].x = zri;
+        acc[0] += (double)(rf * zri);
+        acc[1] += ri * ri;
+        acc[2] += qi * qi;
+      };
+      sell_rows_g<8, 1, double, float>(D.A, g, g, e);
+    }
+    grid_partial<3>(acc, D.partials, S_PCG0, red);
+    if (!sync(P_PCG_INIT)) return -1;
+    double tot[3], ex0[2];
+    totals_x<3, 2>(tot, ex0, S_PCG0, [&](const double* v, double* e) {
+      const double bnd = fmax(tol * fmax(1.0, sqrt(v[2])), rel0 * sqrt(v[1]));
+      e[0] = bnd * bnd;
+      e[1] = v[1] > e[0] ? 1.0 : 0.0;
+    });
+    double rz = tot[0];
+    const double bound2 = ex0[0];
+    if (ex0[1] == 0.0) return 0;
+    {
+      auto g = [&](int i) -> float { return zd_cur[i].x; };
+      auto e = [&](int j, float v, float) { ut[j].x = v; };
+      sell_rows_g<8, 1, float, float>(D.AT, g, g, e);
+    }
+    if (!sync(P_PCG_INIT)) return -1;
+    float be = 0.f;
+    int k = 0;
+    for (;;) {
+      if (k >= maxit) return -2;
+      const bool first = k == 0;
+      float a1 = 0.f;
+      {
+        auto g = [&](int j) -> float {
+          const float2 w = ut[j];
+          return first ? w.x : w.x + be * w.y;
+        };
+        struct RowOps { float zr, p, dinv; };
+        auto pre = [&](int i) -> RowOps {
+          RowOps o{0.f, 0.f, 0.f};
+          if (i >= 0) { o.zr = zd_cur[i].x; o.p = p[i]; o.dinv = D.dinv[i]; }
+          return o;
+        };
+        auto e = [&](int i, float v, float, RowOps o) {
+          const float pi = first ? o.zr : o.zr + be * o.p;
+          const float gp = pi + v;
+          p[i] = pi;
+          Gp[i] = gp;
+          zd_cur[i].y = o.dinv * gp;
+          a1 += pi * gp;
+        };
+        sell_rows_gp<8, 1, float, float>(D.A, g, g, pre, e);
+      }
+      {
+        float a1v[1] = {a1};
+        grid_partial_t<1, float>(a1v, D.partials, S_PGP, red);
+      }
+      if (!sync(P_CG_A)) return -1;
+      double pgp[1], exa[1];
+      totals_x<1, 1>(pgp, exa, S_PGP, [&](const double* v, double* e) { e[0] = rz / v[0]; });
+      const float al = (float)exa[0];
+      {
+        auto g = [&](int i) -> float {
+          const float2 w = zd_cur[i];
+          return w.x - al * w.y;
+        };
+        auto pre = [&](int j) -> float2 {
+          float2 w = make_float2(0.f, 0.f);
+          if (j >= 0) w = ut[j];
+          return w;
+        };
+        auto e = [&](int j, float v, float, float2 w) {
+          ut[j] = make_float2(v, first ? w.x : w.x + be * w.y);
+        };
+        sell_rows_gp<8, 1, float, float>(D.AT, g, g, pre, e);
+      }
+      mark(P_CG_AT);
+      float a2[2] = {0.f, 0.f};
+      for (int i = th.gtid; i < D.m; i += th.nthr) {
+        dz[i] += al * p[i];
+        const float ri = r[i] - al * Gp[i];
+        const float zri = D.dinv[i] * ri;
+        r[i] = ri;
+        zd_nxt[i].x = zri;
+        a2[0] += ri * zri;
+        a2[1] += ri * ri;
+      }
+      grid_partial_t<2, float>(a2, D.partials, S_RZ, red);
+      if (!sync(P_CG_UPD)) return -1;
+      double t2[2], exb[2];
+      totals_x<2, 2>(t2, exb, S_RZ, [&](const double* v, double* e) {
+        e[0] = v[0] / rz;
+        e[1] = v[1] > bound2 ? 1.0 : 0.0;
+      });
+      be = (float)exb[0];
+      rz = t2[0];
+      float2* sw = zd_cur; zd_cur = zd_nxt; zd_nxt = sw;
+      ++k;
+      if (exb[1] == 0.0) break;
+    }
+    return k;
+  }
+
+  // The nine sums of the Sec. 4.1 tests and Eq. inner-stop from the products of the
+  // current iterate, in FP64:
+  //   0 ||Qu-v||^2 (vector blocks), 1 ||Ax/tau - b||^2, 2 ||(A^T y + s)/tau - c||^2,
+  //   3 ||Ax||^2, 4 ||A^T y + s||^2, 5 b^T y, 6 bbar^T y, 7 c^T x, 8 cbar^T x.
+  __device__ __forceinline__ void row_sums(int i, double ax, double tau, double itau, double theta,
+                                           double (&acc)[9]) const {
+    const double bi = D.b[i], bb = D.bbar[i], yi = D.y[i];
+    const double ry = ax - bi * tau + bb * theta;
+    const double pr = ax * itau - bi;
+    acc[0] += ry * ry;
+    acc[1] += pr * pr;
+    acc[3] += ax * ax;
+    acc[5] += bi * yi;
+    acc[6] += bb * yi;
+  }
+  __device__ __forceinline__ void col_sums(int j, double aty, double tau, double itau, double theta,
+                                           double (&acc)[9]) const {
+    const double sj = D.s[j], cj = D.c[j], cb = D.cbar[j], xj = D.x[j];
+    const double rx = -aty + cj * tau - cb * theta - sj;
+    const double dr = (aty + sj) * itau - cj;
+    acc[0] += rx * rx;
+    acc[2] += dr * dr;
+    acc[4] += (aty + sj) * (aty + sj);
+    acc[7] += cj * xj;
+    acc[8] += cb * xj;
+  }
+
+  // Exact products of the current iterate (FP64 gathers and sums): Ax, As, A^T y,
+  // A^T z_y, and the nine sums into slot S_RES.  No barrier.
+  __device__ void exact_products(double tau, double theta) {
+    double acc[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    const double itau = 1.0 / tau;
+    {
+      auto g0 = [&](int j) -> double { return D.x[j]; };
+      auto g1 = [&](int j) -> double { return D.s[j]; };
+      auto e = [&](int i, double ax, double as) {
+        D.Ax[i] = ax;
+        D.As[i] = as;
+        row_sums(i, ax, tau, itau, theta, acc);
+      };
+      sell_rows_g<8, 2, double, float>(D.A, g0, g1, e);
+    }
+    {
+      auto g0 = [&](int i) -> double { return D.y[i]; };
+      auto g1 = [&](int i) -> double { return D.zy[i]; };
+      auto e = [&](int j, double aty, double atz) {
+        D.ATy[j] = aty;
+        D.ATz[j] = atz;
+        col_sums(j, aty, tau, itau, theta, acc);
+      };
+      sell_rows_g<8, 2, double, float>(D.AT, g0, g1, e);
+    }
+    grid_partial<9>(acc, D.partials, S_RES, red);
+  }
+
+  // Maintained products after an update: Ax += A dx, As += A ds, A^T y += A^T dy (FP32
+  // products of the changes), and the nine sums into slot S_RES.  No barrier.
+  __device__ void maintained_products(double tau, double theta) {
+    double acc[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    const double itau = 1.0 / tau;
+    {
+      auto gp = [&](int j) -> float2 { return D.dxs[j]; };
+      auto e = [&](int i, float adx, float ads) {
+        const double ax = D.Ax[i] + (double)adx;
+        D.Ax[i] = ax;
+        D.As[i] = D.As[i] + (double)ads;
+        row_sums(i, ax, tau, itau, theta, acc);
+      };
+      sell_rows_pair<8, float, float>(D.A, gp, e);
+    }
+    {
+      auto g = [&](int i) -> float { return D.dy[i]; };
+      auto e = [&](int j, float v, float) {
+        const double aty = D.ATy[j] + (double)v;
+        D.ATy[j] = aty;
+        col_sums(j, aty, tau, itau, theta, acc);
+      };
+      sell_rows_g<8, 1, float, float>(D.AT, g, g, e);
+    }
+    grid_partial<9>(acc, D.partials, S_RES, red);
+  }
+
+  // Thread 0 only: the nine sums -> e = (inner2 = ||Qu - v||^2, pres, dres, dgap, c^T x,
+  // b^T y, finite flag, Sec. 4.1 test result with the given margin or 0).
+  __device__ __noinline__ void derive_sums(const double* a, double* e, bool with_tests, double margin,
+                                           double tau, double kappa, double theta) {
+    const double zbar = C->zbar, xi = C->xi, nb = C->nb, nc = C->nc, eps = C->eps;
+    const double rt = a[5] - a[7] + zbar * theta - kappa;
+    const double rth = -a[6] + a[8] - zbar * tau - xi;
+    e[0] = a[0] + rt * rt + rth * rth;
+    e[1] = sqrt(a[1]) / (1.0 + nb);
+    e[2] = sqrt(a[2]) / (1.0 + nc);
+    e[3] = fabs(a[7] / tau - a[5] / tau) / (1.0 + fabs(a[7] / tau) + fabs(a[5] / tau));
+    e[4] = a[7];
+    e[5] = a[5];
+    e[6] = (isfinite(e[0]) && isfinite(e[1]) && isfinite(e[2])) ? 1.0 : 0.0;
+    int st = 0;
+    if (with_tests) {
+      if (e[1] <= margin * eps && e[2] <= margin * eps && e[3] <= margin * eps) st = ABIP_OPTIMAL;
+      else if (a[5] > 0 && sqrt(a[4]) <= margin * eps * a[5] / nb) st = ABIP_PRIMAL_INFEASIBLE;
+      else if (a[7] < 0 && sqrt(a[3]) <= margin * eps * (-a[7]) / nc) st = ABIP_DUAL_INFEASIBLE;
+    }
+    e[7] = (double)st;
+  }
+
+  // Thread 0 only: t = K^{-1} (w_{tau,theta} + H^T z) from v = H^T z, and the relaxed
+  // barrier and dual steps of (tau, kappa) and theta (Sec. 4.2):
+  // e = (t1, t2, tau, kappa, theta, mu/beta).
+  __device__ __noinline__ void scalar_step(const double* v, double* e, double tau, double kappa,
+                                           double theta, double mu) {
+    const double alpha = C->alpha, beta = C->beta, xi = C->xi;
+    const double v1 = tau + kappa + v[0], v2 = theta + xi + v[1];
+    const double t1 = C->Kinv[0] * v1 + C->Kinv[1] * v2, t2 = C->Kinv[2] * v1 + C->Kinv[3] * v2;
+    const double th_ = alpha * t1 + (1.0 - alpha) * tau;
+    double tn, kn;
+    barrier_step<double>(th_ - kappa, mu / beta, tn, kn);
+    e[0] = t1; e[1] = t2; e[2] = tn; e[3] = kn;
+    e[4] = alpha * t2 + (1.0 - alpha) * theta;
+    e[5] = mu / beta;
+  }
+
+  // One FP64 solve with M (Sec. 4.4) at setup: [gy; gx] = M^{-1} [hy; hx], i.e.
+  // G gy = hy - A hx and gx = hx + A^T gy, by FP32 PCG rounds on the FP64 residual until a
+  // round starts below the tolerance.  Uses zy, ATz, Ax as scratch.  Returns false on
+  // failure (flag set).
+  template <typename HY, typename HX>
+  __device__ bool setup_solve(HY hy, HX hx, double* gy, double* gx) {
+    const Thr t = th;
+    for (int j = t.gtid; j < D.n; j += t.nthr) { gx[j] = hx(j); D.ATz[j] = 0.0; }
+    for (int i = t.gtid; i < D.m; i += t.nthr) D.zy[i] = 0.0;
+    if (!sync(P_SETUP)) return false;
+    {
+      auto g = [&](int j) -> double { return gx[j]; };
+      auto e = [&](int i, double v, double) { D.Ax[i] = v; };
+      sell_rows_g<8, 1, double, float>(D.A, g, g, e);
+    }
+    if (!sync(P_SETUP)) return false;
+    auto qf = [&](int i) -> double { return hy(i) - D.Ax[i]; };
+    int rounds = 0;
+    for (;; ++rounds) {
+      if (rounds >= kSetupRounds) { flag(DEV_ERR_PCG); sync(P_SETUP); return false; }
+      const int it = pcg(qf, C->cg_tol, kSetupRoundRed, C->cg_max, 0);
+      if (it == -1) return false;
+      if (it == -2) { flag(DEV_ERR_PCG); sync(P_SETUP); return false; }
+      if (it == 0) break;   // converged from an FP64 residual
+      for (int i = t.gtid; i < D.m; i += t.nthr) D.zy[i] += (double)D.dz[i];
+      if (!sync(P_SETUP)) return false;
+      {
+        auto g = [&](int i) -> double { return D.zy[i]; };
+        auto e = [&](int j, double v, double) { D.ATz[j] = v; };
+        sell_rows_g<8, 1, double, float>(D.AT, g, g, e);
+      }
+      if (!sync(P_SETUP)) return false;
+    }
+    for (int i = t.gtid; i < D.m; i += t.nthr) gy[i] = D.zy[i];
+    for (int j = t.gtid; j < D.n; j += t.nthr) gx[j] += D.ATz[j];
+    if (threadIdx.x == 0 && blockIdx.x == 0) C->setup_rounds += rounds + 1;
+    return sync(P_SETUP);
+  }
+
+  // MODE_SETUP: bbar = b - A e, cbar = c - e, zbar = c^T e + 1 (Eq. bar-b-c-z-re), the
+  // Jacobi diagonal 1 + sum_j A_ij^2, norms; M^{-1} h1 and M^{-1} h2 with h1 = [-b; c],
+  // h2 = [bbar; -cbar] (Sec. 4.4, 4-block form) and H^T M^{-1} H, all in FP64.
+  __device__ void setup() {
+    const Thr t = th;
+    double acc[3] = {0.0, 0.0, 0.0};
+    {
+      auto e = [&](int i, double rs, double sq) {
+        D.bbar[i] = D.b[i] - rs;
+        D.dinv[i] = (float)(1.0 / (1.0 + sq));
+      };
+      sell_rowstats<double, float>(D.A, e);
+    }
+    for (int i = t.gtid; i < D.m; i += t.nthr) acc[1] += D.b[i] * D.b[i];
+    for (int j = t.gtid; j < D.n; j += t.nthr) {
+      D.cbar[j] = D.c[j] - 1.0;
+      acc[0] += D.c[j];
+      acc[2] += D.c[j] * D.c[j];
+    }
+    grid_partial<3>(acc, D.partials, S_SETUP, red);
+    if (!sync(P_SETUP)) return;
+    double tot[3], none[1];
+    totals_x<3, 1>(tot, none, S_SETUP, [](const double*, double* e) { e[0] = 0.0; });
+    if (!setup_solve([&](int i) { return -D.b[i]; }, [&](int j) { return D.c[j]; }, D.g1y, D.g1x)) return;
+    if (!setup_solve([&](int i) { return D.bbar[i]; }, [&](int j) { return -D.cbar[j]; }, D.g2y, D.g2x)) return;
+    double k4[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int i = t.gtid; i < D.m; i += t.nthr) {
+      const double bi = D.b[i], bbi = D.bbar[i], g1 = D.g1y[i], g2 = D.g2y[i];
+      k4[0] += -bi * g1; k4[1] += -bi * g2; k4[2] += bbi * g1; k4[3] += bbi * g2;
+    }
+    for (int j = t.gtid; j < D.n; j += t.nthr) {
+      const double cj = D.c[j], cbj = D.cbar[j], g1 = D.g1x[j], g2 = D.g2x[j];
+      k4[0] += cj * g1; k4[1] += cj * g2; k4[2] += -cbj * g1; k4[3] += -cbj * g2;
+    }
+    grid_partial<4>(k4, D.partials, S_K, red);
+    if (!sync(P_SETUP)) return;
+    double kt[4];
+    totals_x<4, 1>(kt, none, S_K, [](const double*, double* e) { e[0] = 0.0; });
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      C->sum_c = tot[0]; C->sum_b2 = tot[1]; C->sum_c2 = tot[2];
+      C->K[0] = 1.0 + kt[0];
+      C->K[1] = tot[0] + 1.0 + kt[1];      // zbar = c^T e + 1
+      C->K[2] = -(tot[0] + 1.0) + kt[2];
+      C->K[3] = 1.0 + kt[3];
+    }
+  }
+
+  // MODE_SOLVE: Algorithm 2 from the state in D / C.
+  __device__ void solve() {
+    const Thr t = th;
+    const double alpha = C->alpha, beta = C->beta, gamma = C->gamma, eps = C->eps;
+    const double cg_rel = C->cg_rel;
+    const double sqrt_gamma = sqrt(gamma);
+    double tau = C->tau, kappa = C->kappa, theta = C->theta, mu = C->mu;
+    int64_t total = C->admm_iters;
+    int64_t cgtot = C->cg_iters;
+    int64_t refreshes = 0;
+    int outer = C->outer_iters;
+    int status = 0;
+    int since_refresh = 0;
+    int64_t next_confirm = 0;
+    double tot[9];
+    double inner2 = 0, pres = 0, dres = 0, dgap = 0, ctx = 0, bty = 0;
+
+    // sums in slot S_RES (after a barrier) -> the scalars; tests with `margin` if asked
+    auto absorb = [&](bool with_tests, double margin) -> int {
+      double e[8];
+      totals_x<9, 8>(tot, e, S_RES, [&](const double* a, double* ee) {
+        derive_sums(a, ee, with_tests, margin, tau, kappa, theta);
+      });
+      inner2 = e[0]; pres = e[1]; dres = e[2]; dgap = e[3]; ctx = e[4]; bty = e[5];
+      if (e[6] == 0.0) { flag(DEV_ERR_NONFINITE); return -1; }
+      return (int)e[7];
+    };
+    auto exact = [&](int phase) -> bool {
+      exact_products(tau, theta);
+      ++refreshes;
+      since_refresh = 0;
+      return sync(phase);
+    };
+    // After an update: maintained products (or the scheduled exact recomputation); the
+    // Sec. 4.1 tests screened on them with a factor-4 margin and, when the screen passes,
+    // decided on exact products (reading A5 cadence; check_every spaces the decisions).
+    auto evaluate_update = [&]() -> bool {
+      const bool want = C->stop_rule == 0;
+      bool exact_now = ++since_refresh >= kDeltaRefresh;
+      if (exact_now) { if (!exact(P_RES)) return false; }
+      else {
+        maintained_products(tau, theta);
+        if (!sync(P_RES)) return false;
+      }
+      int st = absorb(want, exact_now ? 1.0 : 4.0);
+      if (st < 0) return false;
+      if (st != 0 && !exact_now) {
+        if (total < next_confirm) return true;
+        if (!exact(P_RES)) return false;
+        st = absorb(true, 1.0);
+        if (st < 0) return false;
+        next_confirm = total + C->check_every;
+      }
+      status = want ? st : 0;
+      return true;
+    };
+
+    if (!exact(P_RES)) return;
+    if (absorb(false, 1.0) < 0) return;
+    for (;;) {
+      // inner stop, Eq. inner-stop: ||Q u - v||^2 <= mu
+      if (inner2 <= mu) {
+        mu *= gamma;
+        ++outer;
+        if (C->stop_rule == 1 && mu < eps) { status = ABIP_OPTIMAL; break; }
+        if (outer >= kMaxOuter) { status = ABIP_MAX_ITER; break; }   // mu has underflowed
+        // warm start (Sec. 5 heuristic, or Eq. update-next-iterate), then exact products
+        if (C->warmstart == 1) {
+          for (int j = t.gtid; j < D.n; j += t.nthr) { D.x[j] *= sqrt_gamma; D.s[j] *= sqrt_gamma; }
+          tau *= sqrt_gamma; kappa *= sqrt_gamma;
+        } else {
+          for (int j = t.gtid; j < D.n; j += t.nthr) {
+            const double xj = D.x[j], sj = D.s[j];
+            if (xj >= sj) D.s[j] = gamma * sj; else D.x[j] = gamma * xj;
+          }
+          if (tau >= kappa) kappa *= gamma; else tau *= gamma;
+        }
+        for (int i = t.gtid; i < D.m; i += t.nthr) D.y[i] *= sqrt_gamma;
+        theta *= sqrt_gamma;
+        if (!sync(P_WARM)) return;
+        if (!exact(P_WARM)) return;
+        if (absorb(false, 1.0) < 0) return;
+        continue;
+      }
+      // ---- one ADMM update -------------------------------------------------
+      // projection (Eq. Simple-Update:Affine) with w = u + v: w_y = y (r = 0),
+      // w_x = x + s, w_tau = tau + kappa, w_theta = theta + xi;
+      // z = M^{-1} w_yx: G z_y = q = y - Ax - As, z_x = w_x + A^T z_y.
+      auto qf = [&](int i) -> double { return D.y[i] - (D.Ax[i] + D.As[i]); };
+      const double kkt = fmax(pres, fmax(dres, dgap));
+      const double tol = cg_rel > 0.0 ? fmax(C->cg_tol, cg_rel * kkt) : C->cg_tol;
+      const int extrap = (C->cg_warm == 2 && total >= 3) ? 2 : (C->cg_warm >= 1 && total >= 2) ? 1 : 0;
+      const int it = pcg(qf, tol, 0.0, C->cg_max, extrap);
+      if (it == -1) return;
+      if (it == -2) { flag(DEV_ERR_PCG); sync(P_CG_UPD); return; }
+      cgtot += it;
+      // z_y += delta, A^T z_y += A^T delta, z_x = x + s + A^T z_y, H^T z
+      double hz[2] = {0.0, 0.0};
+      {
+        auto g = [&](int i) -> float { return D.dz[i]; };
+        auto e = [&](int j, float v, float) {
+          const double a = D.ATz[j] + (double)v;
+          D.ATz[j] = a;
+          const double zxj = (D.x[j] + D.s[j]) + a;
+          hz[0] += D.c[j] * zxj;
+          hz[1] -= D.cbar[j] * zxj;
+        };
+        sell_rows_g<8, 1, float, float>(D.AT, g, g, e);
+      }
+      for (int i = t.gtid; i < D.m; i += t.nthr) {
+        const float d = D.dz[i];
+        const double zyi = D.zy[i] + (double)d;
+        D.zy[i] = zyi;
+        D.d2[i] = D.d1[i];
+        D.d1[i] = d;
+        hz[0] -= D.b[i] * zyi;
+        hz[1] += D.bbar[i] * zyi;
+      }
+      grid_partial<2>(hz, D.partials, S_HZ, red);
+      if (!sync(P_ZX)) return;
+      double h[2], sc[6];
+      totals_x<2, 6>(h, sc, S_HZ, [&](const double* v, double* e) { scalar_step(v, e, tau, kappa, theta, mu); });
+      // u~_yx = z - [g1 g2] t; relaxation (Sec. 4.2); barrier and dual steps in FP64;
+      // the FP32-rounded changes feed the maintained products
+      const double t1 = sc[0], t2 = sc[1], cmu = sc[5], a1 = 1.0 - alpha;
+      for (int i = t.gtid; i < D.m; i += t.nthr) {
+        const double uy = D.zy[i] - D.g1y[i] * t1 - D.g2y[i] * t2;
+        const double y0 = D.y[i];
+        const double yn = alpha * uy + a1 * y0;
+        D.y[i] = yn;
+        D.dy[i] = (float)(yn - y0);
+      }
+      for (int j = t.gtid; j < D.n; j += t.nthr) {
+        const double x0 = D.x[j], s0 = D.s[j];
+        const double ux = (x0 + s0 + D.ATz[j]) - D.g1x[j] * t1 - D.g2x[j] * t2;
+        const double xh = alpha * ux + a1 * x0;
+        double xn, sn;
+        barrier_step<double>(xh - s0, cmu, xn, sn);
+        D.x[j] = xn;
+        D.s[j] = sn;
+        D.dxs[j] = make_float2((float)(xn - x0), (float)(sn - s0));
+      }
+      tau = sc[2]; kappa = sc[3]; theta = sc[4];
+      if (!sync(P_UPD)) return;
+      ++total;
+      if (!evaluate_update()) return;
+      if (status != 0) break;
+      if (total >= C->max_admm) { status = ABIP_MAX_ITER; break; }
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      C->tau = tau; C->kappa = kappa; C->theta = theta; C->mu = mu;
+      C->admm_iters = total; C->cg_iters = cgtot; C->outer_iters = outer; C->status = status;
+      C->pres = pres; C->dres = dres; C->dgap = dgap; C->ctx = ctx; C->bty = bty; C->inner2 = inner2;
+      C->refreshes = refreshes;
+    }
+  }
+};
+
+__global__ void __launch_bounds__(kGridThreads, 1) grid_delta_kernel(GridDelta d) {
+  __shared__ double red[32 * 12];
+  DeltaSolver S(d, red);
+  if (d.ctl->mode == MODE_SETUP) S.setup();
+  else S.solve();
+}
+
+}  // namespace
+
+cudaError_t launch_grid_delta(const GridDelta& d, int grid, cudaStream_t st) {
+  void* args[] = {const_cast<GridDelta*>(&d)};
+  return cudaLaunchCooperativeKernel((const void*)grid_delta_kernel, dim3(grid), dim3(kGridThreads), args, 0, st);
+}
+
+int grid_delta_max_ctas(int device) {
+  int sms = 0, per = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, grid_delta_kernel, kGridThreads, 0);
+  return sms * per;
+}
+
+}  // namespace abip

@@ -5,7 +5,8 @@ is that of the central point of the homogeneous self-dual embedding at that mu
 (system HSD-log-kkt, Sec. 3.2), of which the ADMM iterate is the fixed point.
 Forward: `abip_solve_batch` (dense instances, one persistent launch).  Backward:
 `abip_backward_batch` (damped Newton polish onto the central point, then the adjoint
-through A X S^-1 A^T, one CTA per instance).  Both run in the library's CUDA kernels;
+through the LU factors of the reduced KKT matrix K = Q + diag(0, S X^-1, kappa/tau, 0),
+one CTA per instance).  Both run in the library's CUDA kernels;
 this module only marshals tensors.
 """
 from __future__ import annotations

@@ -141,9 +141,9 @@ def test_pcg_planted_end_to_end(abip):
     _check_end(info, ref, lp)
 
 
-def test_pcg_sparse_end_to_end(abip):
+def test_pcg_sparse_end_to_end(abip, oracle_memo):
     lp = W.planted_sparse(80, seed=W.seed_for(W.SPARSE_PLANTED, 10))
-    ref = O.solve(lp.A.to_scipy(), lp.b, lp.c, O.Params(linsys=1, cg_tol=1e-10))
+    ref = oracle_memo(("sparse", 80, 10), lambda: O.solve(lp.A.to_scipy(), lp.b, lp.c, O.Params(linsys=1, cg_tol=1e-10)))
     s = abip.Solver(lp.A, lp.b, lp.c, cg_tol=1e-10)
     info, x, y, sv = s.solve()
     _check_end(info, ref, lp)

@@ -35,7 +35,10 @@ def abip():
     return _abip
 
 
-def _noalloc(abip, lp, params):
+def _noalloc(abip, lp, params, free_bytes=None):
+    """One call through the C ABI.  free_bytes (a list): receives the device's free memory
+    (cudaMemGetInfo) read just before and just after the call, with no allocation by this
+    process in between."""
     m, n = lp.A.shape
     dev = torch.device("cuda")
     A = torch.from_numpy(np.ascontiguousarray(lp.A)).to(dev)
@@ -45,11 +48,16 @@ def _noalloc(abip, lp, params):
     y = torch.full((m,), np.nan, dtype=torch.float64, device=dev)
     s = torch.full((n,), np.nan, dtype=torch.float64, device=dev)
     info = abip.abip_info()
+    torch.cuda.synchronize()
+    if free_bytes is not None:
+        free_bytes.append(torch.cuda.mem_get_info()[0])
     rc = abip.lib().abip_solve_dense_noalloc(m, n, A.data_ptr(), n, b.data_ptr(), c.data_ptr(),
                                              C.byref(params), x.data_ptr(), y.data_ptr(), s.data_ptr(),
                                              C.byref(info), None)
-    assert rc == 0, abip.lib().abip_last_error(None)
     torch.cuda.synchronize()
+    if free_bytes is not None:
+        free_bytes.append(torch.cuda.mem_get_info()[0])
+    assert rc == 0, abip.lib().abip_last_error(None)
     return info, x.cpu().numpy(), y.cpu().numpy(), s.cpu().numpy()
 
 
@@ -63,8 +71,11 @@ def test_noalloc_matches_setup_and_solve_twice(abip, m, n):
     prm = abip.default_params()
     ref = abip.Solver(lp.A, lp.b, lp.c)
     rinfo, rx, ry, rs = ref.solve()
-    for _ in range(2):                       # two calls in a row share the fixed scratch
-        info, x, y, s = _noalloc(abip, lp, prm)
+    for call in range(2):                    # two calls in a row share the fixed scratch
+        free = []
+        info, x, y, s = _noalloc(abip, lp, prm, free)
+        if call == 1:                        # the first call may load the module; the second allocates nothing
+            assert free[0] == free[1], free
         assert info.status == rinfo["status"]
         assert info.admm_iters == rinfo["admm_iters"]
         assert _rel(x, rx) <= TOL and _rel(y, ry) <= TOL and _rel(s, rs) <= TOL
