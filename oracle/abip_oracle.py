@@ -31,8 +31,9 @@ A1 4-block Q; A2 fixed gamma; A3 beta = mu0 = 1; A4 heuristic warm start for
 (x,s),(tau,kappa) and sqrt(gamma) for y, theta, ties keep x; A6 dgap normaliser uses
 the tau-scaled candidate; A8 certificate signs and test order; A9 two-root stable
 prox; A10 CG stop rule; A13 MAX_ITER status; B5 Barzilai-Borwein beta (Sec. 4.3,
-opt-in): continue from the trial iterates, at most 5 redo rounds; B6 the curvature
-pairs with the printed signs.
+opt-in): continue from the trial iterates, at most 5 redo rounds and never past the
+update cap, keeping the beta that produced the state when the rounds run out; B6 the
+curvature pairs with the printed signs.
 
 Parity status: every function here is pinned by tests in tests/test_oracle_*.py
 except the exact iteration trajectory of `solve` (iteration counts, the iterates
@@ -457,14 +458,21 @@ def bb_estimate(dv_hat: np.ndarray, du_tilde: np.ndarray, du: np.ndarray, beta: 
     return float(beta)
 
 
-def bb_select(P: Problem, proj: Projection, st0: dict, mu: float, beta: float, prm: Params):
+def bb_select(P: Problem, proj: Projection, st0: dict, mu: float, beta: float, prm: Params,
+              budget: Optional[int] = None):
     """Sec. 4.3 at the start of an outer iteration: two ADMM updates from st0 with beta give
-    the curvature pairs; then the heuristic selection (reading B5).  Returns (beta for this
-    outer iteration, state to continue from, ADMM updates spent)."""
+    the curvature pairs; then the heuristic selection (reading B5).  A redo starts again
+    from st0 with the new beta; rounds stop after prm.bb_max_redo redos, or before a round
+    would take the updates spent past `budget`.  Returns (beta for this outer iteration,
+    state to continue from, ADMM updates spent); when the rounds stop without a selection
+    the beta returned is the one that produced the returned state."""
     a = prm.alpha
     spent = 0
     st = st0
-    for redo in range(prm.bb_max_redo + 1):
+    used = beta
+    for _ in range(prm.bb_max_redo + 1):
+        if budget is not None and spent + 2 > budget:
+            break
         st = {k: (v.copy() if isinstance(v, np.ndarray) else v) for k, v in st0.items()}
         u0, v0 = _u_vec(st), _v_vec(P, st)
         ut1 = np.concatenate(list(map(np.atleast_1d, admm_step(P, proj, st, mu, prm, beta))))
@@ -472,6 +480,7 @@ def bb_select(P: Problem, proj: Projection, st0: dict, mu: float, beta: float, p
         ut2 = np.concatenate(list(map(np.atleast_1d, admm_step(P, proj, st, mu, prm, beta))))
         u2 = _u_vec(st)
         spent += 2
+        used = beta
         vh1 = v0 - a * ut1 - (1 - a) * u0 + a * u1
         vh2 = v1 - a * ut2 - (1 - a) * u1 + a * u2
         beta_hat = bb_estimate(vh2 - vh1, a * (ut2 - ut1) + (1 - a) * (u1 - u0), -(u2 - u1), beta, prm.eps_cor)
@@ -480,7 +489,7 @@ def bb_select(P: Problem, proj: Projection, st0: dict, mu: float, beta: float, p
         if abs(beta_hat - beta) <= prm.eps_penalty:
             return 0.5 * (beta + beta_hat), st, spent
         beta = beta_hat                            # redo from the same initial point
-    return beta, st, spent
+    return used, st, spent
 
 
 def warm_start(st: dict, gamma: float, rule: int):
@@ -550,9 +559,12 @@ def solve(A, b, c, prm: Optional[Params] = None, trace_iters: int = 0,
     status = 0
     while status == 0:
         if prm.bb_beta and total + 2 <= prm.max_admm_iters:
-            beta_k, st, spent = bb_select(P, proj, st, mu, beta_k, prm)
+            beta_k, st, spent = bb_select(P, proj, st, mu, beta_k, prm, budget=prm.max_admm_iters - total)
             total += spent
             betas.append(beta_k)
+            if total >= prm.max_admm_iters:      # the trial updates used the last of the cap
+                status = MAX_ITER
+                break
         # inner loop at fixed mu (Algorithm 2)
         while True:
             if inner_residual_sq(P, st) <= mu:

@@ -425,6 +425,83 @@ def test_bb_estimate_collinear_and_orthogonal_cases():
     assert O.bb_estimate(2.0 * d, d, e, 0.7, 0.2) == pytest.approx(2.0, rel=1e-12)
 
 
+def test_bb_hybrid_step_rule():
+    """The hybrid spectral step of Sec. 4.3: the minimum-gradient step when 2 MG > SD, else
+    SD - MG/2.  With du = d and dv = d + t e (e orthogonal to d, |e| = |d|):
+    SD = 1 + t^2, MG = 1; t = 0.5 gives MG, t = 1.5 gives SD - MG/2 = 2.75."""
+    rng = np.random.default_rng(8)
+    d = rng.standard_normal(30)
+    e = rng.standard_normal(30)
+    e -= (e @ d) / (d @ d) * d
+    e *= np.linalg.norm(d) / np.linalg.norm(e)
+    orth = rng.standard_normal(30)
+    orth -= (orth @ d) / (d @ d) * d + (orth @ e) / (e @ e) * e
+    # psi's pair is orthogonal (fails the safeguard), so beta_hat = phi alone
+    assert O.bb_estimate(d + 0.5 * e, d, orth, 1.0, 0.2) == pytest.approx(1.0, rel=1e-12)
+    assert O.bb_estimate(d + 1.5 * e, d, orth, 1.0, 0.2) == pytest.approx(1.0 + 1.5 ** 2 - 0.5, rel=1e-12)
+
+
+class _ScriptedBB:
+    """Stand-ins for admm_step and bb_estimate that let a test drive bb_select's branches:
+    every trial update adds its beta to theta (so the returned state tells which beta
+    advanced it), and the estimates come from a script."""
+
+    def __init__(self, monkeypatch, estimates):
+        self.betas = []
+        self.estimates = iter(estimates)
+        monkeypatch.setattr(O, "admm_step", self.step)
+        monkeypatch.setattr(O, "bb_estimate", lambda *a, **k: next(self.estimates))
+
+    def step(self, P, proj, st, mu, prm, beta=None):
+        self.betas.append(beta)
+        st["theta"] = st["theta"] + beta
+        return np.zeros(P.m), np.zeros(P.n), 0.0, 0.0
+
+
+def _bb_setup():
+    lp = W.planted_dense(4, 9, seed=3)
+    P = O.Problem(lp.A, lp.b, lp.c)
+    prm = O.Params(bb_beta=True)
+    return P, O.Projection(P, O.make_linsys(P, prm)), prm
+
+
+@pytest.mark.parametrize("script,beta,spent,used", [
+    ([1.0], 1.0, 2, [1.0, 1.0]),                                  # beta_hat == beta: keep it
+    ([1.06], 1.03, 2, [1.0, 1.0]),                                # |beta_hat - beta| <= 0.1: average
+    ([3.0, 3.04], 3.02, 4, [1.0, 1.0, 3.0, 3.0]),                 # redo with 3, then average
+    ([3.0, 5.0, 7.0, 9.0, 11.0, 13.0], 11.0, 12,                  # five redos, then stop with the
+     [1.0, 1.0, 3.0, 3.0, 5.0, 5.0, 7.0, 7.0, 9.0, 9.0, 11.0, 11.0]),   # beta that made the state
+])
+def test_bb_select_branches(monkeypatch, script, beta, spent, used):
+    """Sec. 4.3 heuristic selection (reading B5): keep, average, redo from the same start,
+    and the bound on redo rounds; each round restarts from the outer step's start point."""
+    P, proj, prm = _bb_setup()
+    fake = _ScriptedBB(monkeypatch, script)
+    st0 = O.initial_state(P)
+    b, st, n = O.bb_select(P, proj, st0, 1.0, 1.0, prm)
+    assert b == pytest.approx(beta, rel=1e-15) and n == spent
+    assert fake.betas == used
+    # the returned state is the last round's: two updates from st0 with that round's beta
+    assert st["theta"] == pytest.approx(st0["theta"] + 2 * used[-1], rel=1e-15)
+    assert st0["theta"] == 1.0
+
+
+def test_bb_select_respects_the_update_budget(monkeypatch):
+    """A budget of 5 updates allows two rounds (4 updates): the second round's beta is kept
+    and no third round starts."""
+    P, proj, prm = _bb_setup()
+    fake = _ScriptedBB(monkeypatch, [3.0, 5.0, 7.0])
+    b, st, n = O.bb_select(P, proj, O.initial_state(P), 1.0, 1.0, prm, budget=5)
+    assert (b, n) == (3.0, 4) and fake.betas == [1.0, 1.0, 3.0, 3.0]
+
+
+def test_bb_beta_solve_never_passes_the_cap():
+    lp = W.planted_dense(20, 60, seed=23)
+    for cap in (2, 3, 7, 40):
+        r = O.solve(lp.A, lp.b, lp.c, O.Params(bb_beta=True, max_admm_iters=cap))
+        assert r.admm_iters <= cap
+
+
 def test_bb_beta_solve_reaches_the_planted_optimum():
     lp = W.planted_dense(20, 60, seed=23)
     r = O.solve(lp.A, lp.b, lp.c, O.Params(bb_beta=True))
