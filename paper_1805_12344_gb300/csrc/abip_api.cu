@@ -179,16 +179,25 @@ struct HostSell {
   std::vector<int32_t> perm;
 };
 
-// Contiguous slice ranges per global warp with about equal work (slice width + 2).
+// Loads a lane issues for a slice of width w in the device traversal (sell.cuh): batches
+// of 8, the rest in one batch of the next power of two.
+double slice_cost(int64_t w) {
+  const int64_t r = w % 8;
+  const int64_t tail = r > 4 ? 8 : r > 2 ? 4 : r;
+  return (double)(w - r + tail);
+}
+
+// Contiguous slice ranges per global warp with about equal work (loads of the slice + 2
+// for the row bookkeeping).
 std::vector<int32_t> warp_partition(const HostSell& S, int nwarp) {
   std::vector<int32_t> w(nwarp + 1, 0);
   double total = 0;
-  for (int sl = 0; sl < S.nslices; ++sl) total += (double)((S.sp[sl + 1] - S.sp[sl]) / 32) + 2.0;
+  for (int sl = 0; sl < S.nslices; ++sl) total += slice_cost((S.sp[sl + 1] - S.sp[sl]) / 32) + 2.0;
   const double per = total / nwarp;
   double acc = 0;
   int k = 1;
   for (int sl = 0; sl < S.nslices; ++sl) {
-    acc += (double)((S.sp[sl + 1] - S.sp[sl]) / 32) + 2.0;
+    acc += slice_cost((S.sp[sl + 1] - S.sp[sl]) / 32) + 2.0;
     while (k < nwarp && acc >= per * k - 1e-9) w[k++] = sl + 1;
   }
   while (k <= nwarp) w[k++] = S.nslices;
@@ -272,11 +281,11 @@ void assign_vectors(abip::GridDelta& g, Arena& ar, int m, int n) {
   g.g1y = ar.take<double>(m); g.g1x = ar.take<double>(n); g.g2y = ar.take<double>(m); g.g2x = ar.take<double>(n);
   g.y = ar.take<double>(m); g.x = ar.take<double>(n); g.s = ar.take<double>(n);
   g.Ax = ar.take<double>(m); g.As = ar.take<double>(m); g.ATy = ar.take<double>(n);
-  g.zy = ar.take<double>(m); g.ATz = ar.take<double>(n); g.wv = ar.take<double>(n);
+  g.zy = ar.take<double>(m); g.ATz = ar.take<double>(n);
   g.dinv = ar.take<float>(m); g.dz = ar.take<float>(m); g.d1 = ar.take<float>(m); g.d2 = ar.take<float>(m);
   g.r = ar.take<float>(m); g.p = ar.take<float>(m); g.Gp = ar.take<float>(m);
   g.ut = ar.take<float2>(n); g.zd = ar.take<float2>(m); g.zd2 = ar.take<float2>(m);
-  g.dxs = ar.take<float2>(n); g.dy = ar.take<float>(m);
+  g.wdel = ar.take<float>(n); g.xsw = ar.take<abip::XSW>(n); g.dy = ar.take<float>(m);
 }
 
 cudaError_t launch_persistent(abip_handle* h, cudaStream_t st) {
@@ -408,6 +417,7 @@ void init_grid_state(abip_handle* h, cudaStream_t st) {
     fill_kernel<double><<<64, 256, 0, st>>>(g.zy, m, 0.0);
     fill_kernel<float><<<64, 256, 0, st>>>(g.d1, m, 0.f);
     fill_kernel<float><<<64, 256, 0, st>>>(g.d2, m, 0.f);
+    fill_kernel<float><<<64, 256, 0, st>>>(g.dz, m, 0.f);
   } else {
     GridData<double>& g = h->gd64;
     fill_kernel<double><<<64, 256, 0, st>>>(g.zy, m, 0.0);
@@ -454,7 +464,7 @@ int solve_grid_path(abip_handle* h, cudaStream_t st) {
   float ms = 0.f;
   cudaEventElapsedTime(&ms, h->ev0, h->ev1);
   h->kernel_s = ms * 1e-3;
-  h->launches = (resume ? 0 : 3) + 3 + 1;   // fills and the persistent solve kernel
+  h->launches = (resume ? 0 : 3) + (h->mixed ? 4 : 3) + 1;   // fills and the persistent solve kernel
   if (prof) {
     unsigned long long pv[abip::kProfBuckets];
     cudaMemcpy(pv, prof, sizeof(pv), cudaMemcpyDeviceToHost);
@@ -1090,14 +1100,18 @@ int abip_solve_batch_shared(int32_t count, const abip_matrix* A, const double* c
   sp.beta = prm.beta; sp.gamma = prm.gamma; sp.alpha = prm.alpha; sp.eps = prm.eps;
   sp.max_admm = prm.max_admm_iters; sp.warmstart = prm.warmstart; sp.stop_rule = prm.stop_rule;
   sp.mixed = prm.precision != ABIP_PREC_F64 ? 1 : 0;
-  sp.tc = prm.precision == ABIP_PREC_MIXED_BF16 ? 1 : 0;
-  if (sp.tc) {   // the tensor-core products use A in bfloat16: it must be exact there
+  sp.tc = 0;
+  if (prm.precision == ABIP_PREC_MIXED_BF16) {
+    // the tensor-core products take A as bfloat16 terms: one when A is exact in bfloat16,
+    // three otherwise (they hold A's FP32 value exactly); A must lie in the FP32 range
+    sp.tc = 1;
     for (const double v : Ah) {
       const float f = (float)v;
+      if (!std::isfinite(f))
+        return fail(nullptr, ABIP_E_INVALID_ARG, "ABIP_PREC_MIXED_BF16 needs A within the FP32 range");
       uint32_t u;
       std::memcpy(&u, &f, 4);
-      if ((double)f != v || (u & 0xFFFFu) != 0)
-        return fail(nullptr, ABIP_E_INVALID_ARG, "ABIP_PREC_MIXED_BF16 needs A exactly representable in bfloat16");
+      if ((double)f != v || (u & 0xFFFFu) != 0) sp.tc = 3;
     }
   }
   sp.n = n;

@@ -94,6 +94,13 @@ struct GridData {
   SolveCtl* ctl;
 };
 
+// Per column of the mixed sparse path: the FP32 change (dx, ds) of the iterate and
+// W = A^T (z_y + delta_0) in FP64, gathered together (16 bytes) by the products with A.
+struct XSW {
+  float dx, ds;
+  double w;
+};
+
 // Device pointers of the sparse mixed-precision path (grid_delta.cu): the iterate, the
 // products the update needs and the embedding data in FP64; the matrix values, the
 // changes of the iterate and the PCG work vectors of the correction solve in FP32.
@@ -107,13 +114,14 @@ struct GridDelta {
   double* y; double* x; double* s;             // iterate (r = 0, xi = -n-1 implicit)
   double* Ax; double* As; double* ATy;         // maintained products for the residuals
   double* zy; double* ATz;                     // z_y = G^{-1} q and A^T z_y
-  double* wv;                                  // n: A^T z_y + A^T delta_0 (start residual of a solve)
   float* dinv;                                 // Jacobi diagonal 1 / (1 + sum_j A_ij^2)
-  float* dz;                                   // correction of z_y (PCG iterate)
+  float* dz;                                   // correction of z_y: the start of the next solve, then its
+                                               // PCG iterate
   float* d1; float* d2;                        // the last two corrections (extrapolated start)
   float* r; float* p; float* Gp;               // PCG work vectors
   float2* ut; float2* zd; float2* zd2;         // (A^T zr, A^T p); (zr, D^{-1} Gp), double-buffered
-  float2* dxs;                                 // (dx, ds) per column: change of the iterate
+  float* wdel;                                 // n: sum over PCG iterations of alpha A^T p
+  XSW* xsw;                                    // per column: (dx, ds, W), W = A^T (z_y + start)
   float* dy;                                   // change of y
   double* partials;                            // kNumSlots * gridDim doubles
   unsigned long long* bar;                     // barrier arrival counter
@@ -225,7 +233,8 @@ struct ShParams {
   int32_t warmstart, stop_rule, mixed, n;
   int64_t confirm_gap;
   int32_t refresh;                 // mixed: FP64 recomputation of the maintained products every `refresh` cycles
-  int32_t tc;                      // mixed: products with A on the tensor cores (A exact in bfloat16)
+  int32_t tc;                      // mixed: products with A on the tensor cores: 0 off, else the number
+                                   // of bfloat16 terms of A (1: A exact in bfloat16, 3: A in FP32)
 };
 
 // Device arrays of one iteration type; every vector is [length x B], instance fastest.

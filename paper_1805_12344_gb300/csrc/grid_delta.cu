@@ -32,13 +32,14 @@ namespace {
 
 using namespace sell;
 
-// reduction slots (a slot is never rewritten before a barrier separates its previous read)
+// reduction slots (a slot is never rewritten before a barrier separates its previous read);
+// S_RES and S_PCG0 are adjacent so that one read gives the tests and the next PCG start
 enum Slot : int {
-  S_PCG0 = 0,    // 3: r.zr, r.r, q.q
-  S_PGP = 3,     // 1: p.Gp
-  S_RZ = 4,      // 2: r.zr, r.r
-  S_HZ = 6,      // 2: h1.z, h2.z
-  S_RES = 8,     // 9: residual sums
+  S_RES = 0,     // 9: residual sums
+  S_PCG0 = 9,    // 3: r.zr, r.r, q.q of the next projection's start
+  S_PGP = 12,    // 1: p.Gp
+  S_RZ = 13,     // 2: r.zr, r.r
+  S_HZ = 15,     // 2: h1.z, h2.z
   S_SETUP = 17,  // 3: sum c, ||b||^2, ||c||^2
   S_K = 20,      // 4: H^T M^{-1} H
 };
@@ -46,6 +47,34 @@ enum Slot : int {
 constexpr int kDeltaRefresh = 100;   // updates between exact FP64 recomputations
 constexpr int kSetupRounds = 12;     // refinement rounds of one setup solve, at most
 constexpr double kSetupRoundRed = 1e-5;   // residual reduction asked of one FP32 round
+
+// start of the correction solve that follows `done` ADMM updates (reading A10 restated
+// on corrections): 0 none, 1 the last correction (the linear extrapolation 2 z_k - z_{k-1}
+// of the solutions), 2 twice the last minus the one before (the quadratic one)
+__device__ __forceinline__ int extrap_for(int cg_warm, int64_t done) {
+  return (cg_warm == 2 && done >= 3) ? 2 : (cg_warm >= 1 && done >= 2) ? 1 : 0;
+}
+__device__ __forceinline__ float start_of(float d1, float d2, int extrap) {
+  return extrap == 2 ? 2.f * d1 - d2 : extrap == 1 ? d1 : 0.f;
+}
+
+// accumulator of the products with A after an update: A dx, A ds (FP32) and A W (FP64)
+struct MaintSt {
+  using G = XSW;
+  float adx = 0.f, ads = 0.f;
+  double aw = 0.0;
+  __device__ __forceinline__ void add(float a, const XSW& g) {
+    adx += a * g.dx;
+    ads += a * g.ds;
+    aw += (double)a * g.w;
+  }
+  template <int L>
+  __device__ __forceinline__ void group() {
+    adx = group_sum<L>(adx);
+    ads = group_sum<L>(ads);
+    aw = group_sum<L>(aw);
+  }
+};
 
 struct DeltaSolver {
   const GridDelta& D;
@@ -113,69 +142,35 @@ struct DeltaSolver {
     mark(P_TOTALS);
   }
 
-  // start of the correction solve (reading A10 restated on corrections): 0 none,
-  // 1 the last correction d1 (linear extrapolation of the solutions), 2 2 d1 - d2
-  // (quadratic extrapolation)
-  __device__ __forceinline__ float start(int i, int extrap) const {
-    if (extrap == 2) return 2.f * D.d1[i] - D.d2[i];
-    if (extrap == 1) return D.d1[i];
-    return 0.f;
+  // Start of a correction solve for row i (Sec. 4.4 with iterative refinement): the
+  // FP64 residual r_0 = q - z_y - delta_0 - (A W)_i of the start point z_y + delta_0,
+  // delta_0 = dz (set when the previous solve ended), W = A^T (z_y + delta_0); stores r_0
+  // and zr_0 = D^{-1} r_0 in FP32 and adds r.zr, r.r, q.q to pc.
+  __device__ __forceinline__ void start_row(int i, double qi, double zyi, double aw, double (&pc)[3]) const {
+    const float d0 = D.dz[i];
+    const double ri = qi - zyi - (double)d0 - aw;
+    const float rf = (float)ri;
+    const float zri = D.dinv[i] * rf;
+    D.r[i] = rf;
+    D.zd[i].x = zri;
+    pc[0] += (double)(rf * zri);
+    pc[1] += ri * ri;
+    pc[2] += qi * qi;
   }
 
-  // Jacobi-PCG (Sec. 4.4) on G delta = e, e = q - z_y - A ATz in FP64, from delta_0 =
-  // start(extrap); leaves delta in D.dz.  Stop when ||r|| <= max(tol max(1, ||q||),
-  // rel0 ||r_0||): the first term is the FP64 path's rule for the full system, whose
-  // residual r equals (reading A10); rel0 > 0 ends a setup refinement round early.
-  // The iteration is the FP64 path's two-phase PCG in FP32:
+  // Jacobi-PCG (Sec. 4.4) on G delta = e from the start prepared by start_row (r, zr and
+  // delta = dz in place, rz = r.zr), the FP64 path's two-phase iteration in FP32:
   //   phase A (rows of A):   p = zr + beta p;  Gp = p + A (u + beta t);  p.Gp
-  //   phase B (rows of A^T): t <- u + beta t (= A^T p);  u <- A^T zr_new, gathering
-  //                          zr_new = zr - alpha D^{-1} Gp;  rows of A: dz += alpha p,
-  //                          r -= alpha Gp, zr_new = D^{-1} r;  r.zr, r.r
-  // Returns iterations, -1 on barrier failure, -2 past the cap.
-  template <typename QF>
-  __device__ int pcg(QF qf, double tol, double rel0, int maxit, int extrap) {
+  //   phase B (rows of A^T): t <- u + beta t (= A^T p);  wdel += alpha t;  u <- A^T zr_new,
+  //                          gathering zr_new = zr - alpha D^{-1} Gp;  rows of A:
+  //                          dz += alpha p, r -= alpha Gp, zr_new = D^{-1} r;  r.zr, r.r
+  // so that at the end wdel = A^T (delta - delta_0).  Stops when ||r||^2 <= bound2.
+  // Returns iterations (>= 1), -1 on barrier failure, -2 past the cap.
+  __device__ int pcg_run(double rz, double bound2, int maxit) {
     float* dz = D.dz; float* r = D.r; float* p = D.p; float* Gp = D.Gp;
     float2* ut = D.ut;
     float2* zd_cur = D.zd;
     float2* zd_nxt = D.zd2;
-    if (extrap > 0) {
-      // wv = A^T z_y + A^T delta_0
-      auto g = [&](int i) -> float { return start(i, extrap); };
-      auto e = [&](int j, float v, float) { D.wv[j] = D.ATz[j] + (double)v; };
-      sell_rows_g<8, 1, float, float>(D.AT, g, g, e);
-      if (!sync(P_PCG_INIT)) return -1;
-    }
-    const double* wsrc = extrap > 0 ? D.wv : D.ATz;
-    double acc[3] = {0.0, 0.0, 0.0};
-    {
-      // r_0 = q - z_y - delta_0 - A wv in FP64
-      auto g = [&](int j) -> double { return wsrc[j]; };
-      auto e = [&](int i, double v, double) {
-        const double qi = qf(i);
-        const float d0 = start(i, extrap);
-        const double ri = qi - D.zy[i] - (double)d0 - v;
-        const float rf = (float)ri;
-        const float zri = D.dinv[i] * rf;
-        dz[i] = d0;
-        r[i] = rf;
-        zd_cur[i].x = zri;
-        acc[0] += (double)(rf * zri);
-        acc[1] += ri * ri;
-        acc[2] += qi * qi;
-      };
-      sell_rows_g<8, 1, double, float>(D.A, g, g, e);
-    }
-    grid_partial<3>(acc, D.partials, S_PCG0, red);
-    if (!sync(P_PCG_INIT)) return -1;
-    double tot[3], ex0[2];
-    totals_x<3, 2>(tot, ex0, S_PCG0, [&](const double* v, double* e) {
-      const double bnd = fmax(tol * fmax(1.0, sqrt(v[2])), rel0 * sqrt(v[1]));
-      e[0] = bnd * bnd;
-      e[1] = v[1] > e[0] ? 1.0 : 0.0;
-    });
-    double rz = tot[0];
-    const double bound2 = ex0[0];
-    if (ex0[1] == 0.0) return 0;
     {
       auto g = [&](int i) -> float { return zd_cur[i].x; };
       auto e = [&](int j, float v, float) { ut[j].x = v; };
@@ -228,7 +223,9 @@ struct DeltaSolver {
           return w;
         };
         auto e = [&](int j, float v, float, float2 w) {
-          ut[j] = make_float2(v, first ? w.x : w.x + be * w.y);
+          const float t = first ? w.x : w.x + be * w.y;
+          ut[j] = make_float2(v, t);
+          D.wdel[j] = first ? al * t : D.wdel[j] + al * t;
         };
         sell_rows_gp<8, 1, float, float>(D.AT, g, g, pre, e);
       }
@@ -259,13 +256,12 @@ struct DeltaSolver {
     return k;
   }
 
-  // The nine sums of the Sec. 4.1 tests and Eq. inner-stop from the products of the
-  // current iterate, in FP64:
+  // The nine sums of the Sec. 4.1 tests and Eq. inner-stop, in FP64:
   //   0 ||Qu-v||^2 (vector blocks), 1 ||Ax/tau - b||^2, 2 ||(A^T y + s)/tau - c||^2,
   //   3 ||Ax||^2, 4 ||A^T y + s||^2, 5 b^T y, 6 bbar^T y, 7 c^T x, 8 cbar^T x.
-  __device__ __forceinline__ void row_sums(int i, double ax, double tau, double itau, double theta,
-                                           double (&acc)[9]) const {
-    const double bi = D.b[i], bb = D.bbar[i], yi = D.y[i];
+  __device__ __forceinline__ void row_sums(int i, double ax, double yi, double tau, double itau, double theta,
+                                           double (&acc)[12]) const {
+    const double bi = D.b[i], bb = D.bbar[i];
     const double ry = ax - bi * tau + bb * theta;
     const double pr = ax * itau - bi;
     acc[0] += ry * ry;
@@ -275,7 +271,7 @@ struct DeltaSolver {
     acc[6] += bb * yi;
   }
   __device__ __forceinline__ void col_sums(int j, double aty, double tau, double itau, double theta,
-                                           double (&acc)[9]) const {
+                                           double (&acc)[12]) const {
     const double sj = D.s[j], cj = D.c[j], cb = D.cbar[j], xj = D.x[j];
     const double rx = -aty + cj * tau - cb * theta - sj;
     const double dr = (aty + sj) * itau - cj;
@@ -285,49 +281,30 @@ struct DeltaSolver {
     acc[7] += cj * xj;
     acc[8] += cb * xj;
   }
-
-  // Exact products of the current iterate (FP64 gathers and sums): Ax, As, A^T y,
-  // A^T z_y, and the nine sums into slot S_RES.  No barrier.
-  __device__ void exact_products(double tau, double theta) {
-    double acc[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
-    const double itau = 1.0 / tau;
-    {
-      auto g0 = [&](int j) -> double { return D.x[j]; };
-      auto g1 = [&](int j) -> double { return D.s[j]; };
-      auto e = [&](int i, double ax, double as) {
-        D.Ax[i] = ax;
-        D.As[i] = as;
-        row_sums(i, ax, tau, itau, theta, acc);
-      };
-      sell_rows_g<8, 2, double, float>(D.A, g0, g1, e);
-    }
-    {
-      auto g0 = [&](int i) -> double { return D.y[i]; };
-      auto g1 = [&](int i) -> double { return D.zy[i]; };
-      auto e = [&](int j, double aty, double atz) {
-        D.ATy[j] = aty;
-        D.ATz[j] = atz;
-        col_sums(j, aty, tau, itau, theta, acc);
-      };
-      sell_rows_g<8, 2, double, float>(D.AT, g0, g1, e);
-    }
-    grid_partial<9>(acc, D.partials, S_RES, red);
+  __device__ __forceinline__ void put_sums(double (&acc)[12]) {
+    grid_partial<12>(acc, D.partials, S_RES, red);
   }
 
-  // Maintained products after an update: Ax += A dx, As += A ds, A^T y += A^T dy (FP32
-  // products of the changes), and the nine sums into slot S_RES.  No barrier.
-  __device__ void maintained_products(double tau, double theta) {
-    double acc[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+  // After an update: Ax += A dx, As += A ds, A^T y += A^T dy (FP32 products of the
+  // changes), the nine sums, and the start of the next projection (start_row with
+  // A W gathered in the same pass).  Partials in S_RES..S_PCG0; no barrier.
+  __device__ void maintained_phase(double tau, double theta) {
+    double acc[12] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+    double pc[3] = {0.0, 0.0, 0.0};
     const double itau = 1.0 / tau;
     {
-      auto gp = [&](int j) -> float2 { return D.dxs[j]; };
-      auto e = [&](int i, float adx, float ads) {
-        const double ax = D.Ax[i] + (double)adx;
+      auto gf = [&](int j) -> XSW { return D.xsw[j]; };
+      auto pre = [](int) { return NoPre{}; };
+      auto e = [&](int i, const MaintSt& st, NoPre) {
+        const double ax = D.Ax[i] + (double)st.adx;
+        const double as = D.As[i] + (double)st.ads;
         D.Ax[i] = ax;
-        D.As[i] = D.As[i] + (double)ads;
-        row_sums(i, ax, tau, itau, theta, acc);
+        D.As[i] = as;
+        const double yi = D.y[i];
+        row_sums(i, ax, yi, tau, itau, theta, acc);
+        start_row(i, yi - (ax + as), D.zy[i], st.aw, pc);
       };
-      sell_rows_pair<8, float, float>(D.A, gp, e);
+      sell_fold<8, float, MaintSt>(D.A, gf, pre, e);
     }
     {
       auto g = [&](int i) -> float { return D.dy[i]; };
@@ -338,11 +315,55 @@ struct DeltaSolver {
       };
       sell_rows_g<8, 1, float, float>(D.AT, g, g, e);
     }
-    grid_partial<9>(acc, D.partials, S_RES, red);
+    acc[9] = pc[0]; acc[10] = pc[1]; acc[11] = pc[2];
+    put_sums(acc);
   }
 
-  // Thread 0 only: the nine sums -> e = (inner2 = ||Qu - v||^2, pres, dres, dgap, c^T x,
-  // b^T y, finite flag, Sec. 4.1 test result with the given margin or 0).
+  // Exact FP64 products of the current iterate and the next projection's start, in two
+  // phases: (1) Ax, As, A^T y and W = A^T (z_y + delta_0) with FP64 gathers, the nine sums;
+  // (2) A W and start_row.  Returns false on barrier failure; the partials are in
+  // S_RES..S_PCG0 after it.
+  __device__ bool exact_phase(double tau, double theta, int phase) {
+    double acc[12] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+    const double itau = 1.0 / tau;
+    {
+      auto g0 = [&](int j) -> double { return D.x[j]; };
+      auto g1 = [&](int j) -> double { return D.s[j]; };
+      auto e = [&](int i, double ax, double as) {
+        D.Ax[i] = ax;
+        D.As[i] = as;
+        row_sums(i, ax, D.y[i], tau, itau, theta, acc);
+      };
+      sell_rows_g<8, 2, double, float>(D.A, g0, g1, e);
+    }
+    {
+      auto g0 = [&](int i) -> double { return D.y[i]; };
+      auto g1 = [&](int i) -> double { return D.zy[i] + (double)D.dz[i]; };
+      auto e = [&](int j, double aty, double w) {
+        D.ATy[j] = aty;
+        D.xsw[j].w = w;
+        col_sums(j, aty, tau, itau, theta, acc);
+      };
+      sell_rows_g<8, 2, double, float>(D.AT, g0, g1, e);
+    }
+    if (!sync(phase)) return false;
+    double pc[3] = {0.0, 0.0, 0.0};
+    {
+      auto g = [&](int j) -> double { return D.xsw[j].w; };
+      auto e = [&](int i, double aw, double) {
+        start_row(i, D.y[i] - (D.Ax[i] + D.As[i]), D.zy[i], aw, pc);
+      };
+      sell_rows_g<8, 1, double, float>(D.A, g, g, e);
+    }
+    acc[9] = pc[0]; acc[10] = pc[1]; acc[11] = pc[2];
+    put_sums(acc);
+    return sync(phase);
+  }
+
+  // Thread 0 only: the twelve sums -> e = (inner2 = ||Qu - v||^2, pres, dres, dgap, c^T x,
+  // b^T y, finite flag, Sec. 4.1 test result with the given margin or 0, bound^2 of the
+  // next PCG solve, whether its start is above the bound).  The PCG tolerance is cg_tol,
+  // or with cg_rel > 0 max(cg_tol, cg_rel * relative KKT residual) (reading A10).
   __device__ __noinline__ void derive_sums(const double* a, double* e, bool with_tests, double margin,
                                            double tau, double kappa, double theta) {
     const double zbar = C->zbar, xi = C->xi, nb = C->nb, nc = C->nc, eps = C->eps;
@@ -354,7 +375,7 @@ struct DeltaSolver {
     e[3] = fabs(a[7] / tau - a[5] / tau) / (1.0 + fabs(a[7] / tau) + fabs(a[5] / tau));
     e[4] = a[7];
     e[5] = a[5];
-    e[6] = (isfinite(e[0]) && isfinite(e[1]) && isfinite(e[2])) ? 1.0 : 0.0;
+    e[6] = (isfinite(e[0]) && isfinite(e[1]) && isfinite(e[2]) && isfinite(a[9]) && isfinite(a[10])) ? 1.0 : 0.0;
     int st = 0;
     if (with_tests) {
       if (e[1] <= margin * eps && e[2] <= margin * eps && e[3] <= margin * eps) st = ABIP_OPTIMAL;
@@ -362,6 +383,11 @@ struct DeltaSolver {
       else if (a[7] < 0 && sqrt(a[3]) <= margin * eps * (-a[7]) / nc) st = ABIP_DUAL_INFEASIBLE;
     }
     e[7] = (double)st;
+    const double kkt = fmax(e[1], fmax(e[2], e[3]));
+    const double tol = C->cg_rel > 0.0 ? fmax(C->cg_tol, C->cg_rel * kkt) : C->cg_tol;
+    const double bnd = tol * fmax(1.0, sqrt(a[11]));
+    e[8] = bnd * bnd;
+    e[9] = a[10] > e[8] ? 1.0 : 0.0;
   }
 
   // Thread 0 only: t = K^{-1} (w_{tau,theta} + H^T z) from v = H^T z, and the relaxed
@@ -382,13 +408,14 @@ struct DeltaSolver {
 
   // One FP64 solve with M (Sec. 4.4) at setup: [gy; gx] = M^{-1} [hy; hx], i.e.
   // G gy = hy - A hx and gx = hx + A^T gy, by FP32 PCG rounds on the FP64 residual until a
-  // round starts below the tolerance.  Uses zy, ATz, Ax as scratch.  Returns false on
+  // round starts below cg_tol; each round asks the FP32 iteration for a reduction of
+  // kSetupRoundRed.  Uses zy, ATz, Ax, dz and xsw[].w as scratch.  Returns false on
   // failure (flag set).
   template <typename HY, typename HX>
   __device__ bool setup_solve(HY hy, HX hx, double* gy, double* gx) {
     const Thr t = th;
-    for (int j = t.gtid; j < D.n; j += t.nthr) { gx[j] = hx(j); D.ATz[j] = 0.0; }
-    for (int i = t.gtid; i < D.m; i += t.nthr) D.zy[i] = 0.0;
+    for (int j = t.gtid; j < D.n; j += t.nthr) { gx[j] = hx(j); D.xsw[j].w = 0.0; }
+    for (int i = t.gtid; i < D.m; i += t.nthr) { D.zy[i] = 0.0; D.dz[i] = 0.f; }
     if (!sync(P_SETUP)) return false;
     {
       auto g = [&](int j) -> double { return gx[j]; };
@@ -396,25 +423,42 @@ struct DeltaSolver {
       sell_rows_g<8, 1, double, float>(D.A, g, g, e);
     }
     if (!sync(P_SETUP)) return false;
-    auto qf = [&](int i) -> double { return hy(i) - D.Ax[i]; };
     int rounds = 0;
     for (;; ++rounds) {
       if (rounds >= kSetupRounds) { flag(DEV_ERR_PCG); sync(P_SETUP); return false; }
-      const int it = pcg(qf, C->cg_tol, kSetupRoundRed, C->cg_max, 0);
+      // start residual of G gy = hy - A hx from the current gy (W = A^T gy)
+      double pc[3] = {0.0, 0.0, 0.0};
+      {
+        auto g = [&](int j) -> double { return D.xsw[j].w; };
+        auto e = [&](int i, double aw, double) { start_row(i, hy(i) - D.Ax[i], D.zy[i], aw, pc); };
+        sell_rows_g<8, 1, double, float>(D.A, g, g, e);
+      }
+      grid_partial<3>(pc, D.partials, S_PCG0, red);
+      if (!sync(P_SETUP)) return false;
+      double tot[3], ex[2];
+      totals_x<3, 2>(tot, ex, S_PCG0, [&](const double* v, double* e) {
+        const double b = fmax(C->cg_tol * fmax(1.0, sqrt(v[2])), kSetupRoundRed * sqrt(v[1]));
+        e[0] = b * b;
+        e[1] = v[1] > C->cg_tol * C->cg_tol * fmax(1.0, v[2]) ? 1.0 : 0.0;
+      });
+      if (ex[1] == 0.0) break;   // converged: the FP64 residual is below cg_tol
+      const int it = pcg_run(tot[0], ex[0], C->cg_max);
       if (it == -1) return false;
       if (it == -2) { flag(DEV_ERR_PCG); sync(P_SETUP); return false; }
-      if (it == 0) break;   // converged from an FP64 residual
-      for (int i = t.gtid; i < D.m; i += t.nthr) D.zy[i] += (double)D.dz[i];
+      for (int i = t.gtid; i < D.m; i += t.nthr) {
+        D.zy[i] += (double)D.dz[i];
+        D.dz[i] = 0.f;
+      }
       if (!sync(P_SETUP)) return false;
       {
         auto g = [&](int i) -> double { return D.zy[i]; };
-        auto e = [&](int j, double v, double) { D.ATz[j] = v; };
+        auto e = [&](int j, double v, double) { D.xsw[j].w = v; };
         sell_rows_g<8, 1, double, float>(D.AT, g, g, e);
       }
       if (!sync(P_SETUP)) return false;
     }
     for (int i = t.gtid; i < D.m; i += t.nthr) gy[i] = D.zy[i];
-    for (int j = t.gtid; j < D.n; j += t.nthr) gx[j] += D.ATz[j];
+    for (int j = t.gtid; j < D.n; j += t.nthr) gx[j] += D.xsw[j].w;
     if (threadIdx.x == 0 && blockIdx.x == 0) C->setup_rounds += rounds + 1;
     return sync(P_SETUP);
   }
@@ -466,11 +510,13 @@ struct DeltaSolver {
     }
   }
 
-  // MODE_SOLVE: Algorithm 2 from the state in D / C.
+  // MODE_SOLVE: Algorithm 2 from the state in D / C.  Each ADMM update is four phases
+  // plus the PCG iterations: [PCG: A^T zr_0, then (A, A^T) per iteration] -> [H^T z:
+  // z_y += delta, A^T z_y = W + wdel] -> [update: prox and dual steps, A^T delta_0 of the
+  // next solve] -> [products of the changes, the Sec. 4.1 sums and the next start residual].
   __device__ void solve() {
     const Thr t = th;
     const double alpha = C->alpha, beta = C->beta, gamma = C->gamma, eps = C->eps;
-    const double cg_rel = C->cg_rel;
     const double sqrt_gamma = sqrt(gamma);
     double tau = C->tau, kappa = C->kappa, theta = C->theta, mu = C->mu;
     int64_t total = C->admm_iters;
@@ -480,34 +526,38 @@ struct DeltaSolver {
     int status = 0;
     int since_refresh = 0;
     int64_t next_confirm = 0;
-    double tot[9];
+    double tot[12];
     double inner2 = 0, pres = 0, dres = 0, dgap = 0, ctx = 0, bty = 0;
+    double bound2 = 0.0, rz0 = 0.0;
+    bool cold = true;   // the start residual is below the PCG bound
 
-    // sums in slot S_RES (after a barrier) -> the scalars; tests with `margin` if asked
+    // the twelve sums (after a barrier) -> the scalars, the next PCG start; the Sec. 4.1
+    // tests with `margin` if asked.  Returns the test result, or -1 on a non-finite sum.
     auto absorb = [&](bool with_tests, double margin) -> int {
-      double e[8];
-      totals_x<9, 8>(tot, e, S_RES, [&](const double* a, double* ee) {
+      double e[10];
+      totals_x<12, 10>(tot, e, S_RES, [&](const double* a, double* ee) {
         derive_sums(a, ee, with_tests, margin, tau, kappa, theta);
       });
       inner2 = e[0]; pres = e[1]; dres = e[2]; dgap = e[3]; ctx = e[4]; bty = e[5];
+      bound2 = e[8]; cold = e[9] == 0.0; rz0 = tot[9];
       if (e[6] == 0.0) { flag(DEV_ERR_NONFINITE); return -1; }
       return (int)e[7];
     };
     auto exact = [&](int phase) -> bool {
-      exact_products(tau, theta);
       ++refreshes;
       since_refresh = 0;
-      return sync(phase);
+      return exact_phase(tau, theta, phase);
     };
     // After an update: maintained products (or the scheduled exact recomputation); the
     // Sec. 4.1 tests screened on them with a factor-4 margin and, when the screen passes,
     // decided on exact products (reading A5 cadence; check_every spaces the decisions).
     auto evaluate_update = [&]() -> bool {
       const bool want = C->stop_rule == 0;
-      bool exact_now = ++since_refresh >= kDeltaRefresh;
-      if (exact_now) { if (!exact(P_RES)) return false; }
-      else {
-        maintained_products(tau, theta);
+      const bool exact_now = ++since_refresh >= kDeltaRefresh;
+      if (exact_now) {
+        if (!exact(P_RES)) return false;
+      } else {
+        maintained_phase(tau, theta);
         if (!sync(P_RES)) return false;
       }
       int st = absorb(want, exact_now ? 1.0 : 4.0);
@@ -553,34 +603,34 @@ struct DeltaSolver {
       // ---- one ADMM update -------------------------------------------------
       // projection (Eq. Simple-Update:Affine) with w = u + v: w_y = y (r = 0),
       // w_x = x + s, w_tau = tau + kappa, w_theta = theta + xi;
-      // z = M^{-1} w_yx: G z_y = q = y - Ax - As, z_x = w_x + A^T z_y.
-      auto qf = [&](int i) -> double { return D.y[i] - (D.Ax[i] + D.As[i]); };
-      const double kkt = fmax(pres, fmax(dres, dgap));
-      const double tol = cg_rel > 0.0 ? fmax(C->cg_tol, cg_rel * kkt) : C->cg_tol;
-      const int extrap = (C->cg_warm == 2 && total >= 3) ? 2 : (C->cg_warm >= 1 && total >= 2) ? 1 : 0;
-      const int it = pcg(qf, tol, 0.0, C->cg_max, extrap);
-      if (it == -1) return;
-      if (it == -2) { flag(DEV_ERR_PCG); sync(P_CG_UPD); return; }
+      // z = M^{-1} w_yx: G z_y = q = y - Ax - As, z_x = w_x + A^T z_y.  The start
+      // residual of the correction solve was formed with the last products.
+      int it = 0;
+      if (!cold) {
+        it = pcg_run(rz0, bound2, C->cg_max);
+        if (it == -1) return;
+        if (it == -2) { flag(DEV_ERR_PCG); sync(P_CG_UPD); return; }
+      }
       cgtot += it;
-      // z_y += delta, A^T z_y += A^T delta, z_x = x + s + A^T z_y, H^T z
+      // z_y += delta; A^T z_y = W + wdel; z_x = x + s + A^T z_y; H^T z; the corrections
+      // history and the start of the next solve
+      const int exn = extrap_for(C->cg_warm, total + 1);
       double hz[2] = {0.0, 0.0};
-      {
-        auto g = [&](int i) -> float { return D.dz[i]; };
-        auto e = [&](int j, float v, float) {
-          const double a = D.ATz[j] + (double)v;
-          D.ATz[j] = a;
-          const double zxj = (D.x[j] + D.s[j]) + a;
-          hz[0] += D.c[j] * zxj;
-          hz[1] -= D.cbar[j] * zxj;
-        };
-        sell_rows_g<8, 1, float, float>(D.AT, g, g, e);
+      for (int j = t.gtid; j < D.n; j += t.nthr) {
+        const double a = it > 0 ? D.xsw[j].w + (double)D.wdel[j] : D.xsw[j].w;
+        D.ATz[j] = a;
+        const double zxj = (D.x[j] + D.s[j]) + a;
+        hz[0] += D.c[j] * zxj;
+        hz[1] -= D.cbar[j] * zxj;
       }
       for (int i = t.gtid; i < D.m; i += t.nthr) {
         const float d = D.dz[i];
         const double zyi = D.zy[i] + (double)d;
         D.zy[i] = zyi;
-        D.d2[i] = D.d1[i];
+        const float dprev = D.d1[i];
+        D.d2[i] = dprev;
         D.d1[i] = d;
+        D.dz[i] = start_of(d, dprev, exn);
         hz[0] -= D.b[i] * zyi;
         hz[1] += D.bbar[i] * zyi;
       }
@@ -588,8 +638,9 @@ struct DeltaSolver {
       if (!sync(P_ZX)) return;
       double h[2], sc[6];
       totals_x<2, 6>(h, sc, S_HZ, [&](const double* v, double* e) { scalar_step(v, e, tau, kappa, theta, mu); });
-      // u~_yx = z - [g1 g2] t; relaxation (Sec. 4.2); barrier and dual steps in FP64;
-      // the FP32-rounded changes feed the maintained products
+      // u~_yx = z - [g1 g2] t; relaxation (Sec. 4.2); barrier and dual steps in FP64 for
+      // each column in the epilogue of the A^T delta_0 pass, which also gives the next
+      // W = A^T z_y + A^T delta_0; the FP32-rounded changes feed the maintained products
       const double t1 = sc[0], t2 = sc[1], cmu = sc[5], a1 = 1.0 - alpha;
       for (int i = t.gtid; i < D.m; i += t.nthr) {
         const double uy = D.zy[i] - D.g1y[i] * t1 - D.g2y[i] * t2;
@@ -598,15 +649,23 @@ struct DeltaSolver {
         D.y[i] = yn;
         D.dy[i] = (float)(yn - y0);
       }
-      for (int j = t.gtid; j < D.n; j += t.nthr) {
-        const double x0 = D.x[j], s0 = D.s[j];
-        const double ux = (x0 + s0 + D.ATz[j]) - D.g1x[j] * t1 - D.g2x[j] * t2;
-        const double xh = alpha * ux + a1 * x0;
-        double xn, sn;
-        barrier_step<double>(xh - s0, cmu, xn, sn);
-        D.x[j] = xn;
-        D.s[j] = sn;
-        D.dxs[j] = make_float2((float)(xn - x0), (float)(sn - s0));
+      {
+        auto g = [&](int i) -> float { return D.dz[i]; };
+        auto e = [&](int j, float v, float) {
+          const double x0 = D.x[j], s0 = D.s[j], atz = D.ATz[j];
+          const double ux = (x0 + s0 + atz) - D.g1x[j] * t1 - D.g2x[j] * t2;
+          const double xh = alpha * ux + a1 * x0;
+          double xn, sn;
+          barrier_step<double>(xh - s0, cmu, xn, sn);
+          D.x[j] = xn;
+          D.s[j] = sn;
+          XSW o;
+          o.dx = (float)(xn - x0);
+          o.ds = (float)(sn - s0);
+          o.w = atz + (double)v;
+          D.xsw[j] = o;
+        };
+        sell_rows_g<8, 1, float, float>(D.AT, g, g, e);
       }
       tau = sc[2]; kappa = sc[3]; theta = sc[4];
       if (!sync(P_UPD)) return;

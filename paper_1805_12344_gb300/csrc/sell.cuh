@@ -1,9 +1,11 @@
 // Sliced-ELL (SELL) row products shared by the persistent grid kernels: the
-// thread geometry of a persistent launch, row products with L lanes per row and
-// U gathers in flight per lane, and per-row statistics for the setup.
+// thread geometry of a persistent launch, one generic traversal that folds each
+// row's stored entries into per-lane accumulators with U gathers in flight per
+// lane, and the row products and per-row statistics built on it.
 #pragma once
 
 #include <cstdint>
+#include <type_traits>
 
 #include "abip_device.cuh"
 #include "abip_internal.h"
@@ -22,14 +24,39 @@ struct Thr {
   }
 };
 
-// Row products for every row of a SELL matrix with L lanes per row:
-// dot0 = sum_k A_ik g0(k), dot1 = sum_k A_ik g1(k) (NV = 2), accumulated in Acc;
-// epi(row, dot0, dot1, pv) runs on the first lane of the row with pv = pre(row),
-// which is loaded when the slice starts so the row's own operands arrive while
-// the gathers are in flight.  g0/g1 map a column index to the gathered value.
-// Each lane keeps U gathers in flight.
-template <int L, int U, int NV, typename Acc, typename V, typename G0, typename G1, typename Pre, typename Epi>
-__device__ __forceinline__ void sell_rows_L(const SellMat& S, G0& g0, G1& g1, Pre& pre, Epi& epi) {
+// One batch of B entries starting at entry k of the lane's row: the B index and value
+// loads, then the B gathers, are issued before the first is used.  Positions at or past
+// the slice's width w repeat its last entry with value 0, so every gathered index is in
+// range.
+template <int B, typename V, typename St, typename GF>
+__device__ __forceinline__ void sell_batch(const int32_t* __restrict__ ci, const V* __restrict__ va, int k, int w,
+                                           GF& gf, St& st) {
+  int j[B];
+  V a[B];
+#pragma unroll
+  for (int u = 0; u < B; ++u) {
+    const int kk = min(k + u, w - 1);
+    j[u] = __ldg(ci + kk * 32);
+    a[u] = k + u < w ? __ldg(va + kk * 32) : V(0);
+  }
+#pragma unroll
+  for (int u = 0; u < B; ++u) st.add(a[u], gf(j[u]));
+}
+
+// Generic SELL traversal over the slices of this warp (S.wsl), L lanes per row.
+// For every row: the lane's entries (column j, value a) are folded into an
+// accumulator St by st.add(a, gf(j)); the L lanes of the row are combined by
+// st.template group<L>(); epi(row, st, pv) runs on the row's first lane with
+// pv = pre(row), loaded when the slice starts so the row's own operands arrive while
+// the gathers are in flight.  Entries go in batches of U, the rest of a slice (every
+// lane of a slice holds the same number of entries, so the choice is uniform across
+// the warp) in one batch of the next power of two, so no entry is loaded on its own
+// and at most half of the last batch's loads are repeats.
+//   St: default-constructible (zero); add(V a, const G& g) for the gathered type G;
+//       template <int L> group().
+template <int L, int U, typename V, typename St, typename GF, typename Pre, typename Epi>
+__device__ __forceinline__ void sell_fold_L(const SellMat& S, GF& gf, Pre& pre, Epi& epi) {
+  static_assert(U == 8, "the tail batches below assume U = 8");
   const Thr th;
   constexpr int C = 32 / L;
   const V* __restrict__ val = static_cast<const V*>(S.val);
@@ -42,49 +69,96 @@ __device__ __forceinline__ void sell_rows_L(const SellMat& S, G0& g0, G1& g1, Pr
     const auto pv = pre(owner ? row : -1);
     const int32_t* __restrict__ ci = S.ci + base + th.lane;
     const V* __restrict__ va = val + base + th.lane;
-    Acc a0 = Acc(0), a1 = Acc(0);
+    St st;
     int k = 0;
-    for (; k + U <= w; k += U) {
-      int j[U];
-      Acc a[U];
-#pragma unroll
-      for (int u = 0; u < U; ++u) {
-        j[u] = __ldg(ci + (k + u) * 32);
-        a[u] = static_cast<Acc>(__ldg(va + (k + u) * 32));
-      }
-#pragma unroll
-      for (int u = 0; u < U; ++u) {
-        a0 += a[u] * static_cast<Acc>(g0(j[u]));
-        if (NV == 2) a1 += a[u] * static_cast<Acc>(g1(j[u]));
-      }
-    }
-    for (; k < w; ++k) {
-      const int j = __ldg(ci + k * 32);
-      const Acc a = static_cast<Acc>(__ldg(va + k * 32));
-      a0 += a * static_cast<Acc>(g0(j));
-      if (NV == 2) a1 += a * static_cast<Acc>(g1(j));
-    }
-    if (L > 1) {
-      a0 = group_sum<L>(a0);
-      if (NV == 2) a1 = group_sum<L>(a1);
-    }
-    if (owner) epi(row, a0, a1, pv);
+    for (; k + U <= w; k += U) sell_batch<U, V>(ci, va, k, w, gf, st);
+    const int r = w - k;
+    if (r > 4) sell_batch<8, V>(ci, va, k, w, gf, st);
+    else if (r > 2) sell_batch<4, V>(ci, va, k, w, gf, st);
+    else if (r == 2) sell_batch<2, V>(ci, va, k, w, gf, st);
+    else if (r == 1) sell_batch<1, V>(ci, va, k, w, gf, st);
+    if (L > 1) st.template group<L>();
+    if (owner) epi(row, st, pv);
   }
+}
+
+template <int U, typename V, typename St, typename GF, typename Pre, typename Epi>
+__device__ __forceinline__ void sell_fold(const SellMat& S, GF& gf, Pre& pre, Epi& epi) {
+  switch (S.lanes) {
+    case 1: sell_fold_L<1, U, V, St>(S, gf, pre, epi); break;
+    case 2: sell_fold_L<2, U, V, St>(S, gf, pre, epi); break;
+    case 4: sell_fold_L<4, U, V, St>(S, gf, pre, epi); break;
+    case 8: sell_fold_L<8, U, V, St>(S, gf, pre, epi); break;
+    case 16: sell_fold_L<16, U, V, St>(S, gf, pre, epi); break;
+    default: sell_fold_L<32, U, V, St>(S, gf, pre, epi); break;
+  }
+}
+
+// One or two dot products accumulated in Acc from a gathered pair (x: first vector,
+// y: second vector, unused when NV = 1).
+template <typename Acc, typename P, int NV>
+struct DotSt {
+  using G = P;
+  Acc a0 = Acc(0), a1 = Acc(0);
+  template <typename V>
+  __device__ __forceinline__ void add(V a, const G& g) {
+    const Acc av = static_cast<Acc>(a);
+    a0 += av * static_cast<Acc>(g.x);
+    if (NV == 2) a1 += av * static_cast<Acc>(g.y);
+  }
+  template <int L>
+  __device__ __forceinline__ void group() {
+    a0 = group_sum<L>(a0);
+    if (NV == 2) a1 = group_sum<L>(a1);
+  }
+};
+
+template <typename T>
+struct Two {
+  T x, y;
+};
+template <typename T>
+struct One {
+  T x, y;   // y is never read (NV = 1); kept so DotSt compiles for both shapes
+};
+
+template <typename P, int NV>
+struct MakePair;
+template <typename P>
+struct MakePair<P, 2> {
+  template <typename G0, typename G1>
+  __device__ __forceinline__ static P get(G0& g0, G1& g1, int j) {
+    P p;
+    p.x = g0(j);
+    p.y = g1(j);
+    return p;
+  }
+};
+template <typename P>
+struct MakePair<P, 1> {
+  template <typename G0, typename G1>
+  __device__ __forceinline__ static P get(G0& g0, G1&, int j) {
+    P p;
+    p.x = g0(j);
+    return p;
+  }
+};
+
+// Row products for every row of a SELL matrix: dot0 = sum_k A_ik g0(k), dot1 = sum_k
+// A_ik g1(k) (NV = 2), accumulated in Acc; epi(row, dot0, dot1, pv) with pv = pre(row)
+// on the first lane of the row.  g0/g1 map a column index to the gathered value.
+template <int U, int NV, typename Acc, typename V, typename G0, typename G1, typename Pre, typename Epi>
+__device__ __forceinline__ void sell_rows_gp(const SellMat& S, G0& g0, G1& g1, Pre& pre, Epi& epi) {
+  using R0 = decltype(g0(0));
+  using R1 = decltype(g1(0));
+  using R = typename std::conditional<(sizeof(R0) >= sizeof(R1)), R0, R1>::type;
+  using P = typename std::conditional<NV == 2, Two<R>, One<R>>::type;
+  auto gf = [&](int j) -> P { return MakePair<P, NV>::get(g0, g1, j); };
+  auto e = [&](int row, const DotSt<Acc, P, NV>& st, decltype(pre(0)) pv) { epi(row, st.a0, st.a1, pv); };
+  sell_fold<U, V, DotSt<Acc, P, NV>>(S, gf, pre, e);
 }
 
 struct NoPre {};
-
-template <int U, int NV, typename Acc, typename V, typename G0, typename G1, typename Pre, typename Epi>
-__device__ __forceinline__ void sell_rows_gp(const SellMat& S, G0& g0, G1& g1, Pre& pre, Epi& epi) {
-  switch (S.lanes) {
-    case 1: sell_rows_L<1, U, NV, Acc, V>(S, g0, g1, pre, epi); break;
-    case 2: sell_rows_L<2, U, NV, Acc, V>(S, g0, g1, pre, epi); break;
-    case 4: sell_rows_L<4, U, NV, Acc, V>(S, g0, g1, pre, epi); break;
-    case 8: sell_rows_L<8, U, NV, Acc, V>(S, g0, g1, pre, epi); break;
-    case 16: sell_rows_L<16, U, NV, Acc, V>(S, g0, g1, pre, epi); break;
-    default: sell_rows_L<32, U, NV, Acc, V>(S, g0, g1, pre, epi); break;
-  }
-}
 
 // Row products without prefetched row operands: epi(row, dot0, dot1).
 template <int U, int NV, typename Acc, typename V, typename G0, typename G1, typename Epi>
@@ -95,100 +169,40 @@ __device__ __forceinline__ void sell_rows_g(const SellMat& S, G0& g0, G1& g1, Ep
 }
 
 // Row products with two vectors stored interleaved: gp(k) returns the pair
-// (v0_k, v1_k) in one load (float2 / double2); epi(row, dot0, dot1) on the first
-// lane of the row.  Each lane keeps U pair gathers in flight.
-template <int L, int U, typename Acc, typename V, typename GP, typename Epi>
-__device__ __forceinline__ void sell_pair_L(const SellMat& S, GP& gp, Epi& epi) {
-  const Thr th;
-  constexpr int C = 32 / L;
-  const V* __restrict__ val = static_cast<const V*>(S.val);
-  const int s1 = __ldg(S.wsl + th.gw + 1);
-  for (int sl = __ldg(S.wsl + th.gw); sl < s1; ++sl) {
-    const int64_t base = __ldg(S.sp + sl);
-    const int w = (int)((__ldg(S.sp + sl + 1) - base) >> 5);
-    const int row = __ldg(S.perm + sl * C + th.lane / L);
-    const bool owner = row >= 0 && (th.lane % L) == 0;
-    const int32_t* __restrict__ ci = S.ci + base + th.lane;
-    const V* __restrict__ va = val + base + th.lane;
-    Acc a0 = Acc(0), a1 = Acc(0);
-    int k = 0;
-    for (; k + U <= w; k += U) {
-      int j[U];
-      Acc a[U];
-#pragma unroll
-      for (int u = 0; u < U; ++u) {
-        j[u] = __ldg(ci + (k + u) * 32);
-        a[u] = static_cast<Acc>(__ldg(va + (k + u) * 32));
-      }
-#pragma unroll
-      for (int u = 0; u < U; ++u) {
-        const auto g = gp(j[u]);
-        a0 += a[u] * static_cast<Acc>(g.x);
-        a1 += a[u] * static_cast<Acc>(g.y);
-      }
-    }
-    for (; k < w; ++k) {
-      const int j = __ldg(ci + k * 32);
-      const Acc a = static_cast<Acc>(__ldg(va + k * 32));
-      const auto g = gp(j);
-      a0 += a * static_cast<Acc>(g.x);
-      a1 += a * static_cast<Acc>(g.y);
-    }
-    if (L > 1) {
-      a0 = group_sum<L>(a0);
-      a1 = group_sum<L>(a1);
-    }
-    if (owner) epi(row, a0, a1);
-  }
-}
-
+// (v0_k, v1_k) in one load (float2 / double2); epi(row, dot0, dot1).
 template <int U, typename Acc, typename V, typename GP, typename Epi>
 __device__ __forceinline__ void sell_rows_pair(const SellMat& S, GP& gp, Epi& epi) {
-  switch (S.lanes) {
-    case 1: sell_pair_L<1, U, Acc, V>(S, gp, epi); break;
-    case 2: sell_pair_L<2, U, Acc, V>(S, gp, epi); break;
-    case 4: sell_pair_L<4, U, Acc, V>(S, gp, epi); break;
-    case 8: sell_pair_L<8, U, Acc, V>(S, gp, epi); break;
-    case 16: sell_pair_L<16, U, Acc, V>(S, gp, epi); break;
-    default: sell_pair_L<32, U, Acc, V>(S, gp, epi); break;
-  }
+  using P = decltype(gp(0));
+  auto pre = [](int) { return NoPre{}; };
+  auto e = [&](int row, const DotSt<Acc, P, 2>& st, NoPre) { epi(row, st.a0, st.a1); };
+  sell_fold<U, V, DotSt<Acc, P, 2>>(S, gp, pre, e);
 }
 
-// Per-row sum and sum of squares of a SELL matrix with L lanes per row (setup only).
-template <int L, typename T, typename V, typename Epi>
-__device__ void sell_rowstats_L(const SellMat& S, Epi& epi) {
-  const Thr th;
-  constexpr int C = 32 / L;
-  const V* val = static_cast<const V*>(S.val);
-  const int s1 = S.wsl[th.gw + 1];
-  for (int sl = S.wsl[th.gw]; sl < s1; ++sl) {
-    const int64_t base = S.sp[sl];
-    const int w = (int)((S.sp[sl + 1] - base) >> 5);
-    const int row = S.perm[sl * C + th.lane / L];
-    T sum = T(0), sq = T(0);
-    for (int k = 0; k < w; ++k) {
-      const T a = static_cast<T>(val[base + k * 32 + th.lane]);
-      sum += a;
-      sq += a * a;
-    }
-    if (L > 1) {
-      sum = group_sum<L>(sum);
-      sq = group_sum<L>(sq);
-    }
-    if (row >= 0 && (th.lane % L) == 0) epi(row, sum, sq);
+// Per-row sum and sum of squares of a SELL matrix, accumulated in T (setup only).
+template <typename T>
+struct StatSt {
+  struct G {};
+  T sum = T(0), sq = T(0);
+  template <typename V>
+  __device__ __forceinline__ void add(V a, const G&) {
+    const T t = static_cast<T>(a);
+    sum += t;
+    sq += t * t;
   }
-}
+  template <int L>
+  __device__ __forceinline__ void group() {
+    sum = group_sum<L>(sum);
+    sq = group_sum<L>(sq);
+  }
+};
 
 template <typename T, typename V, typename Epi>
 __device__ void sell_rowstats(const SellMat& S, Epi& epi) {
-  switch (S.lanes) {
-    case 1: sell_rowstats_L<1, T, V>(S, epi); break;
-    case 2: sell_rowstats_L<2, T, V>(S, epi); break;
-    case 4: sell_rowstats_L<4, T, V>(S, epi); break;
-    case 8: sell_rowstats_L<8, T, V>(S, epi); break;
-    case 16: sell_rowstats_L<16, T, V>(S, epi); break;
-    default: sell_rowstats_L<32, T, V>(S, epi); break;
-  }
+  using St = StatSt<T>;
+  auto gf = [](int) { return typename St::G{}; };
+  auto pre = [](int) { return NoPre{}; };
+  auto e = [&](int row, const St& st, NoPre) { epi(row, st.sum, st.sq); };
+  sell_fold<8, V, St>(S, gf, pre, e);
 }
 
 }  // namespace sell

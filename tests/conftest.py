@@ -26,3 +26,23 @@ def oracle_memo():
             _ORACLE_MEMO[key] = fn()
         return _ORACLE_MEMO[key]
     return memo
+
+
+@pytest.fixture(scope="session")
+def oracle_pool():
+    """run(jobs) -> oracle results: jobs are (A, b, c, Params) tuples, solved by
+    oracle.abip_oracle.solve in a pool of spawned processes (spawned, not forked: the
+    parent holds a CUDA context)."""
+    import multiprocessing as mp
+    from concurrent.futures import ProcessPoolExecutor
+
+    from oracle import abip_oracle as O
+
+    ex = ProcessPoolExecutor(max_workers=max(1, min(16, os.cpu_count() or 1)), mp_context=mp.get_context("spawn"))
+
+    def run(jobs):
+        futs = [ex.submit(O.solve, A, b, c, prm) for (A, b, c, prm) in jobs]
+        return [f.result() for f in futs]
+
+    yield run
+    ex.shutdown()
