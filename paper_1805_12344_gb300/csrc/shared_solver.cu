@@ -142,32 +142,148 @@ __global__ void accum_kernel(const float* __restrict__ Cp, int splits, int M, in
 }
 
 // ---------------------------------------------------------------------------
-// One-CTA Cholesky and the explicit inverse of G (setup only, FP64)
+// Blocked Cholesky G = L L^T and the explicit inverse of G (setup only, FP64)
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kThr) cholesky_kernel(double* L, int m, int* err) {
+// Right-looking, kCB-wide block columns (G row-major m x m, lower triangle read and
+// overwritten by L).  For block column k0:
+//   chol_diag_kernel   (one CTA):          factor the diagonal block L_kk in shared memory;
+//   chol_panel_kernel  (CTA per kCB rows): L_ik = G_ik L_kk^{-T} for the rows below;
+//   chol_update_kernel (CTA per tile):     G_ij -= L_ik L_jk^T on the trailing lower
+//                                          triangle, kCB x kCB tiles, 4 x 4 outputs/thread.
+// A non-positive or non-finite pivot sets *err; every later kernel then returns at once.
+constexpr int kCB = 64;
+
+__global__ void __launch_bounds__(kThr) chol_diag_kernel(double* __restrict__ L, int m, int k0, int* err) {
+  __shared__ double T[kCB][kCB + 1];
   __shared__ int ok;
+  if (*err) return;
+  const int nb = min(kCB, m - k0);
+  for (int e = threadIdx.x; e < nb * nb; e += kThr) {
+    const int r = e / nb, c = e % nb;
+    T[r][c] = c <= r ? L[(size_t)(k0 + r) * m + k0 + c] : 0.0;
+  }
   if (threadIdx.x == 0) ok = 1;
   __syncthreads();
-  for (int k = 0; k < m; ++k) {
+  for (int j = 0; j < nb; ++j) {
     if (threadIdx.x == 0) {
-      const double d = L[(size_t)k * m + k];
+      const double d = T[j][j];
       if (!(d > 0.0) || !isfinite(d)) ok = 0;
-      L[(size_t)k * m + k] = sqrt(d);
+      T[j][j] = sqrt(d);
     }
     __syncthreads();
     if (!ok) break;
-    const double dk = L[(size_t)k * m + k];
-    for (int i = k + 1 + threadIdx.x; i < m; i += kThr) L[(size_t)i * m + k] /= dk;
+    const double djj = T[j][j];
+    for (int i = j + 1 + threadIdx.x; i < nb; i += kThr) T[i][j] /= djj;
     __syncthreads();
-    // trailing update of the lower triangle, one row per warp pass
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    for (int i = k + 1 + wid; i < m; i += kThrWarps) {
-      const double lik = L[(size_t)i * m + k];
-      for (int j = k + 1 + lane; j <= i; j += 32) L[(size_t)i * m + j] -= lik * L[(size_t)j * m + k];
+    for (int e = threadIdx.x; e < (nb - j - 1) * (nb - j - 1); e += kThr) {
+      const int i = j + 1 + e / (nb - j - 1), l = j + 1 + e % (nb - j - 1);
+      if (l <= i) T[i][l] -= T[i][j] * T[l][j];
     }
     __syncthreads();
   }
-  if (threadIdx.x == 0 && !ok) *err = DEV_ERR_CHOLESKY;
+  if (!ok) {
+    if (threadIdx.x == 0) atomicExch(err, DEV_ERR_CHOLESKY);
+    return;
+  }
+  for (int e = threadIdx.x; e < nb * nb; e += kThr) {
+    const int r = e / nb, c = e % nb;
+    if (c <= r) L[(size_t)(k0 + r) * m + k0 + c] = T[r][c];
+  }
+}
+
+// rows k0 + kCB + blockIdx.x * kCB ...: x L_kk^T = g  (forward substitution per row)
+constexpr size_t kCholSmem = 2 * sizeof(double) * kCB * (kCB + 1);   // two kCB x (kCB + 1) tiles
+
+__global__ void __launch_bounds__(kThr) chol_panel_kernel(double* __restrict__ L, int m, int k0, const int* err) {
+  extern __shared__ double chol_sm[];
+  auto D = reinterpret_cast<double(*)[kCB + 1]>(chol_sm);
+  auto X = reinterpret_cast<double(*)[kCB + 1]>(chol_sm + kCB * (kCB + 1));
+  if (*err) return;
+  const int nb = min(kCB, m - k0);
+  const int r0 = k0 + nb + blockIdx.x * kCB;
+  const int nr = min(kCB, m - r0);
+  if (nr <= 0) return;
+  for (int e = threadIdx.x; e < nb * nb; e += kThr) {
+    const int r = e / nb, c = e % nb;
+    D[r][c] = c <= r ? L[(size_t)(k0 + r) * m + k0 + c] : 0.0;
+  }
+  for (int e = threadIdx.x; e < nr * nb; e += kThr) {
+    const int r = e / nb, c = e % nb;
+    X[r][c] = L[(size_t)(r0 + r) * m + k0 + c];
+  }
+  __syncthreads();
+  // four threads per row: column j of every row, then the rows' remaining columns
+  const int row = threadIdx.x / 4, q = threadIdx.x % 4;
+  for (int j = 0; j < nb; ++j) {
+    if (row < nr && q == 0) X[row][j] /= D[j][j];
+    __syncthreads();
+    if (row < nr) {
+      const double xj = X[row][j];
+      for (int l = j + 1 + q; l < nb; l += 4) X[row][l] -= xj * D[l][j];
+    }
+    __syncthreads();
+  }
+  for (int e = threadIdx.x; e < nr * nb; e += kThr) {
+    const int r = e / nb, c = e % nb;
+    L[(size_t)(r0 + r) * m + k0 + c] = X[r][c];
+  }
+}
+
+// tile (bi, bj), bi >= bj, of the trailing matrix below and right of block column k0
+__global__ void __launch_bounds__(kThr) chol_update_kernel(double* __restrict__ L, int m, int k0, const int* err) {
+  extern __shared__ double chol_sm[];
+  auto Pi = reinterpret_cast<double(*)[kCB + 1]>(chol_sm);
+  auto Pj = reinterpret_cast<double(*)[kCB + 1]>(chol_sm + kCB * (kCB + 1));
+  if (*err) return;
+  const int bi = blockIdx.y, bj = blockIdx.x;
+  if (bj > bi) return;
+  const int nb = min(kCB, m - k0);
+  const int t0 = k0 + nb;
+  const int i0 = t0 + bi * kCB, j0 = t0 + bj * kCB;
+  const int ni = min(kCB, m - i0), nj = min(kCB, m - j0);
+  for (int e = threadIdx.x; e < kCB * nb; e += kThr) {
+    const int r = e / nb, c = e % nb;
+    Pi[r][c] = r < ni ? L[(size_t)(i0 + r) * m + k0 + c] : 0.0;
+    Pj[r][c] = r < nj ? L[(size_t)(j0 + r) * m + k0 + c] : 0.0;
+  }
+  __syncthreads();
+  const int tr = threadIdx.x / 16, tc = threadIdx.x % 16;
+  double acc[4][4] = {};
+  for (int l = 0; l < nb; ++l) {
+    double a[4], b[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) { a[u] = Pi[tr + 16 * u][l]; b[u] = Pj[tc + 16 * u][l]; }
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int v = 0; v < 4; ++v) acc[u][v] += a[u] * b[v];
+  }
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int i = tr + 16 * u;
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      const int j = tc + 16 * v;
+      if (i < ni && j < nj && j0 + j <= i0 + i) L[(size_t)(i0 + i) * m + j0 + j] -= acc[u][v];
+    }
+  }
+}
+
+// G = L L^T in place (lower triangle), err <- DEV_ERR_CHOLESKY on breakdown.
+cudaError_t cholesky_blocked(double* G, int m, int* err, cudaStream_t st) {
+  cudaError_t e = cudaFuncSetAttribute(chol_panel_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kCholSmem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(chol_update_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kCholSmem);
+  if (e != cudaSuccess) return e;
+  for (int k0 = 0; k0 < m; k0 += kCB) {
+    chol_diag_kernel<<<1, kThr, 0, st>>>(G, m, k0, err);
+    const int rest = m - k0 - kCB;
+    if (rest <= 0) break;
+    const int nt = (rest + kCB - 1) / kCB;
+    chol_panel_kernel<<<nt, kThr, kCholSmem, st>>>(G, m, k0, err);
+    chol_update_kernel<<<dim3(nt, nt), kThr, kCholSmem, st>>>(G, m, k0, err);
+  }
+  return cudaGetLastError();
 }
 
 // Column k of G^{-1} = L^{-T} L^{-1} e_k, one column per CTA pass (w in shared memory).
@@ -245,16 +361,22 @@ __global__ void convert_kernel(const double* __restrict__ src, T* __restrict__ d
     dst[e] = (T)src[e];
 }
 
-// bfloat16 copies of A (m x n) and A^T (n x m) for the tensor-core products; A is exact in
-// bfloat16 (checked by the host), so the conversion loses nothing.
-__global__ void bf16_copies_kernel(const double* __restrict__ A, int m, int n, __nv_bfloat16* __restrict__ A16,
-                                   __nv_bfloat16* __restrict__ AT16) {
+// bfloat16 terms of A (m x n) and A^T (n x m) for the tensor-core products: plane t holds
+// the bfloat16 rounding of what planes 0 .. t-1 leave of A's FP32 value.  One plane is
+// exact for an A representable in bfloat16, three for any A representable in FP32
+// (the host picks `terms`).
+__global__ void bf16_copies_kernel(const double* __restrict__ A, int m, int n, int terms,
+                                   __nv_bfloat16* __restrict__ A16, __nv_bfloat16* __restrict__ AT16) {
   const size_t tot = (size_t)m * n;
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < tot; e += (size_t)gridDim.x * blockDim.x) {
     const int i = (int)(e / n), j = (int)(e % n);
-    const __nv_bfloat16 v = __float2bfloat16_rn((float)A[e]);
-    A16[e] = v;
-    AT16[(size_t)j * m + i] = v;
+    float rest = (float)A[e];
+    for (int t = 0; t < terms; ++t) {
+      const __nv_bfloat16 v = __float2bfloat16_rn(rest);
+      rest -= __bfloat162float(v);
+      A16[t * tot + e] = v;
+      AT16[t * tot + (size_t)j * m + i] = v;
+    }
   }
 }
 
@@ -810,15 +932,15 @@ cudaError_t gemm_acc(bool trans, const float* A, int64_t lda, int M, int N, int 
   return cudaGetLastError();
 }
 
-// Tensor-core product of deltas (tcgen05, A16 exact bfloat16, W split in three bfloat16
-// terms), accumulated into an FP64 running product like gemm_acc.
+// Tensor-core product of deltas (tcgen05, A in `terms` bfloat16 planes, W split in three
+// bfloat16 terms), accumulated into an FP64 running product like gemm_acc.
 struct TcPlan {
   int splits = 1, kchunk = 0;
 };
-TcPlan plan_tc(int M, int N, int K, int sms) {
-  // one wave: CTAs per SM from the two-stage shared memory, split K to fill the SMs
+TcPlan plan_tc(int M, int N, int K, int sms, int terms) {
+  // one wave: CTAs per SM from the staged shared memory, split K to fill the SMs
   TcPlan p;
-  const int occ = std::max(1, (int)((227 * 1024) / tc::tc2_smem_bytes(N)));
+  const int occ = std::max(1, (int)((227 * 1024) / tc::tc2_smem_bytes(N, terms)));
   const int tiles = M / tc::kTM, kblocks = K / tc::kTK;
   int splits = std::max(1, (sms * occ) / tiles);
   splits = std::min(splits, std::max(1, kblocks / 4));
@@ -829,19 +951,41 @@ TcPlan plan_tc(int M, int N, int K, int sms) {
 bool tc_shape_ok(int m, int n, int B) {
   return m % tc::kTM == 0 && n % tc::kTM == 0 && B % 16 == 0 && 2 * B <= 256;
 }
-cudaError_t gemm_tc(const __nv_bfloat16* A16, int64_t lda, int M, int N, int K, const float* W, int64_t ldw, int B,
-                    double* acc64, float* out32, const ShInst* mask, float* work, size_t work_elems,
-                    __nv_bfloat16* wt, int sms, int* err, cudaStream_t st) {
-  const TcPlan p = plan_tc(M, N, K, sms);
+
+// the tcgen05 kernel instance for (stages, terms); nullptr if there is none
+using TcKernel = void (*)(const __nv_bfloat16*, int64_t, int64_t, int, int, int, const __nv_bfloat16*, float*, int,
+                          int*);
+TcKernel tc_kernel_for(int stages, int terms) {
+  if (terms == 1) {
+    switch (stages) {
+      case 4: return tc::tc_gemm2_kernel<4, 1>;
+      case 3: return tc::tc_gemm2_kernel<3, 1>;
+      case 2: return tc::tc_gemm2_kernel<2, 1>;
+      default: return nullptr;
+    }
+  }
+  if (terms == 3) {
+    switch (stages) {
+      case 4: return tc::tc_gemm2_kernel<4, 3>;
+      case 3: return tc::tc_gemm2_kernel<3, 3>;
+      case 2: return tc::tc_gemm2_kernel<2, 3>;
+      default: return nullptr;
+    }
+  }
+  return nullptr;
+}
+
+cudaError_t gemm_tc(const __nv_bfloat16* A16, int64_t lda, int64_t aplane, int terms, int M, int N, int K,
+                    const float* W, int64_t ldw, int B, double* acc64, float* out32, const ShInst* mask, float* work,
+                    size_t work_elems, __nv_bfloat16* wt, int sms, int* err, cudaStream_t st) {
+  const TcPlan p = plan_tc(M, N, K, sms, terms);
   if ((size_t)p.splits * M * N > work_elems) return cudaErrorInvalidValue;
+  const TcKernel kern = tc_kernel_for(tc::tc2_stages(N, terms), terms);
+  if (!kern) return cudaErrorInvalidValue;
   tc::split3_kernel<<<dim3((K + 31) / 32, (N + 31) / 32), dim3(32, 8), 0, st>>>(W, ldw, K, N, wt);
   const dim3 grid(M / tc::kTM, p.splits);
-  const size_t smem = tc::tc2_smem_bytes(N);
-  switch (tc::tc2_stages(N)) {
-    case 4: tc::tc_gemm2_kernel<4><<<grid, tc::kTCThreads, smem, st>>>(A16, lda, M, N, K, wt, work, p.kchunk, err); break;
-    case 3: tc::tc_gemm2_kernel<3><<<grid, tc::kTCThreads, smem, st>>>(A16, lda, M, N, K, wt, work, p.kchunk, err); break;
-    default: tc::tc_gemm2_kernel<2><<<grid, tc::kTCThreads, smem, st>>>(A16, lda, M, N, K, wt, work, p.kchunk, err); break;
-  }
+  kern<<<grid, tc::kTCThreads, tc::tc2_smem_bytes(N, terms), st>>>(A16, lda, aplane, M, N, K, wt, work, p.kchunk,
+                                                                  err);
   const size_t MN = (size_t)M * N;
   const int rb = (int)std::min<size_t>((MN + kThr - 1) / kThr, (size_t)sms * 8);
   accum_kernel<<<std::max(rb, 1), kThr, 0, st>>>(work, p.splits, M, N, B, acc64, out32, mask);
@@ -899,12 +1043,14 @@ int shared_batch_run(const SharedBatchArgs& a, std::vector<SharedBatchResult>& o
                                 gemm_work<double>(m, 2 * B, m, sms), gemm_work<double>(n, 2 * B, m, sms),
                                 gemm_work<double>(n, B, m, sms), gemm_work<double>(m, B, m, sms)});
   const bool tc = mixed && a.prm.tc != 0 && tc_shape_ok(m, n, B);
+  const int terms = a.prm.tc == 3 ? 3 : 1;   // bfloat16 planes of A on the tensor-core path
+  const size_t aplane = (size_t)m * n;
   size_t wk32 = mixed ? std::max({gemm_work<float>(m, 2 * B, n, sms), gemm_work<float>(n, B, m, sms),
                                   gemm_work<float>(m, B, m, sms)})
                       : 0;
   if (tc)
-    wk32 = std::max({wk32, (size_t)plan_tc(m, 2 * B, n, sms).splits * m * 2 * B,
-                     (size_t)plan_tc(n, B, m, sms).splits * n * B});
+    wk32 = std::max({wk32, (size_t)plan_tc(m, 2 * B, n, sms, terms).splits * m * 2 * B,
+                     (size_t)plan_tc(n, B, m, sms, terms).splits * n * B});
   ShView<double> V{};
   __nv_bfloat16 *A16 = nullptr, *AT16 = nullptr, *WT16 = nullptr;
   double *A64 = nullptr, *AT64 = nullptr, *G = nullptr, *Ginv64 = nullptr, *Ae = nullptr, *work64 = nullptr;
@@ -947,8 +1093,8 @@ int shared_batch_run(const SharedBatchArgs& a, std::vector<SharedBatchResult>& o
     V.AXS = bp.take<double>((size_t)m * 2 * B); V.ATY = bp.take<double>((size_t)n * B);
     V.Q = bp.take<double>((size_t)m * B); V.ZY = bp.take<double>((size_t)m * B); V.ZX = bp.take<double>((size_t)n * B);
     if (tc) {
-      A16 = bp.take<__nv_bfloat16>((size_t)m * n);
-      AT16 = bp.take<__nv_bfloat16>((size_t)n * m);
+      A16 = bp.take<__nv_bfloat16>(terms * aplane);
+      AT16 = bp.take<__nv_bfloat16>(terms * aplane);
       WT16 = bp.take<__nv_bfloat16>(3 * std::max((size_t)2 * B * n, (size_t)B * m));
     }
     if (mixed) {
@@ -1009,7 +1155,7 @@ int shared_batch_run(const SharedBatchArgs& a, std::vector<SharedBatchResult>& o
   // G = I + A A^T (Sec. 4.4), its Cholesky factor and the explicit inverse
   transpose_kernel<double><<<dim3((n + 31) / 32, (m + 31) / 32), dim3(32, 8), 0, st>>>(A64, m, n, AT64);
   ck(gemm<double>(false, A64, n, m, m, n, AT64, m, G, work64, wk64, sms, st, 1.0), "Gram");
-  cholesky_kernel<<<1, kThr, 0, st>>>(G, m, derr);
+  ck(cholesky_blocked(G, m, derr, st), "Cholesky");
   const size_t inv_smem = (size_t)m * 8;
   ck(cudaFuncSetAttribute(inverse_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)inv_smem), "smem");
   inverse_kernel<<<std::min(m, sms * 2), kThr, inv_smem, st>>>(G, m, Ginv64);
@@ -1027,14 +1173,12 @@ int shared_batch_run(const SharedBatchArgs& a, std::vector<SharedBatchResult>& o
   if (mixed) {
     const int cb = sms * 8;
     if (tc) {
-      bf16_copies_kernel<<<cb, kThr, 0, st>>>(A64, m, n, A16, AT16);
+      bf16_copies_kernel<<<cb, kThr, 0, st>>>(A64, m, n, terms, A16, AT16);
       for (int N : {B, 2 * B}) {
-        const int smem = (int)tc::tc2_smem_bytes(N);
-        switch (tc::tc2_stages(N)) {
-          case 4: ck(cudaFuncSetAttribute(tc::tc_gemm2_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem), "tc smem"); break;
-          case 3: ck(cudaFuncSetAttribute(tc::tc_gemm2_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem), "tc smem"); break;
-          default: ck(cudaFuncSetAttribute(tc::tc_gemm2_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem), "tc smem"); break;
-        }
+        const TcKernel kern = tc_kernel_for(tc::tc2_stages(N, terms), terms);
+        if (!kern) ck(cudaErrorInvalidValue, "tc stages");
+        else ck(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)tc::tc2_smem_bytes(N, terms)), "tc smem");
       }
     } else {
       convert_kernel<float><<<cb, kThr, 0, st>>>(A64, A32, (size_t)m * n);
@@ -1093,7 +1237,8 @@ int shared_batch_run(const SharedBatchArgs& a, std::vector<SharedBatchResult>& o
     refresh();
     // projection on the change of Q: ZY += G^{-1} dQ, A^T ZY += A^T (G^{-1} dQ)
     ck(gemm_acc(false, Ginv32, m, m, B, m, dQ, B, B, V.ZY, dZY, insts, work32, wk32, sms, st), "Ginv dQ");
-    if (tc) ck(gemm_tc(AT16, m, n, B, m, dZY, B, B, ATZY, nullptr, nullptr, work32, wk32, WT16, sms, derr + 1, st),
+    if (tc) ck(gemm_tc(AT16, m, aplane, terms, n, B, m, dZY, B, B, ATZY, nullptr, nullptr, work32, wk32, WT16, sms,
+                       derr + 1, st),
                "A^T dZY");
     else ck(gemm_acc(true, A32, n, n, B, m, dZY, B, B, ATZY, nullptr, nullptr, work32, wk32, sms, st), "A^T dZY");
     hz_delta_kernel<<<red_ctas, kThr, 0, st>>>(V, ATZY, Qprev, insts, partials);
@@ -1102,9 +1247,11 @@ int shared_batch_run(const SharedBatchArgs& a, std::vector<SharedBatchResult>& o
     update_kernel<double><<<eb, kThr, 0, st>>>(V, insts, a.prm, dY, dXS);
     // maintained products of the new state: AX, AS += A [dX dS], A^T Y += A^T dY
     if (tc) {
-      ck(gemm_tc(A16, n, m, 2 * B, n, dXS, 2 * B, B, V.AXS, nullptr, nullptr, work32, wk32, WT16, sms, derr + 1, st),
+      ck(gemm_tc(A16, n, aplane, terms, m, 2 * B, n, dXS, 2 * B, B, V.AXS, nullptr, nullptr, work32, wk32, WT16, sms,
+                 derr + 1, st),
          "A dXS");
-      ck(gemm_tc(AT16, m, n, B, m, dY, B, B, V.ATY, nullptr, nullptr, work32, wk32, WT16, sms, derr + 1, st),
+      ck(gemm_tc(AT16, m, aplane, terms, n, B, m, dY, B, B, V.ATY, nullptr, nullptr, work32, wk32, WT16, sms,
+                 derr + 1, st),
          "A^T dY");
     } else {
       ck(gemm_acc(false, A32, n, m, 2 * B, n, dXS, 2 * B, B, V.AXS, nullptr, nullptr, work32, wk32, sms, st), "A dXS");

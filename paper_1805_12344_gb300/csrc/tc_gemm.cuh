@@ -1,21 +1,23 @@
 // tcgen05 (5th-generation tensor core) GEMM for the shared-A batch, sm_103a.
 //
-//   Cpart[z][M x N] (FP32) = A16[M x K_z] * W[K_z x N]
+//   Cpart[z][M x N] (FP32) = A[M x K_z] * W[K_z x N]
 //
-// A16: BF16, row-major (K contiguous), exactly the shared matrix (the batch uses this
-// path only when A is representable in bfloat16).  W: FP32 row-major (N contiguous), the
-// changes of the batched iterates; each element is split into three bfloat16 terms
-// w = hi + mid + lo (each the bfloat16 rounding of the remainder), so the three
-// accumulated MMAs reproduce an FP32-accurate product: every BF16 x BF16 product is exact
-// and the accumulation is FP32 in tensor memory.
+// A: TA bfloat16 terms A16[t] (M x lda each, row-major, K contiguous) with A = sum of the
+// terms, each the bfloat16 rounding of what the terms before it leave: TA = 1 when A is
+// exact in bfloat16, TA = 3 for any A exact in FP32 (8 + 8 + 8 significant bits).  W: FP32
+// row-major (N contiguous), the changes of the batched iterates, each element split the
+// same way into three bfloat16 terms.  Every BF16 x BF16 product is exact and the
+// accumulation is FP32 in tensor memory; of the term products A_a W_w the kernel issues
+// those with a + w <= 2 (3 for TA = 1, 6 for TA = 3): the ones left out are below
+// 2^-24 of the product, so the result has FP32 accuracy.
 //
 // One CTA (128 threads) owns a 128-row tile of C and one K range (split-K over
-// gridDim.y).  Per 64-wide K step the A tile and the three W tiles sit in shared memory in
-// the no-swizzle K-major core-matrix layout (8 rows x 16 bytes per core matrix; core
+// gridDim.y).  Per 64-wide K step the TA A tiles and the three W tiles sit in shared memory
+// in the no-swizzle K-major core-matrix layout (8 rows x 16 bytes per core matrix; core
 // matrices adjacent in K are 128 bytes apart, adjacent in M/N 1024 bytes); one thread
-// issues 4 x 3 tcgen05.mma (K = 16 each) into the TMEM accumulator and commits them to an
-// mbarrier.  The epilogue reads the accumulator with tcgen05.ld (warp w owns TMEM lanes
-// 32w..32w+31, one lane per row) and writes the FP32 partial tile.
+// issues 4 x (3 or 6) tcgen05.mma (K = 16 each) into the TMEM accumulator and commits them
+// to an mbarrier.  The epilogue reads the accumulator with tcgen05.ld (warp w owns TMEM
+// lanes 32w..32w+31, one lane per row) and writes the FP32 partial tile.
 #pragma once
 
 #include <cstdint>
@@ -183,24 +185,32 @@ __device__ __forceinline__ void cp_async_wait() {
   asm volatile("cp.async.wait_group %0;" ::"n"(NPEND) : "memory");
 }
 
-__host__ __device__ inline size_t tc2_stage_bytes(int N) {
-  return static_cast<size_t>(kTM) * kTK * 2 + 3 * static_cast<size_t>(N) * kTK * 2;
+__host__ __device__ inline size_t tc2_stage_bytes(int N, int TA) {
+  return static_cast<size_t>(TA) * kTM * kTK * 2 + 3 * static_cast<size_t>(N) * kTK * 2;
 }
-// shared-memory stages: as many as fit in about 200 KB (4 for N <= 64, 3 up to N = 128)
-__host__ __device__ inline int tc2_stages(int N) { return N <= 64 ? 4 : (N <= 128 ? 3 : 2); }
-__host__ __device__ inline size_t tc2_smem_bytes(int N) { return 1024 + tc2_stages(N) * tc2_stage_bytes(N); }
+// shared-memory stages: as many as fit in the 227 KB a CTA may use (less 2 KB for the
+// 1024-byte alignment of the tiles and the static variables), at most 4
+constexpr size_t kTcSmemCap = 227 * 1024 - 2048;
+__host__ __device__ inline int tc2_stages(int N, int TA) {
+  const int s = static_cast<int>(kTcSmemCap / tc2_stage_bytes(N, TA));
+  return s < 4 ? s : 4;
+}
+__host__ __device__ inline size_t tc2_smem_bytes(int N, int TA) {
+  return 1024 + tc2_stages(N, TA) * tc2_stage_bytes(N, TA);
+}
 
 // Requirements (refused on the device with kErrShape): M % 128 == 0, K % 64 == 0,
-// kchunk % 64 == 0, N % 16 == 0 and 16 <= N <= 256, lda % 8 == 0, A16 and Wt 16-byte
-// aligned.  Dynamic shared memory: tc2_smem_bytes(N).
-template <int S>
+// kchunk % 64 == 0, N % 16 == 0 and 16 <= N <= 256, lda % 8 == 0, aplane % 8 == 0, A16 and
+// Wt 16-byte aligned, tc2_stages(N, TA) == S >= 2.  A16: TA planes aplane elements apart.
+// Dynamic shared memory: tc2_smem_bytes(N, TA).
+template <int S, int TA>
 __global__ void __launch_bounds__(kTCThreads, 1)
-    tc_gemm2_kernel(const __nv_bfloat16* __restrict__ A16, int64_t lda, int M, int N, int K,
+    tc_gemm2_kernel(const __nv_bfloat16* __restrict__ A16, int64_t lda, int64_t aplane, int M, int N, int K,
                     const __nv_bfloat16* __restrict__ Wt, float* __restrict__ Cp, int kchunk, int* err) {
   // shapes the tiles and the 16-byte copies need; anything else is refused here
   if (M % kTM != 0 || K % kTK != 0 || kchunk <= 0 || kchunk % kTK != 0 || N % 16 != 0 || N < 16 || N > 256 ||
-      lda % 8 != 0 || (reinterpret_cast<uintptr_t>(A16) & 15) != 0 || (reinterpret_cast<uintptr_t>(Wt) & 15) != 0 ||
-      tc2_stages(N) != S) {
+      lda % 8 != 0 || aplane % 8 != 0 || (reinterpret_cast<uintptr_t>(A16) & 15) != 0 ||
+      (reinterpret_cast<uintptr_t>(Wt) & 15) != 0 || tc2_stages(N, TA) != S || S < 2) {
     if (threadIdx.x == 0 && blockIdx.x == 0 && blockIdx.y == 0) atomicExch(err, kErrShape);
     return;
   }
@@ -209,8 +219,8 @@ __global__ void __launch_bounds__(kTCThreads, 1)
   __shared__ uint32_t tslot;
   __shared__ int failed;
   uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(tc_smem_raw) + 1023) & ~uintptr_t(1023));
-  const uint32_t stage = static_cast<uint32_t>(tc2_stage_bytes(N));
-  const uint32_t abytes = kTM * kTK * 2, wbytes = static_cast<uint32_t>(N) * kTK * 2;
+  const uint32_t stage = static_cast<uint32_t>(tc2_stage_bytes(N, TA));
+  const uint32_t atile = kTM * kTK * 2, abytes = TA * atile, wbytes = static_cast<uint32_t>(N) * kTK * 2;
   const size_t plane = static_cast<size_t>(N) * K;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int m0 = blockIdx.x * kTM;
@@ -234,9 +244,9 @@ __global__ void __launch_bounds__(kTCThreads, 1)
   auto load_stage = [&](int j) {
     const int k0 = kz0 + j * kTK;
     const uint32_t sa = s0 + (j % S) * stage;
-    for (int e = tid; e < kTM * 8; e += kTCThreads) {
-      const int r = e >> 3, kc = e & 7;
-      cp_async16(sa + core_off(r, kc), A16 + (size_t)(m0 + r) * lda + k0 + kc * 8);
+    for (int e = tid; e < TA * kTM * 8; e += kTCThreads) {
+      const int t = e / (kTM * 8), rem = e % (kTM * 8), r = rem >> 3, kc = rem & 7;
+      cp_async16(sa + t * atile + core_off(r, kc), A16 + t * aplane + (size_t)(m0 + r) * lda + k0 + kc * 8);
     }
     for (int e = tid; e < 3 * N * 8; e += kTCThreads) {
       const int t = e / (N * 8), rem = e % (N * 8), n = rem >> 3, kc = rem & 7;
@@ -274,11 +284,14 @@ __global__ void __launch_bounds__(kTCThreads, 1)
       const uint32_t a0 = s0 + (j % S) * stage, w0 = a0 + abytes;
 #pragma unroll
       for (int s = 0; s < kTK / 16; ++s) {
-        const uint64_t ad = smem_desc(a0 + s * 256, 128, 1024);
 #pragma unroll
-        for (int t = 0; t < 3; ++t) {
-          const uint64_t bd = smem_desc(w0 + t * wbytes + s * 256, 128, 1024);
-          mma_bf16(tmem, ad, bd, idesc, (j > 0 || s > 0 || t > 0) ? 1u : 0u);
+        for (int ta = 0; ta < TA; ++ta) {
+          const uint64_t ad = smem_desc(a0 + ta * atile + s * 256, 128, 1024);
+#pragma unroll
+          for (int t = 0; t + ta < 3; ++t) {
+            const uint64_t bd = smem_desc(w0 + t * wbytes + s * 256, 128, 1024);
+            mma_bf16(tmem, ad, bd, idesc, (j > 0 || s > 0 || ta > 0 || t > 0) ? 1u : 0u);
+          }
         }
       }
       mma_commit(&mbar[j % S]);

@@ -183,6 +183,43 @@ def planted_sparse(m: int = 100000, n_r: Optional[int] = None, per_col: int = 8,
               meta=dict(kind="planted_sparse", m=m, n=n, nnz=A.nnz, per_col=per_col))
 
 
+RANDOM_UDV = 5        # the random dense LPs of the paper's experiments (Sec. 5.1)
+
+
+def _sprandn(rng: np.random.Generator, rows: int, cols: int, density: float) -> np.ndarray:
+    """Dense array holding a sparse random matrix: round(density * rows * cols) positions
+    chosen uniformly without repetition, values N(0, 1), zeros elsewhere."""
+    M = np.zeros(rows * cols)
+    k = int(round(density * rows * cols))
+    M[rng.choice(rows * cols, k, replace=False)] = rng.standard_normal(k)
+    return M.reshape(rows, cols)
+
+
+def random_udv(m: int = 500, n: int = 5000, seed: Optional[int] = None) -> LP:
+    """The random dense LP of Sec. 5.1 (Tables 1 and 2): A = U^T D V with D = diag(N(0,1)^m),
+    U (m x m) and V (m x n) sparse random with density 0.2 and N(0,1) values.  The planted
+    x has 60 % of its entries 0, 10 % |N(0,1)| * 10 and the other 30 % |N(0,1)| / 10; s is
+    |N(0,1)| on x's zero set and 0 elsewhere (x o s = 0); y ~ N(0,1); b = A x, c = A^T y + s.
+    The paper calls x and s Gaussian; their magnitudes are used here so that x, s >= 0
+    (the LP is in standard form).  The optimal value is c^T x = b^T y."""
+    rng = np.random.default_rng(seed_for(RANDOM_UDV) if seed is None else seed)
+    U = _sprandn(rng, m, m, 0.2)
+    D = rng.standard_normal(m)
+    V = _sprandn(rng, m, n, 0.2)
+    A = U.T @ (D[:, None] * V)
+    perm = rng.permutation(n)
+    n0, n1 = int(round(0.6 * n)), int(round(0.1 * n))
+    x0 = np.abs(rng.standard_normal(n))
+    x0[perm[:n0]] = 0.0
+    x0[perm[n0:n0 + n1]] *= 10.0
+    x0[perm[n0 + n1:]] /= 10.0
+    s0 = np.zeros(n)
+    s0[perm[:n0]] = np.abs(rng.standard_normal(n0))
+    y0 = rng.standard_normal(m)
+    return LP(A=A, b=A @ x0, c=A.T @ y0 + s0, x0=x0, y0=y0, s0=s0, expect="optimal",
+              meta=dict(kind="random_udv", m=m, n=n))
+
+
 def tiny_random(m: int, n: int, seed: int) -> LP:
     """Tiny unplanted LP with random signs: may be optimal, infeasible or unbounded."""
     rng = np.random.default_rng(seed)
@@ -298,14 +335,18 @@ class SharedBatch:
 
 
 def basis_pursuit(m: int = 2048, n_d: int = 8192, batch: int = 64, density: float = 0.05,
-                  seed: Optional[int] = None) -> SharedBatch:
+                  seed: Optional[int] = None, bf16: bool = False) -> SharedBatch:
     """Basis pursuit  min ||x||_1  s.t.  D x = b_k  as the standard-form LP with x = x+ - x-:
-    A = [D, -D] (m x 2 n_d), c = e, b_k = D x_true_k.  D iid N(0, 1/m) rounded to
-    bfloat16-representable values; x_true_k has round(density * n_d) nonzeros N(0, 1).
-    meta["x_true"]: the planted sparse vectors (x_true is feasible, so the optimum is at most
-    ||x_true||_1, with equality when l1 recovery succeeds)."""
+    A = [D, -D] (m x 2 n_d), c = e, b_k = D x_true_k (in float64 from the exact D).  D iid
+    N(0, 1/m) in float32 (with bf16=True rounded further to bfloat16-representable values,
+    a case the tensor-core path stores in one bfloat16 term); x_true_k has
+    round(density * n_d) nonzeros N(0, 1).  meta["x_true"]: the planted sparse vectors
+    (x_true is feasible, so the optimum is at most ||x_true||_1, with equality when l1
+    recovery succeeds)."""
     rng = np.random.default_rng(seed_for(BASIS_PURSUIT) if seed is None else seed)
-    D = bf16_exact(rng.standard_normal((m, n_d)) / np.sqrt(m))
+    D = (rng.standard_normal((m, n_d)) / np.sqrt(m)).astype(np.float32).astype(np.float64)
+    if bf16:
+        D = bf16_exact(D)
     A = np.concatenate([D, -D], axis=1)
     k = int(round(density * n_d))
     xs, bs = [], []
@@ -317,4 +358,4 @@ def basis_pursuit(m: int = 2048, n_d: int = 8192, batch: int = 64, density: floa
         bs.append(D @ xt)
     cs = [np.ones(2 * n_d) for _ in range(batch)]
     return SharedBatch(A=A, bs=bs, cs=cs, meta=dict(kind="basis_pursuit", m=m, n=2 * n_d, n_d=n_d,
-                                                    density=density, x_true=xs))
+                                                    density=density, x_true=xs, bf16=bf16))

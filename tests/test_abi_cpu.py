@@ -118,13 +118,26 @@ def test_shared_and_backward_argument_errors_without_device(lib):
     with pytest.raises(abip.AbipError) as e:
         abip.abip_solve_batch_shared(csr, [np.ones(2)], [np.ones(3)])
     assert e.value.code == abip.ABIP_E_UNSUPPORTED
-    # the tensor-core products need A exact in bfloat16
+    # the tensor-core products hold A as bfloat16 terms of its FP32 value: beyond FP32's range
     A = np.full((2, 3), 0.1)
+    A[1, 2] = 1e39
     with pytest.raises(abip.AbipError) as e:
         abip.abip_solve_batch_shared(A, [np.ones(2)], [np.ones(3)],
                                      abip.default_params(precision=abip.ABIP_PREC_MIXED_BF16))
     assert e.value.code == abip.ABIP_E_INVALID_ARG
-    assert b"bfloat16" in lib.abip_last_error(None)
+    assert b"FP32 range" in lib.abip_last_error(None)
+    # the Barzilai-Borwein selection is provided on the dense FP64 path only
+    with pytest.raises(abip.AbipError) as e:
+        abip.abip_solve_batch_shared(np.eye(2, 3), [np.ones(2)], [np.ones(3)], abip.default_params(bb_beta=1))
+    assert e.value.code == abip.ABIP_E_UNSUPPORTED
+    with pytest.raises(abip.AbipError) as e:
+        abip.abip_solve_batch([np.eye(2, 3)], [np.ones(2)], [np.ones(3)],
+                              abip.default_params(bb_beta=1, precision=abip.ABIP_PREC_MIXED))
+    assert e.value.code == abip.ABIP_E_UNSUPPORTED
+    for bad in (dict(bb_beta=2), dict(bb_beta=1, eps_cor=-1.0), dict(bb_beta=1, bb_max_redo=-1)):
+        with pytest.raises(abip.AbipError) as e:
+            abip.abip_solve_batch([np.eye(2, 3)], [np.ones(2)], [np.ones(3)], abip.default_params(**bad))
+        assert e.value.code == abip.ABIP_E_INVALID_ARG
     # no gradient at an infeasibility certificate (status from the forward's infos)
     with pytest.raises(abip.AbipError) as e:
         abip.abip_backward_batch([np.eye(2, 3)], [np.ones(2)], [np.ones(3)], [np.ones(3)], [np.ones(2)],

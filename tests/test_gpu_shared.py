@@ -136,10 +136,13 @@ def test_shared_chunks_past_64(abip):
         assert abs(infos[k]["obj"] - ref.obj) <= OBJ_TOL * max(1.0, abs(ref.obj))
 
 
-def test_shared_tensor_cores_end_to_end(abip):
-    """ABIP_PREC_MIXED_BF16: the products with A run on tcgen05 (A exact in bfloat16, the
-    changes split in three bfloat16 terms); same bars as the other paths."""
-    sb = W.basis_pursuit(128, 256, batch=16, seed=9)
+@pytest.mark.parametrize("m,nd,bf16", [(128, 256, False), (256, 1024, False), (128, 256, True)])
+def test_shared_tensor_cores_end_to_end(abip, m, nd, bf16):
+    """ABIP_PREC_MIXED_BF16: the products with A run on tcgen05, the changes split in three
+    bfloat16 terms and A in three (float32 D, as the basis-pursuit workload draws it) or in
+    one (D rounded to bfloat16); same bars as the other paths, plus the l1 bound
+    ||x_true||_1 (x_true is feasible).  The oracle solves three of the sixteen instances."""
+    sb = W.basis_pursuit(m, nd, batch=16, seed=9 + m, bf16=bf16)
     prm = abip.default_params(precision=abip.ABIP_PREC_MIXED_BF16)
     infos, xs, ys, ss = abip.abip_solve_batch_shared(sb.A, sb.bs, sb.cs, prm)
     for k in range(16):
@@ -147,6 +150,7 @@ def test_shared_tensor_cores_end_to_end(abip):
         assert f["status"] == O.OPTIMAL, (k, f["status_name"])
         assert max(f["pres"], f["dres"], f["dgap"]) <= 1e-6
         assert np.linalg.norm(sb.A @ xs[k] - sb.bs[k]) <= 1e-6 * (1 + np.linalg.norm(sb.bs[k])) * 1.01
+        assert np.linalg.norm(sb.A.T @ ys[k] + ss[k] - sb.cs[k]) <= 1e-6 * (1 + np.linalg.norm(sb.cs[k])) * 1.01
         assert f["obj"] <= np.abs(sb.meta["x_true"][k]).sum() * (1 + 1e-5)
     for k in (0, 7, 15):
         ref = O.solve(sb.A, sb.bs[k], sb.cs[k])
@@ -154,8 +158,27 @@ def test_shared_tensor_cores_end_to_end(abip):
         assert abs(infos[k]["obj"] - ref.obj) <= OBJ_TOL * max(1.0, abs(ref.obj))
 
 
-def test_shared_tensor_cores_need_bfloat16_A(abip):
+def test_shared_tensor_cores_refuse_A_beyond_fp32(abip):
+    """The tensor-core path holds A as bfloat16 terms of its FP32 value: an entry beyond
+    the FP32 range cannot be represented and is refused."""
     A, bs, cs, _ = _shared_planted(128, 256, 16, seed=3)
+    A = A.copy()
+    A[5, 7] = 1e39
     with pytest.raises(abip.AbipError) as e:
         abip.abip_solve_batch_shared(A, bs, cs, abip.default_params(precision=abip.ABIP_PREC_MIXED_BF16))
     assert e.value.code == abip.ABIP_E_INVALID_ARG
+
+
+def test_shared_tensor_cores_general_A_matches_fp32_products(abip):
+    """A general float64 A (not exact in FP32): the tensor-core path (A in three bfloat16
+    terms of its FP32 rounding) and the FP32 SIMT path reach the same statuses and optima."""
+    A, bs, cs, expect = _shared_planted(128, 256, 14, seed=4)   # 16 instances: the tensor-core shape
+    assert len(bs) == 16
+    p1 = abip.default_params(precision=abip.ABIP_PREC_MIXED_BF16)
+    p2 = abip.default_params(precision=abip.ABIP_PREC_MIXED)
+    i1, *_ = abip.abip_solve_batch_shared(A, bs, cs, p1)
+    i2, *_ = abip.abip_solve_batch_shared(A, bs, cs, p2)
+    for k in range(16):
+        assert i1[k]["status"] == i2[k]["status"] == expect[k]
+        if expect[k] == O.OPTIMAL:
+            assert abs(i1[k]["obj"] - i2[k]["obj"]) <= OBJ_TOL * max(1.0, abs(i2[k]["obj"]))
