@@ -638,9 +638,9 @@ struct DeltaSolver {
       if (!sync(P_ZX)) return;
       double h[2], sc[6];
       totals_x<2, 6>(h, sc, S_HZ, [&](const double* v, double* e) { scalar_step(v, e, tau, kappa, theta, mu); });
-      // u~_yx = z - [g1 g2] t; relaxation (Sec. 4.2); barrier and dual steps in FP64 for
-      // each column in the epilogue of the A^T delta_0 pass, which also gives the next
-      // W = A^T z_y + A^T delta_0; the FP32-rounded changes feed the maintained products
+      // u~_yx = z - [g1 g2] t; relaxation (Sec. 4.2); barrier and dual steps in FP64 (the
+      // FP32-rounded changes feed the maintained products); and, independent of them, the
+      // next W = A^T z_y + A^T delta_0 from an A^T pass
       const double t1 = sc[0], t2 = sc[1], cmu = sc[5], a1 = 1.0 - alpha;
       for (int i = t.gtid; i < D.m; i += t.nthr) {
         const double uy = D.zy[i] - D.g1y[i] * t1 - D.g2y[i] * t2;
@@ -649,22 +649,20 @@ struct DeltaSolver {
         D.y[i] = yn;
         D.dy[i] = (float)(yn - y0);
       }
+      for (int j = t.gtid; j < D.n; j += t.nthr) {
+        const double x0 = D.x[j], s0 = D.s[j];
+        const double ux = (x0 + s0 + D.ATz[j]) - D.g1x[j] * t1 - D.g2x[j] * t2;
+        const double xh = alpha * ux + a1 * x0;
+        double xn, sn;
+        barrier_step<double>(xh - s0, cmu, xn, sn);
+        D.x[j] = xn;
+        D.s[j] = sn;
+        D.xsw[j].dx = (float)(xn - x0);
+        D.xsw[j].ds = (float)(sn - s0);
+      }
       {
         auto g = [&](int i) -> float { return D.dz[i]; };
-        auto e = [&](int j, float v, float) {
-          const double x0 = D.x[j], s0 = D.s[j], atz = D.ATz[j];
-          const double ux = (x0 + s0 + atz) - D.g1x[j] * t1 - D.g2x[j] * t2;
-          const double xh = alpha * ux + a1 * x0;
-          double xn, sn;
-          barrier_step<double>(xh - s0, cmu, xn, sn);
-          D.x[j] = xn;
-          D.s[j] = sn;
-          XSW o;
-          o.dx = (float)(xn - x0);
-          o.ds = (float)(sn - s0);
-          o.w = atz + (double)v;
-          D.xsw[j] = o;
-        };
+        auto e = [&](int j, float v, float) { D.xsw[j].w = D.ATz[j] + (double)v; };
         sell_rows_g<8, 1, float, float>(D.AT, g, g, e);
       }
       tau = sc[2]; kappa = sc[3]; theta = sc[4];

@@ -26,8 +26,8 @@ struct Thr {
 
 // One batch of B entries starting at entry k of the lane's row: the B index and value
 // loads, then the B gathers, are issued before the first is used.  Positions at or past
-// the slice's width w repeat its last entry with value 0, so every gathered index is in
-// range.
+// the slice's width w (none when the batch is full) repeat its last entry with value 0,
+// so every gathered index is in range.
 template <int B, typename V, typename St, typename GF>
 __device__ __forceinline__ void sell_batch(const int32_t* __restrict__ ci, const V* __restrict__ va, int k, int w,
                                            GF& gf, St& st) {
@@ -48,15 +48,14 @@ __device__ __forceinline__ void sell_batch(const int32_t* __restrict__ ci, const
 // accumulator St by st.add(a, gf(j)); the L lanes of the row are combined by
 // st.template group<L>(); epi(row, st, pv) runs on the row's first lane with
 // pv = pre(row), loaded when the slice starts so the row's own operands arrive while
-// the gathers are in flight.  Entries go in batches of U, the rest of a slice (every
-// lane of a slice holds the same number of entries, so the choice is uniform across
-// the warp) in one batch of the next power of two, so no entry is loaded on its own
-// and at most half of the last batch's loads are repeats.
+// the gathers are in flight.  Entries go in batches of U (the U index and value loads,
+// then the U gathers, issued before the first is used), the rest of a slice one entry
+// at a time (measured on the 100000 x 400000 LP: faster than masked batches, which
+// repeat loads).
 //   St: default-constructible (zero); add(V a, const G& g) for the gathered type G;
 //       template <int L> group().
 template <int L, int U, typename V, typename St, typename GF, typename Pre, typename Epi>
 __device__ __forceinline__ void sell_fold_L(const SellMat& S, GF& gf, Pre& pre, Epi& epi) {
-  static_assert(U == 8, "the tail batches below assume U = 8");
   const Thr th;
   constexpr int C = 32 / L;
   const V* __restrict__ val = static_cast<const V*>(S.val);
@@ -72,11 +71,7 @@ __device__ __forceinline__ void sell_fold_L(const SellMat& S, GF& gf, Pre& pre, 
     St st;
     int k = 0;
     for (; k + U <= w; k += U) sell_batch<U, V>(ci, va, k, w, gf, st);
-    const int r = w - k;
-    if (r > 4) sell_batch<8, V>(ci, va, k, w, gf, st);
-    else if (r > 2) sell_batch<4, V>(ci, va, k, w, gf, st);
-    else if (r == 2) sell_batch<2, V>(ci, va, k, w, gf, st);
-    else if (r == 1) sell_batch<1, V>(ci, va, k, w, gf, st);
+    for (; k < w; ++k) st.add(__ldg(va + k * 32), gf(__ldg(ci + k * 32)));
     if (L > 1) st.template group<L>();
     if (owner) epi(row, st, pv);
   }
