@@ -116,6 +116,23 @@ typedef struct {
     int64_t barrier_limit_ns; /* sparse (PCG) path: wall-clock limit of one grid-barrier wait in
                                  the persistent kernel; a wait past it ends the solve with
                                  ABIP_E_TIMEOUT (the kernel returns).  0: 4 s (default) */
+    int32_t bb_beta;        /* 1: choose beta at the start of every outer iteration by the
+                               Barzilai-Borwein spectral rule with safeguarding and the heuristic
+                               selection of Sec. 4.3 (two trial ADMM updates per estimate, a redo
+                               from the same start when the estimate moves by more than
+                               eps_penalty, at most bb_max_redo redos, never past max_admm_iters;
+                               the trial updates count as ADMM updates).  Dense Cholesky path in
+                               FP64 only (ABIP_E_UNSUPPORTED elsewhere).  Default 0 */
+    int32_t bb_max_redo;    /* redos of one selection; default 5 */
+    double eps_cor;         /* curvature-quality threshold of the safeguard; default 0.2 (Sec. 5) */
+    double eps_penalty;     /* threshold of the heuristic selection; default 0.1 (Sec. 5) */
+    int32_t autotune;       /* abip_solve_batch: 1 = time the occupancy variants of the solve kernel
+                               on a 30-update run of this batch and use the fastest; the choice is
+                               cached per (GPU, precision, batch shape) for the process and, when the
+                               environment names a file in ABIP_TUNE_CACHE, in that JSON file.
+                               Results do not depend on the choice.  Default 0 */
+    int32_t batch_order;    /* abip_solve_batch: 1 = hand the instances to the CTAs largest first
+                               (m n + m^2 descending), 0 = in the given order; default 1 */
     int32_t reserved[6];
 } abip_params;
 
@@ -133,6 +150,10 @@ typedef struct {
     int64_t fp32_iters;     /* ADMM updates whose products were FP32 (mixed precision: every path
                                keeps the iterate and its products in FP64 and updates them with
                                FP32 products of the changes) */
+    double beta;            /* beta of the last outer iteration (params.beta unless bb_beta) */
+    int32_t ctas_per_sm;    /* resident CTAs per SM of the dense solve launch (dense paths) */
+    int32_t tuned;          /* abip_solve_batch with autotune: 1 chosen by timing in this call,
+                               2 taken from the cache; 0 otherwise */
 } abip_info;
 
 typedef struct abip_handle abip_handle;
@@ -235,7 +256,8 @@ ABIP_API int abip_backward(abip_handle* h, const double* dl_dx,
  * abip_backward for the instances of one abip_solve_batch call, one CTA per
  * instance in one launch.  A, b, c, p: as given to abip_solve_batch.  x, y, s,
  * infos: what that call returned (the outputs are x/tau, y/tau, s/tau; the raw
- * iterate is rebuilt from them and infos[k].tau, theta, kappa, mu).  dl_dx[k]
+ * iterate is rebuilt from them and infos[k].tau, theta, kappa, mu, beta; beta = 0 reads
+ * as p->beta).  dl_dx[k]
  * (n_k), outputs dl_dc[k] (n_k), dl_db[k] (m_k), dl_dA[k] (m_k*n_k): per-instance
  * pointers, host or device; the output arrays and their entries may be NULL.
  * Every instance needs status OPTIMAL or MAX_ITER.  Errors as abip_backward.

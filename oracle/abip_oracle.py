@@ -33,7 +33,8 @@ the tau-scaled candidate; A8 certificate signs and test order; A9 two-root stabl
 prox; A10 CG stop rule; A13 MAX_ITER status; B5 Barzilai-Borwein beta (Sec. 4.3,
 opt-in): continue from the trial iterates, at most 5 redo rounds and never past the
 update cap, keeping the beta that produced the state when the rounds run out; B6 the
-curvature pairs with the printed signs.
+curvature pairs with the printed signs; B7 the selection starts at the second outer
+iteration.
 
 Parity status: every function here is pinned by tests in tests/test_oracle_*.py
 except the exact iteration trajectory of `solve` (iteration counts, the iterates
@@ -558,7 +559,10 @@ def solve(A, b, c, prm: Optional[Params] = None, trace_iters: int = 0,
     chk = None
     status = 0
     while status == 0:
-        if prm.bb_beta and total + 2 <= prm.max_admm_iters:
+        # reading B7: from the second outer iteration on (the first starts at the exact
+        # central point of mu0 = beta, where the ADMM map does not move and the curvature
+        # pairs would be rounding noise)
+        if prm.bb_beta and outer >= 1 and total + 2 <= prm.max_admm_iters:
             beta_k, st, spent = bb_select(P, proj, st, mu, beta_k, prm, budget=prm.max_admm_iters - total)
             total += spent
             betas.append(beta_k)

@@ -65,7 +65,9 @@ class abip_params(C.Structure):
                 ("max_admm_iters", C.c_int64), ("linsys", C.c_int32), ("cg_tol", C.c_double),
                 ("cg_max_iter", C.c_int32), ("cg_rel", C.c_double), ("cg_warm", C.c_int32), ("precision", C.c_int32), ("warmstart", C.c_int32),
                 ("stop_rule", C.c_int32), ("check_every", C.c_int32), ("grid_ctas", C.c_int32),
-                ("barrier_limit_ns", C.c_int64), ("reserved", C.c_int32 * 6)]
+                ("barrier_limit_ns", C.c_int64), ("bb_beta", C.c_int32), ("bb_max_redo", C.c_int32),
+                ("eps_cor", C.c_double), ("eps_penalty", C.c_double), ("autotune", C.c_int32),
+                ("batch_order", C.c_int32), ("reserved", C.c_int32 * 6)]
 
 
 class abip_info(C.Structure):
@@ -73,7 +75,8 @@ class abip_info(C.Structure):
                 ("cg_iters", C.c_int64), ("tau", C.c_double), ("kappa", C.c_double), ("theta", C.c_double),
                 ("mu", C.c_double), ("obj", C.c_double), ("pres", C.c_double), ("dres", C.c_double),
                 ("dgap", C.c_double), ("setup_s", C.c_double), ("solve_s", C.c_double),
-                ("kernel_s", C.c_double), ("launches", C.c_int64), ("fp32_iters", C.c_int64)]
+                ("kernel_s", C.c_double), ("launches", C.c_int64), ("fp32_iters", C.c_int64),
+                ("beta", C.c_double), ("ctas_per_sm", C.c_int32), ("tuned", C.c_int32)]
 
     def as_dict(self) -> dict:
         d = {k: getattr(self, k) for k, _ in self._fields_}

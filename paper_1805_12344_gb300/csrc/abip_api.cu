@@ -6,6 +6,10 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <fstream>
+#include <map>
+#include <mutex>
+#include <sstream>
 #include <string>
 #include <vector>
 
@@ -131,6 +135,13 @@ int check_params(const abip_params& p, std::string& why) {
   if (p.cg_warm < 0 || p.cg_warm > 2) { why = "cg_warm must be 0, 1 or 2"; return 0; }
   if (p.stop_rule != 0 && p.stop_rule != 1) { why = "stop_rule must be 0 or 1"; return 0; }
   if (p.barrier_limit_ns < 0) { why = "barrier_limit_ns must be >= 0"; return 0; }
+  if (p.bb_beta != 0 && p.bb_beta != 1) { why = "bb_beta must be 0 or 1"; return 0; }
+  if (p.autotune != 0 && p.autotune != 1) { why = "autotune must be 0 or 1"; return 0; }
+  if (p.batch_order != 0 && p.batch_order != 1) { why = "batch_order must be 0 or 1"; return 0; }
+  if (p.bb_beta && (p.bb_max_redo < 0 || !(p.eps_cor >= 0) || !(p.eps_penalty >= 0))) {
+    why = "bb_max_redo, eps_cor and eps_penalty must be >= 0";
+    return 0;
+  }
   return 1;
 }
 
@@ -179,13 +190,8 @@ struct HostSell {
   std::vector<int32_t> perm;
 };
 
-// Loads a lane issues for a slice of width w in the device traversal (sell.cuh): batches
-// of 8, the rest in one batch of the next power of two.
-double slice_cost(int64_t w) {
-  const int64_t r = w % 8;
-  const int64_t tail = r > 4 ? 8 : r > 2 ? 4 : r;
-  return (double)(w - r + tail);
-}
+// Loads a lane issues for a slice of width w in the device traversal (sell.cuh).
+double slice_cost(int64_t w) { return (double)w; }
 
 // Contiguous slice ranges per global warp with about equal work (loads of the slice + 2
 // for the row bookkeeping).
@@ -509,7 +515,7 @@ size_t dense_setup_smem(int m, int n) {
 
 // Allocate and fill the device descriptors of a set of dense instances.
 int dense_alloc(abip_handle* h, const std::vector<DenseHostInst>& hi, void** arena_out, DenseInst** dinst,
-                int** queue, std::vector<DenseInst>& hdesc, bool mixed = false) {
+                int** queue, std::vector<DenseInst>& hdesc, bool mixed = false, bool bb = false) {
   const int count = (int)hi.size();
   auto layout = [&](Arena& ar, std::vector<DenseInst>& d) {
     DenseInst* di = ar.take<DenseInst>(count);
@@ -527,7 +533,7 @@ int dense_alloc(abip_handle* h, const std::vector<DenseHostInst>& hi, void** are
       I.g1 = ar.take<double>(m + n); I.g2 = ar.take<double>(m + n);
       I.y = ar.take<double>(m); I.x = ar.take<double>(n); I.s = ar.take<double>(n);
       I.out_y = ar.take<double>(m); I.out_x = ar.take<double>(n); I.out_s = ar.take<double>(n);
-      I.work = nullptr;
+      I.work = bb ? ar.take<double>(abip::bb_work_doubles(m, n)) : nullptr;
       I.ldf = (n + 3) / 4 * 4;
       I.ldtf = (m + 3) / 4 * 4;
       if (mixed) {
@@ -585,16 +591,20 @@ int dense_run_setup(abip_handle* h, DenseInst* dinst, int* queue, int count, int
   return ABIP_OK;
 }
 
+DenseParams dense_params(const abip_params& p) {
+  return DenseParams{p.beta, p.gamma, p.alpha, p.eps, p.max_admm_iters, p.warmstart, p.stop_rule,
+                     p.precision != ABIP_PREC_F64 ? 1 : 0, std::max(1, p.check_every), p.bb_beta ? 1 : 0,
+                     p.bb_max_redo, p.eps_cor, p.eps_penalty};
+}
+
 int dense_run_solve(abip_handle* h, DenseInst* dinst, int* queue, int count, int grid, size_t smem,
-                    const abip_params& p, cudaStream_t st) {
-  DenseParams dp{p.beta, p.gamma, p.alpha, p.eps, p.max_admm_iters, p.warmstart, p.stop_rule,
-                 p.precision != ABIP_PREC_F64 ? 1 : 0, std::max(1, p.check_every)};
+                    const DenseParams& dp, cudaStream_t st, const int* order = nullptr, int variant = 0) {
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
   cudaMemsetAsync(queue, 0, 8, st);
   cudaEventRecord(e0, st);
-  cudaError_t e = abip::launch_dense_solve(dinst, count, dp, queue, grid, smem, st);
+  cudaError_t e = abip::launch_dense_solve(dinst, count, dp, queue, order, grid, smem, variant, st);
   cudaEventRecord(e1, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   float ms = 0.f;
@@ -605,6 +615,66 @@ int dense_run_solve(abip_handle* h, DenseInst* dinst, int* queue, int count, int
   h->kernel_s = ms * 1e-3;
   h->launches = 1;
   return ABIP_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Batch autotuner: the occupancy variant of the dense solve kernel, chosen by timing a
+// short capped run of the batch itself, cached per (GPU, precision, batch shape)
+// ---------------------------------------------------------------------------
+struct TuneCache {
+  std::mutex mu;
+  bool loaded = false;
+  std::map<std::string, int> best;
+};
+
+TuneCache& tune_cache() {
+  static TuneCache c;
+  return c;
+}
+
+std::string tune_key(int device, bool mixed, const std::vector<DenseHostInst>& hi) {
+  cudaDeviceProp prop;
+  if (cudaGetDeviceProperties(&prop, device) != cudaSuccess) {
+    cudaGetLastError();
+    std::strcpy(prop.name, "unknown");
+  }
+  double mn = 0.0;
+  int mmax = 0;
+  for (const DenseHostInst& x : hi) {
+    mn += (double)x.m * x.n;
+    mmax = std::max(mmax, x.m);
+  }
+  char buf[384];
+  std::snprintf(buf, sizeof buf, "%s|%s|count=%d|mmax=%d|mn=%.1e", prop.name, mixed ? "mixed" : "f64",
+                (int)hi.size(), mmax, mn);
+  std::string k(buf);
+  for (char& ch : k)
+    if (ch == '"' || ch == ':' || ch == '\\') ch = '_';
+  return k;
+}
+
+// the file the environment names in ABIP_TUNE_CACHE: one JSON object {"key": variant, ...}
+void tune_load(TuneCache& c) {
+  c.loaded = true;
+  const char* path = std::getenv("ABIP_TUNE_CACHE");
+  if (!path || !path[0]) return;
+  std::ifstream f(path);
+  std::string line;
+  while (std::getline(f, line)) {
+    const size_t q0 = line.find('"'), q1 = line.find('"', q0 + 1), colon = line.rfind(':');
+    if (q0 == std::string::npos || q1 == std::string::npos || colon == std::string::npos || colon < q1) continue;
+    c.best[line.substr(q0 + 1, q1 - q0 - 1)] = std::atoi(line.c_str() + colon + 1);
+  }
+}
+
+void tune_store(const TuneCache& c) {
+  const char* path = std::getenv("ABIP_TUNE_CACHE");
+  if (!path || !path[0]) return;
+  std::ofstream f(path);
+  f << "{\n";
+  size_t k = 0;
+  for (const auto& kv : c.best) f << "  \"" << kv.first << "\": " << kv.second << (++k < c.best.size() ? ",\n" : "\n");
+  f << "}\n";
 }
 
 int read_matrix_dense(abip_handle* h, const abip_matrix* A, std::vector<double>& out) {
@@ -828,6 +898,12 @@ int abip_default_params(abip_params* p) {
   p->stop_rule = 0;
   p->check_every = 1;
   p->grid_ctas = 0;
+  p->bb_beta = 0;
+  p->bb_max_redo = 5;
+  p->eps_cor = 0.2;
+  p->eps_penalty = 0.1;
+  p->autotune = 0;
+  p->batch_order = 1;
   return ABIP_OK;
 }
 
@@ -866,6 +942,11 @@ int abip_setup(const abip_matrix* A, const double* b, const double* c, const abi
   }
   int linsys = prm.linsys;
   if (linsys < 0) linsys = A->fmt == ABIP_CSR ? ABIP_LINSYS_PCG : ABIP_LINSYS_DENSE_CHOL;
+  if (prm.bb_beta && (linsys != ABIP_LINSYS_DENSE_CHOL || prm.precision != ABIP_PREC_F64)) {
+    g_err = "bb_beta needs the dense Cholesky path in FP64";
+    abip_free(h);
+    return ABIP_E_UNSUPPORTED;
+  }
   h->prm.linsys = linsys;
   h->mixed = prm.precision != ABIP_PREC_F64;
   if (linsys == ABIP_LINSYS_PCG) {
@@ -888,7 +969,7 @@ int abip_setup(const abip_matrix* A, const double* b, const double* c, const abi
       hi[0].m = m; hi[0].n = n; hi[0].b = hb; hi[0].c = hc;
       rc = read_matrix_dense(h, A, hi[0].A);
       std::vector<DenseInst> hd;
-      if (rc == ABIP_OK) rc = dense_alloc(h, hi, &h->arena, &h->dinst, &h->queue, hd, h->mixed != 0);
+      if (rc == ABIP_OK) rc = dense_alloc(h, hi, &h->arena, &h->dinst, &h->queue, hd, h->mixed != 0, prm.bb_beta != 0);
       if (rc == ABIP_OK) {
         h->hinst = hd[0];
         rc = dense_run_setup(h, h->dinst, h->queue, 1, 1, dense_setup_smem(m, n), 0);
@@ -932,6 +1013,7 @@ int abip_solve(abip_handle* h, double* x, double* y, double* s, abip_info* info,
     inf.status = hc.status; inf.outer_iters = hc.outer_iters; inf.admm_iters = hc.admm_iters; inf.cg_iters = hc.cg_iters;
     inf.tau = hc.tau; inf.kappa = hc.kappa; inf.theta = hc.theta; inf.mu = hc.mu;
     inf.obj = hc.ctx / hc.tau; inf.pres = hc.pres; inf.dres = hc.dres; inf.dgap = hc.dgap;
+    inf.beta = h->prm.beta;
     inf.fp32_iters = h->mixed ? hc.admm_iters : 0;
     double sx = 1.0 / hc.tau, sy = 1.0 / hc.tau;
     if (hc.status == ABIP_PRIMAL_INFEASIBLE) { sx = 1.0; sy = 1.0 / hc.bty; }
@@ -961,7 +1043,7 @@ int abip_solve(abip_handle* h, double* x, double* y, double* s, abip_info* info,
       cudaMemcpy(h->dinst, &I, sizeof(DenseInst), cudaMemcpyHostToDevice);
       h->resume = false;
     }
-    rc = dense_run_solve(h, h->dinst, h->queue, 1, 1, dense_solve_smem(m, n, h->mixed != 0), h->prm, st);
+    rc = dense_run_solve(h, h->dinst, h->queue, 1, 1, dense_solve_smem(m, n, h->mixed != 0), dense_params(h->prm), st);
     if (rc) return rc;
     cudaMemcpy(&h->hinst, h->dinst, sizeof(DenseInst), cudaMemcpyDeviceToHost);
     const DenseInst& I = h->hinst;
@@ -971,6 +1053,7 @@ int abip_solve(abip_handle* h, double* x, double* y, double* s, abip_info* info,
     if (h->mixed && !I.fp32_iters_lo && !I.fp32_iters_hi) inf.fp32_iters = I.admm_iters;
     inf.tau = I.tau; inf.kappa = I.kappa; inf.theta = I.theta; inf.mu = I.mu;
     inf.obj = I.obj; inf.pres = I.pres; inf.dres = I.dres; inf.dgap = I.dgap;
+    inf.beta = I.beta_last;
     rc = copy_out(h, x, I.out_x, n, st);
     if (!rc) rc = copy_out(h, y, I.out_y, m, st);
     if (!rc) rc = copy_out(h, s, I.out_s, n, st);
@@ -1000,6 +1083,7 @@ int abip_solve_batch(int32_t count, const abip_matrix* A, const double* const* b
   std::string why;
   if (!check_params(prm, why)) return fail(nullptr, ABIP_E_INVALID_ARG, why);
   const bool mixed = prm.precision != ABIP_PREC_F64;
+  if (prm.bb_beta && mixed) return fail(nullptr, ABIP_E_UNSUPPORTED, "bb_beta needs FP64 (precision = ABIP_PREC_F64)");
   abip_handle tmp;
   cudaGetDevice(&tmp.device);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -1028,13 +1112,60 @@ int abip_solve_batch(int32_t count, const abip_matrix* A, const double* const* b
   DenseInst* dinst = nullptr;
   int* queue = nullptr;
   std::vector<DenseInst> hd;
-  int rc = dense_alloc(&tmp, hi, &arena, &dinst, &queue, hd, mixed);
+  int rc = dense_alloc(&tmp, hi, &arena, &dinst, &queue, hd, mixed, prm.bb_beta != 0);
   if (rc) return fail(nullptr, rc, tmp.err);
+  // hand-out order: largest first (the batch's wall time is its slowest instance)
+  int* order = nullptr;
+  if (prm.batch_order == 1 && count > 1) {
+    std::vector<int> ord(count);
+    for (int k = 0; k < count; ++k) ord[k] = k;
+    std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) {
+      const double ca = (double)hi[a].m * hi[a].n + (double)hi[a].m * hi[a].m;
+      const double cb = (double)hi[b].m * hi[b].n + (double)hi[b].m * hi[b].m;
+      return ca > cb;
+    });
+    if (cudaMalloc(&order, count * sizeof(int)) != cudaSuccess) {
+      cudaGetLastError();
+      cudaFree(arena);
+      return fail(nullptr, ABIP_E_OOM, "batch order: device allocation failed");
+    }
+    cudaMemcpy(order, ord.data(), count * sizeof(int), cudaMemcpyHostToDevice);
+  }
   const int sms = abip::dense_max_ctas(tmp.device);
-  const int per = std::max(1, abip::dense_solve_ctas_per_sm(mixed, smem_solve));
-  const int grid = std::min(count, sms * per);
+  const DenseParams dp = dense_params(prm);
   rc = dense_run_setup(&tmp, dinst, queue, count, std::min(count, sms * 4), smem_setup, st);
-  if (!rc) rc = dense_run_solve(&tmp, dinst, queue, count, grid, smem_solve, prm, st);
+  // occupancy variant: 0, or the autotuner's (cached, or timed on this batch)
+  int variant = 0, tuned = 0;
+  if (!rc && prm.autotune) {
+    TuneCache& tc = tune_cache();
+    const std::string key = tune_key(tmp.device, mixed, hi);
+    {
+      std::lock_guard<std::mutex> lock(tc.mu);
+      if (!tc.loaded) tune_load(tc);
+      auto it = tc.best.find(key);
+      if (it != tc.best.end() && it->second >= 0 && it->second < abip::kDenseVariants) { variant = it->second; tuned = 2; }
+    }
+    if (!tuned) {
+      DenseParams probe = dp;   // 30 updates of every instance, no test can stop them
+      probe.max_admm = 30;
+      probe.eps = 0.0;
+      probe.bb = 0;
+      double best_s = 1e300;
+      for (int v = 0; v < abip::kDenseVariants && !rc; ++v) {
+        const int per_v = abip::dense_solve_ctas_per_sm(mixed, smem_solve, v);
+        if (per_v < 1) continue;
+        rc = dense_run_solve(&tmp, dinst, queue, count, std::min(count, sms * per_v), smem_solve, probe, st, order, v);
+        if (!rc && tmp.kernel_s < best_s) { best_s = tmp.kernel_s; variant = v; }
+      }
+      tuned = 1;
+      std::lock_guard<std::mutex> lock(tc.mu);
+      tc.best[key] = variant;
+      tune_store(tc);
+    }
+  }
+  const int per = std::max(1, abip::dense_solve_ctas_per_sm(mixed, smem_solve, variant));
+  const int grid = std::min(count, sms * per);
+  if (!rc) rc = dense_run_solve(&tmp, dinst, queue, count, grid, smem_solve, dp, st, order, variant);
   if (!rc) {
     std::vector<DenseInst> res(count);
     cudaMemcpy(res.data(), dinst, sizeof(DenseInst) * count, cudaMemcpyDeviceToHost);
@@ -1050,6 +1181,9 @@ int abip_solve_batch(int32_t count, const abip_matrix* A, const double* const* b
         if (mixed && !I.fp32_iters_lo && !I.fp32_iters_hi) f.fp32_iters = I.admm_iters;
         f.tau = I.tau; f.kappa = I.kappa; f.theta = I.theta; f.mu = I.mu;
         f.obj = I.obj; f.pres = I.pres; f.dres = I.dres; f.dgap = I.dgap;
+        f.beta = I.beta_last;
+        f.ctas_per_sm = per;
+        f.tuned = tuned;
         f.solve_s = el;
         f.kernel_s = tmp.kernel_s;
         f.launches = tmp.launches;
@@ -1063,6 +1197,7 @@ int abip_solve_batch(int32_t count, const abip_matrix* A, const double* const* b
   } else {
     g_err = tmp.err;
   }
+  if (order) cudaFree(order);
   cudaFree(arena);
   return rc;
 }
@@ -1075,6 +1210,7 @@ int abip_solve_batch_shared(int32_t count, const abip_matrix* A, const double* c
   if (count == 0) return ABIP_OK;
   if (!A || !b || !c) return fail(nullptr, ABIP_E_INVALID_ARG, "A, b or c is NULL");
   if (A->fmt != ABIP_DENSE_ROWMAJOR) return fail(nullptr, ABIP_E_UNSUPPORTED, "the shared-A batch takes a dense A");
+  if (p && p->bb_beta) return fail(nullptr, ABIP_E_UNSUPPORTED, "bb_beta is not provided on the shared-A batch");
   abip_params prm;
   if (p) prm = *p;
   else abip_default_params(&prm);
@@ -1137,6 +1273,7 @@ int abip_solve_batch_shared(int32_t count, const abip_matrix* A, const double* c
         f.fp32_iters = sp.mixed ? I.total : 0;
         f.tau = I.tau; f.kappa = I.kappa; f.theta = I.theta; f.mu = I.mu;
         f.obj = I.ctx / I.tau; f.pres = I.pres; f.dres = I.dres; f.dgap = I.dgap;
+        f.beta = prm.beta;
         f.setup_s = res[k].setup_s; f.solve_s = el; f.kernel_s = res[k].kernel_s; f.launches = res[k].launches;
       }
       auto put = [&](double* dst, const std::vector<double>& v) {
@@ -1169,7 +1306,7 @@ int abip_backward(abip_handle* h, const double* dl_dx, double* dl_dc, double* dl
       fetch(I.s, n, true, it.s) != cudaSuccess || fetch(dl_dx, n, is_device_ptr(dl_dx), it.g) != cudaSuccess)
     return fail(h, ABIP_E_CUDA, "reading the state or dl_dx");
   if (!finite_all(it.g.data(), n)) return fail(h, ABIP_E_INVALID_ARG, "dl_dx has non-finite entries");
-  it.tau = I.tau; it.theta = I.theta; it.kappa = I.kappa; it.cmu = I.mu / h->prm.beta;
+  it.tau = I.tau; it.theta = I.theta; it.kappa = I.kappa; it.cmu = I.mu / (h->prm.bb_beta ? I.beta_last : h->prm.beta);
   it.out_dA = dl_dA; it.out_db = dl_db; it.out_dc = dl_dc;
   return run_backward(h, items, nullptr);
 }
@@ -1219,7 +1356,7 @@ int abip_backward_batch(int32_t count, const abip_matrix* A, const double* const
     if (!finite_all(it.b_host.data(), m) || !finite_all(it.c_host.data(), n) || !finite_all(it.y.data(), m) ||
         !finite_all(it.g.data(), n))
       return fail(nullptr, ABIP_E_INVALID_ARG, at + "non-finite input");
-    it.tau = f.tau; it.theta = f.theta; it.kappa = f.kappa; it.cmu = f.mu / prm.beta;
+    it.tau = f.tau; it.theta = f.theta; it.kappa = f.kappa; it.cmu = f.mu / (f.beta > 0 ? f.beta : prm.beta);
     it.out_dA = dl_dA ? dl_dA[k] : nullptr;
     it.out_db = dl_db ? dl_db[k] : nullptr;
     it.out_dc = dl_dc ? dl_dc[k] : nullptr;

@@ -148,7 +148,7 @@ struct DenseInst {
   double* bbar; double* cbar;  // embedding constants
   double* g1; double* g2;      // M^{-1} h1, M^{-1} h2, (m + n) each: [y part, x part]
   double* y; double* x; double* s;   // iterate
-  double* work;                // 3*(m + n) doubles
+  double* work;                // bb_work_doubles(m, n) when the Barzilai-Borwein rule is on, else null
   double* out_x; double* out_y; double* out_s;   // device outputs (may be null)
   // mixed precision (null on the FP64 path): FP32 A (rows padded to ldf), FP32 A^T
   // (rows padded to ldtf) and the FP32 explicit inverse of G = I + A A^T (m x ldtf)
@@ -169,6 +169,7 @@ struct DenseInst {
   int32_t fp32_iters_lo;
   int32_t ldf, ldtf;           // padded row lengths of Af (n) and of ATf / Ginvf (m), multiples of 4
   int32_t pad3;
+  double beta_last;            // beta of the last outer iteration
 };
 
 // One instance of the central-point differentiation (dense A, FP64, device pointers).
@@ -196,12 +197,20 @@ struct DenseParams {
   int32_t warmstart, stop_rule;
   int32_t mixed;          // 1: FP32 iterates with FP64 termination decisions
   int32_t check_every;    // mixed: minimum spacing of FP64 confirmations (updates)
+  int32_t bb;             // 1: Barzilai-Borwein beta at each outer iteration (FP64 path)
+  int32_t bb_max_redo;
+  double eps_cor, eps_penalty;
 };
 
+// global scratch of the Barzilai-Borwein selection per instance (DenseInst::work)
+inline size_t bb_work_doubles(int m, int n) { return 4 * (size_t)m + 6 * (size_t)n; }
+
 cudaError_t launch_dense_setup(DenseInst* inst, int count, int* queue, int grid, size_t smem, cudaStream_t st);
-cudaError_t launch_dense_solve(DenseInst* inst, int count, DenseParams prm, int* queue, int grid,
-                               size_t smem, cudaStream_t st);
-int dense_solve_ctas_per_sm(bool mixed, size_t smem);
+// Occupancy variants of the dense solve kernel (the batch autotuner's choice)
+constexpr int kDenseVariants = 3;
+cudaError_t launch_dense_solve(DenseInst* inst, int count, DenseParams prm, int* queue, const int* order,
+                               int grid, size_t smem, int variant, cudaStream_t st);
+int dense_solve_ctas_per_sm(bool mixed, size_t smem, int variant);
 int dense_max_ctas(int device);
 cudaError_t launch_dense_backward(BackwardInst* insts, int count, int grid, cudaStream_t st);
 inline size_t backward_work_doubles(int m, int n) { return 2 * (size_t)m + 4 * (size_t)n + 5 * ((size_t)m + n + 2); }

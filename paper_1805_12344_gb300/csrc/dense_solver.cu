@@ -23,14 +23,17 @@ namespace {
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
 
-// next instance id from the work queue (thread 0), broadcast to the CTA
-__device__ __forceinline__ int next_instance(int* queue, int count) {
+// next instance id from the work queue (thread 0), broadcast to the CTA; `order` (may be
+// null) lists the instances in the order they are handed out
+__device__ __forceinline__ int next_instance(int* queue, int count, const int* order = nullptr) {
   __shared__ int s_id;
   __syncthreads();
-  if (threadIdx.x == 0) s_id = atomicAdd(queue, 1);
+  if (threadIdx.x == 0) {
+    const int q = atomicAdd(queue, 1);
+    s_id = q < count ? (order ? order[q] : q) : -1;
+  }
   __syncthreads();
-  const int id = s_id;
-  return id < count ? id : -1;
+  return s_id;
 }
 
 // w <- L^{-1} w, L lower triangular (row-major, leading dimension m), w in shared memory.
@@ -333,6 +336,29 @@ __device__ void residual_sums(const DView<T>& V, int m, int n, int64_t ld, const
   block_allsum<9>(out, red);
 }
 
+// Sec. 4.3 spectral estimate from the dot products d = (<dv,dv>, <dv,du~>, <du~,du~>,
+// <dv,du>, <du,du>) of the curvature pairs: for each pair the steepest-descent and
+// minimum-gradient steps SD = <dv,dv>/<dv,d>, MG = <dv,d>/<d,d>, their hybrid (MG when
+// 2 MG > SD, else SD - MG/2) and the correlation <dv,d>/(|dv||d|); the safeguard keeps the
+// estimates whose correlation exceeds eps_cor (both: their geometric mean) and returns
+// beta when neither does.
+__device__ double bb_estimate(const double* d, double beta, double eps_cor) {
+  const double vv = d[0], nv = sqrt(vv);
+  auto pair = [&](double vd, double dd, double& step) -> double {
+    if (vd == 0.0 || dd == 0.0 || nv == 0.0) { step = 0.0; return -1.0; }
+    const double sd = vv / vd, mg = vd / dd;
+    step = 2.0 * mg > sd ? mg : sd - mg / 2.0;
+    return vd / (nv * sqrt(dd));
+  };
+  double phi, psi;
+  const double phi_cor = pair(d[1], d[2], phi);
+  const double psi_cor = pair(d[3], d[4], psi);
+  if (phi_cor > eps_cor && psi_cor > eps_cor) return sqrt(phi * psi);
+  if (phi_cor > eps_cor) return phi;
+  if (psi_cor > eps_cor) return psi;
+  return beta;
+}
+
 // Algorithm 2 for one instance with the CTA, FP64 iterates (T = double).  Shared
 // layout: y, zy, w, Ax, As (m each), x, s, zx (n each).
 template <typename T>
@@ -396,29 +422,11 @@ __device__ void dense_solve_one(DenseInst& I, const DenseParams& P, T* sm, doubl
     return true;
   };
 
-  bool ok = evaluate(false);
-  while (ok) {
-    if (inner2 <= mu) {
-      mu *= gamma;
-      ++outer;
-      if (P.stop_rule == 1 && mu < eps) { status = ABIP_OPTIMAL; break; }
-      if (outer >= kMaxOuter) { status = ABIP_MAX_ITER; break; }   // mu has underflowed
-      const T g = (T)gamma, sg = (T)sqrt(gamma);
-      if (P.warmstart == 1) {
-        for (int j = threadIdx.x; j < n; j += kThreads) { x[j] *= sg; s[j] *= sg; }
-        tau *= sqrt(gamma); kappa *= sqrt(gamma);
-      } else {
-        for (int j = threadIdx.x; j < n; j += kThreads) {
-          if (x[j] >= s[j]) s[j] *= g; else x[j] *= g;
-        }
-        if (tau >= kappa) kappa *= gamma; else tau *= gamma;
-      }
-      for (int i = threadIdx.x; i < m; i += kThreads) y[i] *= sg;
-      theta *= sqrt(gamma);
-      __syncthreads();
-      ok = evaluate(false);
-      continue;
-    }
+  // One ADMM update with barrier weight bk (Algorithm 2 with the relaxation of Sec. 4.2),
+  // from the state and its products Ax, As.  ut (global, m + n, may be null) receives the
+  // projection u~ = (u~_y, u~_x); (t1, t2) = (u~_tau, u~_theta).
+  double t1 = 0.0, t2 = 0.0;
+  auto admm_update = [&](double bk, double* ut) {
     // projection: w_y = y, w_x = x + s; zy = G^{-1}(y - A(x + s)) = G^{-1}(y - Ax - As)
     for (int i = threadIdx.x; i < m; i += kThreads) zy[i] = y[i] - (Ax[i] + As[i]);
     for (int j = threadIdx.x; j < n; j += kThreads) zx[j] = x[j] + s[j];
@@ -449,14 +457,17 @@ __device__ void dense_solve_one(DenseInst& I, const DenseParams& P, T* sm, doubl
     double hz[2] = {(double)hz0, (double)hz1};
     block_allsum<2>(hz, red);
     const double v1 = tau + kappa + hz[0], v2 = theta + xi + hz[1];
-    const double t1 = Ki0 * v1 + Ki1 * v2, t2 = Ki2 * v1 + Ki3 * v2;
-    const T a = (T)alpha, a1 = (T)(1.0 - alpha), t1T = (T)t1, t2T = (T)t2, cmu = (T)(mu / beta);
+    t1 = Ki0 * v1 + Ki1 * v2;
+    t2 = Ki2 * v1 + Ki3 * v2;
+    const T a = (T)alpha, a1 = (T)(1.0 - alpha), t1T = (T)t1, t2T = (T)t2, cmu = (T)(mu / bk);
     for (int i = threadIdx.x; i < m; i += kThreads) {
       const T uy = zy[i] - V.g1[i] * t1T - V.g2[i] * t2T;
+      if (ut) ut[i] = (double)uy;
       y[i] = a * uy + a1 * y[i];
     }
     for (int j = threadIdx.x; j < n; j += kThreads) {
       const T ux = zx[j] - V.g1[m + j] * t1T - V.g2[m + j] * t2T;
+      if (ut) ut[m + j] = (double)ux;
       const T xh = a * ux + a1 * x[j];
       T xn, sn;
       barrier_step<T>(xh - s[j], cmu, xn, sn);
@@ -466,12 +477,121 @@ __device__ void dense_solve_one(DenseInst& I, const DenseParams& P, T* sm, doubl
     {
       const double th_ = alpha * t1 + (1.0 - alpha) * tau;
       double tn, kn;
-      barrier_step<double>(th_ - kappa, mu / beta, tn, kn);
+      barrier_step<double>(th_ - kappa, mu / bk, tn, kn);
       tau = tn;
       kappa = kn;
       theta = alpha * t2 + (1.0 - alpha) * theta;
     }
     __syncthreads();
+  };
+
+  // Sec. 4.3 at the start of an outer iteration k >= 1 (readings B5, B7): from the start point S0, two
+  // trial updates with beta_k give the curvature pairs
+  //   dv = v^_2 - v^_1, v^_i = v_{i-1} - alpha u~_i - (1 - alpha) u_{i-1} + alpha u_i,
+  //   du~ = alpha (u~_2 - u~_1) + (1 - alpha) (u_1 - u_0),  du = -(u_2 - u_1)
+  // (u = (y, x, tau, theta), v = (r, s, kappa, xi), r = 0 and xi fixed); the safeguarded
+  // spectral estimate beta^ (bb_estimate) keeps beta_k (no reliable curvature), averages
+  // it with beta^ (|beta^ - beta_k| <= eps_penalty), or becomes the new beta_k for a redo
+  // from S0.  At most bb_max_redo redos, and no round that would pass `budget` updates;
+  // the iteration continues from the last trial state.  Returns the updates spent.
+  double beta_k = beta;
+  auto bb_select = [&](int64_t budget) -> int64_t {
+    double* S0 = I.work;            // y0, x0, s0
+    double* S1 = S0 + m + 2 * n;    // y1, x1, s1
+    double* U1 = S1 + m + 2 * n;    // u~_1 (y, x parts)
+    double* U2 = U1 + m + n;        // u~_2
+    for (int i = threadIdx.x; i < m; i += kThreads) S0[i] = (double)y[i];
+    for (int j = threadIdx.x; j < n; j += kThreads) { S0[m + j] = (double)x[j]; S0[m + n + j] = (double)s[j]; }
+    const double tau0 = tau, kappa0 = kappa, theta0 = theta;
+    double b = beta_k, used = beta_k;
+    int64_t spent = 0;
+    for (int round = 0; round <= P.bb_max_redo; ++round) {
+      if (spent + 2 > budget) break;
+      if (round > 0) {
+        for (int i = threadIdx.x; i < m; i += kThreads) y[i] = (T)S0[i];
+        for (int j = threadIdx.x; j < n; j += kThreads) { x[j] = (T)S0[m + j]; s[j] = (T)S0[m + n + j]; }
+        tau = tau0; kappa = kappa0; theta = theta0;
+      }
+      __syncthreads();
+      gemv_rows<true, T>(V.A, I.ld, m, n, x, s, Ax, As);
+      __syncthreads();
+      admm_update(b, U1);
+      const double ut1 = t1, uth1 = t2, tau1 = tau, kappa1 = kappa, theta1 = theta;
+      for (int i = threadIdx.x; i < m; i += kThreads) S1[i] = (double)y[i];
+      for (int j = threadIdx.x; j < n; j += kThreads) { S1[m + j] = (double)x[j]; S1[m + n + j] = (double)s[j]; }
+      gemv_rows<true, T>(V.A, I.ld, m, n, x, s, Ax, As);
+      __syncthreads();
+      admm_update(b, U2);
+      spent += 2;
+      used = b;
+      // <dv,dv>, <dv,du~>, <du~,du~>, <dv,du>, <du,du>
+      double d[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+      auto add = [&](double u0, double u1, double u2, double w1, double w2, double v0, double v1) {
+        const double vh1 = v0 - alpha * w1 - (1.0 - alpha) * u0 + alpha * u1;
+        const double vh2 = v1 - alpha * w2 - (1.0 - alpha) * u1 + alpha * u2;
+        const double dv = vh2 - vh1;
+        const double dt = alpha * (w2 - w1) + (1.0 - alpha) * (u1 - u0);
+        const double du = -(u2 - u1);
+        d[0] += dv * dv; d[1] += dv * dt; d[2] += dt * dt; d[3] += dv * du; d[4] += du * du;
+      };
+      for (int i = threadIdx.x; i < m; i += kThreads) add(S0[i], S1[i], (double)y[i], U1[i], U2[i], 0.0, 0.0);
+      for (int j = threadIdx.x; j < n; j += kThreads)
+        add(S0[m + j], S1[m + j], (double)x[j], U1[m + j], U2[m + j], S0[m + n + j], S1[m + n + j]);
+      if (threadIdx.x == 0) {
+        add(tau0, tau1, tau, ut1, t1, kappa0, kappa1);     // tau position: v = kappa
+        add(theta0, theta1, theta, uth1, t2, xi, xi);      // theta position: v = xi
+      }
+      block_allsum<5>(d, red);
+      const double bh = bb_estimate(d, b, P.eps_cor);
+      if (bh == b) return spent;
+      if (fabs(bh - b) <= P.eps_penalty) { beta_k = 0.5 * (b + bh); return spent; }
+      b = bh;
+    }
+    beta_k = used;
+    return spent;
+  };
+  // the start of an outer iteration: the selection of beta (when on), then the sums of the
+  // state; false stops the solve (non-finite sums, or the selection reached the cap)
+  auto outer_start = [&]() -> bool {
+    // reading B7: from the second outer iteration on (the first starts at the exact central
+    // point of mu0 = beta, a fixed point of the ADMM map: its curvature pairs are rounding noise)
+    if (P.bb && outer >= 1 && total + 2 <= P.max_admm) {
+      total += bb_select(P.max_admm - total);
+      if (total >= P.max_admm) {
+        status = ABIP_MAX_ITER;
+        double a[9];
+        residual_sums<T>(V, m, n, I.ld, x, s, y, tau, theta, Ax, As, a, red);
+        absorb(a);
+        return false;
+      }
+    }
+    return evaluate(false);
+  };
+
+  bool ok = outer_start();
+  while (ok) {
+    if (inner2 <= mu) {
+      mu *= gamma;
+      ++outer;
+      if (P.stop_rule == 1 && mu < eps) { status = ABIP_OPTIMAL; break; }
+      if (outer >= kMaxOuter) { status = ABIP_MAX_ITER; break; }   // mu has underflowed
+      const T g = (T)gamma, sg = (T)sqrt(gamma);
+      if (P.warmstart == 1) {
+        for (int j = threadIdx.x; j < n; j += kThreads) { x[j] *= sg; s[j] *= sg; }
+        tau *= sqrt(gamma); kappa *= sqrt(gamma);
+      } else {
+        for (int j = threadIdx.x; j < n; j += kThreads) {
+          if (x[j] >= s[j]) s[j] *= g; else x[j] *= g;
+        }
+        if (tau >= kappa) kappa *= gamma; else tau *= gamma;
+      }
+      for (int i = threadIdx.x; i < m; i += kThreads) y[i] *= sg;
+      theta *= sqrt(gamma);
+      __syncthreads();
+      ok = outer_start();
+      continue;
+    }
+    admm_update(beta_k, nullptr);
     ++total;
     ok = evaluate(true);
     if (status != 0) break;
@@ -496,7 +616,9 @@ __device__ void dense_solve_one(DenseInst& I, const DenseParams& P, T* sm, doubl
     I.resume = 0;
     I.pres = pres; I.dres = dres; I.dgap = dgap; I.ctx = ctx; I.bty = bty; I.obj = ctx / tau;
     I.admm_iters = total; I.outer_iters = outer; I.status = status;
-    if (!ok) I.err = DEV_ERR_NONFINITE;
+    I.beta_last = beta_k;
+    // ok is also false when the trial updates of the selection reached the cap (finite sums)
+    if (!ok && !(status == ABIP_MAX_ITER && isfinite(inner2))) I.err = DEV_ERR_NONFINITE;
   }
   __syncthreads();
 }
@@ -808,12 +930,17 @@ __device__ void dense_solve_delta(DenseInst& I, const DenseParams& P, unsigned c
   __syncthreads();
 }
 
-__global__ void __launch_bounds__(kThreads) dense_solve_mixed_kernel(DenseInst* insts, int count, DenseParams P,
-                                                                     int* queue) {
+// Solve kernels, one CTA per instance at a time.  MINB (resident CTAs per SM the
+// compiler plans registers for) is the knob of the batch autotuner: the variants run the
+// same arithmetic and differ only in occupancy.
+template <int MINB>
+__global__ void __launch_bounds__(kThreads, MINB) dense_solve_mixed_kernel(DenseInst* insts, int count,
+                                                                           DenseParams P, int* queue,
+                                                                           const int* order) {
   extern __shared__ double sm_raw[];
   __shared__ double red[32 * 9];
   for (;;) {
-    const int id = next_instance(queue, count);
+    const int id = next_instance(queue, count, order);
     if (id < 0) return;
     DenseInst& I = insts[id];
     if (I.err != 0) continue;
@@ -821,14 +948,14 @@ __global__ void __launch_bounds__(kThreads) dense_solve_mixed_kernel(DenseInst* 
   }
 }
 
-template <typename T>
-__global__ void __launch_bounds__(kThreads) dense_solve_kernel(DenseInst* insts, int count, DenseParams P,
-                                                               int* queue) {
+template <typename T, int MINB>
+__global__ void __launch_bounds__(kThreads, MINB) dense_solve_kernel(DenseInst* insts, int count, DenseParams P,
+                                                                     int* queue, const int* order) {
   extern __shared__ double sm_raw[];
   __shared__ double red[32 * 9];
   T* sm = reinterpret_cast<T*>(sm_raw);
   for (;;) {
-    const int id = next_instance(queue, count);
+    const int id = next_instance(queue, count, order);
     if (id < 0) return;
     DenseInst& I = insts[id];
     if (I.err != 0) continue;
@@ -1344,30 +1471,31 @@ cudaError_t launch_dense_setup(DenseInst* inst, int count, int* queue, int grid,
   return cudaGetLastError();
 }
 
-cudaError_t launch_dense_solve(DenseInst* inst, int count, DenseParams prm, int* queue, int grid,
-                               size_t smem, cudaStream_t st) {
+// the solve kernel of a precision and an occupancy variant (0, 1, 2: MINB 1, 2, 3 for FP64
+// and 2, 3, 4 for mixed precision), with its dynamic shared memory limit raised
+using DenseSolveFn = void (*)(DenseInst*, int, DenseParams, int*, const int*);
+DenseSolveFn dense_solve_fn(bool mixed, int variant) {
+  DenseSolveFn f;
+  if (mixed) f = variant == 2 ? dense_solve_mixed_kernel<4> : variant == 1 ? dense_solve_mixed_kernel<3>
+                                                                             : dense_solve_mixed_kernel<2>;
+  else f = variant == 2 ? dense_solve_kernel<double, 3> : variant == 1 ? dense_solve_kernel<double, 2>
+                                                                         : dense_solve_kernel<double, 1>;
+  cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDenseSmemMax);
+  return f;
+}
+
+cudaError_t launch_dense_solve(DenseInst* inst, int count, DenseParams prm, int* queue, const int* order,
+                               int grid, size_t smem, int variant, cudaStream_t st) {
   // the caller sizes smem for the largest instance: (5m + 3n) doubles (FP64), 48m + 40n bytes (mixed)
-  if (prm.mixed) {
-    cudaError_t e = cudaFuncSetAttribute(dense_solve_mixed_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDenseSmemMax);
-    if (e != cudaSuccess) return e;
-    dense_solve_mixed_kernel<<<grid, kThreads, smem, st>>>(inst, count, prm, queue);
-  } else {
-    cudaError_t e = cudaFuncSetAttribute(dense_solve_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDenseSmemMax);
-    if (e != cudaSuccess) return e;
-    dense_solve_kernel<double><<<grid, kThreads, smem, st>>>(inst, count, prm, queue);
-  }
+  DenseSolveFn f = dense_solve_fn(prm.mixed != 0, variant);
+  cudaGetLastError();
+  f<<<grid, kThreads, smem, st>>>(inst, count, prm, queue, order);
   return cudaGetLastError();
 }
 
-int dense_solve_ctas_per_sm(bool mixed, size_t smem) {
+int dense_solve_ctas_per_sm(bool mixed, size_t smem, int variant) {
   int per = 0;
-  if (mixed) {
-    cudaFuncSetAttribute(dense_solve_mixed_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDenseSmemMax);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, dense_solve_mixed_kernel, kThreads, smem);
-  } else {
-    cudaFuncSetAttribute(dense_solve_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDenseSmemMax);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, dense_solve_kernel<double>, kThreads, smem);
-  }
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, dense_solve_fn(mixed, variant), kThreads, smem);
   return per;
 }
 
@@ -1432,6 +1560,7 @@ extern "C" ABIP_API int abip_solve_dense_noalloc(int32_t m, int32_t n, const dou
   std::string why;
   if (!abip::check_params_internal(prm, why)) return abip::noalloc_fail(ABIP_E_INVALID_ARG, why);
   if (prm.precision != ABIP_PREC_F64) return abip::noalloc_fail(ABIP_E_UNSUPPORTED, "abip_solve_dense_noalloc is FP64 only");
+  if (prm.bb_beta) return abip::noalloc_fail(ABIP_E_UNSUPPORTED, "abip_solve_dense_noalloc has no scratch for bb_beta");
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return abip::noalloc_fail(ABIP_E_CUDA, "cudaGetDevice failed");
   const void* ptrs[6] = {A, b, c, x, y, s};
@@ -1479,9 +1608,9 @@ extern "C" ABIP_API int abip_solve_dense_noalloc(int32_t m, int32_t n, const dou
   abip::dense_setup_kernel<<<1, abip::kThreads, smem_setup, st>>>(dinst, 1, queue);
   cudaMemsetAsync(queue, 0, 2 * sizeof(int), st);
   abip::DenseParams dp{prm.beta, prm.gamma, prm.alpha, prm.eps, prm.max_admm_iters, prm.warmstart,
-                       prm.stop_rule, 0, 1};
+                       prm.stop_rule, 0, 1, 0, 0, 0.0, 0.0};
   const size_t smem_solve = (size_t)(5 * m + 3 * n) * sizeof(double);
-  abip::dense_solve_kernel<double><<<1, abip::kThreads, smem_solve, st>>>(dinst, 1, dp, queue);
+  abip::dense_solve_kernel<double, 1><<<1, abip::kThreads, smem_solve, st>>>(dinst, 1, dp, queue, nullptr);
   cudaError_t e = cudaGetLastError();
   if (e == cudaSuccess) e = cudaMemcpyAsync(&I, dinst, sizeof(I), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);

@@ -352,6 +352,20 @@ def test_central_point_gradient_vertex_limit():
     assert np.abs(g["dA"] - dA).max() <= 1e-6 * np.abs(dA).max()
 
 
+def test_random_udv_lp_reaches_its_planted_value():
+    """The random LP of Sec. 5.1: x0 >= 0, s0 >= 0 with x0 o s0 = 0, b = A x0, c = A^T y0 + s0,
+    so x0 and (y0, s0) are optimal and the optimum is c^T x0 = b^T y0 exactly.  (At m = 20
+    the 0.2-dense U is singular for some seeds; seed 12 gives A full row rank, as the
+    paper's sizes do with high probability.)"""
+    lp = W.random_udv(20, 60, seed=12)
+    assert np.all(lp.x0 >= 0) and np.all(lp.s0 >= 0) and np.all(lp.x0 * lp.s0 == 0)
+    assert (lp.x0 == 0).sum() == 36 and abs(lp.c @ lp.x0 - lp.b @ lp.y0) <= 1e-9 * abs(lp.c @ lp.x0)
+    assert np.linalg.matrix_rank(lp.A) == 20
+    r = O.solve(lp.A, lp.b, lp.c)
+    assert r.status == O.OPTIMAL
+    assert abs(r.obj - lp.p_star) <= 1e-5 * max(1.0, abs(lp.p_star))
+
+
 def test_basis_pursuit_recovers_sparse_vector():
     """Basis pursuit LP (min ||x||_1, D x = b as [D, -D] in standard form): x_true is feasible,
     so the optimum is at most ||x_true||_1; with 5 % nonzeros and m = n_d / 4 Gaussian
@@ -508,5 +522,5 @@ def test_bb_beta_solve_reaches_the_planted_optimum():
     assert r.status == O.OPTIMAL
     p_star = lp.c @ lp.x0
     assert abs(r.obj - p_star) <= 1e-5 * max(1.0, abs(p_star))
-    assert len(r.raw["betas"]) == r.outer_iters + 1
+    assert len(r.raw["betas"]) == r.outer_iters        # one selection per outer iteration k >= 1
     assert all(b > 0 for b in r.raw["betas"])
