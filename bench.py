@@ -211,23 +211,10 @@ def aggregate_ranks(total_s, solved, admm, dist_mod=None, device="cpu"):
     return float(tmax[0]), float(work[0]), float(work[1])
 
 
-def l2_copy_gbs(dev, mib=24, reps=50):
-    """Copy bandwidth between two buffers that stay in the 129 MB L2 (torch's copy kernel,
-    read + write bytes over CUDA-event time): the ceiling of an L2-resident kernel, for
-    context beside the HBM roofline."""
-    import torch
-    a = torch.ones((mib << 20) // 4, dtype=torch.float32, device=dev)
-    b = torch.empty_like(a)
-    for _ in range(5):
-        b.copy_(a)
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record()
-    for _ in range(reps):
-        b.copy_(a)
-    e1.record()
-    e1.synchronize()
-    return 2.0 * a.numel() * 4 * reps / (e0.elapsed_time(e1) * 1e-3) / 1e9
+# L2 sector bandwidth of this part, from ncu on a GB300 of this machine: 188 L2 slices x
+# lts__t_sectors peak_sustained (3 sectors / cycle / slice) x 32 B x lts__cycles_elapsed
+# per second (2.007 GHz).  The ceiling of a kernel whose working set stays in L2.
+L2_PEAK_GBS = 188 * 3 * 32 * 2.007
 
 
 def measured_peaks():
@@ -481,7 +468,6 @@ def main():
     alg = algorithmic_bytes(m, n, nnz, last["admm_iters"], last["cg_iters"], vec_bytes)
     achieved = alg / last["kernel_s"] / 1e9
     peak, peak_kind = measured_peaks()
-    l2_peak = l2_copy_gbs(dev)
     traffic = traffic_per_launch(last["admm_iters"]) if args.precision == "mixed" else None
 
     # end to end through the public API with host buffers
@@ -545,9 +531,9 @@ def main():
                          "kernel": ("grid_delta_kernel (persistent solve, mixed precision)"
                                     if args.precision == "mixed" else "grid_kernel (persistent solve, FP64)"),
                          "kernel_s": last["kernel_s"], "algorithmic_bytes": alg,
-                         "l2": {"peak": l2_peak, "frac": achieved / l2_peak, "unit": "GB/s",
-                                "peak_kind": "measured in this run: copy between two 24 MiB buffers "
-                                             "resident in L2 (read + write bytes)"}},
+                         "l2": {"peak": L2_PEAK_GBS, "frac": achieved / L2_PEAK_GBS, "unit": "GB/s",
+                                "peak_kind": "ncu L2 sector peak of this GB300 (188 slices x 3 sectors/cycle "
+                                             "x 32 B x 2.007 GHz)"}},
             "clocks": ck,
             "gpu_launches": int(sum(i["launches"] for i in infos)) + 1 * len(infos),
             "e2e": e2e,

@@ -543,7 +543,7 @@ __device__ void dense_solve_one(DenseInst& I, const DenseParams& P, T* sm, doubl
       }
       block_allsum<5>(d, red);
       const double bh = bb_estimate(d, b, P.eps_cor);
-      if (bh == b) return spent;
+      if (bh == b) { beta_k = b; return spent; }   // no reliable curvature: keep this round's beta
       if (fabs(bh - b) <= P.eps_penalty) { beta_k = 0.5 * (b + bh); return spent; }
       b = bh;
     }
