@@ -133,7 +133,14 @@ typedef struct {
                                Results do not depend on the choice.  Default 0 */
     int32_t batch_order;    /* abip_solve_batch: 1 = hand the instances to the CTAs largest first
                                (m n + m^2 descending), 0 = in the given order; default 1 */
-    int32_t reserved[6];
+    double gamma_max;       /* adaptive decrease ratio (Sec. 5 raises gamma near the optimum without a
+                               rule): 0 = gamma at every mu <- gamma mu (default); else in [gamma, 1):
+                               each decrease takes gamma + (gamma_max - gamma) t, t the position of
+                               log10 rho between log10 0.1 (t = 0) and log10 eps (t = 1), clamped to
+                               [0, 1], rho = max(pres, dres, dgap) of the iterate at the decrease.
+                               Every path; the warm start of Eq. update-next-iterate takes the same
+                               ratio */
+    int32_t reserved[4];
 } abip_params;
 
 typedef struct {

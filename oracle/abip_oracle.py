@@ -34,7 +34,7 @@ prox; A10 CG stop rule; A13 MAX_ITER status; B5 Barzilai-Borwein beta (Sec. 4.3,
 opt-in): continue from the trial iterates, at most 5 redo rounds and never past the
 update cap, keeping the beta that produced the state when the rounds run out; B6 the
 curvature pairs with the printed signs; B7 the selection starts at the second outer
-iteration.
+iteration; B11 the adaptive decrease ratio (opt-in).
 
 Parity status: every function here is pinned by tests in tests/test_oracle_*.py
 except the exact iteration trajectory of `solve` (iteration counts, the iterates
@@ -86,6 +86,9 @@ class Params:
     eps_cor: float = 0.2         # Sec. 4.3 curvature-quality threshold (value from Sec. 5)
     eps_penalty: float = 0.1     # Sec. 4.3 heuristic threshold (value from Sec. 5)
     bb_max_redo: int = 5         # reading B5: the paper does not bound the "redo" loop
+    gamma_max: float = 0.0       # Sec. 5 adaptive decrease ratio (reading B11): 0 keeps gamma fixed;
+                                 # else gamma_for() raises gamma from `gamma` toward gamma_max as the
+                                 # relative KKT residual falls from 1e-1 to eps
 
 
 @dataclass
@@ -493,6 +496,22 @@ def bb_select(P: Problem, proj: Projection, st0: dict, mu: float, beta: float, p
     return used, st, spent
 
 
+GAMMA_FAR = 1e-1   # reading B11: residual at and above which the decrease ratio is prm.gamma
+
+
+def gamma_for(prm: Params, rho: float) -> float:
+    """The decrease ratio of the next mu <- gamma mu.  Sec. 5 increases gamma as the iterate
+    approaches the optimal solution without a formula (reading B11): with gamma_max > 0,
+    gamma moves from prm.gamma to gamma_max linearly in log10 of the relative KKT residual
+    rho = max(pres, dres, dgap) of the current iterate, from rho >= 1e-1 to rho <= eps."""
+    if prm.gamma_max <= 0.0:
+        return prm.gamma
+    rho = rho if rho > 1e-300 else 1e-300      # also a NaN residual: the largest ratio
+    t = np.log10(GAMMA_FAR / rho) / np.log10(GAMMA_FAR / prm.eps)
+    t = min(1.0, max(0.0, float(t)))
+    return prm.gamma + (prm.gamma_max - prm.gamma) * t
+
+
 def warm_start(st: dict, gamma: float, rule: int):
     """Rescale after mu <- gamma mu.  rule 0 (Sec. 5): for each j keep the larger of
     x_j, s_j and multiply the other by gamma (ties keep x), the same for (tau, kappa),
@@ -543,6 +562,8 @@ def solve(A, b, c, prm: Optional[Params] = None, trace_iters: int = 0,
     updates.  on_iter(k, mu, state): optional callback after every update.
     """
     prm = prm or Params()
+    if prm.gamma_max != 0.0 and not (prm.gamma <= prm.gamma_max < 1.0):
+        raise ValueError("gamma_max must be 0 (off) or in [gamma, 1)")
     P = Problem(A, b, c)
     lin = make_linsys(P, prm)
     proj = Projection(P, lin)
@@ -553,6 +574,7 @@ def solve(A, b, c, prm: Optional[Params] = None, trace_iters: int = 0,
     mu = prm.beta                      # mu0 = beta
     beta_k = prm.beta
     betas = []
+    gammas = []                        # the ratio of every mu <- gamma mu (reading B11)
     total = 0
     outer = 0
     trace = []
@@ -589,7 +611,12 @@ def solve(A, b, c, prm: Optional[Params] = None, trace_iters: int = 0,
                 break
         if status != 0:
             break
-        mu *= prm.gamma
+        g = prm.gamma
+        if prm.gamma_max > 0.0:     # reading B11: from the residuals of the current state
+            cur = termination(P, st["y"], st["x"], st["s"], st["tau"], prm.eps, nb, nc)
+            g = gamma_for(prm, max(cur.pres, cur.dres, cur.dgap))
+        gammas.append(g)
+        mu *= g
         outer += 1
         if prm.stop_rule == 1 and mu < prm.eps:
             status = OPTIMAL
@@ -597,7 +624,7 @@ def solve(A, b, c, prm: Optional[Params] = None, trace_iters: int = 0,
         if outer >= MAX_OUTER:          # mu has underflowed; stop as unsolved
             status = MAX_ITER
             break
-        warm_start(st, prm.gamma, prm.warmstart)
+        warm_start(st, g, prm.warmstart)
     if chk is None:
         chk = termination(P, st["y"], st["x"], st["s"], st["tau"], prm.eps, nb, nc)
     tau = st["tau"]
@@ -612,7 +639,7 @@ def solve(A, b, c, prm: Optional[Params] = None, trace_iters: int = 0,
                   mu=mu, admm_iters=total, outer_iters=outer, cg_iters=getattr(lin, "iters", 0),
                   pres=chk.pres, dres=chk.dres, dgap=chk.dgap, obj=chk.ctx / tau,
                   raw=dict(y=y.copy(), x=x.copy(), s=s.copy(), tau=tau, kappa=st["kappa"], theta=st["theta"],
-                           betas=betas),
+                           betas=betas, gammas=gammas),
                   trace=trace)
 
 

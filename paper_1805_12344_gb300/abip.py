@@ -67,7 +67,8 @@ class abip_params(C.Structure):
                 ("stop_rule", C.c_int32), ("check_every", C.c_int32), ("grid_ctas", C.c_int32),
                 ("barrier_limit_ns", C.c_int64), ("bb_beta", C.c_int32), ("bb_max_redo", C.c_int32),
                 ("eps_cor", C.c_double), ("eps_penalty", C.c_double), ("autotune", C.c_int32),
-                ("batch_order", C.c_int32), ("reserved", C.c_int32 * 6)]
+                ("batch_order", C.c_int32), ("gamma_max", C.c_double),
+                ("reserved", C.c_int32 * 4)]
 
 
 class abip_info(C.Structure):

@@ -136,6 +136,10 @@ int check_params(const abip_params& p, std::string& why) {
   if (p.stop_rule != 0 && p.stop_rule != 1) { why = "stop_rule must be 0 or 1"; return 0; }
   if (p.barrier_limit_ns < 0) { why = "barrier_limit_ns must be >= 0"; return 0; }
   if (p.bb_beta != 0 && p.bb_beta != 1) { why = "bb_beta must be 0 or 1"; return 0; }
+  if (!(p.gamma_max == 0.0 || (p.gamma_max >= p.gamma && p.gamma_max < 1.0))) {
+    why = "gamma_max must be 0 (off) or in [gamma, 1)";
+    return 0;
+  }
   if (p.autotune != 0 && p.autotune != 1) { why = "autotune must be 0 or 1"; return 0; }
   if (p.batch_order != 0 && p.batch_order != 1) { why = "batch_order must be 0 or 1"; return 0; }
   if (p.bb_beta && (p.bb_max_redo < 0 || !(p.eps_cor >= 0) || !(p.eps_penalty >= 0))) {
@@ -373,6 +377,7 @@ int setup_grid_path(abip_handle* h, G& g, const HostCSR& A, const std::vector<do
   cudaMemcpy((void*)g.c, c.data(), n * sizeof(double), cudaMemcpyHostToDevice);
   SolveCtl hc{};
   hc.beta = h->prm.beta; hc.gamma = h->prm.gamma; hc.alpha = h->prm.alpha; hc.eps = h->prm.eps;
+  hc.gamma_max = h->prm.gamma_max;
   hc.cg_tol = h->prm.cg_tol; hc.cg_rel = h->prm.cg_rel; hc.cg_max = h->prm.cg_max_iter; hc.max_admm = h->prm.max_admm_iters;
   hc.warmstart = h->prm.warmstart; hc.stop_rule = h->prm.stop_rule; hc.check_every = std::max(1, h->prm.check_every);
   hc.cg_warm = h->prm.cg_warm;
@@ -594,7 +599,7 @@ int dense_run_setup(abip_handle* h, DenseInst* dinst, int* queue, int count, int
 DenseParams dense_params(const abip_params& p) {
   return DenseParams{p.beta, p.gamma, p.alpha, p.eps, p.max_admm_iters, p.warmstart, p.stop_rule,
                      p.precision != ABIP_PREC_F64 ? 1 : 0, std::max(1, p.check_every), p.bb_beta ? 1 : 0,
-                     p.bb_max_redo, p.eps_cor, p.eps_penalty};
+                     p.bb_max_redo, p.eps_cor, p.eps_penalty, p.gamma_max};
 }
 
 int dense_run_solve(abip_handle* h, DenseInst* dinst, int* queue, int count, int grid, size_t smem,
@@ -1234,6 +1239,7 @@ int abip_solve_batch_shared(int32_t count, const abip_matrix* A, const double* c
   }
   abip::ShParams sp{};
   sp.beta = prm.beta; sp.gamma = prm.gamma; sp.alpha = prm.alpha; sp.eps = prm.eps;
+  sp.gamma_max = prm.gamma_max;
   sp.max_admm = prm.max_admm_iters; sp.warmstart = prm.warmstart; sp.stop_rule = prm.stop_rule;
   sp.mixed = prm.precision != ABIP_PREC_F64 ? 1 : 0;
   sp.tc = 0;

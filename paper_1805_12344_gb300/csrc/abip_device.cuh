@@ -236,6 +236,20 @@ __device__ __forceinline__ void barrier_step(T omega, T c, T& x, T& s) {
   }
 }
 
+// ---------------------------------------------------------------------------
+// decrease ratio of mu <- gamma mu (Sec. 5)
+// ---------------------------------------------------------------------------
+// Sec. 5 raises gamma as the iterate approaches the optimum but gives no rule (reading
+// B11): with gamma_max > 0 the ratio moves from gamma to gamma_max linearly in log10 of
+// rho = max(pres, dres, dgap) of the current iterate, from rho >= 1e-1 down to rho <= eps.
+constexpr double kGammaFar = 1e-1;
+__device__ __forceinline__ double adaptive_gamma(double gamma, double gamma_max, double eps, double rho) {
+  if (!(gamma_max > 0.0)) return gamma;
+  double t = log10(kGammaFar / fmax(rho, 1e-300)) / log10(kGammaFar / eps);
+  t = fmin(1.0, fmax(0.0, t));
+  return gamma + (gamma_max - gamma) * t;
+}
+
 template <typename T> __device__ __forceinline__ T ldv(const T* p) { return *p; }
 
 template <typename V>

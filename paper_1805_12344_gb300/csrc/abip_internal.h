@@ -22,6 +22,7 @@ enum GridMode : int { MODE_SETUP = 0, MODE_SOLVE = 1 };
 struct SolveCtl {
   // inputs
   double beta, gamma, alpha, eps, cg_tol, cg_rel;
+  double gamma_max;               // > 0: adaptive decrease ratio (adaptive_gamma)
   double zbar, xi, nb, nc;
   double Kinv[4];                 // inverse of the 2x2 Schur complement, row-major
   int64_t max_admm;
@@ -200,6 +201,7 @@ struct DenseParams {
   int32_t bb;             // 1: Barzilai-Borwein beta at each outer iteration (FP64 path)
   int32_t bb_max_redo;
   double eps_cor, eps_penalty;
+  double gamma_max;       // > 0: adaptive decrease ratio (adaptive_gamma)
 };
 
 // global scratch of the Barzilai-Borwein selection per instance (DenseInst::work)
@@ -234,6 +236,7 @@ struct ShInst {
   int64_t total, level_start, next_confirm;
   int32_t outer, status, action, last, err;
   int32_t pending;                 // mixed: the FP32-maintained screen passed; decide at the next refresh
+  double gam;                      // the decrease ratio of the last mu <- gam mu (the warm start's)
 };
 
 struct ShParams {
@@ -244,6 +247,7 @@ struct ShParams {
   int32_t refresh;                 // mixed: FP64 recomputation of the maintained products every `refresh` cycles
   int32_t tc;                      // mixed: products with A on the tensor cores: 0 off, else the number
                                    // of bfloat16 terms of A (1: A exact in bfloat16, 3: A in FP32)
+  double gamma_max;                // > 0: adaptive decrease ratio (adaptive_gamma)
 };
 
 // Device arrays of one iteration type; every vector is [length x B], instance fastest.

@@ -571,22 +571,23 @@ __device__ void dense_solve_one(DenseInst& I, const DenseParams& P, T* sm, doubl
   bool ok = outer_start();
   while (ok) {
     if (inner2 <= mu) {
-      mu *= gamma;
+      const double gk = adaptive_gamma(gamma, P.gamma_max, eps, fmax(pres, fmax(dres, dgap)));
+      mu *= gk;
       ++outer;
       if (P.stop_rule == 1 && mu < eps) { status = ABIP_OPTIMAL; break; }
       if (outer >= kMaxOuter) { status = ABIP_MAX_ITER; break; }   // mu has underflowed
-      const T g = (T)gamma, sg = (T)sqrt(gamma);
+      const T g = (T)gk, sg = (T)sqrt(gk);
       if (P.warmstart == 1) {
         for (int j = threadIdx.x; j < n; j += kThreads) { x[j] *= sg; s[j] *= sg; }
-        tau *= sqrt(gamma); kappa *= sqrt(gamma);
+        tau *= sqrt(gk); kappa *= sqrt(gk);
       } else {
         for (int j = threadIdx.x; j < n; j += kThreads) {
           if (x[j] >= s[j]) s[j] *= g; else x[j] *= g;
         }
-        if (tau >= kappa) kappa *= gamma; else tau *= gamma;
+        if (tau >= kappa) kappa *= gk; else tau *= gk;
       }
       for (int i = threadIdx.x; i < m; i += kThreads) y[i] *= sg;
-      theta *= sqrt(gamma);
+      theta *= sqrt(gk);
       __syncthreads();
       ok = outer_start();
       continue;
@@ -817,22 +818,23 @@ __device__ void dense_solve_delta(DenseInst& I, const DenseParams& P, unsigned c
   bool ok = evaluate(false);
   while (ok) {
     if (inner2 <= mu) {
-      mu *= gamma;
+      const double gk = adaptive_gamma(gamma, P.gamma_max, eps, fmax(pres, fmax(dres, dgap)));
+      mu *= gk;
       ++outer;
       if (P.stop_rule == 1 && mu < eps) { status = ABIP_OPTIMAL; break; }
       if (outer >= kMaxOuter) { status = ABIP_MAX_ITER; break; }
-      const double sg = sqrt(gamma);
+      const double sg = sqrt(gk);
       for (int j = threadIdx.x; j < n; j += kThreads) {
         const double x0 = x[j], s0 = s[j];
         if (P.warmstart == 1) { x[j] = x0 * sg; s[j] = s0 * sg; }
-        else if (x0 >= s0) s[j] = s0 * gamma;
-        else x[j] = x0 * gamma;
+        else if (x0 >= s0) s[j] = s0 * gk;
+        else x[j] = x0 * gk;
         dx[j] = (float)(x[j] - x0);
         ds[j] = (float)(s[j] - s0);
       }
       if (P.warmstart == 1) { tau *= sg; kappa *= sg; }
-      else if (tau >= kappa) kappa *= gamma;
-      else tau *= gamma;
+      else if (tau >= kappa) kappa *= gk;
+      else tau *= gk;
       for (int i = threadIdx.x; i < m; i += kThreads) {
         const double y0 = y[i];
         y[i] = y0 * sg;
@@ -1608,7 +1610,7 @@ extern "C" ABIP_API int abip_solve_dense_noalloc(int32_t m, int32_t n, const dou
   abip::dense_setup_kernel<<<1, abip::kThreads, smem_setup, st>>>(dinst, 1, queue);
   cudaMemsetAsync(queue, 0, 2 * sizeof(int), st);
   abip::DenseParams dp{prm.beta, prm.gamma, prm.alpha, prm.eps, prm.max_admm_iters, prm.warmstart,
-                       prm.stop_rule, 0, 1, 0, 0, 0.0, 0.0};
+                       prm.stop_rule, 0, 1, 0, 0, 0.0, 0.0, prm.gamma_max};
   const size_t smem_solve = (size_t)(5 * m + 3 * n) * sizeof(double);
   abip::dense_solve_kernel<double, 1><<<1, abip::kThreads, smem_solve, st>>>(dinst, 1, dp, queue, nullptr);
   cudaError_t e = cudaGetLastError();

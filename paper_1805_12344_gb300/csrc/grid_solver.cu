@@ -459,7 +459,6 @@ struct Solver {
     const Thr t = th;
     const double alpha = C->alpha, beta = C->beta, gamma = C->gamma, eps = C->eps;
     const double cg_rel = C->cg_rel;
-    const double sqrt_gamma = sqrt(gamma);
     double tau = C->tau, kappa = C->kappa, theta = C->theta, mu = C->mu;
     int64_t total = C->admm_iters;
     int64_t cgtot = C->cg_iters;
@@ -507,24 +506,26 @@ struct Solver {
     for (;;) {
       // inner stop, Eq. inner-stop: ||Q u - v||^2 <= mu
       if (inner2 <= mu) {
-        mu *= gamma;
+        const double gk = adaptive_gamma(gamma, C->gamma_max, eps, fmax(pres, fmax(dres, dgap)));
+        const double sqrt_gk = sqrt(gk);
+        mu *= gk;
         ++outer;
         if (C->stop_rule == 1 && mu < eps) { status = ABIP_OPTIMAL; break; }
         if (outer >= kMaxOuter) { status = ABIP_MAX_ITER; break; }   // mu has underflowed
         // warm start (Sec. 5 heuristic, or Eq. update-next-iterate)
-        const T g = (T)gamma, sg = (T)sqrt_gamma;
+        const T g = (T)gk, sg = (T)sqrt_gk;
         if (C->warmstart == 1) {
           for (int j = t.gtid; j < D.n; j += t.nthr) { D.x[j] *= sg; D.s[j] *= sg; }
-          tau *= sqrt_gamma; kappa *= sqrt_gamma;
+          tau *= sqrt_gk; kappa *= sqrt_gk;
         } else {
           for (int j = t.gtid; j < D.n; j += t.nthr) {
             const T xj = D.x[j], sj = D.s[j];
             if (xj >= sj) D.s[j] = g * sj; else D.x[j] = g * xj;
           }
-          if (tau >= kappa) kappa *= gamma; else tau *= gamma;
+          if (tau >= kappa) kappa *= gk; else tau *= gk;
         }
         for (int i = t.gtid; i < D.m; i += t.nthr) D.y[i] *= sg;
-        theta *= sqrt_gamma;
+        theta *= sqrt_gk;
         if (!sync(P_WARM)) return;
         if (!evaluate(false)) return;
         continue;

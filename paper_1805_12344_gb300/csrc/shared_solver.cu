@@ -611,19 +611,20 @@ __global__ void ctrl_eval_kernel(ShInst* insts, int B, int n, const double* part
   }
   atomicAdd(&flags[0], 1);
   if (I.inner2 <= I.mu) {
-    I.mu *= P.gamma;
+    I.gam = adaptive_gamma(P.gamma, P.gamma_max, P.eps, fmax(I.pres, fmax(I.dres, I.dgap)));
+    I.mu *= I.gam;
     I.outer += 1;
     I.level_start = I.total;
     if (P.stop_rule == 1 && I.mu < P.eps) { I.status = ABIP_OPTIMAL; I.action = SH_DONE; return; }
     if (I.outer >= kMaxOuter) { I.status = ABIP_MAX_ITER; I.action = SH_DONE; return; }
-    const double sg = sqrt(P.gamma);
+    const double sg = sqrt(I.gam);
     if (P.warmstart == 1) {
       I.tau *= sg;
       I.kappa *= sg;
     } else if (I.tau >= I.kappa) {
-      I.kappa *= P.gamma;
+      I.kappa *= I.gam;
     } else {
-      I.tau *= P.gamma;
+      I.tau *= I.gam;
     }
     I.theta *= sg;
     I.action = SH_WARM;
@@ -720,7 +721,7 @@ __global__ void update_kernel(ShView<T> V, const ShInst* __restrict__ insts, ShP
         *sp = sn;
       }
     } else if (act == SH_WARM) {
-      const T sg = (T)sqrt(P.gamma), g = (T)P.gamma;
+      const T sg = (T)sqrt(I.gam), g = (T)I.gam;
       if (r < m) {
         V.Y[(size_t)r * B + k] *= sg;
       } else {

@@ -134,7 +134,8 @@ def test_shared_and_backward_argument_errors_without_device(lib):
         abip.abip_solve_batch([np.eye(2, 3)], [np.ones(2)], [np.ones(3)],
                               abip.default_params(bb_beta=1, precision=abip.ABIP_PREC_MIXED))
     assert e.value.code == abip.ABIP_E_UNSUPPORTED
-    for bad in (dict(bb_beta=2), dict(bb_beta=1, eps_cor=-1.0), dict(bb_beta=1, bb_max_redo=-1)):
+    for bad in (dict(bb_beta=2), dict(bb_beta=1, eps_cor=-1.0), dict(bb_beta=1, bb_max_redo=-1),
+                dict(gamma_max=0.05), dict(gamma_max=1.0), dict(gamma_max=-0.5)):   # [gamma, 1) or 0
         with pytest.raises(abip.AbipError) as e:
             abip.abip_solve_batch([np.eye(2, 3)], [np.ones(2)], [np.ones(3)], abip.default_params(**bad))
         assert e.value.code == abip.ABIP_E_INVALID_ARG

@@ -524,3 +524,72 @@ def test_bb_beta_solve_reaches_the_planted_optimum():
     assert abs(r.obj - p_star) <= 1e-5 * max(1.0, abs(p_star))
     assert len(r.raw["betas"]) == r.outer_iters        # one selection per outer iteration k >= 1
     assert all(b > 0 for b in r.raw["betas"])
+
+
+# --- Sec. 5: the adaptive decrease ratio (reading B11) -------------------------------
+
+def test_gamma_for_endpoints_and_log_linear_midpoint():
+    """The ratio is gamma far from the optimum (residual >= 1e-1), gamma_max at the target
+    (residual <= eps), the mean of the two at the geometric mean of 1e-1 and eps, never
+    outside [gamma, gamma_max], and gamma itself when the rule is off."""
+    prm = O.Params(gamma=0.1, gamma_max=0.5, eps=1e-6)
+    assert O.gamma_for(prm, 10.0) == 0.1
+    assert O.gamma_for(prm, 1e-1) == 0.1
+    assert O.gamma_for(prm, 1e-6) == pytest.approx(0.5, abs=1e-15)
+    assert O.gamma_for(prm, 1e-12) == 0.5
+    assert O.gamma_for(prm, 0.0) == 0.5
+    assert O.gamma_for(prm, math.sqrt(1e-1 * 1e-6)) == pytest.approx(0.3, rel=1e-12)
+    rhos = np.logspace(1, -9, 61)
+    g = [O.gamma_for(prm, r) for r in rhos]
+    assert all(0.1 <= v <= 0.5 for v in g)
+    assert all(b >= a for a, b in zip(g, g[1:]))        # smaller residual, larger ratio
+    assert O.gamma_for(O.Params(gamma=0.2), 1e-5) == 0.2
+
+
+def _rel_kkt(A, b, c, st):
+    """Sec. 4.1 relative residuals of the candidate (x, y, s) / tau, in plain numpy."""
+    tau = st["tau"]
+    x, y, s = st["x"] / tau, st["y"] / tau, st["s"] / tau
+    pres = np.linalg.norm(A @ x - b) / (1 + np.linalg.norm(b))
+    dres = np.linalg.norm(A.T @ y + s - c) / (1 + np.linalg.norm(c))
+    gap = abs(c @ x - b @ y) / (1 + abs(c @ x) + abs(b @ y))
+    return max(pres, dres, gap)
+
+
+def test_adaptive_gamma_follows_the_residual_of_the_iterate():
+    """Every decrease mu <- g mu takes g from the residual of the iterate it leaves: the
+    recorded ratios multiply to mu_final / mu0, each lies in [gamma, gamma_max], and each
+    decrease that follows an ADMM update matches the ratio of that update's iterate
+    (its residuals recomputed here from Sec. 4.1's definitions)."""
+    lp = W.planted_dense(8, 20, seed=5)
+    prm = O.Params(gamma=0.1, gamma_max=0.4)
+    last = {}
+
+    def on_iter(k, mu, st):
+        last[mu] = {key: (v.copy() if isinstance(v, np.ndarray) else v) for key, v in st.items()}
+
+    r = O.solve(lp.A, lp.b, lp.c, prm, on_iter=on_iter)
+    gam = r.raw["gammas"]
+    assert r.status == O.OPTIMAL and len(gam) == r.outer_iters > 0
+    assert math.prod(gam) * prm.beta == pytest.approx(r.mu, rel=1e-12)
+    assert all(0.1 <= g <= 0.4 for g in gam)
+    assert gam[-1] > 0.1                                  # the rule moved the ratio
+    mu, checked = prm.beta, 0
+    for g in gam:
+        if mu in last:
+            assert g == pytest.approx(O.gamma_for(prm, _rel_kkt(lp.A, lp.b, lp.c, last[mu])), rel=1e-9)
+            checked += 1
+        mu *= g
+    assert checked >= len(gam) - 1
+
+
+def test_adaptive_gamma_off_and_flat_reproduce_the_fixed_ratio():
+    """gamma_max = gamma gives the fixed-ratio iteration exactly, and the adaptive run
+    reaches the planted optimum (Theorem 3.1 holds for any ratio in (0, 1))."""
+    lp = W.planted_dense(8, 20, seed=5)
+    a = O.solve(lp.A, lp.b, lp.c, O.Params(gamma=0.2))
+    b = O.solve(lp.A, lp.b, lp.c, O.Params(gamma=0.2, gamma_max=0.2))
+    assert a.admm_iters == b.admm_iters and np.array_equal(a.x, b.x) and np.array_equal(a.y, b.y)
+    c = O.solve(lp.A, lp.b, lp.c, O.Params(gamma=0.1, gamma_max=0.5))
+    assert c.status == O.OPTIMAL
+    assert abs(c.obj - lp.p_star) <= 1e-5 * max(1.0, abs(lp.p_star))
