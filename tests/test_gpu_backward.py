@@ -1,6 +1,7 @@
 """GPU gradients of x* = x / tau at the central point of the final mu (abip_backward,
 abip_backward_batch and the autograd layer) against the oracle's dense KKT gradient,
-the vertex limit and FP64 central differences of the oracle's central-point map.
+the checkpointed unrolled backward through the inner iterations, the vertex limit and
+FP64 central differences of the oracle's central-point map.
 
 Bar: 1e-5 relative (per block, against the block's largest entry).  The L1-SVM LP is
 dual degenerate (the bias is split into two free columns of zero cost), so its central
@@ -118,6 +119,28 @@ def test_backward_central_differences(abip):
             fd[k] = (vals[0] - vals[1]) / (2 * h)
         scale = np.abs(out[which]).max()
         assert np.abs(got - fd).max() <= GRAD_TOL * scale, (which, np.abs(got - fd).max() / scale)
+
+
+@pytest.mark.parametrize("d,N", [(8, 40), (16, 96)])
+def test_backward_matches_unrolled_backward(abip, d, N):
+    """The adjoint kernel (abip_backward_batch) at the central point of mu = 1e-2 against the
+    checkpointed unrolled backward: reverse mode through 2000 inner iterations of Algorithm 2
+    from the same point (oracle/unrolled.py), a route with no KKT solve at all."""
+    from oracle.unrolled import unrolled_grad
+    lp = W.l1_svm(d=d, N=N, seed=5)
+    mu = 1e-2
+    cp = O.central_point(lp.A, lp.b, lp.c, mu)
+    tau = cp["tau"]
+    xs = cp["x"] / tau
+    g = 2.0 * (xs - lp.meta["x_target"])
+    info = dict(status=abip.ABIP_OPTIMAL, tau=tau, kappa=cp["kappa"], theta=cp["theta"], mu=mu)
+    dcs, dbs, dAs = abip.abip_backward_batch([lp.A], [lp.b], [lp.c], [xs], [cp["y"] / tau], [cp["s"] / tau],
+                                             [info], [g])
+    start = {k: cp[k] for k in ("y", "x", "tau", "theta", "s", "kappa")}
+    ref = unrolled_grad(lp.A, lp.b, lp.c, mu, lambda x_: g, start, iters=2000, segment=200)
+    assert _blockrel(dcs[0], ref["dc"]) <= GRAD_TOL, _blockrel(dcs[0], ref["dc"])
+    assert _blockrel(dbs[0], ref["db"]) <= GRAD_TOL, _blockrel(dbs[0], ref["db"])
+    assert _blockrel(dAs[0], ref["dA"]) <= GRAD_TOL, _blockrel(dAs[0], ref["dA"])
 
 
 def test_backward_batch_matches_single(abip):
