@@ -678,7 +678,7 @@ struct DeltaSolver {
         const double ux = (x0 + s0 + D.ATz[j]) - D.g1x[j] * t1 - D.g2x[j] * t2;
         const double xh = alpha * ux + a1 * x0;
         double xn, sn;
-        barrier_step<double>(xh - s0, cmu, xn, sn);
+        barrier_step_newton(xh - s0, cmu, xn, sn);
         D.x[j] = xn;
         D.s[j] = sn;
         D.xsw[j].dx = (float)(xn - x0);
