@@ -72,8 +72,9 @@ extern "C" {
                                     solve, with an FP64 right-hand side); FP64 tests.  A CSR A's values
                                     are used rounded to FP32 */
 #define ABIP_PREC_MIXED_BF16 2   /* as MIXED; the shared-A batch runs its products with A on the tensor
-                                    cores (tcgen05, bfloat16 operands, FP32 accumulation) and needs an
-                                    A exactly representable in bfloat16; other paths treat it as MIXED */
+                                    cores (tcgen05, bfloat16 operands, FP32 accumulation): A as one
+                                    bfloat16 plane when exact in bfloat16, else as three (any A within
+                                    the FP32 range); other paths treat it as MIXED */
 
 /* linear system for the projection (Sec. 4.4) */
 #define ABIP_LINSYS_DENSE_CHOL  0   /* G = I + A A^T formed once, Cholesky G = L L^T, triangular solves */
@@ -316,6 +317,60 @@ ABIP_API int64_t abip_state_size(const abip_handle* h);
 ABIP_API int abip_solve_dense_noalloc(int32_t m, int32_t n, const double* A, int64_t ld,
                                       const double* b, const double* c, const abip_params* p,
                                       double* x, double* y, double* s, abip_info* info, void* stream);
+
+/* ---- presolve (Sec. 4.5) --------------------------------------------------- */
+/*
+ * Host presolve of the general LP
+ *     min c^T x  s.t.  A x = b,  l <= x <= w        (l_j may be -inf, w_j +inf)
+ * into the standard form the solver takes (min chat^T xhat, Ahat xhat = bhat, xhat >= 0):
+ * the reductions P1-P7 of Sec. 4.5 (empty rows and columns, infeasible, fixed and free
+ * variables, singleton rows, and the rows the Dulmage-Mendelsohn decomposition shows
+ * dependent), the rewriting of the bounds (x = l + xbar with xbar + t = w - l when both are
+ * finite, x = w - xbar when only w is, x = x+ - x- when free), then `ruiz` passes of Ruiz
+ * equilibration (Ahat = D A E, bhat = D b, chat = E c; the Remark closing Sec. 4.5).
+ * The objective of the original LP is chat^T xhat + info->obj_offset.
+ *   A: host matrix (dense or CSR, F32 or F64; m >= 0, n >= 1, no n >= m requirement).
+ *   b (m), c (n), l (n), w (n): host; non-finite b, c or NaN bounds -> ABIP_E_INVALID_ARG.
+ *   tol in (0, 1): the tolerance of the zero tests (1e-9 is a good default).
+ *   *out: receives the presolved problem (free with abip_presolve_free), also when the
+ *   reductions alone decide the LP: info->status is then ABIP_PRIMAL_INFEASIBLE or
+ *   ABIP_DUAL_INFEASIBLE (the reason in abip_last_error(NULL)), else 0.
+ * Host code only; no GPU is needed.
+ */
+typedef struct abip_presolved abip_presolved;
+
+typedef struct {
+    int32_t status;          /* 0: the standard-form LP below is to be solved; else the status */
+    int32_t m, n;            /* standard form */
+    int64_t nnz;
+    double obj_offset;
+    int32_t empty_rows;      /* P1 */
+    int32_t singleton_rows;  /* P6 (each fixes one column) */
+    int32_t dependent_rows;  /* P7 */
+    int32_t fixed_cols;      /* P4 */
+    int32_t empty_cols;      /* P2 */
+    int32_t free_split;      /* P5: free columns written as x+ - x- */
+    int32_t upper_rows;      /* rows xbar + t = w - l added for finite upper bounds */
+    int32_t reserved[5];
+} abip_presolve_info;
+
+ABIP_API int abip_presolve(const abip_matrix* A, const double* b, const double* c, const double* l,
+                           const double* w, double tol, int32_t ruiz, abip_presolved** out,
+                           abip_presolve_info* info);
+
+/* Copy the standard-form LP out (host arrays sized from the info: row_ptr m+1, col_idx
+   and val nnz, b m, c n; any may be NULL).  ABIP_E_INVALID_ARG when status != 0. */
+ABIP_API int abip_presolved_lp(const abip_presolved* P, int64_t* row_ptr, int32_t* col_idx, double* val,
+                               double* b, double* c);
+
+/* Map a solution (x n, y m; s unused, may be NULL) of the standard-form LP back to the
+   original LP (host): x_out (n0), y_out (m0, may be NULL), z_out = c - A^T y_out (n0, may
+   be NULL), obj = c^T x_out (may be NULL).  Dropped rows get y = 0; a singleton row gets
+   the y that makes the reduced cost of the column it fixed zero. */
+ABIP_API int abip_postsolve(const abip_presolved* P, const double* x, const double* y, const double* s,
+                            double* x_out, double* y_out, double* z_out, double* obj);
+
+ABIP_API void abip_presolve_free(abip_presolved* P);
 
 /* Release every resource of h (NULL is accepted). */
 ABIP_API void abip_free(abip_handle* h);

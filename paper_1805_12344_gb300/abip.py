@@ -71,6 +71,13 @@ class abip_params(C.Structure):
                 ("reserved", C.c_int32 * 4)]
 
 
+class abip_presolve_info(C.Structure):
+    _fields_ = [("status", C.c_int32), ("m", C.c_int32), ("n", C.c_int32), ("nnz", C.c_int64),
+                ("obj_offset", C.c_double), ("empty_rows", C.c_int32), ("singleton_rows", C.c_int32),
+                ("dependent_rows", C.c_int32), ("fixed_cols", C.c_int32), ("empty_cols", C.c_int32),
+                ("free_split", C.c_int32), ("upper_rows", C.c_int32), ("reserved", C.c_int32 * 5)]
+
+
 class abip_info(C.Structure):
     _fields_ = [("status", C.c_int32), ("outer_iters", C.c_int32), ("admm_iters", C.c_int64),
                 ("cg_iters", C.c_int64), ("tau", C.c_double), ("kappa", C.c_double), ("theta", C.c_double),
@@ -111,6 +118,12 @@ _SIGS = {
     "abip_set_state": (C.c_int, [C.c_void_p, C.c_void_p]),
     "abip_state_size": (C.c_int64, [C.c_void_p]),
     "abip_free": (None, [C.c_void_p]),
+    "abip_presolve": (C.c_int, [C.POINTER(abip_matrix), C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                C.c_double, C.c_int32, C.POINTER(C.c_void_p), C.c_void_p]),
+    "abip_presolved_lp": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "abip_postsolve": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                 C.c_void_p, C.c_void_p]),
+    "abip_presolve_free": (None, [C.c_void_p]),
     "abip_status_str": (C.c_char_p, [C.c_int32]),
     "abip_last_error": (C.c_char_p, [C.c_void_p]),
     "abip_version": (C.c_char_p, []),
@@ -380,6 +393,58 @@ def abip_solve_batch_shared(A, bs: Sequence, cs: Sequence, params: Optional[abip
                                        sptr if want_solution else None, infos, _stream_arg(stream))
     _check(rc)
     return [infos[k].as_dict() for k in range(count)], xs, ys, ss
+
+
+class Presolved:
+    """abip_presolve of  min c^T x, A x = b, l <= x <= w  (Sec. 4.5) on the host: `info` (dict),
+    `lp()` the standard-form LP (a workloads.CSR, b, c), `postsolve(x, y)` the original
+    (x, y, z = c - A^T y, objective).  l / w: use -inf / +inf for absent bounds."""
+
+    def __init__(self, A, b, c, l, w, tol: float = 1e-9, ruiz: int = 10):
+        M, keep = _matrix(A)
+        arrs = [np.ascontiguousarray(v, dtype=np.float64) for v in (b, c, l, w)]
+        self._h = C.c_void_p()
+        inf = abip_presolve_info()
+        rc = lib().abip_presolve(C.byref(M), *[a.ctypes.data for a in arrs], tol, ruiz, C.byref(self._h),
+                                 C.byref(inf))
+        _check(rc)
+        self.info = {k: getattr(inf, k) for k, _ in abip_presolve_info._fields_ if k != "reserved"}
+        self.status = inf.status
+        self.why = lib().abip_last_error(None).decode() if inf.status else ""
+        self.m0, self.n0 = M.m, M.n
+
+    def lp(self):
+        m, n, nnz = self.info["m"], self.info["n"], self.info["nnz"]
+        rp = np.zeros(m + 1, dtype=np.int64)
+        ci = np.zeros(nnz, dtype=np.int32)
+        val = np.zeros(nnz, dtype=np.float64)
+        b = np.zeros(m)
+        c = np.zeros(n)
+        _check(lib().abip_presolved_lp(self._h, rp.ctypes.data, ci.ctypes.data, val.ctypes.data,
+                                       b.ctypes.data, c.ctypes.data))
+        return _W.CSR(m=m, n=n, row_ptr=rp, col_idx=ci, val=val), b, c
+
+    def postsolve(self, x, y):
+        x = np.ascontiguousarray(x, dtype=np.float64)
+        y = np.ascontiguousarray(y, dtype=np.float64)
+        xo = np.zeros(self.n0)
+        yo = np.zeros(self.m0)
+        zo = np.zeros(self.n0)
+        obj = C.c_double()
+        _check(lib().abip_postsolve(self._h, x.ctypes.data, y.ctypes.data, None, xo.ctypes.data,
+                                    yo.ctypes.data, zo.ctypes.data, C.byref(obj)))
+        return xo, yo, zo, obj.value
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().abip_presolve_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Solver:

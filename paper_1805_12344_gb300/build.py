@@ -12,7 +12,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(os.path.dirname(PKG), "include")
 BUILD_DIR = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libabip.so")
-SOURCES = ["abip_api.cu", "grid_solver.cu", "grid_delta.cu", "dense_solver.cu", "shared_solver.cu"]
+SOURCES = ["abip_api.cu", "grid_solver.cu", "grid_delta.cu", "dense_solver.cu", "shared_solver.cu", "presolve.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden"]
 

@@ -33,6 +33,14 @@ int fail(abip_handle* h, int code, const std::string& msg) {
   return code;
 }
 
+}  // namespace
+
+namespace abip {
+void set_global_error(const std::string& msg) { g_err = msg; }
+}  // namespace abip
+
+namespace {
+
 double now_s() {
   return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
 }

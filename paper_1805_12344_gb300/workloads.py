@@ -359,3 +359,136 @@ def basis_pursuit(m: int = 2048, n_d: int = 8192, batch: int = 64, density: floa
     cs = [np.ones(2 * n_d) for _ in range(batch)]
     return SharedBatch(A=A, bs=bs, cs=cs, meta=dict(kind="basis_pursuit", m=m, n=2 * n_d, n_d=n_d,
                                                     density=density, x_true=xs, bf16=bf16))
+
+
+# --- general-form LPs for the presolve (Sec. 4.5) and the SICE LPs (Sec. 5.2) ------------
+
+GENERAL = 6           # general-form LPs with bounds
+SICE = 7              # sparse inverse covariance estimation subproblems
+
+
+@dataclass
+class GeneralLP:
+    """min c^T x  s.t.  A x = b,  l <= x <= w  (l_j may be -inf, w_j +inf), dense A.
+    With a planted optimum (x0, y0, z0): z0 = c - A^T y0 has z0_j >= 0 where x0_j = l_j < w_j,
+    <= 0 where x0_j = w_j > l_j, 0 where l_j < x0_j < w_j (any sign where l_j = w_j), so
+    p_star = c^T x0 (the KKT conditions of the bounded LP)."""
+    A: np.ndarray
+    b: np.ndarray
+    c: np.ndarray
+    l: np.ndarray
+    w: np.ndarray
+    x0: Optional[np.ndarray] = None
+    y0: Optional[np.ndarray] = None
+    z0: Optional[np.ndarray] = None
+    p_star: Optional[float] = None
+    meta: dict = field(default_factory=dict)
+
+
+def general_lp(m: int = 24, n: int = 60, density: float = 0.3, seed: Optional[int] = None,
+               extras: bool = True) -> GeneralLP:
+    """A general-form LP with every kind of bound and, with `extras`, the structures each
+    reduction of Sec. 4.5 removes: two empty rows (P1), two empty columns (P2), two fixed
+    variables (P4), free variables (P5), two singleton rows (P6), and three rows on two
+    otherwise unused columns (a structurally over-determined block, P7).
+    Column kinds of the m x n core (N(0,1) entries at `density`): 35 % [l, inf),
+    25 % [l, w], 10 % (-inf, w], 10 % free, 20 % [l, inf) held at l; bounds l ~ U(-2, 1),
+    w = l + U(0.5, 3).  Each bounded variable sits at a bound (nonzero z0 of the matching
+    sign) or strictly inside (z0 = 0); y0 ~ N(0, 1)."""
+    rng = np.random.default_rng(seed_for(GENERAL) if seed is None else seed)
+    A = _sprandn(rng, m, n, density)
+    kind = rng.choice(5, size=n, p=[0.35, 0.25, 0.10, 0.10, 0.20])
+    l = np.full(n, -np.inf)
+    w = np.full(n, np.inf)
+    x0 = np.zeros(n)
+    z0 = np.zeros(n)
+    lo = rng.uniform(-2.0, 1.0, n)
+    width = rng.uniform(0.5, 3.0, n)
+    for j in range(n):
+        k = kind[j]
+        if k in (0, 4):                        # [l, inf)
+            l[j] = lo[j]
+            if k == 4 or rng.random() < 0.4:
+                x0[j], z0[j] = l[j], rng.uniform(0.5, 2.0)
+            else:
+                x0[j] = l[j] + rng.uniform(0.5, 2.0)
+        elif k == 1:                           # [l, w]
+            l[j], w[j] = lo[j], lo[j] + width[j]
+            r = rng.random()
+            if r < 1 / 3:
+                x0[j], z0[j] = l[j], rng.uniform(0.5, 2.0)
+            elif r < 2 / 3:
+                x0[j], z0[j] = w[j], -rng.uniform(0.5, 2.0)
+            else:
+                x0[j] = l[j] + width[j] * rng.uniform(0.2, 0.8)
+        elif k == 2:                           # (-inf, w]
+            w[j] = lo[j] + width[j]
+            if rng.random() < 0.5:
+                x0[j], z0[j] = w[j], -rng.uniform(0.5, 2.0)
+            else:
+                x0[j] = w[j] - rng.uniform(0.5, 2.0)
+        else:                                  # free
+            x0[j] = rng.standard_normal()
+    y0 = rng.standard_normal(m)
+    if extras:
+        # fixed variables (P4): two interior columns of the core get l = w = x0
+        inner = [j for j in range(n) if z0[j] == 0.0 and np.isfinite(l[j])][:2]
+        for j in inner:
+            l[j] = w[j] = x0[j]
+            z0[j] = rng.standard_normal()
+        # empty columns (P2): c > 0 at a finite lower bound, c < 0 at a finite upper bound
+        Ae = np.zeros((m, 2))
+        le = np.array([rng.uniform(-1, 1), -np.inf])
+        we = np.array([np.inf, rng.uniform(-1, 1)])
+        xe = np.array([le[0], we[1]])
+        ze = np.array([rng.uniform(0.5, 2.0), -rng.uniform(0.5, 2.0)])
+        # over-determined block (P7): two columns used only by three rows
+        xb = rng.uniform(0.5, 2.0, 2)
+        A = np.hstack([A, Ae, np.zeros((m, 2))])
+        l = np.concatenate([l, le, [0.0, 0.0]])
+        w = np.concatenate([w, we, [np.inf, np.inf]])
+        x0 = np.concatenate([x0, xe, xb])
+        z0 = np.concatenate([z0, ze, [0.0, 0.0]])
+        N = A.shape[1]
+        blk = np.zeros((3, N))
+        blk[:, N - 2:] = [[1.0, 1.0], [1.0, -1.0], [1.0, 2.0]]
+        # singleton rows (P6) on two interior core columns, empty rows (P1)
+        sing = np.zeros((2, N))
+        cols = [j for j in range(n) if z0[j] == 0.0 and np.isfinite(l[j]) and l[j] < w[j]][:2]
+        for r, j in enumerate(cols):
+            sing[r, j] = rng.uniform(0.5, 2.0) * rng.choice([-1.0, 1.0])
+        A = np.vstack([A[:m // 2], np.zeros((1, N)), sing, A[m // 2:], blk, np.zeros((1, N))])
+        y0 = rng.standard_normal(A.shape[0])
+    b = A @ x0
+    c = A.T @ y0 + z0
+    return GeneralLP(A=A, b=b, c=c, l=l, w=w, x0=x0, y0=y0, z0=z0, p_star=float(c @ x0),
+                     meta=dict(kind="general", m=A.shape[0], n=A.shape[1], extras=extras))
+
+
+def sice(d: int = 50, samples: Optional[int] = None, seed: Optional[int] = None):
+    """Sample covariance Sigma (d x d) of `samples` (default 2d) draws of a zero-mean Gaussian
+    whose precision matrix is tridiagonal (1 on the diagonal, -0.4 beside it), and the
+    tolerance lam = 1.5 sqrt(log d / samples) of Sec. 5.2."""
+    rng = np.random.default_rng(seed_for(SICE) if seed is None else seed)
+    N = 2 * d if samples is None else samples
+    Om = np.eye(d) - 0.4 * (np.eye(d, k=1) + np.eye(d, k=-1))
+    L = np.linalg.cholesky(np.linalg.inv(Om))
+    X = rng.standard_normal((N, d)) @ L.T
+    X -= X.mean(axis=0)
+    Sigma = X.T @ X / N
+    lam = 1.5 * np.sqrt(np.log(d) / N)
+    return Sigma, float(lam)
+
+
+def sice_general_lp(Sigma: np.ndarray, lam: float, j: int) -> GeneralLP:
+    """Column j of SICE (Sec. 5.2): min ||beta||_1 s.t. ||Sigma beta - e_j||_inf <= lam, as the
+    general LP  min e^T beta+ + e^T beta-  s.t.  Sigma beta+ - Sigma beta- - r = e_j,
+    beta+/- >= 0, -lam <= r <= lam  (no planted optimum)."""
+    d = Sigma.shape[0]
+    A = np.hstack([Sigma, -Sigma, -np.eye(d)])
+    b = np.zeros(d)
+    b[j] = 1.0
+    c = np.concatenate([np.ones(2 * d), np.zeros(d)])
+    l = np.concatenate([np.zeros(2 * d), np.full(d, -lam)])
+    w = np.concatenate([np.full(2 * d, np.inf), np.full(d, lam)])
+    return GeneralLP(A=A, b=b, c=c, l=l, w=w, meta=dict(kind="sice", d=d, j=j, lam=lam))
