@@ -11,6 +11,7 @@
 #include <mutex>
 #include <sstream>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "abip_device.cuh"
@@ -93,13 +94,6 @@ template <typename T>
 __global__ void output_kernel(const T* v, int64_t n, double scale, double* out) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     out[i] = static_cast<double>(v[i]) * scale;
-}
-
-int lanes_for(int64_t nnz, int rows) {
-  const double mean = rows > 0 ? (double)nnz / rows : 1.0;
-  int L = 2;
-  while (L < 32 && L < mean) L *= 2;
-  return L;
 }
 
 bool finite_all(const double* p, size_t n) {
@@ -222,13 +216,15 @@ std::vector<int32_t> warp_partition(const HostSell& S, int nwarp) {
   return w;
 }
 
-// lanes per row: the smallest power of two that leaves at most about 16 entries per lane
-// (on the 100000 x 400000 benchmark LP: 2 lanes for A's 25 entries per row, 1 for A^T's
-// 6.25; 2 lanes for A ran 6 % more updates per second than 4 or 8 in a 3000-update sweep)
-int sell_lanes(const HostCSR& M) {
+// lanes per row: the smallest power of two that leaves at most about `per_lane` entries
+// per lane.  On the 100000 x 400000 benchmark LP (25 entries per row of A, 6.25 of A^T):
+// the FP64 kernel takes 16 (2 lanes for A; 6 % more updates per second than 4 or 8 lanes),
+// the mixed-precision kernel, whose traversals batch the tail of a slice, 32 (1 lane for
+// A; 4 % faster than 2 lanes, 8 % faster than 4).
+int sell_lanes(const HostCSR& M, double per_lane) {
   const double mean = M.m > 0 ? (double)M.rp[M.m] / M.m : 0.0;
   int L = 1;
-  while (L < 32 && mean > 16.0 * L) L *= 2;
+  while (L < 32 && mean > per_lane * L) L *= 2;
   return L;
 }
 
@@ -327,7 +323,12 @@ int setup_grid_path(abip_handle* h, G& g, const HostCSR& A, const std::vector<do
   int grid = h->prm.grid_ctas > 0 ? std::min(h->prm.grid_ctas, cap) : cap;
   h->grid = grid;
 
-  const HostSell SA = to_sell(A, sell_lanes(A)), ST = to_sell(AT, sell_lanes(AT));
+  constexpr bool delta = std::is_same<G, abip::GridDelta>::value;
+  const double per_lane = delta ? 32.0 : 16.0;
+  const HostSell SA = to_sell(A, sell_lanes(A, per_lane)), ST = to_sell(AT, sell_lanes(AT, per_lane));
+  const int wpc = abip::kGridThreads / 32;
+  const std::vector<int32_t> wpA = warp_partition(SA, grid * wpc), wpT = warp_partition(ST, grid * wpc);
+
   auto layout_sell = [&](Arena& ar, SellMat& M, const HostSell& H) {
     M.rows = H.rows;
     M.nslices = H.nslices;
@@ -366,11 +367,10 @@ int setup_grid_path(abip_handle* h, G& g, const HostCSR& A, const std::vector<do
   h->padded_nnz_a = (int64_t)SA.ci.size();
   h->padded_nnz_at = (int64_t)ST.ci.size();
   cudaMemset(mem, 0, probe.off);
-  auto upload_sell = [&](const SellMat& M, const HostSell& H) {
+  auto upload_sell = [&](const SellMat& M, const HostSell& H, const std::vector<int32_t>& wp) {
     cudaMemcpy((void*)M.sp, H.sp.data(), H.sp.size() * 8, cudaMemcpyHostToDevice);
     cudaMemcpy((void*)M.ci, H.ci.data(), H.ci.size() * 4, cudaMemcpyHostToDevice);
     cudaMemcpy((void*)M.perm, H.perm.data(), H.perm.size() * 4, cudaMemcpyHostToDevice);
-    const std::vector<int32_t> wp = warp_partition(H, grid * (abip::kGridThreads / 32));
     cudaMemcpy((void*)M.wsl, wp.data(), wp.size() * 4, cudaMemcpyHostToDevice);
     if (vf64) {
       cudaMemcpy((void*)M.val, H.v.data(), H.v.size() * 8, cudaMemcpyHostToDevice);
@@ -379,8 +379,8 @@ int setup_grid_path(abip_handle* h, G& g, const HostCSR& A, const std::vector<do
       cudaMemcpy((void*)M.val, f.data(), f.size() * 4, cudaMemcpyHostToDevice);
     }
   };
-  upload_sell(g.A, SA);
-  upload_sell(g.AT, ST);
+  upload_sell(g.A, SA, wpA);
+  upload_sell(g.AT, ST, wpT);
   cudaMemcpy((void*)g.b, b.data(), m * sizeof(double), cudaMemcpyHostToDevice);
   cudaMemcpy((void*)g.c, c.data(), n * sizeof(double), cudaMemcpyHostToDevice);
   SolveCtl hc{};

@@ -58,29 +58,6 @@ __device__ __forceinline__ float start_of(float d1, float d2, int extrap) {
   return extrap == 2 ? 2.f * d1 - d2 : extrap == 1 ? d1 : 0.f;
 }
 
-// The barrier and dual step of one column (Eqs. Simple-Update:Barrier-X and
-// Simple-Update:Dual, reading A9) with few FP64 operations: the larger root L of
-// t^2 - |omega| t - c = 0 from an FP32 square root, refined by one Newton step in FP64
-// whose derivative 2L - |omega| = D is taken from the FP32 estimate; the smaller root
-// c / L through an FP32 reciprocal refined by one Newton step.  Error below 2e-14
-// relative to the closed form (checked over omega in +-[1e-12, 1e12], c in [1e-15, 1e2]);
-// outside the range where the FP32 estimates are safe the closed form is used.
-__device__ __forceinline__ void barrier_step_newton(double omega, double c, double& x, double& s) {
-  const double disc = omega * omega + 4.0 * c;
-  if (!(disc > 1e-30 && disc < 1e30)) {
-    barrier_step<double>(omega, c, x, s);
-    return;
-  }
-  const double aw = fabs(omega);
-  const float d32 = sqrtf((float)disc);
-  double L = 0.5 * (aw + (double)d32);
-  L -= (L * (L - aw) - c) * (double)(1.0f / d32);
-  const double r0 = (double)(1.0f / (float)L);
-  const double small = c * (r0 + r0 * (1.0 - L * r0));
-  if (omega >= 0.0) { x = L; s = small; }
-  else { x = small; s = L; }
-}
-
 // accumulator of the products with A after an update: A dx, A ds (FP32) and A W (FP64)
 struct MaintSt {
   using G = XSW;
@@ -197,7 +174,7 @@ struct DeltaSolver {
     {
       auto g = [&](int i) -> float { return zd_cur[i].x; };
       auto e = [&](int j, float v, float) { ut[j].x = v; };
-      sell_rows_g<8, 1, float, float>(D.AT, g, g, e);
+      sell_rows_g<8, 1, float, float>(D.AT, g, g, e, BinaryTail{});
     }
     if (!sync(P_PCG_INIT)) return -1;
     float be = 0.f;
@@ -225,7 +202,7 @@ struct DeltaSolver {
           zd_cur[i].y = o.dinv * gp;
           a1 += pi * gp;
         };
-        sell_rows_gp<8, 1, float, float>(D.A, g, g, pre, e);
+        sell_rows_gp<8, 1, float, float>(D.A, g, g, pre, e, BinaryTail{});
       }
       {
         float a1v[1] = {a1};
@@ -250,7 +227,7 @@ struct DeltaSolver {
           ut[j] = make_float2(v, t);
           D.wdel[j] = first ? al * t : D.wdel[j] + al * t;
         };
-        sell_rows_gp<8, 1, float, float>(D.AT, g, g, pre, e);
+        sell_rows_gp<8, 1, float, float>(D.AT, g, g, pre, e, BinaryTail{});
       }
       mark(P_CG_AT);
       float a2[2] = {0.f, 0.f};
@@ -327,7 +304,7 @@ struct DeltaSolver {
         row_sums(i, ax, yi, tau, itau, theta, acc);
         start_row(i, yi - (ax + as), D.zy[i], st.aw, pc);
       };
-      sell_fold<8, float, MaintSt>(D.A, gf, pre, e);
+      sell_fold<8, float, MaintSt>(D.A, gf, pre, e, BinaryTail{});
     }
     {
       auto g = [&](int i) -> float { return D.dy[i]; };
@@ -336,7 +313,7 @@ struct DeltaSolver {
         D.ATy[j] = aty;
         col_sums(j, aty, tau, itau, theta, acc);
       };
-      sell_rows_g<8, 1, float, float>(D.AT, g, g, e);
+      sell_rows_g<8, 1, float, float>(D.AT, g, g, e, BinaryTail{});
     }
     acc[9] = pc[0]; acc[10] = pc[1]; acc[11] = pc[2];
     put_sums(acc);
@@ -539,7 +516,7 @@ struct DeltaSolver {
   // next solve] -> [products of the changes, the Sec. 4.1 sums and the next start residual].
   __device__ void solve() {
     const Thr t = th;
-    const double alpha = C->alpha, beta = C->beta, gamma = C->gamma, eps = C->eps;
+    const double alpha = C->alpha, gamma = C->gamma, eps = C->eps;
     double tau = C->tau, kappa = C->kappa, theta = C->theta, mu = C->mu;
     int64_t total = C->admm_iters;
     int64_t cgtot = C->cg_iters;
@@ -687,7 +664,7 @@ struct DeltaSolver {
       {
         auto g = [&](int i) -> float { return D.dz[i]; };
         auto e = [&](int j, float v, float) { D.xsw[j].w = D.ATz[j] + (double)v; };
-        sell_rows_g<8, 1, float, float>(D.AT, g, g, e);
+        sell_rows_g<8, 1, float, float>(D.AT, g, g, e, BinaryTail{});
       }
       tau = sc[2]; kappa = sc[3]; theta = sc[4];
       if (!sync(P_UPD)) return;

@@ -457,7 +457,7 @@ struct Solver {
   // MODE_SOLVE: Algorithm 2 from the state in D / C.
   __device__ void solve() {
     const Thr t = th;
-    const double alpha = C->alpha, beta = C->beta, gamma = C->gamma, eps = C->eps;
+    const double alpha = C->alpha, gamma = C->gamma, eps = C->eps;
     const double cg_rel = C->cg_rel;
     double tau = C->tau, kappa = C->kappa, theta = C->theta, mu = C->mu;
     int64_t total = C->admm_iters;

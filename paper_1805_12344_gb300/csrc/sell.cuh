@@ -43,6 +43,15 @@ __device__ __forceinline__ void sell_batch(const int32_t* __restrict__ ci, const
   for (int u = 0; u < B; ++u) st.add(a[u], gf(j[u]));
 }
 
+// How a traversal takes the entries of a slice past its last full batch of U: one at a
+// time (SerialTail), or in batches of U/2, U/4, ..., 1 (BinaryTail: every load issued
+// once, at most log2(U) rounds of loads in flight).  Measured on the 100000 x 400000 LP:
+// the binary tail with one lane per row of A is 4 % faster in the mixed-precision kernel;
+// the FP64 kernel, with twice the gathered bytes per entry, is 2-4 % faster with the
+// serial one.
+struct SerialTail { static constexpr bool binary = false; };
+struct BinaryTail { static constexpr bool binary = true; };
+
 // Generic SELL traversal over the slices of this warp (S.wsl), L lanes per row.
 // For every row: the lane's entries (column j, value a) are folded into an
 // accumulator St by st.add(a, gf(j)); the L lanes of the row are combined by
@@ -54,8 +63,9 @@ __device__ __forceinline__ void sell_batch(const int32_t* __restrict__ ci, const
 // repeat loads).
 //   St: default-constructible (zero); add(V a, const G& g) for the gathered type G;
 //       template <int L> group().
-template <int L, int U, typename V, typename St, typename GF, typename Pre, typename Epi>
-__device__ __forceinline__ void sell_fold_L(const SellMat& S, GF& gf, Pre& pre, Epi& epi) {
+template <int L, int U, typename V, typename St, typename GF, typename Pre, typename Epi, typename Tail>
+__device__ __forceinline__ void sell_fold_L(const SellMat& S, GF& gf, Pre& pre, Epi& epi, Tail) {
+  static_assert(!Tail::binary || U == 8, "the binary tail is written for batches of 8");
   const Thr th;
   constexpr int C = 32 / L;
   const V* __restrict__ val = static_cast<const V*>(S.val);
@@ -71,23 +81,30 @@ __device__ __forceinline__ void sell_fold_L(const SellMat& S, GF& gf, Pre& pre, 
     St st;
     int k = 0;
     for (; k + U <= w; k += U) sell_batch<U, V>(ci, va, k, w, gf, st);
-    for (; k < w; ++k) st.add(__ldg(va + k * 32), gf(__ldg(ci + k * 32)));
+    if constexpr (Tail::binary) {
+      if (w - k >= 4) { sell_batch<4, V>(ci, va, k, w, gf, st); k += 4; }
+      if (w - k >= 2) { sell_batch<2, V>(ci, va, k, w, gf, st); k += 2; }
+      if (k < w) st.add(__ldg(va + k * 32), gf(__ldg(ci + k * 32)));
+    } else {
+      for (; k < w; ++k) st.add(__ldg(va + k * 32), gf(__ldg(ci + k * 32)));
+    }
     if (L > 1) st.template group<L>();
     if (owner) epi(row, st, pv);
   }
 }
 
-template <int U, typename V, typename St, typename GF, typename Pre, typename Epi>
-__device__ __forceinline__ void sell_fold(const SellMat& S, GF& gf, Pre& pre, Epi& epi) {
+template <int U, typename V, typename St, typename GF, typename Pre, typename Epi, typename Tail = SerialTail>
+__device__ __forceinline__ void sell_fold(const SellMat& S, GF& gf, Pre& pre, Epi& epi, Tail t = Tail{}) {
   switch (S.lanes) {
-    case 1: sell_fold_L<1, U, V, St>(S, gf, pre, epi); break;
-    case 2: sell_fold_L<2, U, V, St>(S, gf, pre, epi); break;
-    case 4: sell_fold_L<4, U, V, St>(S, gf, pre, epi); break;
-    case 8: sell_fold_L<8, U, V, St>(S, gf, pre, epi); break;
-    case 16: sell_fold_L<16, U, V, St>(S, gf, pre, epi); break;
-    default: sell_fold_L<32, U, V, St>(S, gf, pre, epi); break;
+    case 1: sell_fold_L<1, U, V, St>(S, gf, pre, epi, t); break;
+    case 2: sell_fold_L<2, U, V, St>(S, gf, pre, epi, t); break;
+    case 4: sell_fold_L<4, U, V, St>(S, gf, pre, epi, t); break;
+    case 8: sell_fold_L<8, U, V, St>(S, gf, pre, epi, t); break;
+    case 16: sell_fold_L<16, U, V, St>(S, gf, pre, epi, t); break;
+    default: sell_fold_L<32, U, V, St>(S, gf, pre, epi, t); break;
   }
 }
+
 
 // One or two dot products accumulated in Acc from a gathered pair (x: first vector,
 // y: second vector, unused when NV = 1).
@@ -142,25 +159,27 @@ struct MakePair<P, 1> {
 // Row products for every row of a SELL matrix: dot0 = sum_k A_ik g0(k), dot1 = sum_k
 // A_ik g1(k) (NV = 2), accumulated in Acc; epi(row, dot0, dot1, pv) with pv = pre(row)
 // on the first lane of the row.  g0/g1 map a column index to the gathered value.
-template <int U, int NV, typename Acc, typename V, typename G0, typename G1, typename Pre, typename Epi>
-__device__ __forceinline__ void sell_rows_gp(const SellMat& S, G0& g0, G1& g1, Pre& pre, Epi& epi) {
+template <int U, int NV, typename Acc, typename V, typename G0, typename G1, typename Pre, typename Epi,
+          typename Tail = SerialTail>
+__device__ __forceinline__ void sell_rows_gp(const SellMat& S, G0& g0, G1& g1, Pre& pre, Epi& epi, Tail t = Tail{}) {
   using R0 = decltype(g0(0));
   using R1 = decltype(g1(0));
   using R = typename std::conditional<(sizeof(R0) >= sizeof(R1)), R0, R1>::type;
   using P = typename std::conditional<NV == 2, Two<R>, One<R>>::type;
   auto gf = [&](int j) -> P { return MakePair<P, NV>::get(g0, g1, j); };
   auto e = [&](int row, const DotSt<Acc, P, NV>& st, decltype(pre(0)) pv) { epi(row, st.a0, st.a1, pv); };
-  sell_fold<U, V, DotSt<Acc, P, NV>>(S, gf, pre, e);
+  sell_fold<U, V, DotSt<Acc, P, NV>>(S, gf, pre, e, t);
 }
 
 struct NoPre {};
 
 // Row products without prefetched row operands: epi(row, dot0, dot1).
-template <int U, int NV, typename Acc, typename V, typename G0, typename G1, typename Epi>
-__device__ __forceinline__ void sell_rows_g(const SellMat& S, G0& g0, G1& g1, Epi& epi) {
+template <int U, int NV, typename Acc, typename V, typename G0, typename G1, typename Epi,
+          typename Tail = SerialTail>
+__device__ __forceinline__ void sell_rows_g(const SellMat& S, G0& g0, G1& g1, Epi& epi, Tail t = Tail{}) {
   auto pre = [](int) { return NoPre{}; };
   auto e = [&](int row, Acc a0, Acc a1, NoPre) { epi(row, a0, a1); };
-  sell_rows_gp<U, NV, Acc, V>(S, g0, g1, pre, e);
+  sell_rows_gp<U, NV, Acc, V>(S, g0, g1, pre, e, t);
 }
 
 // Row products with two vectors stored interleaved: gp(k) returns the pair

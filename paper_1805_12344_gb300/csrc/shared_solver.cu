@@ -679,26 +679,27 @@ __global__ void ctrl_step_kernel(ShInst* insts, int B, int n, const double* part
 }
 
 // Elementwise part of the update (STEP) or of the warm start (WARM), per (row, instance).
-// Mixed path (dY, dXS non-null): also the FP32 changes of y, x, s (zero where the
-// instance did not move), the inputs of the maintained products.
+// Mixed path (dXS non-null): also the FP32 changes of x and s (zero where the instance
+// did not move), the input of the maintained product A [dX dS].
+//   ATZY, ATG1, ATG2 (mixed path, else null): A^T y of the new state follows from the
+//   update's linearity in y: y <- alpha (zy - g1y t1 - g2y t2) + (1 - alpha) y gives
+//   A^T y <- alpha (A^T zy - (A^T g1y) t1 - (A^T g2y) t2) + (1 - alpha) A^T y, with A^T zy
+//   maintained for the projection and A^T g1y, A^T g2y formed once at setup; the warm
+//   start scales it with y.  This replaces a product with A^T per cycle.
 template <typename T>
-__global__ void update_kernel(ShView<T> V, const ShInst* __restrict__ insts, ShParams P, float* dY, float* dXS) {
+__global__ void update_kernel(ShView<T> V, const ShInst* __restrict__ insts, ShParams P, float* dXS,
+                              const T* __restrict__ ATZY, const T* __restrict__ ATG1, const T* __restrict__ ATG2) {
   const int m = V.m, n = V.n, B = V.B;
   const size_t tot = (size_t)(m + n) * B;
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < tot; e += (size_t)gridDim.x * blockDim.x) {
     const int r = (int)(e / B), k = (int)(e % B);
     const ShInst& I = insts[k];
     const int act = I.last;
-    if (dY) {
-      if (r < m) {
-        dY[(size_t)r * B + k] = 0.0f;
-      } else {
-        const int j = r - m;
-        dXS[(size_t)j * 2 * B + k] = 0.0f;
-        dXS[(size_t)j * 2 * B + B + k] = 0.0f;
-      }
+    if (r >= m && dXS) {
+      const int j = r - m;
+      dXS[(size_t)j * 2 * B + k] = 0.0f;
+      dXS[(size_t)j * 2 * B + B + k] = 0.0f;
     }
-    const T y0 = r < m ? V.Y[(size_t)r * B + k] : T(0);
     const T x0 = r < m ? T(0) : V.XS[(size_t)(r - m) * 2 * B + k];
     const T s0 = r < m ? T(0) : V.XS[(size_t)(r - m) * 2 * B + B + k];
     if (act == SH_STEP) {
@@ -716,9 +717,11 @@ __global__ void update_kernel(ShView<T> V, const ShInst* __restrict__ insts, ShP
         T* sp = xp + B;
         const T xh = a * ux + a1 * *xp;
         T xn, sn;
-        barrier_step<T>(xh - *sp, (T)I.cmu, xn, sn);
+        if (dXS) barrier_step_newton(xh - *sp, (T)I.cmu, xn, sn);   // mixed: few FP64 operations
+        else barrier_step<T>(xh - *sp, (T)I.cmu, xn, sn);
         *xp = xn;
         *sp = sn;
+        if (ATG1) V.ATY[q] = a * (ATZY[q] - ATG1[q] * t1 - ATG2[q] * t2) + a1 * V.ATY[q];
       }
     } else if (act == SH_WARM) {
       const T sg = (T)sqrt(I.gam), g = (T)I.gam;
@@ -731,12 +734,11 @@ __global__ void update_kernel(ShView<T> V, const ShInst* __restrict__ insts, ShP
         if (P.warmstart == 1) { *xp *= sg; *sp *= sg; }
         else if (*xp >= *sp) *sp *= g;
         else *xp *= g;
+        if (ATG1) V.ATY[(size_t)j * B + k] *= sg;
       }
     }
-    if (dY && (act == SH_STEP || act == SH_WARM)) {
-      if (r < m) {
-        dY[(size_t)r * B + k] = (float)(V.Y[(size_t)r * B + k] - y0);
-      } else {
+    if ((act == SH_STEP || act == SH_WARM) && r >= m && dXS) {
+      {
         const int j = r - m;
         dXS[(size_t)j * 2 * B + k] = (float)(V.XS[(size_t)j * 2 * B + k] - x0);
         dXS[(size_t)j * 2 * B + B + k] = (float)(V.XS[(size_t)j * 2 * B + B + k] - s0);
@@ -1058,7 +1060,8 @@ int shared_batch_run(const SharedBatchArgs& a, std::vector<SharedBatchResult>& o
   double* totals = nullptr;
   double *partials = nullptr, *W2 = nullptr, *P2 = nullptr, *R = nullptr, *ZY2 = nullptr, *ZX2 = nullptr;
   double *Xo = nullptr, *Yo = nullptr, *So = nullptr, *ATZY = nullptr, *Qprev = nullptr;
-  float *A32 = nullptr, *Ginv32 = nullptr, *work32 = nullptr, *dY = nullptr, *dXS = nullptr, *dQ = nullptr,
+  double *ATG1 = nullptr, *ATG2 = nullptr;
+  float *A32 = nullptr, *Ginv32 = nullptr, *work32 = nullptr, *dXS = nullptr, *dQ = nullptr,
         *dZY = nullptr;
   ShInst* insts = nullptr;
   int *flags = nullptr, *derr = nullptr;
@@ -1100,11 +1103,12 @@ int shared_batch_run(const SharedBatchArgs& a, std::vector<SharedBatchResult>& o
     }
     if (mixed) {
       ATZY = bp.take<double>((size_t)n * B);
+      ATG1 = bp.take<double>((size_t)n * B);
+      ATG2 = bp.take<double>((size_t)n * B);
       Qprev = bp.take<double>((size_t)m * B);
       A32 = bp.take<float>((size_t)(tc ? 1 : m) * (tc ? 1 : n));
       Ginv32 = bp.take<float>((size_t)m * m);
       work32 = bp.take<float>(wk32);
-      dY = bp.take<float>((size_t)m * B);
       dXS = bp.take<float>((size_t)n * 2 * B);
       dQ = bp.take<float>((size_t)m * B);
       dZY = bp.take<float>((size_t)m * B);
@@ -1172,6 +1176,9 @@ int shared_batch_run(const SharedBatchArgs& a, std::vector<SharedBatchResult>& o
   setup_ctrl_kernel<<<1, kMaxBatch, 0, st>>>(insts, B, partials, red_ctas, 1, a.prm);
   init_state_kernel<double><<<eb, kThr, 0, st>>>(V);
   if (mixed) {
+    // A^T g1y, A^T g2y per instance: the y-parts of M^{-1} h1, M^{-1} h2 (rows 0..m-1 of G1, G2)
+    ck(gemm<double>(true, A64, n, n, B, m, V.G1, B, ATG1, work64, wk64, sms, st), "A^T G1");
+    ck(gemm<double>(true, A64, n, n, B, m, V.G2, B, ATG2, work64, wk64, sms, st), "A^T G2");
     const int cb = sms * 8;
     if (tc) {
       bf16_copies_kernel<<<cb, kThr, 0, st>>>(A64, m, n, terms, A16, AT16);
@@ -1227,7 +1234,7 @@ int shared_batch_run(const SharedBatchArgs& a, std::vector<SharedBatchResult>& o
     hz_kernel<double><<<red_ctas, kThr, 0, st>>>(V, partials);
     partials_total_kernel<2><<<B, kThr, 0, st>>>(partials, red_ctas, totals);
     ctrl_step_kernel<<<1, kMaxBatch, 0, st>>>(insts, B, n, totals, 1, a.prm);
-    update_kernel<double><<<eb, kThr, 0, st>>>(V, insts, a.prm, nullptr, nullptr);
+    update_kernel<double><<<eb, kThr, 0, st>>>(V, insts, a.prm, nullptr, nullptr, nullptr, nullptr);
     launches += 15;
   };
   auto cycle_mixed = [&]() {
@@ -1245,20 +1252,15 @@ int shared_batch_run(const SharedBatchArgs& a, std::vector<SharedBatchResult>& o
     hz_delta_kernel<<<red_ctas, kThr, 0, st>>>(V, ATZY, Qprev, insts, partials);
     partials_total_kernel<2><<<B, kThr, 0, st>>>(partials, red_ctas, totals);
     ctrl_step_kernel<<<1, kMaxBatch, 0, st>>>(insts, B, n, totals, 1, a.prm);
-    update_kernel<double><<<eb, kThr, 0, st>>>(V, insts, a.prm, dY, dXS);
-    // maintained products of the new state: AX, AS += A [dX dS], A^T Y += A^T dY
-    if (tc) {
+    update_kernel<double><<<eb, kThr, 0, st>>>(V, insts, a.prm, dXS, ATZY, ATG1, ATG2);
+    // maintained products of the new state: AX, AS += A [dX dS] (A^T Y in update_kernel)
+    if (tc)
       ck(gemm_tc(A16, n, aplane, terms, m, 2 * B, n, dXS, 2 * B, B, V.AXS, nullptr, nullptr, work32, wk32, WT16, sms,
                  derr + 1, st),
          "A dXS");
-      ck(gemm_tc(AT16, m, aplane, terms, n, B, m, dY, B, B, V.ATY, nullptr, nullptr, work32, wk32, WT16, sms,
-                 derr + 1, st),
-         "A^T dY");
-    } else {
+    else
       ck(gemm_acc(false, A32, n, m, 2 * B, n, dXS, 2 * B, B, V.AXS, nullptr, nullptr, work32, wk32, sms, st), "A dXS");
-      ck(gemm_acc(true, A32, n, n, B, m, dY, B, B, V.ATY, nullptr, nullptr, work32, wk32, sms, st), "A^T dY");
-    }
-    launches += tc ? 15 : 12;
+    launches += tc ? 12 : 10;
   };
   if (mixed && rc == ABIP_OK) {
     // exact products of the starting point

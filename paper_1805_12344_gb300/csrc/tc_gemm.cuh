@@ -137,10 +137,15 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
   for (int q = 0; q < 16; ++q) v[q] = __uint_as_float(r[q]);
 }
 
+// K chunks of 8 elements (16 bytes) per tile row, and the byte distance between core
+// matrices adjacent in M (or N): a row group of 8 holds kKC core matrices of 128 bytes.
+constexpr int kKC = kTK / 8;
+constexpr uint32_t kSBO = kKC * 128;
+
 // Byte offset of the 16-byte row chunk (row r, K chunk kc of 8 elements) in a tile of
-// core matrices: core (r / 8, kc) at ((r / 8) * 8 + kc) * 128, row r % 8 at 16 (r % 8).
+// core matrices: core (r / 8, kc) at ((r / 8) * kKC + kc) * 128, row r % 8 at 16 (r % 8).
 __device__ __forceinline__ uint32_t core_off(int r, int kc) {
-  return static_cast<uint32_t>(((r >> 3) * 8 + kc) * 128 + (r & 7) * 16);
+  return static_cast<uint32_t>(((r >> 3) * kKC + kc) * 128 + (r & 7) * 16);
 }
 
 // ---------------------------------------------------------------------------
@@ -244,12 +249,12 @@ __global__ void __launch_bounds__(kTCThreads, 1)
   auto load_stage = [&](int j) {
     const int k0 = kz0 + j * kTK;
     const uint32_t sa = s0 + (j % S) * stage;
-    for (int e = tid; e < TA * kTM * 8; e += kTCThreads) {
-      const int t = e / (kTM * 8), rem = e % (kTM * 8), r = rem >> 3, kc = rem & 7;
+    for (int e = tid; e < TA * kTM * kKC; e += kTCThreads) {
+      const int t = e / (kTM * kKC), rem = e % (kTM * kKC), r = rem / kKC, kc = rem % kKC;
       cp_async16(sa + t * atile + core_off(r, kc), A16 + t * aplane + (size_t)(m0 + r) * lda + k0 + kc * 8);
     }
-    for (int e = tid; e < 3 * N * 8; e += kTCThreads) {
-      const int t = e / (N * 8), rem = e % (N * 8), n = rem >> 3, kc = rem & 7;
+    for (int e = tid; e < 3 * N * kKC; e += kTCThreads) {
+      const int t = e / (N * kKC), rem = e % (N * kKC), n = rem / kKC, kc = rem % kKC;
       cp_async16(sa + abytes + t * wbytes + core_off(n, kc), Wt + t * plane + (size_t)n * K + k0 + kc * 8);
     }
   };
@@ -286,10 +291,10 @@ __global__ void __launch_bounds__(kTCThreads, 1)
       for (int s = 0; s < kTK / 16; ++s) {
 #pragma unroll
         for (int ta = 0; ta < TA; ++ta) {
-          const uint64_t ad = smem_desc(a0 + ta * atile + s * 256, 128, 1024);
+          const uint64_t ad = smem_desc(a0 + ta * atile + s * 256, 128, kSBO);
 #pragma unroll
           for (int t = 0; t + ta < 3; ++t) {
-            const uint64_t bd = smem_desc(w0 + t * wbytes + s * 256, 128, 1024);
+            const uint64_t bd = smem_desc(w0 + t * wbytes + s * 256, 128, kSBO);
             mma_bf16(tmem, ad, bd, idesc, (j > 0 || s > 0 || ta > 0 || t > 0) ? 1u : 0u);
           }
         }
