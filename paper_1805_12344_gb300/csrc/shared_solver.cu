@@ -365,17 +365,20 @@ __global__ void convert_kernel(const double* __restrict__ src, T* __restrict__ d
 // the bfloat16 rounding of what planes 0 .. t-1 leave of A's FP32 value.  One plane is
 // exact for an A representable in bfloat16, three for any A representable in FP32
 // (the host picks `terms`).
+// bfloat16 terms of A (m x n, K = n) and of A^T (n x m, K = m), tile-major (tc::a_tiled),
+// the operands of the tensor-core products.
 __global__ void bf16_copies_kernel(const double* __restrict__ A, int m, int n, int terms,
                                    __nv_bfloat16* __restrict__ A16, __nv_bfloat16* __restrict__ AT16) {
   const size_t tot = (size_t)m * n;
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < tot; e += (size_t)gridDim.x * blockDim.x) {
     const int i = (int)(e / n), j = (int)(e % n);
     float rest = (float)A[e];
+    const size_t ea = tc::a_tiled(i, j, n), eat = tc::a_tiled(j, i, m);
     for (int t = 0; t < terms; ++t) {
       const __nv_bfloat16 v = __float2bfloat16_rn(rest);
       rest -= __bfloat162float(v);
-      A16[t * tot + e] = v;
-      AT16[t * tot + (size_t)j * m + i] = v;
+      A16[t * tot + ea] = v;
+      AT16[t * tot + eat] = v;
     }
   }
 }
@@ -956,11 +959,12 @@ bool tc_shape_ok(int m, int n, int B) {
 }
 
 // the tcgen05 kernel instance for (stages, terms); nullptr if there is none
-using TcKernel = void (*)(const __nv_bfloat16*, int64_t, int64_t, int, int, int, const __nv_bfloat16*, float*, int,
-                          int*);
+using TcKernel = void (*)(const __nv_bfloat16*, int64_t, int, int, int, const __nv_bfloat16*, float*, int, int*);
 TcKernel tc_kernel_for(int stages, int terms) {
   if (terms == 1) {
     switch (stages) {
+      case 6: return tc::tc_gemm2_kernel<6, 1>;
+      case 5: return tc::tc_gemm2_kernel<5, 1>;
       case 4: return tc::tc_gemm2_kernel<4, 1>;
       case 3: return tc::tc_gemm2_kernel<3, 1>;
       case 2: return tc::tc_gemm2_kernel<2, 1>;
@@ -969,6 +973,8 @@ TcKernel tc_kernel_for(int stages, int terms) {
   }
   if (terms == 3) {
     switch (stages) {
+      case 6: return tc::tc_gemm2_kernel<6, 3>;
+      case 5: return tc::tc_gemm2_kernel<5, 3>;
       case 4: return tc::tc_gemm2_kernel<4, 3>;
       case 3: return tc::tc_gemm2_kernel<3, 3>;
       case 2: return tc::tc_gemm2_kernel<2, 3>;
@@ -978,7 +984,7 @@ TcKernel tc_kernel_for(int stages, int terms) {
   return nullptr;
 }
 
-cudaError_t gemm_tc(const __nv_bfloat16* A16, int64_t lda, int64_t aplane, int terms, int M, int N, int K,
+cudaError_t gemm_tc(const __nv_bfloat16* A16, int64_t aplane, int terms, int M, int N, int K,
                     const float* W, int64_t ldw, int B, double* acc64, float* out32, const ShInst* mask, float* work,
                     size_t work_elems, __nv_bfloat16* wt, int sms, int* err, cudaStream_t st) {
   const TcPlan p = plan_tc(M, N, K, sms, terms);
@@ -987,8 +993,7 @@ cudaError_t gemm_tc(const __nv_bfloat16* A16, int64_t lda, int64_t aplane, int t
   if (!kern) return cudaErrorInvalidValue;
   tc::split3_kernel<<<dim3((K + 31) / 32, (N + 31) / 32), dim3(32, 8), 0, st>>>(W, ldw, K, N, wt);
   const dim3 grid(M / tc::kTM, p.splits);
-  kern<<<grid, tc::kTCThreads, tc::tc2_smem_bytes(N, terms), st>>>(A16, lda, aplane, M, N, K, wt, work, p.kchunk,
-                                                                  err);
+  kern<<<grid, tc::kTCThreads, tc::tc2_smem_bytes(N, terms), st>>>(A16, aplane, M, N, K, wt, work, p.kchunk, err);
   const size_t MN = (size_t)M * N;
   const int rb = (int)std::min<size_t>((MN + kThr - 1) / kThr, (size_t)sms * 8);
   accum_kernel<<<std::max(rb, 1), kThr, 0, st>>>(work, p.splits, M, N, B, acc64, out32, mask);
@@ -1245,7 +1250,7 @@ int shared_batch_run(const SharedBatchArgs& a, std::vector<SharedBatchResult>& o
     refresh();
     // projection on the change of Q: ZY += G^{-1} dQ, A^T ZY += A^T (G^{-1} dQ)
     ck(gemm_acc(false, Ginv32, m, m, B, m, dQ, B, B, V.ZY, dZY, insts, work32, wk32, sms, st), "Ginv dQ");
-    if (tc) ck(gemm_tc(AT16, m, aplane, terms, n, B, m, dZY, B, B, ATZY, nullptr, nullptr, work32, wk32, WT16, sms,
+    if (tc) ck(gemm_tc(AT16, aplane, terms, n, B, m, dZY, B, B, ATZY, nullptr, nullptr, work32, wk32, WT16, sms,
                        derr + 1, st),
                "A^T dZY");
     else ck(gemm_acc(true, A32, n, n, B, m, dZY, B, B, ATZY, nullptr, nullptr, work32, wk32, sms, st), "A^T dZY");
@@ -1255,7 +1260,7 @@ int shared_batch_run(const SharedBatchArgs& a, std::vector<SharedBatchResult>& o
     update_kernel<double><<<eb, kThr, 0, st>>>(V, insts, a.prm, dXS, ATZY, ATG1, ATG2);
     // maintained products of the new state: AX, AS += A [dX dS] (A^T Y in update_kernel)
     if (tc)
-      ck(gemm_tc(A16, n, aplane, terms, m, 2 * B, n, dXS, 2 * B, B, V.AXS, nullptr, nullptr, work32, wk32, WT16, sms,
+      ck(gemm_tc(A16, aplane, terms, m, 2 * B, n, dXS, 2 * B, B, V.AXS, nullptr, nullptr, work32, wk32, WT16, sms,
                  derr + 1, st),
          "A dXS");
     else

@@ -2,7 +2,7 @@
 //
 //   Cpart[z][M x N] (FP32) = A[M x K_z] * W[K_z x N]
 //
-// A: TA bfloat16 terms A16[t] (M x lda each, row-major, K contiguous) with A = sum of the
+// A: TA bfloat16 terms A16[t] (M x K each, tile-major, see a_tiled) with A = sum of the
 // terms, each the bfloat16 rounding of what the terms before it leave: TA = 1 when A is
 // exact in bfloat16, TA = 3 for any A exact in FP32 (8 + 8 + 8 significant bits).  W: FP32
 // row-major (N contiguous), the changes of the batched iterates, each element split the
@@ -12,12 +12,16 @@
 // 2^-24 of the product, so the result has FP32 accuracy.
 //
 // One CTA (128 threads) owns a 128-row tile of C and one K range (split-K over
-// gridDim.y).  Per 64-wide K step the TA A tiles and the three W tiles sit in shared memory
-// in the no-swizzle K-major core-matrix layout (8 rows x 16 bytes per core matrix; core
-// matrices adjacent in K are 128 bytes apart, adjacent in M/N 1024 bytes); one thread
-// issues 4 x (3 or 6) tcgen05.mma (K = 16 each) into the TMEM accumulator and commits them
-// to an mbarrier.  The epilogue reads the accumulator with tcgen05.ld (warp w owns TMEM
-// lanes 32w..32w+31, one lane per row) and writes the FP32 partial tile.
+// gridDim.y).  Both operands are stored tile-major in the no-swizzle K-major core-matrix
+// layout the MMA reads (8 rows x 16 bytes per core matrix; core matrices adjacent in K
+// 128 bytes apart, adjacent in M/N kKC * 128 bytes): each K step of kTK is, per term,
+// one contiguous block in HBM that a single bulk copy (cp.async.bulk, the 1-D form of
+// TMA) moves into shared memory, completing on the stage's "full" mbarrier.  One thread
+// issues the copies S - 1 steps ahead, waits for a stage, issues 2 x (3 or 6)
+// tcgen05.mma (K = 16 each) into the TMEM accumulator and commits them to the stage's
+// "empty" mbarrier, which releases the stage for the next copy.  The epilogue reads the
+// accumulator with tcgen05.ld (warp w owns TMEM lanes 32w..32w+31, one lane per row) and
+// writes the FP32 partial tile.  Every wait is bounded (kWaitLimitNs).
 #pragma once
 
 #include <cstdint>
@@ -28,7 +32,7 @@ namespace abip {
 namespace tc {
 
 constexpr int kTM = 128;          // rows per tile (MMA M)
-constexpr int kTK = 64;           // K per staging step
+constexpr int kTK = 32;           // K per staging step
 constexpr int kTCThreads = 128;
 constexpr unsigned long long kWaitLimitNs = 2000000000ull;   // 2 s per wait
 constexpr int kErrTimeout = 1;
@@ -102,9 +106,6 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* mbar, uint32_t parity) {
   }
 }
 
-__device__ __forceinline__ void fence_async_smem() {
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
 __device__ __forceinline__ void tc_fence_after() {
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 }
@@ -144,8 +145,21 @@ constexpr uint32_t kSBO = kKC * 128;
 
 // Byte offset of the 16-byte row chunk (row r, K chunk kc of 8 elements) in a tile of
 // core matrices: core (r / 8, kc) at ((r / 8) * kKC + kc) * 128, row r % 8 at 16 (r % 8).
-__device__ __forceinline__ uint32_t core_off(int r, int kc) {
+__host__ __device__ __forceinline__ uint32_t core_off(int r, int kc) {
   return static_cast<uint32_t>(((r >> 3) * kKC + kc) * 128 + (r & 7) * 16);
+}
+
+// Tile-major bfloat16 layouts (element offsets within one term plane).
+// A (R x K, R % kTM == 0, K % kTK == 0): tile (r / kTM, k / kTK) is the contiguous block
+// number (r / kTM) * (K / kTK) + k / kTK of kTM * kTK elements, core-matrix ordered.
+__host__ __device__ __forceinline__ size_t a_tiled(int r, int k, int K) {
+  const size_t tile = (size_t)(r / kTM) * (K / kTK) + k / kTK;
+  return tile * (kTM * kTK) + core_off(r % kTM, (k % kTK) >> 3) / 2 + (k & 7);
+}
+// W (N rows x K, the changes transposed; N % 16 == 0): K step s is the contiguous block s
+// of N * kTK elements.
+__host__ __device__ __forceinline__ size_t w_tiled(int n, int k, int N) {
+  return (size_t)(k / kTK) * N * kTK + core_off(n, (k % kTK) >> 3) / 2 + (k & 7);
 }
 
 // ---------------------------------------------------------------------------
@@ -155,7 +169,8 @@ __device__ __forceinline__ uint32_t core_off(int r, int kc) {
 // per stage tells when its MMAs have finished reading it.
 // ---------------------------------------------------------------------------
 
-// Wt[t][n][k] = t-th bfloat16 term of W[k][n] (W: K x N FP32 row-major, ldw).
+// Wt[t] (term t, N * K elements, tile-major as w_tiled) = t-th bfloat16 term of W^T
+// (W: K x N FP32 row-major, ldw).
 __global__ void split3_kernel(const float* __restrict__ W, int64_t ldw, int K, int N, __nv_bfloat16* __restrict__ Wt) {
   __shared__ float tile[32][33];
   const int k0 = blockIdx.x * 32, n0 = blockIdx.y * 32;
@@ -173,7 +188,7 @@ __global__ void split3_kernel(const float* __restrict__ W, int64_t ldw, int K, i
       const float r1 = w - __bfloat162float(h);
       const __nv_bfloat16 md = __float2bfloat16_rn(r1);
       const __nv_bfloat16 lo = __float2bfloat16_rn(r1 - __bfloat162float(md));
-      const size_t e = (size_t)n * K + k;
+      const size_t e = w_tiled(n, k, N);
       Wt[e] = h;
       Wt[plane + e] = md;
       Wt[2 * plane + e] = lo;
@@ -181,52 +196,59 @@ __global__ void split3_kernel(const float* __restrict__ W, int64_t ldw, int K, i
   }
 }
 
-__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+// Arrive on the mbarrier and add `bytes` to the transaction count its phase waits for.
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* mbar, uint32_t bytes) {
+  asm volatile(
+      "{\n\t.reg .b64 st;\n\t"
+      "mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}\n" ::"r"(smem_u32(mbar)),
+      "r"(bytes)
+      : "memory");
 }
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int NPEND>
-__device__ __forceinline__ void cp_async_wait() {
-  asm volatile("cp.async.wait_group %0;" ::"n"(NPEND) : "memory");
+// Bulk copy of `bytes` (a multiple of 16; both addresses 16-byte aligned) from global to
+// shared memory, completing `bytes` transactions on the mbarrier.
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint64_t* mbar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+               "l"(src), "r"(bytes), "r"(smem_u32(mbar))
+               : "memory");
 }
 
 __host__ __device__ inline size_t tc2_stage_bytes(int N, int TA) {
   return static_cast<size_t>(TA) * kTM * kTK * 2 + 3 * static_cast<size_t>(N) * kTK * 2;
 }
 // shared-memory stages: as many as fit in the 227 KB a CTA may use (less 2 KB for the
-// 1024-byte alignment of the tiles and the static variables), at most 4
+// 1024-byte alignment of the tiles and the static variables), at most 6
 constexpr size_t kTcSmemCap = 227 * 1024 - 2048;
 __host__ __device__ inline int tc2_stages(int N, int TA) {
   const int s = static_cast<int>(kTcSmemCap / tc2_stage_bytes(N, TA));
-  return s < 4 ? s : 4;
+  return s < 6 ? s : 6;
 }
 __host__ __device__ inline size_t tc2_smem_bytes(int N, int TA) {
   return 1024 + tc2_stages(N, TA) * tc2_stage_bytes(N, TA);
 }
 
-// Requirements (refused on the device with kErrShape): M % 128 == 0, K % 64 == 0,
-// kchunk % 64 == 0, N % 16 == 0 and 16 <= N <= 256, lda % 8 == 0, aplane % 8 == 0, A16 and
-// Wt 16-byte aligned, tc2_stages(N, TA) == S >= 2.  A16: TA planes aplane elements apart.
+// Requirements (refused on the device with kErrShape): M % 128 == 0, K % kTK == 0,
+// kchunk % kTK == 0, N % 16 == 0 and 16 <= N <= 256, aplane % 8 == 0, A16 and Wt 16-byte
+// aligned, tc2_stages(N, TA) == S >= 2.  A16: TA planes of M x K, aplane elements apart,
+// tile-major (a_tiled); Wt: 3 planes of N x K, tile-major (w_tiled).
 // Dynamic shared memory: tc2_smem_bytes(N, TA).
 template <int S, int TA>
 __global__ void __launch_bounds__(kTCThreads, 1)
-    tc_gemm2_kernel(const __nv_bfloat16* __restrict__ A16, int64_t lda, int64_t aplane, int M, int N, int K,
+    tc_gemm2_kernel(const __nv_bfloat16* __restrict__ A16, int64_t aplane, int M, int N, int K,
                     const __nv_bfloat16* __restrict__ Wt, float* __restrict__ Cp, int kchunk, int* err) {
-  // shapes the tiles and the 16-byte copies need; anything else is refused here
+  // shapes the tiles and the bulk copies need; anything else is refused here
   if (M % kTM != 0 || K % kTK != 0 || kchunk <= 0 || kchunk % kTK != 0 || N % 16 != 0 || N < 16 || N > 256 ||
-      lda % 8 != 0 || aplane % 8 != 0 || (reinterpret_cast<uintptr_t>(A16) & 15) != 0 ||
-      (reinterpret_cast<uintptr_t>(Wt) & 15) != 0 || tc2_stages(N, TA) != S || S < 2) {
+      aplane % 8 != 0 || (reinterpret_cast<uintptr_t>(A16) & 15) != 0 || (reinterpret_cast<uintptr_t>(Wt) & 15) != 0 ||
+      tc2_stages(N, TA) != S || S < 2) {
     if (threadIdx.x == 0 && blockIdx.x == 0 && blockIdx.y == 0) atomicExch(err, kErrShape);
     return;
   }
   extern __shared__ uint8_t tc_smem_raw[];
-  __shared__ uint64_t mbar[S];
+  __shared__ uint64_t full[S], empty[S];
   __shared__ uint32_t tslot;
   __shared__ int failed;
   uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(tc_smem_raw) + 1023) & ~uintptr_t(1023));
   const uint32_t stage = static_cast<uint32_t>(tc2_stage_bytes(N, TA));
   const uint32_t atile = kTM * kTK * 2, abytes = TA * atile, wbytes = static_cast<uint32_t>(N) * kTK * 2;
-  const size_t plane = static_cast<size_t>(N) * K;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int m0 = blockIdx.x * kTM;
   const int kz0 = blockIdx.y * kchunk, kz1 = min(K, kz0 + kchunk);
@@ -235,7 +257,10 @@ __global__ void __launch_bounds__(kTCThreads, 1)
   while (ncols < static_cast<uint32_t>(N)) ncols <<= 1;
   if (tid == 0) {
 #pragma unroll
-    for (int b = 0; b < S; ++b) mbar_init(&mbar[b], 1);
+    for (int b = 0; b < S; ++b) {
+      mbar_init(&full[b], 1);
+      mbar_init(&empty[b], 1);
+    }
     failed = 0;
   }
   if (warp == 0) tmem_alloc(&tslot, ncols);
@@ -246,47 +271,30 @@ __global__ void __launch_bounds__(kTCThreads, 1)
   const uint32_t tmem = tslot;
   const uint32_t idesc = instr_desc(kTM, N);
   const uint32_t s0 = smem_u32(base);
-  auto load_stage = [&](int j) {
-    const int k0 = kz0 + j * kTK;
-    const uint32_t sa = s0 + (j % S) * stage;
-    for (int e = tid; e < TA * kTM * kKC; e += kTCThreads) {
-      const int t = e / (kTM * kKC), rem = e % (kTM * kKC), r = rem / kKC, kc = rem % kKC;
-      cp_async16(sa + t * atile + core_off(r, kc), A16 + t * aplane + (size_t)(m0 + r) * lda + k0 + kc * 8);
-    }
-    for (int e = tid; e < 3 * N * kKC; e += kTCThreads) {
-      const int t = e / (N * kKC), rem = e % (N * kKC), n = rem / kKC, kc = rem % kKC;
-      cp_async16(sa + abytes + t * wbytes + core_off(n, kc), Wt + t * plane + (size_t)n * K + k0 + kc * 8);
-    }
-  };
-  // cp.async groups: one per step (empty past the last), so that after the commit of
-  // iteration j, wait_group<S - 1> means the group of step j has landed
-  uint32_t uses[S];
+  if (tid == 0) {
+    // step j of this CTA: A block (row tile blockIdx.x, K tile kz0 / kTK + j) of each term,
+    // W block (K tile kz0 / kTK + j) of each term
+    const char* a0p = reinterpret_cast<const char*>(A16) +
+                      ((size_t)blockIdx.x * (K / kTK) + kz0 / kTK) * (size_t)atile;
+    const char* w0p = reinterpret_cast<const char*>(Wt) + (size_t)(kz0 / kTK) * wbytes;
+    const size_t ap = (size_t)aplane * 2, wp = (size_t)N * K * 2;
+    auto issue = [&](int j) {
+      const int b = j % S;
+      const uint32_t sa = s0 + b * stage;
+      mbar_arrive_expect_tx(&full[b], abytes + 3 * wbytes);
 #pragma unroll
-  for (int b = 0; b < S; ++b) uses[b] = 0u;
-  for (int q = 0; q < S - 1; ++q) {
-    if (q < steps) load_stage(q);
-    cp_async_commit();
-  }
-  for (int j = 0; j < steps; ++j) {
-    const int nxt = j + S - 1;
-    if (nxt < steps) {
-      if (j >= 1) {   // the MMAs of step j - 1 read the stage that step nxt refills
-        const int b = (j - 1) % S;
-        if (!mbar_wait(&mbar[b], (uses[b] - 1) & 1u)) {
-          if (tid == 0) { failed = 1; atomicExch(err, kErrTimeout); }
-        }
-        tc_fence_after();
-      }
-      load_stage(nxt);
-    }
-    cp_async_commit();
-    cp_async_wait<S - 1>();
-    fence_async_smem();
-    __syncthreads();
-    if (failed) break;
-    if (tid == 0) {
+      for (int t = 0; t < TA; ++t) bulk_g2s(sa + t * atile, a0p + t * ap + (size_t)j * atile, atile, &full[b]);
+#pragma unroll
+      for (int t = 0; t < 3; ++t) bulk_g2s(sa + abytes + t * wbytes, w0p + t * wp + (size_t)j * wbytes, wbytes, &full[b]);
+    };
+    int issued = 0, committed = 0;
+    for (; issued < S && issued < steps; ++issued) issue(issued);
+    int j = 0;
+    for (; j < steps; ++j) {
+      const int b = j % S;
+      if (!mbar_wait(&full[b], (j / S) & 1u)) { failed = 1; break; }
       tc_fence_after();
-      const uint32_t a0 = s0 + (j % S) * stage, w0 = a0 + abytes;
+      const uint32_t a0 = s0 + b * stage, w0 = a0 + abytes;
 #pragma unroll
       for (int s = 0; s < kTK / 16; ++s) {
 #pragma unroll
@@ -299,20 +307,31 @@ __global__ void __launch_bounds__(kTCThreads, 1)
           }
         }
       }
-      mma_commit(&mbar[j % S]);
+      mma_commit(&empty[b]);
+      committed = j + 1;
+      // the stage of step j - 1 is free once its MMAs are done: refill it with step j - 1 + S
+      if (j >= 1 && issued < steps) {
+        const int pb = (j - 1) % S;
+        if (!mbar_wait(&empty[pb], ((j - 1) / S) & 1u)) { failed = 1; ++j; break; }
+        issue(issued++);
+      }
     }
-    uses[j % S] += 1;
-  }
-  // all MMAs done: the last commit covers every earlier MMA of this thread
-  if (steps > 0 && !failed) {
-    const int b = (steps - 1) % S;
-    if (!mbar_wait(&mbar[b], (uses[b] - 1) & 1u)) {
-      if (tid == 0) { failed = 1; atomicExch(err, kErrTimeout); }
+    if (!failed && steps > 0) {
+      // the last commit covers every earlier MMA of this thread
+      const int lb = (steps - 1) % S;
+      if (!mbar_wait(&empty[lb], ((steps - 1) / S) & 1u)) failed = 1;
+    }
+    if (failed) {
+      atomicExch(err, kErrTimeout);
+      // no copy may still be writing shared memory, and no MMA still running, when the CTA
+      // leaves and frees its tensor memory (bounded waits)
+      for (int q = j; q < issued; ++q) mbar_wait(&full[q % S], (q / S) & 1u);
+      if (committed > 0) mbar_wait(&empty[(committed - 1) % S], ((committed - 1) / S) & 1u);
     }
   }
-  cp_async_wait<0>();
-  tc_fence_after();
+  tc_fence_before();
   __syncthreads();
+  tc_fence_after();
   float* C = Cp + (size_t)blockIdx.y * M * N;
   const int row = m0 + warp * 32 + lane;
   if (!failed) {
