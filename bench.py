@@ -61,6 +61,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-legs", action="store_true", help="skip the LPs-solved/s legs of the other workloads")
+    ap.add_argument("--svm-count", type=int, default=128, help="L1-SVM instances of the backward leg")
+    ap.add_argument("--svm-cap", type=int, default=2000, help="forward updates of the backward leg")
     ap.add_argument("--f64-updates", type=int, default=5000, help="ADMM updates of the FP64 arm of the sparse LP")
     ap.add_argument("--batch-count", type=int, default=256, help="LPs in the uneven-batch leg")
     ap.add_argument("--batch-cap", type=int, default=20000, help="ADMM update cap of the uneven-batch leg")
@@ -178,6 +180,30 @@ def leg_basis_pursuit(abip, W, args):
             "cap_admm_updates": args.bp_cap, "eps": 1e-6, "lps_solved": solved, "wall_s": wall,
             "lps_solved_per_s": solved / wall, "setup_s": infos[0]["setup_s"], "kernel_s": infos[0]["kernel_s"],
             "max_admm_updates": max(i["admm_iters"] for i in infos)}
+
+
+def leg_svm_backward(abip, W, args):
+    """Config 4's differentiation: 128 L1-SVM LPs (512 x 1154) solved in one launch
+    (mixed precision, `--svm-cap` updates, then MAX_ITER or optimal), then the gradients of
+    ||x* - x_t||^2 with respect to c, b and A at each final iterate in one
+    abip_backward_batch launch (Newton polish onto the central point of the final mu, then
+    the adjoint through the LU of the reduced KKT matrix); wall times of both calls."""
+    import time as _t
+    lps = [W.l1_svm(seed=W.seed_for(W.L1_SVM) + k) for k in range(args.svm_count)]
+    prm = abip.default_params(precision=abip.ABIP_PREC_MIXED, max_admm_iters=args.svm_cap)
+    As, bs, cs = [l.A for l in lps], [l.b for l in lps], [l.c for l in lps]
+    t0 = _t.perf_counter()
+    infos, xs, ys, ss = abip.abip_solve_batch(As, bs, cs, prm)
+    fwd = _t.perf_counter() - t0
+    gs = [2.0 * (x - l.meta["x_target"]) for x, l in zip(xs, lps)]
+    t0 = _t.perf_counter()
+    dcs, dbs, dAs = abip.abip_backward_batch(As, bs, cs, xs, ys, ss, infos, gs, prm)
+    bwd = _t.perf_counter() - t0
+    return {"workload": f"l1_svm_512x1154_batch{len(lps)}", "forward_cap_admm_updates": args.svm_cap,
+            "forward_wall_s": fwd, "forward_kernel_s": infos[0]["kernel_s"],
+            "optimal": sum(1 for i in infos if i["status"] == abip.ABIP_OPTIMAL),
+            "backward_wall_s": bwd, "backward_per_instance_ms": 1e3 * bwd / len(lps),
+            "gradient_entries_per_instance": int(lps[0].A.size + lps[0].A.shape[0] + lps[0].A.shape[1])}
 
 
 def leg_random_udv(abip, W, args):
@@ -501,7 +527,8 @@ def main():
         for key, fn in (("sparse_f64_arm", lambda: leg_sparse_f64(abip, W, lp, args, stream)),
                         ("batch_uneven", lambda: leg_batch_uneven(abip, W, args)),
                         ("basis_pursuit", lambda: leg_basis_pursuit(abip, W, args)),
-                        ("random_udv", lambda: leg_random_udv(abip, W, args))):
+                        ("random_udv", lambda: leg_random_udv(abip, W, args)),
+                        ("svm_backward", lambda: leg_svm_backward(abip, W, args))):
             try:
                 legs[key] = fn()
             except Exception as ex:  # a leg must not sink the main line
