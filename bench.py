@@ -94,12 +94,12 @@ def algorithmic_bytes(m, n, nnz, admm_iters, cg_iters, vec_bytes, val_bytes=4):
 # dram__bytes_write.sum at two update counts: a fixed fill and a per-update part), valid
 # only for the kernel sources it was measured on; None once any of them has changed.
 KERNEL_SOURCES = ("paper_1805_12344_gb300/csrc/grid_delta.cu", "paper_1805_12344_gb300/csrc/sell.cuh",
-                  "paper_1805_12344_gb300/csrc/abip_device.cuh", "paper_1805_12344_gb300/csrc/abip_api.cu")
+                  "paper_1805_12344_gb300/csrc/abip_device.cuh", "paper_1805_12344_gb300/csrc/sell_host.h")
 # DRAM bytes of one solve launch from ncu (dram__bytes_read.sum + dram__bytes_write.sum) at
 # 20 and 60 updates, caches flushed before the launch: 596.0 MB and 1585.0 MB, so
 # 101.5 MB fixed + 24.72 MB per update (profiles/grid_delta_kernel_solve_sparse_m100000.md);
 # valid while the sources above are the ones measured.
-TRAFFIC = {"sources_sha256": "b10157d76ba9e3059ed6ba1225f1aa7f20c3cd704169a2fa8535d68f440e4b38",
+TRAFFIC = {"sources_sha256": "c9e17702ca9d067a39c456c66b8e70d58bde0a93626023c2521eb21554d8e93f",
            "dram_bytes_fixed": 101535488, "dram_bytes_per_update": 24724185.6}
 
 

@@ -1242,12 +1242,14 @@ int shared_batch_run(const SharedBatchArgs& a, std::vector<SharedBatchResult>& o
     update_kernel<double><<<eb, kThr, 0, st>>>(V, insts, a.prm, nullptr, nullptr, nullptr, nullptr);
     launches += 15;
   };
-  auto cycle_mixed = [&]() {
+  // with_refresh: this cycle's number is a multiple of a.prm.refresh, so ctrl_eval_kernel
+  // opens the gate of the FP64 refresh; other cycles leave its kernels out altogether
+  auto cycle_mixed = [&](bool with_refresh) {
     sums_kernel<double><<<red_ctas, kThr, 0, st>>>(V, insts, partials, V.Q, nullptr, Qprev, dQ);
     partials_total_kernel<9><<<B, kThr, 0, st>>>(partials, red_ctas, totals);
     ctrl_eval_kernel<<<1, kMaxBatch, 0, st>>>(insts, B, n, totals, 1, a.prm, flags);
     launches += 3;
-    refresh();
+    if (with_refresh) refresh();
     // projection on the change of Q: ZY += G^{-1} dQ, A^T ZY += A^T (G^{-1} dQ)
     ck(gemm_acc(false, Ginv32, m, m, B, m, dQ, B, B, V.ZY, dZY, insts, work32, wk32, sms, st), "Ginv dQ");
     if (tc) ck(gemm_tc(AT16, aplane, terms, n, B, m, dZY, B, B, ATZY, nullptr, nullptr, work32, wk32, WT16, sms,
@@ -1277,42 +1279,52 @@ int shared_batch_run(const SharedBatchArgs& a, std::vector<SharedBatchResult>& o
   const int64_t max_cycles = 2 * a.prm.max_admm + 2 * (int64_t)kMaxOuter + 16;
   int64_t cycles = 0;
   constexpr int kGroup = 16;
-  // one group of cycles as a CUDA graph (every decision in it is taken on the device);
-  // direct launches if the capture or the instantiation fails
-  cudaGraphExec_t gexec = nullptr;
-  int64_t group_launches = 0;
-  if (rc == ABIP_OK) {
+  // The scheduled FP64 refresh falls on cycles numbered by multiples of a.prm.refresh (a
+  // multiple of kGroup), i.e. on the last cycle of a group: groups are launched from one
+  // of two CUDA graphs, without a refresh or with one in the last cycle (every decision
+  // inside them taken on the device); direct launches if a capture or an instantiation
+  // fails.
+  const bool aligned = mixed && a.prm.refresh > 0 && a.prm.refresh % kGroup == 0;
+  auto group = [&](bool refresh_last) {
+    for (int g = 0; g < kGroup; ++g) {
+      if (mixed) cycle_mixed(aligned ? (refresh_last && g == kGroup - 1) : true);
+      else cycle64();
+    }
+  };
+  cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+  int64_t group_launches[2] = {0, 0};
+  bool graphs = rc == ABIP_OK;
+  for (int v = 0; v < (aligned ? 2 : 1) && graphs; ++v) {
     const int rc0 = rc;
     const int64_t l0 = launches;
     cudaGraph_t graph = nullptr;
+    graphs = false;
     if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
-      for (int g = 0; g < kGroup; ++g) {
-        if (mixed) cycle_mixed();
-        else cycle64();
-      }
+      group(v == 1);
       const cudaError_t ec = cudaStreamEndCapture(st, &graph);
-      if (ec == cudaSuccess && graph && rc == ABIP_OK && cudaGraphInstantiate(&gexec, graph, 0) == cudaSuccess)
-        group_launches = launches - l0;
-      else
-        gexec = nullptr;
+      if (ec == cudaSuccess && graph && rc == ABIP_OK && cudaGraphInstantiate(&gexec[v], graph, 0) == cudaSuccess) {
+        group_launches[v] = launches - l0;
+        graphs = true;
+      } else {
+        gexec[v] = nullptr;
+      }
       if (graph) cudaGraphDestroy(graph);
     }
     launches = l0;
-    if (!gexec) {   // fall back to direct launches
+    if (!graphs) {   // fall back to direct launches
       rc = rc0;
       err.clear();
       cudaGetLastError();
     }
   }
   while (rc == ABIP_OK) {
-    if (gexec) {
-      ck(cudaGraphLaunch(gexec, st), "cycle graph");
-      launches += group_launches;
+    const bool refresh_last = aligned && (cycles + kGroup) % a.prm.refresh == 0;
+    const int v = refresh_last ? 1 : 0;
+    if (graphs) {
+      ck(cudaGraphLaunch(gexec[v], st), "cycle graph");
+      launches += group_launches[v];
     } else {
-      for (int g = 0; g < kGroup; ++g) {
-        if (mixed) cycle_mixed();
-        else cycle64();
-      }
+      group(refresh_last);
     }
     cycles += kGroup;
     ck(cudaGetLastError(), "cycle launches");
@@ -1322,7 +1334,8 @@ int shared_batch_run(const SharedBatchArgs& a, std::vector<SharedBatchResult>& o
     if (cycles > max_cycles) { err = "shared batch: cycle guard reached"; rc = ABIP_E_NUMERICAL; }
   }
   cudaFreeHost(hflags);
-  if (gexec) cudaGraphExecDestroy(gexec);
+  for (cudaGraphExec_t ge : gexec)
+    if (ge) cudaGraphExecDestroy(ge);
   if (rc == ABIP_OK && tc) {
     int herr2 = 0;
     ck(cudaMemcpy(&herr2, derr + 1, sizeof(int), cudaMemcpyDeviceToHost), "tensor-core status");
