@@ -62,6 +62,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-legs", action="store_true", help="skip the LPs-solved/s legs of the other workloads")
     ap.add_argument("--svm-count", type=int, default=128, help="L1-SVM instances of the backward leg")
+    ap.add_argument("--sice-d", type=int, default=256, help="dimension of the SICE leg (d column LPs)")
     ap.add_argument("--svm-cap", type=int, default=2000, help="forward updates of the backward leg")
     ap.add_argument("--f64-updates", type=int, default=5000, help="ADMM updates of the FP64 arm of the sparse LP")
     ap.add_argument("--batch-count", type=int, default=256, help="LPs in the uneven-batch leg")
@@ -204,6 +205,55 @@ def leg_svm_backward(abip, W, args):
             "optimal": sum(1 for i in infos if i["status"] == abip.ABIP_OPTIMAL),
             "backward_wall_s": bwd, "backward_per_instance_ms": 1e3 * bwd / len(lps),
             "gradient_entries_per_instance": int(lps[0].A.size + lps[0].A.shape[0] + lps[0].A.shape[1])}
+
+
+def leg_bb_beta(abip, W, args):
+    """Barzilai-Borwein beta (Sec. 4.3) against a fixed beta on 64 LPs of config 3's recipe,
+    dense FP64 path, same cap and tolerance: LPs solved, ADMM updates and wall time of
+    abip_solve_batch."""
+    import time as _t
+    lps = W.batch_uneven(count=64, seed=W.seed_for(W.BATCH_UNEVEN, 500))
+    out = {"workload": "batch_uneven_64_of_4096_recipe", "precision": "f64", "cap_admm_updates": args.batch_cap,
+           "eps": 1e-6}
+    for name, bb in (("fixed_beta", 0), ("bb_beta", 1)):
+        prm = abip.default_params(max_admm_iters=args.batch_cap, bb_beta=bb)
+        t0 = _t.perf_counter()
+        infos, *_ = abip.abip_solve_batch([l.A for l in lps], [l.b for l in lps], [l.c for l in lps], prm,
+                                          want_solution=False)
+        wall = _t.perf_counter() - t0
+        solved = _solved(infos)
+        out[name] = {"lps_solved": solved, "wall_s": wall, "lps_solved_per_s": solved / wall,
+                     "admm_updates": int(sum(i["admm_iters"] for i in infos))}
+    return out
+
+
+def leg_sice(abip, W, args):
+    """Sparse inverse covariance estimation (Sec. 5.2; a synthetic covariance stands in for
+    the UCI data): the d column LPs in general form go through the host presolve (bounds
+    rewritten, Ruiz scaling), all presolve to one matrix, are solved as shared-A batches
+    (tensor cores) to 1e-6 and postsolved; LPs solved/s over the whole pipeline."""
+    import time as _t
+    d = args.sice_d
+    S, lam = W.sice(d)
+    gs = [W.sice_general_lp(S, lam, j) for j in range(d)]
+    t0 = _t.perf_counter()
+    Ps = [abip.Presolved(g.A, g.b, g.c, g.l, g.w) for g in gs]
+    lps = [P.lp() for P in Ps]
+    t_pre = _t.perf_counter() - t0
+    A = lps[0][0].to_dense()
+    prm = abip.default_params(precision=abip.ABIP_PREC_MIXED_BF16, max_admm_iters=args.bp_cap)
+    t1 = _t.perf_counter()
+    infos, xs, ys, _ = abip.abip_solve_batch_shared(A, [b for _, b, _ in lps], [c for _, _, c in lps], prm)
+    t_solve = _t.perf_counter() - t1
+    t2 = _t.perf_counter()
+    objs = [P.postsolve(x, y)[3] for P, x, y in zip(Ps, xs, ys)]
+    t_post = _t.perf_counter() - t2
+    solved = _solved(infos)
+    wall = t_pre + t_solve + t_post
+    return {"workload": f"sice_d{d} (Sec. 5.2 LP, synthetic covariance)", "lps": d,
+            "standard_form": [int(A.shape[0]), int(A.shape[1])], "lps_solved": solved,
+            "presolve_s": t_pre, "solve_wall_s": t_solve, "postsolve_s": t_post, "lps_solved_per_s": solved / wall,
+            "max_admm_updates": max(i["admm_iters"] for i in infos), "sum_l1_norms": float(sum(objs))}
 
 
 def leg_random_udv(abip, W, args):
@@ -528,7 +578,9 @@ def main():
                         ("batch_uneven", lambda: leg_batch_uneven(abip, W, args)),
                         ("basis_pursuit", lambda: leg_basis_pursuit(abip, W, args)),
                         ("random_udv", lambda: leg_random_udv(abip, W, args)),
-                        ("svm_backward", lambda: leg_svm_backward(abip, W, args))):
+                        ("svm_backward", lambda: leg_svm_backward(abip, W, args)),
+                        ("bb_beta", lambda: leg_bb_beta(abip, W, args)),
+                        ("sice", lambda: leg_sice(abip, W, args))):
             try:
                 legs[key] = fn()
             except Exception as ex:  # a leg must not sink the main line

@@ -150,6 +150,16 @@ void max_matching(int m, int n, const std::vector<std::vector<int>>& adj, std::v
   std::vector<std::pair<int, size_t>> stack;
   std::vector<int> path_col;
   for (int r0 = 0; r0 < m; ++r0) {
+    // a free column of the row itself first (most rows of a full-rank pattern find one)
+    bool direct = false;
+    for (int j : adj[r0])
+      if (row_of_col[j] < 0) {
+        col_of_row[r0] = j;
+        row_of_col[j] = r0;
+        direct = true;
+        break;
+      }
+    if (direct) continue;
     // iterative DFS over alternating paths: row -> column -> matched row ...
     stack.clear();
     path_col.clear();
