@@ -62,7 +62,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-legs", action="store_true", help="skip the LPs-solved/s legs of the other workloads")
     ap.add_argument("--svm-count", type=int, default=128, help="L1-SVM instances of the backward leg")
-    ap.add_argument("--sice-d", type=int, default=256, help="dimension of the SICE leg (d column LPs)")
+    ap.add_argument("--sice-d", type=int, default=128, help="dimension of the SICE leg (d column LPs)")
+    ap.add_argument("--sice-cap", type=int, default=100000, help="ADMM update cap of the SICE leg")
     ap.add_argument("--svm-cap", type=int, default=2000, help="forward updates of the backward leg")
     ap.add_argument("--f64-updates", type=int, default=5000, help="ADMM updates of the FP64 arm of the sparse LP")
     ap.add_argument("--batch-count", type=int, default=256, help="LPs in the uneven-batch leg")
@@ -241,7 +242,7 @@ def leg_sice(abip, W, args):
     lps = [P.lp() for P in Ps]
     t_pre = _t.perf_counter() - t0
     A = lps[0][0].to_dense()
-    prm = abip.default_params(precision=abip.ABIP_PREC_MIXED_BF16, max_admm_iters=args.bp_cap)
+    prm = abip.default_params(precision=abip.ABIP_PREC_MIXED_BF16, max_admm_iters=args.sice_cap)
     t1 = _t.perf_counter()
     infos, xs, ys, _ = abip.abip_solve_batch_shared(A, [b for _, b, _ in lps], [c for _, _, c in lps], prm)
     t_solve = _t.perf_counter() - t1
@@ -250,7 +251,8 @@ def leg_sice(abip, W, args):
     t_post = _t.perf_counter() - t2
     solved = _solved(infos)
     wall = t_pre + t_solve + t_post
-    return {"workload": f"sice_d{d} (Sec. 5.2 LP, synthetic covariance)", "lps": d,
+    return {"workload": f"sice_d{d} (Sec. 5.2 LP, synthetic covariance)", "lps": d, "eps": 1e-6,
+            "cap_admm_updates": args.sice_cap,
             "standard_form": [int(A.shape[0]), int(A.shape[1])], "lps_solved": solved,
             "presolve_s": t_pre, "solve_wall_s": t_solve, "postsolve_s": t_post, "lps_solved_per_s": solved / wall,
             "max_admm_updates": max(i["admm_iters"] for i in infos), "sum_l1_norms": float(sum(objs))}

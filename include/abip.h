@@ -334,7 +334,9 @@ ABIP_API int abip_solve_dense_noalloc(int32_t m, int32_t n, const double* A, int
  *   tol in (0, 1): the tolerance of the zero tests (1e-9 is a good default).
  *   *out: receives the presolved problem (free with abip_presolve_free), also when the
  *   reductions alone decide the LP: info->status is then ABIP_PRIMAL_INFEASIBLE or
- *   ABIP_DUAL_INFEASIBLE (the reason in abip_last_error(NULL)), else 0.
+ *   ABIP_DUAL_INFEASIBLE (the reason in abip_last_error(NULL)), or ABIP_OPTIMAL when they
+ *   removed every row (m = n = 0: abip_postsolve with empty x, y gives the solution);
+ *   else 0.
  * Host code only; no GPU is needed.
  */
 typedef struct abip_presolved abip_presolved;

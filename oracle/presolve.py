@@ -50,6 +50,7 @@ import scipy.sparse as sp
 from scipy.sparse.csgraph import maximum_bipartite_matching
 
 OPTIMAL_SO_FAR = 0          # reductions done; the standard-form LP is to be solved
+OPTIMAL_BY_REDUCTION = 1    # every row removed: the reductions solved the LP (postsolve of empty x, y)
 PRIMAL_INFEASIBLE = 2       # the status codes of the solver (abip_oracle)
 DUAL_INFEASIBLE = 3
 
@@ -286,6 +287,8 @@ def presolve(A, b, c, l, w, tol: float = 1e-9, ruiz: int = 10) -> Presolved:
     P.A, P.b, P.c = Ahat, D * bstd, E * cstd
     P.obj_offset = offset
     P.rows, P.cols, P.D, P.E = rows, kinds, D, E
+    if ms == 0:          # the reductions removed every row (and so every column): solved
+        P.status = OPTIMAL_BY_REDUCTION
     return P
 
 

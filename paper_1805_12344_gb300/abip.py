@@ -410,7 +410,7 @@ class Presolved:
         _check(rc)
         self.info = {k: getattr(inf, k) for k, _ in abip_presolve_info._fields_ if k != "reserved"}
         self.status = inf.status
-        self.why = lib().abip_last_error(None).decode() if inf.status else ""
+        self.why = lib().abip_last_error(None).decode() if inf.status not in (0, ABIP_OPTIMAL) else ""
         self.m0, self.n0 = M.m, M.n
 
     def lp(self):

@@ -489,7 +489,10 @@ int abip_presolve(const abip_matrix* A, const double* b, const double* c, const 
   I.n = n;
   I.nnz = (int64_t)P->ci.size();
   I.obj_offset = offset;
-  I.status = 0;
+  // every row went in the reductions (and so every column): the reductions alone solved
+  // the LP, and postsolve takes empty x, y
+  I.status = m == 0 ? ABIP_OPTIMAL : 0;
+  P->status = I.status;
   if (info) *info = I;
   *out = P;
   return ABIP_OK;
@@ -510,8 +513,14 @@ int abip_presolved_lp(const abip_presolved* P, int64_t* row_ptr, int32_t* col_id
 int abip_postsolve(const abip_presolved* P, const double* x, const double* y, const double* s, double* x_out,
                    double* y_out, double* z_out, double* obj) {
   (void)s;
-  if (!P || !x || !y || !x_out) { abip::set_global_error("NULL argument"); return ABIP_E_INVALID_ARG; }
-  if (P->status != 0) { abip::set_global_error("presolve decided the status: nothing to postsolve"); return ABIP_E_INVALID_ARG; }
+  if (!P || !x_out || (P->n > 0 && !x) || (P->m > 0 && !y)) {
+    abip::set_global_error("NULL argument");
+    return ABIP_E_INVALID_ARG;
+  }
+  if (P->status != 0 && !(P->status == ABIP_OPTIMAL && P->m == 0)) {
+    abip::set_global_error("presolve decided the status: nothing to postsolve");
+    return ABIP_E_INVALID_ARG;
+  }
   const int n0 = P->n0, m0 = P->m0;
   std::vector<double> xo(n0, 0.0), yo(m0, 0.0);
   for (int j = 0; j < n0; ++j) if (P->fixed_flag[j]) xo[j] = P->fixed_val[j];

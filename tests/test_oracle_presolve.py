@@ -183,3 +183,23 @@ def test_sice_columns_share_one_standard_form():
     r = O.solve(Ps[4].A, Ps[4].b, Ps[4].c, O.Params(eps=1e-8))
     x, y, z, obj = PS.postsolve(Ps[4], r.x, r.y, r.s)
     assert abs(obj - _linprog(g)) <= 1e-6 * (1 + abs(obj))
+
+
+def test_reductions_alone_solve_a_determined_lp(abip):
+    """Singleton rows fix every variable (one only after another's substitution leaves its
+    row a singleton): no row is left, the status is decided in presolve, and the postsolve
+    of the empty standard form returns the unique feasible point and duals that make the
+    reduced cost of every fixed column zero."""
+    A = np.array([[2.0, 0.0, 0.0], [1.0, 1.0, 0.0], [0.0, 1.0, -1.0]])
+    x0 = np.array([1.0, 2.0, 0.5])
+    b, c = A @ x0, np.array([1.0, -1.0, 2.0])
+    l, w = np.full(3, -np.inf), np.full(3, np.inf)
+    P = PS.presolve(A, b, c, l, w)
+    assert P.status == PS.OPTIMAL_BY_REDUCTION and P.removed["P6"] == 3 and P.A.shape == (0, 0)
+    x, y, z, obj = PS.postsolve(P, np.zeros(0), np.zeros(0), None)
+    assert np.allclose(x, x0, rtol=0, atol=1e-15) and abs(obj - c @ x0) <= 1e-14
+    assert np.abs(z).max() <= 1e-14                      # c - A^T y = 0: y certifies x0
+    Q = abip.Presolved(A, b, c, l, w)
+    assert Q.status == abip.ABIP_OPTIMAL and Q.info["m"] == 0 and Q.info["n"] == 0
+    x2, y2, z2, obj2 = Q.postsolve(np.zeros(0), np.zeros(0))
+    assert np.allclose(x2, x) and np.allclose(y2, y) and abs(obj2 - obj) <= 1e-14
