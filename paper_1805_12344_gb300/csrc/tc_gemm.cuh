@@ -28,25 +28,18 @@
 
 #include <cuda_bf16.h>
 
+#include "async_copy.cuh"
+
 namespace abip {
 namespace tc {
 
 constexpr int kTM = 128;          // rows per tile (MMA M)
 constexpr int kTK = 32;           // K per staging step
 constexpr int kTCThreads = 128;
-constexpr unsigned long long kWaitLimitNs = 2000000000ull;   // 2 s per wait
 constexpr int kErrTimeout = 1;
 constexpr int kErrShape = 2;
 
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
 
-__device__ __forceinline__ unsigned long long now_ns() {
-  unsigned long long t;
-  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
-  return t;
-}
 
 // Shared-memory matrix descriptor: no swizzle, K-major.  lbo: byte distance between core
 // matrices adjacent in K; sbo: between core matrices adjacent in M (or N).  Bits 46-48
@@ -84,27 +77,7 @@ __device__ __forceinline__ void mma_commit(uint64_t* mbar) {
                : "memory");
 }
 
-__device__ __forceinline__ void mbar_init(uint64_t* mbar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(mbar)), "r"(count) : "memory");
-}
 
-// Wait for the mbarrier phase with the given parity; false after kWaitLimitNs.
-__device__ __forceinline__ bool mbar_wait(uint64_t* mbar, uint32_t parity) {
-  const uint32_t a = smem_u32(mbar);
-  const unsigned long long t0 = now_ns();
-  for (;;) {
-    uint32_t done;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}\n"
-        : "=r"(done)
-        : "r"(a), "r"(parity)
-        : "memory");
-    if (done) return true;
-    if (now_ns() - t0 > kWaitLimitNs) return false;
-  }
-}
 
 __device__ __forceinline__ void tc_fence_after() {
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -196,21 +169,6 @@ __global__ void split3_kernel(const float* __restrict__ W, int64_t ldw, int K, i
   }
 }
 
-// Arrive on the mbarrier and add `bytes` to the transaction count its phase waits for.
-__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* mbar, uint32_t bytes) {
-  asm volatile(
-      "{\n\t.reg .b64 st;\n\t"
-      "mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}\n" ::"r"(smem_u32(mbar)),
-      "r"(bytes)
-      : "memory");
-}
-// Bulk copy of `bytes` (a multiple of 16; both addresses 16-byte aligned) from global to
-// shared memory, completing `bytes` transactions on the mbarrier.
-__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint64_t* mbar) {
-  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
-               "l"(src), "r"(bytes), "r"(smem_u32(mbar))
-               : "memory");
-}
 
 __host__ __device__ inline size_t tc2_stage_bytes(int N, int TA) {
   return static_cast<size_t>(TA) * kTM * kTK * 2 + 3 * static_cast<size_t>(N) * kTK * 2;
