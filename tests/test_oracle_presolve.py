@@ -203,3 +203,34 @@ def test_reductions_alone_solve_a_determined_lp(abip):
     assert Q.status == abip.ABIP_OPTIMAL and Q.info["m"] == 0 and Q.info["n"] == 0
     x2, y2, z2, obj2 = Q.postsolve(np.zeros(0), np.zeros(0))
     assert np.allclose(x2, x) and np.allclose(y2, y) and abs(obj2 - obj) <= 1e-14
+
+
+def test_library_presolve_takes_csr_and_refuses_bad_arguments(abip):
+    """The same LP as a CSR matrix (float64 and float32 values exact in float32) gives the
+    standard form of the dense input; malformed bounds and tolerances are refused."""
+    g = W.general_lp(m=12, n=30, seed=6)
+    g.A = g.A.astype(np.float32).astype(np.float64)
+    g.b = g.A @ g.x0
+    g.c = g.A.T @ g.y0 + g.z0
+    Pd = abip.Presolved(g.A, g.b, g.c, g.l, g.w)
+    Md, bd, cd = Pd.lp()
+    for dtype in (np.float64, np.float32):
+        Pc = abip.Presolved(W.dense_to_csr(g.A, dtype), g.b, g.c, g.l, g.w)
+        Mc, bc, cc = Pc.lp()
+        assert np.array_equal(Mc.row_ptr, Md.row_ptr) and np.array_equal(Mc.col_idx, Md.col_idx)
+        assert np.array_equal(Mc.val, Md.val) and np.array_equal(bc, bd) and np.array_equal(cc, cd)
+    bad_l = g.l.copy()
+    bad_l[0] = np.inf
+    bad_w = g.w.copy()
+    bad_w[1] = np.nan
+    for args, kw in (((g.A, g.b, g.c, bad_l, g.w), {}), ((g.A, g.b, g.c, g.l, bad_w), {}),
+                     ((g.A, g.b, g.c, g.l, g.w), {"tol": 0.0}), ((g.A, g.b, g.c, g.l, g.w), {"ruiz": -1})):
+        with pytest.raises(abip.AbipError) as e:
+            abip.Presolved(*args, **kw)
+        assert e.value.code == abip.ABIP_E_INVALID_ARG
+
+
+def test_oracle_refuses_a_gamma_max_below_gamma():
+    lp = W.planted_dense(6, 14, seed=7)
+    with pytest.raises(ValueError):
+        O.solve(lp.A, lp.b, lp.c, O.Params(gamma=0.2, gamma_max=0.1))
