@@ -43,21 +43,30 @@ def test_default_params(lib):
 
 
 def test_struct_layout_matches_header():
-    """ctypes mirrors of the C structs have the sizes the C compiler gives them."""
+    """ctypes mirrors of the C structs have the sizes and field offsets the C compiler
+    gives them (every field of every struct the boundary passes)."""
     from paper_1805_12344_gb300 import abip
-    code = r'''
-#include <stdio.h>
-#include "abip.h"
-int main(void){printf("%zu %zu %zu\n", sizeof(abip_matrix), sizeof(abip_params), sizeof(abip_info));return 0;}
-'''
+    structs = [("abip_matrix", abip.abip_matrix), ("abip_params", abip.abip_params),
+               ("abip_info", abip.abip_info), ("abip_presolve_info", abip.abip_presolve_info)]
+    lines = []
+    for cname, py in structs:
+        lines.append('printf("%%zu\\n", sizeof(%s));' % cname)
+        for f, _ in py._fields_:
+            lines.append('printf("%%zu\\n", offsetof(%s, %s));' % (cname, f))
+    code = ("#include <stdio.h>\n#include <stddef.h>\n#include \"abip.h\"\nint main(void){" + "".join(lines) +
+            "return 0;}\n")
     import subprocess, tempfile
     with tempfile.TemporaryDirectory() as d:
         src = os.path.join(d, "t.c")
         open(src, "w").write(code)
         exe = os.path.join(d, "t")
         subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), src, "-o", exe])
-        sizes = [int(v) for v in subprocess.check_output([exe]).split()]
-    assert sizes == [C.sizeof(abip.abip_matrix), C.sizeof(abip.abip_params), C.sizeof(abip.abip_info)]
+        got = [int(v) for v in subprocess.check_output([exe]).split()]
+    want = []
+    for _, py in structs:
+        want.append(C.sizeof(py))
+        want += [getattr(py, f).offset for f, _ in py._fields_]
+    assert got == want
 
 
 def test_status_strings(lib):
