@@ -29,7 +29,7 @@ segment's starting state, and the backward pass recomputes one segment at a time
 """
 from __future__ import annotations
 
-from typing import Callable, Optional
+from typing import Callable
 
 import numpy as np
 import torch

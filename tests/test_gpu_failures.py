@@ -7,7 +7,6 @@ returns an error status; the CUDA context stays usable afterwards.
   kernel run past its limit; every CTA leaves the kernel -> ABIP_E_TIMEOUT.
 * Non-finite reduction: finite inputs whose sums overflow FP64 -> ABIP_E_NUMERICAL.
 """
-import numpy as np
 import pytest
 
 from paper_1805_12344_gb300 import workloads as W
