@@ -234,3 +234,24 @@ def test_oracle_refuses_a_gamma_max_below_gamma():
     lp = W.planted_dense(6, 14, seed=7)
     with pytest.raises(ValueError):
         O.solve(lp.A, lp.b, lp.c, O.Params(gamma=0.2, gamma_max=0.1))
+
+
+def test_empty_columns_take_the_bound_their_cost_prefers(abip):
+    """P2 (reading P-A): an empty column sits at l for c_j > 0, at w for c_j < 0 and, with
+    c_j = 0, at the point of [l, w] nearest 0; the objective constant follows."""
+    A = np.array([[1.0, 1.0, 0.0, 0.0, 0.0, 0.0, 0.0]])
+    b = np.array([1.0])
+    c = np.array([1.0, 1.0, 2.0, -3.0, 0.0, 0.0, 0.0])
+    l = np.array([0.0, 0.0, 1.5, -np.inf, 2.0, -3.0, -np.inf])
+    w = np.array([np.inf, np.inf, np.inf, 4.0, 5.0, -1.0, np.inf])
+    want = {2: 1.5, 3: 4.0, 4: 2.0, 5: -1.0, 6: 0.0}
+    P = PS.presolve(A, b, c, l, w)
+    assert P.status == 0 and P.removed["P2"] == 5
+    assert {j: P.fixed[j] for j in want} == want
+    assert P.obj_offset == pytest.approx(2.0 * 1.5 - 3.0 * 4.0)
+    Q = abip.Presolved(A, b, c, l, w)
+    assert Q.info["empty_cols"] == 5 and Q.info["obj_offset"] == pytest.approx(P.obj_offset)
+    r = O.solve(P.A, P.b, P.c, O.Params(eps=1e-9))
+    x, y, z, obj = PS.postsolve(P, r.x, r.y, r.s)
+    assert all(x[j] == v for j, v in want.items())
+    assert obj == pytest.approx(1.0 + P.obj_offset, abs=1e-7)      # x0 + x1 = 1 at cost 1
