@@ -884,7 +884,7 @@ __device__ void dense_solve_delta(DenseInst& I, const DenseParams& P, unsigned c
       const double x0 = x[j], s0 = s[j];
       const double xh = alpha * ux + (1.0 - alpha) * x0;
       double xn, sn;
-      barrier_step<double>(xh - s0, cmu, xn, sn);
+      barrier_step_newton(xh - s0, cmu, xn, sn);   // few FP64 operations (the FP64 pipe binds here)
       x[j] = xn;
       s[j] = sn;
       dx[j] = (float)(xn - x0);
