@@ -416,6 +416,7 @@ def run_cpu_sample(args, admm_iters_per_step):
     d = json.loads(r.stdout.strip().splitlines()[-1])
     step_s = d["setup_s"] + d["s_per_admm_iter"] * admm_iters_per_step
     return {
+        "raw": d,
         "value": admm_iters_per_step / step_s,
         "unit": UNIT,
         "cores": d["cores"],
@@ -427,27 +428,40 @@ def run_cpu_sample(args, admm_iters_per_step):
     }
 
 
+def workload_config(args, m, n, nnz, world):
+    """The `config` both arms print: the workload and the solver parameters of a step."""
+    return {"workload": WORKLOAD, "m": m, "n": n, "nnz": int(nnz), "cg_tol": args.cg_tol, "cg_rel": args.cg_rel,
+            "alpha": args.alpha, "gamma": args.gamma, "eps": 1e-6, "admm_updates_per_step": args.max_admm,
+            "l2": "flushed between timed steps (512 MiB write)", "parallelism": f"replicas{world}"}
+
+
 def reference_main(args, rank, world):
-    """The reference arm: the FP64 oracle on the host cores, one bounded sample per step."""
+    """The reference arm: the FP64 oracle on the host cores, one bounded sample of the
+    workload per step (its setup and the ADMM updates that fit in --cpu-sample-s); value and
+    ms_per_step are those of the samples as run, the config is the GPU arm's."""
     if rank != 0:
         return
-    times = []
-    samples = []
+    times, updates = [], []
+    cs = None
     for i in range(args.warmup + args.steps):
         cs = run_cpu_sample(args, args.max_admm)
         if i >= args.warmup:
-            times.append(args.max_admm / cs["value"])
-            samples.append(cs)
-    value = args.max_admm * len(times) / sum(times)
+            raw = cs.pop("raw")
+            times.append(raw["setup_s"] + raw["s_per_admm_iter"] * raw["admm_iters"])
+            updates.append(raw["admm_iters"])
+    value = sum(updates) / sum(times)
+    m = args.m
+    sample = (f"each step: FP64 numpy oracle, 1 thread, on the same LP and parameters: setup + "
+              f"{updates[-1]} ADMM updates ({times[-1]:.1f} s) of the {args.max_admm}-update step")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "m": args.m, "n": 4 * args.m, "nnz": 25 * args.m,
-                   "admm_updates_per_step": args.max_admm},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": samples[-1]["cores"], "kind": "oracle",
-                         "sample": samples[-1]["sample"]},
+        "config": workload_config(args, m, 4 * m, 25 * m, world),
+        "sample_admm_updates_per_step": updates[-1],
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cs["cores"], "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "note": "the config's l2 and parallelism describe the GPU arm; this arm runs on the host cores",
     }
     print(json.dumps(line), flush=True)
 
@@ -601,11 +615,8 @@ def main():
             "warmup": args.warmup, "ms_per_step": sum(step_ms) / len(step_ms), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
             "dtype": "f32+f64" if args.precision == "mixed" else "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "m": m, "n": n, "nnz": int(nnz), "precision": args.precision,
-                       "cg_tol": args.cg_tol, "cg_rel": args.cg_rel, "alpha": prm.alpha, "gamma": prm.gamma,
-                       "eps": prm.eps, "admm_updates_per_step": args.max_admm,
-                       "l2": "flushed between timed steps (512 MiB write)",
-                       "parallelism": f"replicas{world}"},
+            "config": workload_config(args, m, n, nnz, world),
+            "precision": args.precision,
             "lps_solved_per_s": solved / total_s,
             "lps_solved_note": ("0 on this workload: the paper's inner stop needs more than its 1e6-update cap "
                                 "to reach a 1e-6 gap at n = 400000 (the gap falls like n mu / tau^2)"),
