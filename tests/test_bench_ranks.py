@@ -46,3 +46,51 @@ def test_single_rank_is_identity():
     sys.path.insert(0, ROOT)
     import bench
     assert bench.aggregate_ranks(1.5, 2, 300) == (1.5, 2.0, 300.0)
+
+
+def test_traffic_model_is_keyed_on_the_measured_sources():
+    """roofline.traffic comes from the ncu model only while the kernel sources hash to the
+    measured ones, and scales with the update count: fixed + per-update bytes."""
+    sys.path.insert(0, ROOT)
+    import bench
+    assert bench.TRAFFIC["sources_sha256"] == bench.kernel_sources_hash()
+    t20, t60 = bench.traffic_per_launch(20), bench.traffic_per_launch(60)
+    assert t60 - t20 == 40 * bench.TRAFFIC["dram_bytes_per_update"]
+    saved = dict(bench.TRAFFIC)
+    try:
+        bench.TRAFFIC["sources_sha256"] = "0" * 64
+        assert bench.traffic_per_launch(20) is None
+    finally:
+        bench.TRAFFIC.update(saved)
+
+
+def test_algorithmic_bytes_follow_the_minimum_passes():
+    """Per update: one pass over A and one over A^T plus 20 n-vectors; per PCG iteration two
+    passes plus 6 m-vectors; a pass over a CSR matrix reads nnz (value + index) + row
+    pointers."""
+    sys.path.insert(0, ROOT)
+    import bench
+    m, n, nnz = 1000, 4000, 25000
+    one = bench.algorithmic_bytes(m, n, nnz, admm_iters=1, cg_iters=0, vec_bytes=4)
+    two = bench.algorithmic_bytes(m, n, nnz, admm_iters=2, cg_iters=0, vec_bytes=4)
+    assert two == 2 * one
+    cg = bench.algorithmic_bytes(m, n, nnz, admm_iters=0, cg_iters=1, vec_bytes=4)
+    pass_a = nnz * (4 + 4) + 8 * (m + 1)
+    pass_at = nnz * (4 + 4) + 8 * (n + 1)
+    assert cg == pass_a + pass_at + 6 * m * 4
+    assert one == pass_a + pass_at + 20 * n * 4
+
+
+def test_both_arms_print_one_workload_config(monkeypatch):
+    """The reference arm and the GPU arm build `config` from the same helper, so the driver's
+    ratio compares the same LP and the same solver parameters."""
+    sys.path.insert(0, ROOT)
+    import bench
+    monkeypatch.setattr(sys, "argv", ["bench.py", "--max-admm", "300", "--gamma", "0.2"])
+    args = bench.parse()
+    cfg = bench.workload_config(args, 1000, 4000, 25000, 1)
+    assert cfg["workload"] == bench.WORKLOAD
+    assert (cfg["m"], cfg["n"], cfg["nnz"]) == (1000, 4000, 25000)
+    assert cfg["admm_updates_per_step"] == 300 and cfg["gamma"] == 0.2
+    assert cfg["parallelism"] == "replicas1" and "flushed" in cfg["l2"]
+    assert bench.workload_config(args, 1000, 4000, 25000, 1) == cfg
