@@ -79,6 +79,11 @@ extern "C" {
 /* linear system for the projection (Sec. 4.4) */
 #define ABIP_LINSYS_DENSE_CHOL  0   /* G = I + A A^T formed once, Cholesky G = L L^T, triangular solves */
 #define ABIP_LINSYS_PCG         1   /* Jacobi-preconditioned CG on G, warm-started */
+#define ABIP_LINSYS_SPARSE_LDL  2   /* direct projection through the quasi-definite system
+                                       K = [I A^T; A -I] (Sec. 4.4): minimum-degree order and
+                                       symbolic factor on the host (abip_ldl_analyze), numeric
+                                       LDL^T once per setup and two triangular sweeps per update
+                                       on the GPU.  CSR or dense input, precision F64 only */
 
 /* ---- data ----------------------------------------------------------------- */
 typedef struct {
@@ -373,6 +378,24 @@ ABIP_API int abip_postsolve(const abip_presolved* P, const double* x, const doub
                             double* x_out, double* y_out, double* z_out, double* obj);
 
 ABIP_API void abip_presolve_free(abip_presolved* P);
+
+/*
+ * Symbolic analysis of the sparse direct projection (linsys = ABIP_LINSYS_SPARSE_LDL,
+ * Sec. 4.4).  With yhat = -y the projection's system M [y; x] = r becomes
+ * K [x; yhat] = [r_x; r_y] with the quasi-definite K = [I_n A^T; A -I_m] of order n + m,
+ * node j < n standing for x_j and node n + i for row i of A.  Every symmetric permutation
+ * of K has an LDL^T factor (pivots > 0 on x nodes, < 0 on row nodes); this call orders K
+ * by minimum degree (ties by node number; once the remaining graph is complete, the rest
+ * in node order) and counts the factor's nonzeros.  Host only: no GPU is touched.
+ *   A           the constraint matrix (host pointers, on_device = 0), CSR or dense
+ *   perm        n + m int32 or NULL: perm[p] = node of the p-th pivot
+ *   col_counts  n + m int64 or NULL: strictly-lower nonzeros of column p of L
+ *   nnz_l       NULL or receives their sum
+ * ABIP_E_INVALID_ARG / ABIP_E_DIM for a bad matrix (on_device = 1 included);
+ * ABIP_E_UNSUPPORTED when the factor would hold more than 4e8 nonzeros or the ordering
+ * passes its work limit (the message in abip_last_error(NULL)).
+ */
+ABIP_API int abip_ldl_analyze(const abip_matrix* A, int32_t* perm, int64_t* col_counts, int64_t* nnz_l);
 
 /* Release every resource of h (NULL is accepted). */
 ABIP_API void abip_free(abip_handle* h);

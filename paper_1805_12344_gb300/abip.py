@@ -44,6 +44,7 @@ ABIP_PREC_MIXED = 1
 ABIP_PREC_MIXED_BF16 = 2
 ABIP_LINSYS_DENSE_CHOL = 0
 ABIP_LINSYS_PCG = 1
+ABIP_LINSYS_SPARSE_LDL = 2
 
 STATUS_NAMES = {0: "unsolved", 1: "optimal", 2: "primal_infeasible", 3: "dual_infeasible", 4: "max_iter"}
 
@@ -124,6 +125,7 @@ _SIGS = {
     "abip_postsolve": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                  C.c_void_p, C.c_void_p]),
     "abip_presolve_free": (None, [C.c_void_p]),
+    "abip_ldl_analyze": (C.c_int, [C.POINTER(abip_matrix), C.c_void_p, C.c_void_p, C.POINTER(C.c_int64)]),
     "abip_status_str": (C.c_char_p, [C.c_int32]),
     "abip_last_error": (C.c_char_p, [C.c_void_p]),
     "abip_version": (C.c_char_p, []),
@@ -226,6 +228,19 @@ def abip_setup(A, b, c, params: Optional[abip_params] = None) -> C.c_void_p:
     rc = lib().abip_setup(C.byref(M), bp, cp, C.byref(params) if params is not None else None, C.byref(h))
     _check(rc)
     return h
+
+
+def abip_ldl_analyze(A):
+    """(perm, col_counts, nnz_l) of the sparse direct projection's symbolic factor: the
+    minimum-degree order of K = [I A^T; A -I] (node j < n: x_j, node n + i: row i of A)
+    and the strictly-lower nonzeros of each column of L.  Host only."""
+    M, keep = _matrix(A)
+    N = M.m + M.n
+    perm = np.zeros(N, dtype=np.int32)
+    counts = np.zeros(N, dtype=np.int64)
+    nnz = C.c_int64(0)
+    _check(lib().abip_ldl_analyze(C.byref(M), perm.ctypes.data, counts.ctypes.data, C.byref(nnz)))
+    return perm, counts, int(nnz.value)
 
 
 def abip_solve(h, x=None, y=None, s=None, stream=None) -> dict:

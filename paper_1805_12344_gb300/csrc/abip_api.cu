@@ -16,6 +16,7 @@
 
 #include "abip_device.cuh"
 #include "abip_internal.h"
+#include "ldl_host.h"
 #include "sell_host.h"
 
 using abip::BackwardInst;
@@ -122,6 +123,7 @@ const char* device_error_str(int err) {
     case abip::DEV_ERR_PCG: return "PCG exceeded cg_max_iter";
     case abip::DEV_ERR_NONFINITE: return "non-finite value in a reduction";
     case abip::DEV_ERR_CHOLESKY: return "Cholesky factorisation of I + A A^T broke down";
+    case abip::DEV_ERR_LDL: return "sparse LDL^T factorisation of the quasi-definite system broke down";
     default: return "device error";
   }
 }
@@ -139,7 +141,15 @@ int check_params(const abip_params& p, std::string& why) {
     why = "unknown precision";
     return 0;
   }
-  if (p.linsys != ABIP_LINSYS_DENSE_CHOL && p.linsys != ABIP_LINSYS_PCG && p.linsys != -1) { why = "unknown linsys"; return 0; }
+  if (p.linsys != ABIP_LINSYS_DENSE_CHOL && p.linsys != ABIP_LINSYS_PCG && p.linsys != ABIP_LINSYS_SPARSE_LDL &&
+      p.linsys != -1) {
+    why = "unknown linsys";
+    return 0;
+  }
+  if (p.linsys == ABIP_LINSYS_SPARSE_LDL && p.precision != ABIP_PREC_F64) {
+    why = "the sparse direct projection (linsys = SPARSE_LDL) runs in FP64 (precision = F64)";
+    return 0;
+  }
   if (p.warmstart != 0 && p.warmstart != 1) { why = "warmstart must be 0 or 1"; return 0; }
   if (p.cg_warm < 0 || p.cg_warm > 2) { why = "cg_warm must be 0, 1 or 2"; return 0; }
   if (p.stop_rule != 0 && p.stop_rule != 1) { why = "stop_rule must be 0 or 1"; return 0; }
@@ -189,17 +199,73 @@ void assign_vectors(abip::GridDelta& g, Arena& ar, int m, int n) {
   g.wdel = ar.take<float>(n); g.xsw = ar.take<abip::XSW>(n); g.dy = ar.take<float>(m);
 }
 
+// Arrays of the sparse direct projection (FP64 path only): the factor's pattern, K's
+// values on it (factored in place by the setup launch), pivots, sweep values, flags and
+// the LdlView the device routines read.  `view` receives the host copy of that view.
+void layout_ldl(Arena& ar, GridData<double>& g, const abip::ldl_host::Symbolic* sym, abip::LdlView& view) {
+  g.ldl_N = 0;
+  g.ldlv = nullptr;
+  view = abip::LdlView{};
+  if (!sym) return;
+  const int N = sym->N;
+  const size_t nz = sym->Li.size();
+  abip::LdlDev& L = view.F;
+  L.N = N;
+  L.perm = ar.take<int32_t>(N);
+  L.Lp = ar.take<int64_t>((size_t)N + 1);
+  L.Li = ar.take<int32_t>(nz);
+  L.Lx = ar.take<double>(nz);
+  L.Rp = ar.take<int64_t>((size_t)N + 1);
+  L.Rk = ar.take<int32_t>(nz);
+  L.Rpos = ar.take<int32_t>(nz);
+  L.Dd = ar.take<double>(N);
+  L.zf = ar.take<double>(N);
+  L.wb = ar.take<double>(N);
+  L.flag = ar.take<unsigned long long>(N);
+  view.m = g.m; view.n = g.n;
+  view.b = g.b; view.c = g.c; view.bbar = g.bbar; view.cbar = g.cbar;
+  view.y = g.y; view.x = g.x; view.s = g.s; view.zy = g.zy; view.zx = g.zx;
+  view.g1y = g.g1y; view.g1x = g.g1x; view.g2y = g.g2y; view.g2x = g.g2x;
+  view.partials = g.partials;
+  view.ctl = g.ctl;
+  g.ldlv = ar.take<abip::LdlView>(1);
+  g.ldl_N = N;
+}
+void layout_ldl(Arena&, abip::GridDelta&, const abip::ldl_host::Symbolic*, abip::LdlView&) {}
+
+void upload_ldl(const GridData<double>& g, const abip::ldl_host::Symbolic* sym, const std::vector<double>* lx0,
+                const abip::LdlView& view) {
+  if (!sym) return;
+  const abip::LdlDev& L = view.F;
+  const size_t nz = sym->Li.size();
+  cudaMemcpy((void*)L.perm, sym->perm.data(), sym->perm.size() * 4, cudaMemcpyHostToDevice);
+  cudaMemcpy((void*)L.Lp, sym->Lp.data(), sym->Lp.size() * 8, cudaMemcpyHostToDevice);
+  cudaMemcpy((void*)L.Rp, sym->Rp.data(), sym->Rp.size() * 8, cudaMemcpyHostToDevice);
+  if (nz > 0) {
+    cudaMemcpy((void*)L.Li, sym->Li.data(), nz * 4, cudaMemcpyHostToDevice);
+    cudaMemcpy((void*)L.Lx, lx0->data(), nz * 8, cudaMemcpyHostToDevice);
+    cudaMemcpy((void*)L.Rk, sym->Rk.data(), nz * 4, cudaMemcpyHostToDevice);
+    cudaMemcpy((void*)L.Rpos, sym->Rpos.data(), nz * 4, cudaMemcpyHostToDevice);
+  }
+  cudaMemcpy((void*)g.ldlv, &view, sizeof(view), cudaMemcpyHostToDevice);
+}
+void upload_ldl(const abip::GridDelta&, const abip::ldl_host::Symbolic*, const std::vector<double>*,
+                const abip::LdlView&) {}
+
 cudaError_t launch_persistent(abip_handle* h, cudaStream_t st) {
   if (h->mixed) return abip::launch_grid_delta(h->gdd, h->grid, st);
   return abip::launch_grid_solver_f64(h->gd64, h->val_f64 != 0, h->grid, st);
 }
 
-// Setup of the sparse (PCG) path for one LP: SELL copies of A and A^T, the device
-// arena of G (GridData<double> for FP64, GridDelta for mixed precision) and one
-// launch of the persistent kernel in MODE_SETUP.  vf64: store A's values as double.
+// Setup of the sparse path for one LP: SELL copies of A and A^T, the device arena of G
+// (GridData<double> for FP64, GridDelta for mixed precision) and one launch of the
+// persistent kernel in MODE_SETUP.  vf64: store A's values as double.  sym / lx0 (FP64
+// only): the symbolic factor of the direct projection and K's values on its pattern; the
+// setup launch factors it.  Null: the projection runs Jacobi-PCG.
 template <typename G>
 int setup_grid_path(abip_handle* h, G& g, const HostCSR& A, const std::vector<double>& b,
-                    const std::vector<double>& c, bool vf64, int maxc) {
+                    const std::vector<double>& c, bool vf64, int maxc,
+                    const abip::ldl_host::Symbolic* sym = nullptr, const std::vector<double>* lx0 = nullptr) {
   const int m = A.m, n = A.n;
   HostCSR AT = transpose(A);
   h->val_f64 = vf64 ? 1 : 0;
@@ -226,6 +292,7 @@ int setup_grid_path(abip_handle* h, G& g, const HostCSR& A, const std::vector<do
     M.perm = ar.take<int32_t>(H.perm.size());
     M.wsl = ar.take<int32_t>((size_t)grid * (abip::kGridThreads / 32) + 1);
   };
+  abip::LdlView ldl_view;   // direct projection: host copy of the device view
   auto layout = [&](Arena& ar, G& gg) {
     h->ctl = ar.take<SolveCtl>(1);
     layout_sell(ar, gg.A, SA);
@@ -234,6 +301,9 @@ int setup_grid_path(abip_handle* h, G& g, const HostCSR& A, const std::vector<do
     gg.partials = ar.take<double>((size_t)abip::kNumSlots * grid);
     gg.bar = ar.take<unsigned long long>(1);
     h->stage = ar.take<double>((size_t)m + 2 * (size_t)n);
+    gg.m = m; gg.n = n;
+    gg.ctl = h->ctl;
+    layout_ldl(ar, gg, sym, ldl_view);
   };
   Arena probe;
   G tmp{};
@@ -268,6 +338,7 @@ int setup_grid_path(abip_handle* h, G& g, const HostCSR& A, const std::vector<do
   };
   upload_sell(g.A, SA, wpA);
   upload_sell(g.AT, ST, wpT);
+  upload_ldl(g, sym, lx0, ldl_view);
   cudaMemcpy((void*)g.b, b.data(), m * sizeof(double), cudaMemcpyHostToDevice);
   cudaMemcpy((void*)g.c, c.data(), n * sizeof(double), cudaMemcpyHostToDevice);
   SolveCtl hc{};
@@ -849,12 +920,21 @@ int abip_setup(const abip_matrix* A, const double* b, const double* c, const abi
   }
   h->prm.linsys = linsys;
   h->mixed = prm.precision != ABIP_PREC_F64;
-  if (linsys == ABIP_LINSYS_PCG) {
+  if (linsys == ABIP_LINSYS_PCG || linsys == ABIP_LINSYS_SPARSE_LDL) {
     h->path = 0;
     HostCSR hA;
     bool f32 = false;
     rc = read_matrix_csr(h, A, hA, f32);
-    if (rc == ABIP_OK) {
+    if (rc == ABIP_OK && linsys == ABIP_LINSYS_SPARSE_LDL) {
+      abip::ldl_host::Symbolic sym;
+      std::string why;
+      if (!abip::ldl_host::analyze(hA, sym, why)) {
+        rc = fail(h, ABIP_E_UNSUPPORTED, "sparse direct projection: " + why + "; use linsys = PCG");
+      } else {
+        const std::vector<double> lx0 = abip::ldl_host::initial_values(hA, sym);
+        rc = setup_grid_path(h, h->gd64, hA, hb, hc, !f32, abip::grid_solver_max_ctas(!f32, h->device), &sym, &lx0);
+      }
+    } else if (rc == ABIP_OK) {
       if (h->mixed)   // FP32 values: exact for float input, rounded for double input (FP64 refreshes see them)
         rc = setup_grid_path(h, h->gdd, hA, hb, hc, false, abip::grid_delta_max_ctas(h->device));
       else
@@ -1345,6 +1425,25 @@ const char* abip_status_str(int32_t status) {
 const char* abip_last_error(const abip_handle* h) {
   if (h) return h->err.c_str();
   return g_err.c_str();
+}
+
+int abip_ldl_analyze(const abip_matrix* A, int32_t* perm, int64_t* col_counts, int64_t* nnz_l) {
+  int rc = validate_matrix(nullptr, A);
+  if (rc) return rc;
+  if (A->on_device) return fail(nullptr, ABIP_E_INVALID_ARG, "abip_ldl_analyze reads host matrices only");
+  HostCSR hA;
+  bool f32 = false;
+  rc = read_matrix_csr(nullptr, A, hA, f32);
+  if (rc) return rc;
+  abip::ldl_host::Symbolic sym;
+  std::string why;
+  if (!abip::ldl_host::analyze(hA, sym, why)) return fail(nullptr, ABIP_E_UNSUPPORTED, why);
+  const int N = sym.N;
+  if (perm) std::copy(sym.perm.begin(), sym.perm.end(), perm);
+  if (col_counts)
+    for (int p = 0; p < N; ++p) col_counts[p] = sym.Lp[p + 1] - sym.Lp[p];
+  if (nnz_l) *nnz_l = sym.Lp[N];
+  return ABIP_OK;
 }
 
 const char* abip_version(void) { return "abip-gb300 0.1 (sm_103a)"; }

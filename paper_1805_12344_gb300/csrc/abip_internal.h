@@ -44,6 +44,7 @@ struct SolveCtl {
   int64_t refreshes;              // mixed path: exact FP64 recomputations of the maintained products
   int32_t setup_rounds;           // mixed path: refinement rounds of the setup solves
   int32_t pad4;
+  unsigned long long ldl_epoch;   // sparse direct projection: solves done so far (flag epochs)
 };
 
 // phase timer buckets of the solve kernel (CTA 0's view, nanoseconds)
@@ -73,6 +74,43 @@ template <typename T> struct Vec2;
 template <> struct Vec2<float> { using type = float2; };
 template <> struct Vec2<double> { using type = double2; };
 
+// Device error code of the sparse direct projection, beside the DevErr codes: a pivot of
+// the wrong sign or not finite, or a row missing from the symbolic pattern.
+constexpr int DEV_ERR_LDL = 5;
+
+// Sparse direct projection (Sec. 4.4): the LDL^T factor of P K P^T with the
+// quasi-definite K = [[I_n, A^T], [A, -I_m]] (pattern and order from ldl_host.h), and
+// the arrays of its sync-free factorisation and triangular solves.  N = 0: not used.
+struct LdlDev {
+  int N = 0;
+  const int32_t* perm = nullptr;  // N: node of pivot p (x_j: j, yhat_i: n + i)
+  const int64_t* Lp = nullptr;    // N + 1: column p of L (strictly lower) is Li / Lx[Lp[p] .. Lp[p+1])
+  const int32_t* Li = nullptr;    // nnz(L) row indices, increasing within a column
+  double* Lx = nullptr;           // nnz(L): K's entries when uploaded, L after the factorisation
+  const int64_t* Rp = nullptr;    // N + 1: row p of L is Rk / Rpos[Rp[p] .. Rp[p+1])
+  const int32_t* Rk = nullptr;    // nnz(L): column k < p of each entry of row p, increasing
+  const int32_t* Rpos = nullptr;  // nnz(L): position of L(p, k) in Li / Lx
+  double* Dd = nullptr;           // N: pivots D_p
+  double* zf = nullptr;           // N: forward sweep, L z = P r
+  double* wb = nullptr;           // N: backward sweep, L^T w = D^{-1} z
+  unsigned long long* flag = nullptr;  // N, zeroed at setup: 1 once column p is factored; 2e + 1 /
+                                       // 2e + 2 once row p of solve e's forward / backward sweep is final
+};
+
+// Everything the direct projection's device routines touch, kept in device memory so
+// that they take one plain pointer (the grid kernel's GridData is a kernel parameter).
+struct LdlView {
+  LdlDev F;
+  int m = 0, n = 0;
+  const double* b = nullptr; const double* c = nullptr;
+  const double* bbar = nullptr; const double* cbar = nullptr;
+  const double* y = nullptr; const double* x = nullptr; const double* s = nullptr;   // iterate
+  double* zy = nullptr; double* zx = nullptr;                                        // M^{-1} w
+  double* g1y = nullptr; double* g1x = nullptr; double* g2y = nullptr; double* g2x = nullptr;
+  double* partials = nullptr;
+  SolveCtl* ctl = nullptr;
+};
+
 // Device pointers of the sparse single-instance path.
 template <typename T>
 struct GridData {
@@ -93,6 +131,8 @@ struct GridData {
   double* partials;                                           // kNumSlots * gridDim doubles
   unsigned long long* bar;                                    // barrier arrival counter
   SolveCtl* ctl;
+  int ldl_N;                                                  // > 0: direct projection instead of PCG
+  const LdlView* ldlv;                                        // its arrays (device memory)
 };
 
 // Per column of the mixed sparse path: the FP32 change (dx, ds) of the iterate and

@@ -1,6 +1,7 @@
 // Persistent cooperative kernel running ABIP (Algorithm 2 with the over-relaxation
-// of Sec. 4.2) on one sparse LP: Jacobi-PCG projection (Sec. 4.4) and the Sec. 4.1
-// termination tests, entirely on the device.
+// of Sec. 4.2) on one sparse LP: Jacobi-PCG projection (Sec. 4.4), or the direct
+// projection through a sparse LDL^T factor of the quasi-definite system (Sec. 4.4),
+// and the Sec. 4.1 termination tests, entirely on the device.
 //
 // One launch covers setup (MODE_SETUP: embedding constants of Eq. bar-b-c-z-re,
 // Jacobi diagonal, M^{-1} H and the 2x2 Schur complement) or the whole solve
@@ -36,7 +37,200 @@ enum Slot : int {
 
 constexpr int kMinBlocks = 1;   // resident CTAs per SM requested from the compiler
 
+// Direct projection: the number of factor solves so far (the flag epoch of the last one),
+// per CTA.  Thread 0 loads it at launch and advances it after a __syncthreads that
+// follows every thread's read.
+__shared__ unsigned long long s_ldl_epoch;
+
 using namespace sell;
+
+// ---------------------------------------------------------------------------
+// Sparse direct projection (Sec. 4.4, the quasi-definite system K = [I A^T; A -I]).
+// No grid barrier inside: a row or column is published by a release store of its flag,
+// and a reader acquires the flag before it loads the published values (from L2).
+// Free functions on one LdlView pointer, so that the grid kernel's parameters stay
+// where they are.
+// ---------------------------------------------------------------------------
+
+// Wait (this lane) until *f >= target.  Bounded by the barrier wall-clock limit and left
+// as soon as any thread has flagged an error; returns false in both cases.
+__device__ __noinline__ bool ldl_spin(const unsigned long long* f, unsigned long long target, SolveCtl* C) {
+  const unsigned long long t0 = globaltimer_ns();
+  const unsigned long long limit = C->bar_limit_ns ? C->bar_limit_ns : kBarrierLimitNs;
+  for (unsigned spins = 0;; ++spins) {
+    __nanosleep(16);
+    if (ld_acquire_u64(f) >= target) return true;
+    if ((spins & 31u) == 31u) {
+      if (ld_relaxed_i32(&C->err) != 0) return false;
+      if (globaltimer_ns() - t0 > limit) {
+        atomicCAS(&C->err, 0, (int)DEV_ERR_BARRIER_TIMEOUT);
+        return false;
+      }
+    }
+  }
+}
+__device__ __forceinline__ bool ldl_wait(const unsigned long long* f, unsigned long long target, SolveCtl* C) {
+  return ld_acquire_u64(f) >= target || ldl_spin(f, target, C);
+}
+__device__ __forceinline__ void st_release(unsigned long long* f, unsigned long long v) {
+  asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(f), "l"(v) : "memory");
+}
+
+// Left-looking LDL^T of P K P^T on the symbolic pattern: one warp per column, columns
+// handed out in increasing order (warp w of W takes w, w + W, ...).  Column j needs the
+// columns k < j of row j's entries, each published by its flag; the lowest unfinished
+// column never waits, so the sweep always progresses.  For each such k:
+//   D_j -= L(j,k)^2 D_k,   L(i,j) -= L(i,k) L(j,k) D_k  for the rows i > j of column k
+// (those rows lie in column j's pattern), then L(i,j) /= D_j.  K is quasi-definite, so
+// each pivot's sign is fixed (+ for an x node, - for a yhat node); a pivot of the other
+// sign, or not finite, is a breakdown (DEV_ERR_LDL).  A failing warp leaves; the waits
+// of the others then end on the error flag.
+__device__ __noinline__ void ldl_factor(const LdlView* __restrict__ V) {
+  const LdlDev& F = V->F;
+  SolveCtl* C = V->ctl;
+  const int n = V->n;
+  const int lane = threadIdx.x & 31;
+  const int W = (gridDim.x * blockDim.x) >> 5;
+  const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  for (int j = gw; j < F.N; j += W) {
+    const int64_t c0 = F.Lp[j], c1 = F.Lp[j + 1];
+    const bool pos = F.perm[j] < n;
+    double d = pos ? 1.0 : -1.0;
+    bool ok = true;
+    for (int64_t r = F.Rp[j]; r < F.Rp[j + 1]; ++r) {
+      const int k = F.Rk[r];
+      if (!__all_sync(0xffffffffu, ldl_wait(F.flag + k, 1ull, C))) { ok = false; break; }
+      const int64_t pjk = F.Rpos[r];
+      const double ljk = __ldcg(F.Lx + pjk);
+      const double f = ljk * __ldcg(F.Dd + k);
+      d -= ljk * f;
+      const int64_t k1 = F.Lp[k + 1];
+      bool found = true;
+      for (int64_t e = pjk + 1 + lane; e < k1; e += 32) {
+        const int i = F.Li[e];
+        int64_t lo = c0, hi = c1;
+        while (lo < hi) {
+          const int64_t mid = (lo + hi) >> 1;
+          if (F.Li[mid] < i) lo = mid + 1;
+          else hi = mid;
+        }
+        if (lo < c1 && F.Li[lo] == i) __stcg(F.Lx + lo, __ldcg(F.Lx + lo) - __ldcg(F.Lx + e) * f);
+        else found = false;
+      }
+      if (!__all_sync(0xffffffffu, found)) {
+        if (lane == 0) atomicCAS(&C->err, 0, (int)DEV_ERR_LDL);
+        ok = false;
+        break;
+      }
+    }
+    if (ok && !(isfinite(d) && (pos ? d > 0.0 : d < 0.0))) {
+      if (lane == 0) atomicCAS(&C->err, 0, (int)DEV_ERR_LDL);
+      ok = false;
+    }
+    if (!ok) return;
+    for (int64_t e = c0 + lane; e < c1; e += 32) __stcg(F.Lx + e, __ldcg(F.Lx + e) / d);
+    if (lane == 0) __stcg(F.Dd + j, d);
+    __threadfence();
+    __syncwarp();
+    if (lane == 0) st_release(F.flag + j, 1ull);
+  }
+}
+
+// Solve K [x; yhat] = [r_x; r_y] with the factor: forward sweep L z = P r by rows in
+// increasing order, backward sweep L^T w = D^{-1} z by columns in decreasing order, and
+// [x; yhat] = P^T w.  Each warp takes its forward rows (w, w + W, ...) and then its
+// backward columns (N-1-w, N-1-w-W, ...).  Everything a task reads belongs to an
+// earlier task in that order (forward row p: rows k < p; backward column p: rows i > p
+// and forward row p), published by its flag reaching this solve's value, so the
+// lowest unfinished task never waits.  `epoch` numbers this solve (the flags of the
+// previous one hold smaller values).  rhs(q) is r at node q; put(q, w) receives the
+// solution at node q (lane 0 of the warp that finishes it).  On a failed wait the warp
+// leaves with the error flag set; the caller's next grid barrier reports it.
+template <typename RF, typename PF>
+__device__ __forceinline__ void ldl_solve(const LdlView* __restrict__ V, unsigned long long epoch, RF rhs, PF put) {
+  const LdlDev& F = V->F;
+  SolveCtl* C = V->ctl;
+  const int lane = threadIdx.x & 31;
+  const int W = (gridDim.x * blockDim.x) >> 5;
+  const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const unsigned long long fF = 2 * epoch + 1, fB = 2 * epoch + 2;
+  for (int p = gw; p < F.N; p += W) {
+    double acc = 0.0;
+    bool ok = true;
+    for (int64_t r = F.Rp[p] + lane; r < F.Rp[p + 1]; r += 32) {
+      const int k = F.Rk[r];
+      if (!ldl_wait(F.flag + k, fF, C)) { ok = false; break; }
+      acc += __ldcg(F.Lx + F.Rpos[r]) * __ldcg(F.zf + k);
+    }
+    if (!__all_sync(0xffffffffu, ok)) return;
+    acc = warp_sum(acc);
+    if (lane == 0) {
+      __stcg(F.zf + p, rhs(F.perm[p]) - acc);
+      st_release(F.flag + p, fF);
+    }
+    __syncwarp();
+  }
+  for (int t = gw; t < F.N; t += W) {
+    const int p = F.N - 1 - t;
+    double acc = 0.0;
+    bool ok = true;
+    for (int64_t e = F.Lp[p] + lane; e < F.Lp[p + 1]; e += 32) {
+      const int i = F.Li[e];
+      if (!ldl_wait(F.flag + i, fB, C)) { ok = false; break; }
+      acc += __ldcg(F.Lx + e) * __ldcg(F.wb + i);
+    }
+    if (lane == 0 && ok) ok = ldl_wait(F.flag + p, fF, C);
+    if (!__all_sync(0xffffffffu, ok)) return;
+    acc = warp_sum(acc);
+    if (lane == 0) {
+      const double w = __ldcg(F.zf + p) / __ldcg(F.Dd + p) - acc;
+      __stcg(F.wb + p, w);
+      st_release(F.flag + p, fB);
+      put(F.perm[p], w);
+    }
+    __syncwarp();
+  }
+}
+
+// Setup solve `col` of the direct projection: M^{-1} h1 (col 0) or M^{-1} h2 (col 1)
+// from K [x; yhat] = [h_x; h_y] with y = -yhat (h1 = [-b; c], h2 = [bbar; -cbar]).
+__device__ __noinline__ void ldl_setup_solve(const LdlView* __restrict__ V, int col, unsigned long long epoch) {
+  const int n = V->n;
+  double* gy = col == 0 ? V->g1y : V->g2y;
+  double* gx = col == 0 ? V->g1x : V->g2x;
+  auto rhs = [&](int q) -> double {
+    if (q < n) return col == 0 ? V->c[q] : -V->cbar[q];
+    return col == 0 ? -V->b[q - n] : V->bbar[q - n];
+  };
+  auto put = [&](int q, double w) {
+    if (q < n) gx[q] = w;
+    else gy[q - n] = -w;
+  };
+  ldl_solve(V, epoch, rhs, put);
+}
+
+// Projection of one ADMM update by the factor: K [zx; -zy] = [w_x; w_y] with
+// w = (y, x + s), and the two sums of H^T z into the partials (slot `slot`).
+__device__ __noinline__ void ldl_update_solve(const LdlView* __restrict__ V, unsigned long long epoch, int slot,
+                                              double* red) {
+  const int n = V->n;
+  double hz[2] = {0.0, 0.0};
+  auto rhs = [&](int q) -> double { return q < n ? V->x[q] + V->s[q] : V->y[q - n]; };
+  auto put = [&](int q, double w) {
+    if (q < n) {
+      V->zx[q] = w;
+      hz[0] += V->c[q] * w;
+      hz[1] -= V->cbar[q] * w;
+    } else {
+      const int i = q - n;
+      V->zy[i] = -w;
+      hz[0] += V->b[i] * w;
+      hz[1] -= V->bbar[i] * w;
+    }
+  };
+  ldl_solve(V, epoch, rhs, put);
+  grid_partial_t<2, double>(hz, V->partials, slot, red);
+}
 
 template <typename T, typename V>
 struct Solver {
@@ -369,8 +563,19 @@ struct Solver {
     if (!sync(P_SETUP)) return;
     double tot[3];
     totals<3>(tot, S_SETUP);
+    if (D.ldl_N > 0) {
+      // direct projection: factor P K P^T, then the two setup solves
+      const unsigned long long e0 = s_ldl_epoch;
+      ldl_factor(D.ldlv);
+      if (!sync(P_SETUP)) return;
+      for (int col = 0; col < 2; ++col) {
+        ldl_setup_solve(D.ldlv, col, e0 + 1 + col);
+        if (!sync(P_SETUP)) return;
+      }
+      if (threadIdx.x == 0) s_ldl_epoch = e0 + 2;   // every thread read s_ldl_epoch before the barriers
+    }
     // two solves with M: a = h_y, d = h_x  ->  zy = G^{-1}(a - A d), zx = d + A^T zy
-    for (int col = 0; col < 2; ++col) {
+    for (int col = 0; col < 2 && D.ldl_N == 0; ++col) {
       T* gy = col == 0 ? D.g1y : D.g2y;
       T* gx = col == 0 ? D.g1x : D.g2x;
       for (int j = t.gtid; j < D.n; j += t.nthr) gx[j] = col == 0 ? D.c[j] : -D.cbar[j];
@@ -534,32 +739,38 @@ struct Solver {
       // projection (Eq. Simple-Update:Affine) with w = u + v: w_y = y (r = 0),
       // w_x = x + s, w_tau = tau + kappa, w_theta = theta + xi.
       // z = M^{-1} w_yx: G zy = w_y - A w_x = y - Ax - As (PCG warm-started), zx = w_x + A^T zy.
-      auto qf = [&](int i) -> T { return D.y[i] - (D.Ax[i] + D.As[i]); };
-      // PCG tolerance: fixed, or (cg_rel > 0) loosened to cg_rel times the current
-      // relative KKT residual, never below cg_tol (reading A10, performance mode)
-      const double kkt = fmax(pres, fmax(dres, dgap));
-      const double tol = cg_rel > 0.0 ? fmax(C->cg_tol, cg_rel * kkt) : C->cg_tol;
-      const int extrap = (C->cg_warm == 2 && total >= 3) ? 2 : (C->cg_warm >= 1 && total >= 2) ? 1 : 0;
-      const int it = pcg(D.zy, qf, tol, C->cg_max, extrap, D.zp2, D.zp3);
-      if (it == -1) return;
-      if (it == -2) { flag(DEV_ERR_PCG); sync(P_CG_UPD); return; }
-      cgtot += it;
-      T hz[2] = {T(0), T(0)};
-      {
-        auto e = [&](int j, T v, T) {
-          const T zxj = (D.x[j] + D.s[j]) + v;
-          D.zx[j] = zxj;
-          hz[0] += D.c[j] * zxj;
-          hz[1] -= D.cbar[j] * zxj;
-        };
-        rowsAT(D.zy, e);
+      if (D.ldl_N > 0) {
+        const unsigned long long e = s_ldl_epoch + 1;
+        ldl_update_solve(D.ldlv, e, S_HZ, red);   // its block reduction syncs after every read of e
+        if (threadIdx.x == 0) s_ldl_epoch = e;
+      } else {
+        T hz[2] = {T(0), T(0)};
+        auto qf = [&](int i) -> T { return D.y[i] - (D.Ax[i] + D.As[i]); };
+        // PCG tolerance: fixed, or (cg_rel > 0) loosened to cg_rel times the current
+        // relative KKT residual, never below cg_tol (reading A10, performance mode)
+        const double kkt = fmax(pres, fmax(dres, dgap));
+        const double tol = cg_rel > 0.0 ? fmax(C->cg_tol, cg_rel * kkt) : C->cg_tol;
+        const int extrap = (C->cg_warm == 2 && total >= 3) ? 2 : (C->cg_warm >= 1 && total >= 2) ? 1 : 0;
+        const int it = pcg(D.zy, qf, tol, C->cg_max, extrap, D.zp2, D.zp3);
+        if (it == -1) return;
+        if (it == -2) { flag(DEV_ERR_PCG); sync(P_CG_UPD); return; }
+        cgtot += it;
+        {
+          auto e = [&](int j, T v, T) {
+            const T zxj = (D.x[j] + D.s[j]) + v;
+            D.zx[j] = zxj;
+            hz[0] += D.c[j] * zxj;
+            hz[1] -= D.cbar[j] * zxj;
+          };
+          rowsAT(D.zy, e);
+        }
+        for (int i = t.gtid; i < D.m; i += t.nthr) {
+          const T zyi = D.zy[i];
+          hz[0] -= D.b[i] * zyi;
+          hz[1] += D.bbar[i] * zyi;
+        }
+        grid_partial_t<2, T>(hz, D.partials, S_HZ, red);
       }
-      for (int i = t.gtid; i < D.m; i += t.nthr) {
-        const T zyi = D.zy[i];
-        hz[0] -= D.b[i] * zyi;
-        hz[1] += D.bbar[i] * zyi;
-      }
-      grid_partial_t<2, T>(hz, D.partials, S_HZ, red);
       if (!sync(P_ZX)) return;
       double h[2], sc[6];
       // thread 0: t = K^{-1} (w_{tau,theta} + H^T z), and the relaxed barrier and dual
@@ -596,9 +807,15 @@ struct Solver {
 template <typename T, typename V>
 __global__ void __launch_bounds__(kGridThreads, kMinBlocks) grid_kernel(GridData<T> d) {
   __shared__ double red[32 * 12];
+  if (threadIdx.x == 0) s_ldl_epoch = d.ctl->ldl_epoch;
+  __syncthreads();
   Solver<T, V> S(d, red);
   if (d.ctl->mode == MODE_SETUP) S.setup();
   else S.solve();
+  // the flag epochs of the direct projection carry into the next launch: the largest
+  // count any CTA reached, so that a launch that ended early never reuses one
+  __syncthreads();
+  if (d.ldl_N > 0 && threadIdx.x == 0) atomicMax(&d.ctl->ldl_epoch, s_ldl_epoch);
 }
 
 template <typename T, typename V>

@@ -26,6 +26,7 @@ SPARSE_PLANTED = 1    # [R I] CSR LP, 8 nonzeros per column of R
 BASIS_PURSUIT = 2
 BATCH_UNEVEN = 3
 L1_SVM = 4
+GRID_FLOW = 8         # planted min-cost flow LPs on a 2-D grid (the sparse direct projection's workload)
 TINY = 9              # tiny random LPs for brute-force basis enumeration
 
 
@@ -181,6 +182,46 @@ def planted_sparse(m: int = 100000, n_r: Optional[int] = None, per_col: int = 8,
     c = Asp.T @ y0 + s0
     return LP(A=A, b=b, c=c, x0=x0, y0=y0, s0=s0, expect="optimal",
               meta=dict(kind="planted_sparse", m=m, n=n, nnz=A.nnz, per_col=per_col))
+
+
+def grid_flow(side: int = 48, seed: Optional[int] = None) -> LP:
+    """Planted min-cost flow LP on a side x side grid with 4-neighbour links, CSR.
+
+    One column per directed arc (both directions of every grid link, n = 4 side (side - 1)),
+    one row per node except the last (m = side^2 - 1): A_{v,a} = +1 if arc a leaves node v,
+    -1 if it enters it.  The node-arc incidence matrix of a connected graph has rank
+    nodes - 1, so dropping one node's row leaves A with full row rank (the standing
+    assumption of Sec. 2).  I + A A^T is I plus twice the grid's graph Laplacian with that
+    row and column removed: its condition number grows like side^2, so Jacobi-PCG needs
+    many iterations per projection, while the factor of the quasi-definite system stays
+    sparse under a minimum-degree order.  The planted pair follows _planted_pair (b = A x0,
+    c = A^T y0 + s0), so the optimum is known."""
+    rng = np.random.default_rng(seed_for(GRID_FLOW) if seed is None else seed)
+    nodes = side * side
+    links = [(r * side + q, r * side + q + 1) for r in range(side) for q in range(side - 1)]
+    links += [(r * side + q, (r + 1) * side + q) for r in range(side - 1) for q in range(side)]
+    tails, heads = [], []
+    for u, v in links:
+        tails += [u, v]
+        heads += [v, u]
+    tails = np.asarray(tails)
+    heads = np.asarray(heads)
+    n = tails.size
+    keep = nodes - 1                       # rows 0 .. nodes-2; the last node's row is dropped
+    rows = np.concatenate([tails, heads])
+    cols = np.concatenate([np.arange(n), np.arange(n)])
+    vals = np.concatenate([np.ones(n, np.float32), -np.ones(n, np.float32)])
+    sel = rows < keep
+    rows, cols, vals = rows[sel], cols[sel], vals[sel]
+    order = np.lexsort((cols, rows))
+    rows, cols, vals = rows[order], cols[order], vals[order]
+    row_ptr = np.zeros(keep + 1, dtype=np.int64)
+    np.cumsum(np.bincount(rows, minlength=keep), out=row_ptr[1:])
+    A = CSR(m=keep, n=n, row_ptr=row_ptr, col_idx=cols.astype(np.int32), val=vals.astype(np.float32))
+    x0, y0, s0 = _planted_pair(rng, n, keep)
+    Asp = A.to_scipy()
+    return LP(A=A, b=Asp @ x0, c=Asp.T @ y0 + s0, x0=x0, y0=y0, s0=s0, expect="optimal",
+              meta=dict(kind="grid_flow", side=side, m=keep, n=n, nnz=A.nnz))
 
 
 RANDOM_UDV = 5        # the random dense LPs of the paper's experiments (Sec. 5.1)
