@@ -69,6 +69,8 @@ def parse():
     ap.add_argument("--batch-count", type=int, default=256, help="LPs in the uneven-batch leg")
     ap.add_argument("--batch-cap", type=int, default=20000, help="ADMM update cap of the uneven-batch leg")
     ap.add_argument("--bp-cap", type=int, default=30000, help="ADMM update cap of the basis-pursuit leg")
+    ap.add_argument("--flow-side", type=int, default=16, help="grid side of the direct-projection leg")
+    ap.add_argument("--flow-cap", type=int, default=150000, help="ADMM update cap of the direct-projection leg")
     ap.add_argument("--cpu-sample", action="store_true", help=argparse.SUPPRESS)   # child process mode
     ap.add_argument("--admm-iters-hint", type=int, default=0, help=argparse.SUPPRESS)
     return ap.parse_args()
@@ -225,6 +227,34 @@ def leg_bb_beta(abip, W, args):
         solved = _solved(infos)
         out[name] = {"lps_solved": solved, "wall_s": wall, "lps_solved_per_s": solved / wall,
                      "admm_updates": int(sum(i["admm_iters"] for i in infos))}
+    return out
+
+
+def leg_grid_flow_direct(abip, W, args):
+    """The sparse direct projection (Sec. 4.4, LDL^T of the quasi-definite system) on a
+    planted min-cost flow LP over a side x side grid, whose I + A A^T (a grid Laplacian)
+    makes Jacobi-PCG take many iterations per projection: one solve to 1e-6 through the
+    factor, and the PCG path on the same LP for a capped number of updates (the two paths
+    produce the same iterates up to rounding, so time per update compares them)."""
+    side = args.flow_side
+    lp = W.grid_flow(side)
+    s = abip.Solver(lp.A, lp.b, lp.c, linsys=abip.ABIP_LINSYS_SPARSE_LDL, max_admm_iters=args.flow_cap)
+    info, *_ = s.solve()
+    s.close()
+    _, _, nnz_l = abip.abip_ldl_analyze(lp.A)
+    out = {"workload": f"grid_flow_{side}x{side}", "m": lp.m, "n": lp.n, "nnz_l": nnz_l, "eps": 1e-6,
+           "cap_admm_updates": args.flow_cap,
+           "direct": {"status": abip.STATUS_NAMES.get(info["status"], "?"), "admm_updates": info["admm_iters"],
+                      "setup_s": info["setup_s"], "kernel_s": info["kernel_s"],
+                      "lps_solved_per_s": (1.0 / (info["setup_s"] + info["kernel_s"])) if info["status"] == 1 else 0.0,
+                      "us_per_update": 1e6 * info["kernel_s"] / max(1, info["admm_iters"]),
+                      "obj_rel_err": abs(info["obj"] - lp.p_star) / max(1.0, abs(lp.p_star))}}
+    s = abip.Solver(lp.A, lp.b, lp.c, linsys=abip.ABIP_LINSYS_PCG, max_admm_iters=600, cg_max_iter=5000)
+    info2, *_ = s.solve()
+    s.close()
+    out["pcg_600_updates"] = {"kernel_s": info2["kernel_s"], "us_per_update": 1e6 * info2["kernel_s"] / max(1, info2["admm_iters"]),
+                              "cg_iters_per_update": info2["cg_iters"] / max(1, info2["admm_iters"])}
+    out["direct_speedup_per_update"] = out["pcg_600_updates"]["us_per_update"] / max(1e-9, out["direct"]["us_per_update"])
     return out
 
 
@@ -596,7 +626,8 @@ def main():
                         ("random_udv", lambda: leg_random_udv(abip, W, args)),
                         ("svm_backward", lambda: leg_svm_backward(abip, W, args)),
                         ("bb_beta", lambda: leg_bb_beta(abip, W, args)),
-                        ("sice", lambda: leg_sice(abip, W, args))):
+                        ("sice", lambda: leg_sice(abip, W, args)),
+                        ("grid_flow_direct", lambda: leg_grid_flow_direct(abip, W, args))):
             try:
                 legs[key] = fn()
             except Exception as ex:  # a leg must not sink the main line

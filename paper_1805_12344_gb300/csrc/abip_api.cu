@@ -219,8 +219,8 @@ void layout_ldl(Arena& ar, GridData<double>& g, const abip::ldl_host::Symbolic* 
   L.Rk = ar.take<int32_t>(nz);
   L.Rpos = ar.take<int32_t>(nz);
   L.Dd = ar.take<double>(N);
-  L.zf = ar.take<double>(N);
-  L.wb = ar.take<double>(N);
+  L.zf = ar.take<double>(2 * (size_t)N);
+  L.wb = ar.take<double>(2 * (size_t)N);
   L.flag = ar.take<unsigned long long>(N);
   view.m = g.m; view.n = g.n;
   view.b = g.b; view.c = g.c; view.bbar = g.bbar; view.cbar = g.cbar;
@@ -247,6 +247,9 @@ void upload_ldl(const GridData<double>& g, const abip::ldl_host::Symbolic* sym, 
     cudaMemcpy((void*)L.Rk, sym->Rk.data(), nz * 4, cudaMemcpyHostToDevice);
     cudaMemcpy((void*)L.Rpos, sym->Rpos.data(), nz * 4, cudaMemcpyHostToDevice);
   }
+  const std::vector<unsigned long long> empty(2 * (size_t)L.N, abip::kLdlEmpty);
+  cudaMemcpy((void*)L.zf, empty.data(), empty.size() * 8, cudaMemcpyHostToDevice);
+  cudaMemcpy((void*)L.wb, empty.data(), empty.size() * 8, cudaMemcpyHostToDevice);
   cudaMemcpy((void*)g.ldlv, &view, sizeof(view), cudaMemcpyHostToDevice);
 }
 void upload_ldl(const abip::GridDelta&, const abip::ldl_host::Symbolic*, const std::vector<double>*,

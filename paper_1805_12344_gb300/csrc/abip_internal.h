@@ -91,11 +91,15 @@ struct LdlDev {
   const int32_t* Rk = nullptr;    // nnz(L): column k < p of each entry of row p, increasing
   const int32_t* Rpos = nullptr;  // nnz(L): position of L(p, k) in Li / Lx
   double* Dd = nullptr;           // N: pivots D_p
-  double* zf = nullptr;           // N: forward sweep, L z = P r
-  double* wb = nullptr;           // N: backward sweep, L^T w = D^{-1} z
-  unsigned long long* flag = nullptr;  // N, zeroed at setup: 1 once column p is factored; 2e + 1 /
-                                       // 2e + 2 once row p of solve e's forward / backward sweep is final
+  double* zf = nullptr;           // 2N: forward sweep L z = P r, one buffer of N per solve parity
+  double* wb = nullptr;           // 2N: backward sweep L^T w = D^{-1} z, likewise
+                                  // (an entry not yet computed holds kLdlEmpty)
+  unsigned long long* flag = nullptr;  // N, zeroed at setup: 1 once column p is factored
 };
+
+// Bit pattern of a sweep entry not yet computed: a signalling NaN, which no arithmetic
+// result can be (operations return quiet NaNs), so a reader can wait on the value itself.
+constexpr unsigned long long kLdlEmpty = 0x7FF4A5A5A5A5A5A5ull;
 
 // Everything the direct projection's device routines touch, kept in device memory so
 // that they take one plain pointer (the grid kernel's GridData is a kernel parameter).

@@ -46,20 +46,31 @@ using namespace sell;
 
 // ---------------------------------------------------------------------------
 // Sparse direct projection (Sec. 4.4, the quasi-definite system K = [I A^T; A -I]).
-// No grid barrier inside: a row or column is published by a release store of its flag,
-// and a reader acquires the flag before it loads the published values (from L2).
-// Free functions on one LdlView pointer, so that the grid kernel's parameters stay
-// where they are.
+// No grid barrier inside.  The factorisation publishes a column by a release store of
+// its flag, acquired by its readers.  The sweeps publish each entry by storing the value
+// itself over the kLdlEmpty pattern, and a reader waits until the pattern is gone: one
+// relaxed 64-bit store and one load per dependency, no fences.  Free functions on one
+// LdlView pointer, so that the grid kernel's parameters stay where they are.
 // ---------------------------------------------------------------------------
 
-// Wait (this lane) until *f >= target.  Bounded by the barrier wall-clock limit and left
-// as soon as any thread has flagged an error; returns false in both cases.
-__device__ __noinline__ bool ldl_spin(const unsigned long long* f, unsigned long long target, SolveCtl* C) {
+__device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_relaxed_f64(double* p, double v) {
+  asm volatile("st.relaxed.gpu.global.f64 [%0], %1;" ::"l"(p), "d"(v) : "memory");
+}
+
+// Shared wait loop: until done() holds, bounded by the barrier wall-clock limit and left
+// as soon as any thread has flagged an error; false in both cases.
+template <typename Done>
+__device__ __forceinline__ bool ldl_spin_until(Done done, SolveCtl* C) {
   const unsigned long long t0 = globaltimer_ns();
   const unsigned long long limit = C->bar_limit_ns ? C->bar_limit_ns : kBarrierLimitNs;
   for (unsigned spins = 0;; ++spins) {
     __nanosleep(16);
-    if (ld_acquire_u64(f) >= target) return true;
+    if (done()) return true;
     if ((spins & 31u) == 31u) {
       if (ld_relaxed_i32(&C->err) != 0) return false;
       if (globaltimer_ns() - t0 > limit) {
@@ -69,11 +80,30 @@ __device__ __noinline__ bool ldl_spin(const unsigned long long* f, unsigned long
     }
   }
 }
+
+// Factorisation: wait (this lane) until *f >= target.
+__device__ __noinline__ bool ldl_spin(const unsigned long long* f, unsigned long long target, SolveCtl* C) {
+  return ldl_spin_until([&] { return ld_acquire_u64(f) >= target; }, C);
+}
 __device__ __forceinline__ bool ldl_wait(const unsigned long long* f, unsigned long long target, SolveCtl* C) {
   return ld_acquire_u64(f) >= target || ldl_spin(f, target, C);
 }
 __device__ __forceinline__ void st_release(unsigned long long* f, unsigned long long v) {
   asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(f), "l"(v) : "memory");
+}
+
+// Sweeps: the value at p once it is no longer kLdlEmpty (kLdlEmpty if the wait failed).
+__device__ __noinline__ unsigned long long ldl_spin_value(const unsigned long long* p, SolveCtl* C) {
+  unsigned long long v = kLdlEmpty;
+  ldl_spin_until([&] { v = ld_relaxed_u64(p); return v != kLdlEmpty; }, C);
+  return v;
+}
+__device__ __forceinline__ bool ldl_take(const double* p, double& out, SolveCtl* C) {
+  const unsigned long long* q = reinterpret_cast<const unsigned long long*>(p);
+  unsigned long long v = ld_relaxed_u64(q);
+  if (v == kLdlEmpty) v = ldl_spin_value(q, C);
+  out = __longlong_as_double((long long)v);
+  return v != kLdlEmpty;
 }
 
 // Left-looking LDL^T of P K P^T on the symbolic pattern: one warp per column, columns
@@ -141,54 +171,76 @@ __device__ __noinline__ void ldl_factor(const LdlView* __restrict__ V) {
 // [x; yhat] = P^T w.  Each warp takes its forward rows (w, w + W, ...) and then its
 // backward columns (N-1-w, N-1-w-W, ...).  Everything a task reads belongs to an
 // earlier task in that order (forward row p: rows k < p; backward column p: rows i > p
-// and forward row p), published by its flag reaching this solve's value, so the
-// lowest unfinished task never waits.  `epoch` numbers this solve (the flags of the
-// previous one hold smaller values).  rhs(q) is r at node q; put(q, w) receives the
-// solution at node q (lane 0 of the warp that finishes it).  On a failed wait the warp
-// leaves with the error flag set; the caller's next grid barrier reports it.
+// and forward row p), so the lowest unfinished task never waits.  Solve `epoch` uses the
+// buffer pair of its parity and empties the other pair for the next solve (the one
+// before, which used it, is complete: a grid barrier separates every two solves).
+// rhs(q) is r at node q; put(q, w) receives the solution at node q (lane 0 of the warp
+// that finishes it).  On a failed wait the warp leaves with the error flag set; the
+// caller's next grid barrier reports it.
 template <typename RF, typename PF>
 __device__ __forceinline__ void ldl_solve(const LdlView* __restrict__ V, unsigned long long epoch, RF rhs, PF put) {
   const LdlDev& F = V->F;
   SolveCtl* C = V->ctl;
+  const int N = F.N;
   const int lane = threadIdx.x & 31;
   const int W = (gridDim.x * blockDim.x) >> 5;
   const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const unsigned long long fF = 2 * epoch + 1, fB = 2 * epoch + 2;
-  for (int p = gw; p < F.N; p += W) {
+  const size_t cur = (size_t)(epoch & 1) * N, other = (size_t)((epoch & 1) ^ 1) * N;
+  double* zf = F.zf + cur;
+  double* wb = F.wb + cur;
+  {
+    unsigned long long* zo = reinterpret_cast<unsigned long long*>(F.zf + other);
+    unsigned long long* wo = reinterpret_cast<unsigned long long*>(F.wb + other);
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
+      zo[i] = kLdlEmpty;
+      wo[i] = kLdlEmpty;
+    }
+  }
+  for (int p = gw; p < N; p += W) {
+    const double rp = lane == 0 ? rhs(F.perm[p]) : 0.0;
     double acc = 0.0;
     bool ok = true;
     for (int64_t r = F.Rp[p] + lane; r < F.Rp[p + 1]; r += 32) {
-      const int k = F.Rk[r];
-      if (!ldl_wait(F.flag + k, fF, C)) { ok = false; break; }
-      acc += __ldcg(F.Lx + F.Rpos[r]) * __ldcg(F.zf + k);
+      const double l = __ldcg(F.Lx + F.Rpos[r]);
+      double zk;
+      if (!ldl_take(zf + F.Rk[r], zk, C)) { ok = false; break; }
+      acc += l * zk;
     }
     if (!__all_sync(0xffffffffu, ok)) return;
     acc = warp_sum(acc);
-    if (lane == 0) {
-      __stcg(F.zf + p, rhs(F.perm[p]) - acc);
-      st_release(F.flag + p, fF);
-    }
-    __syncwarp();
+    if (lane == 0) st_relaxed_f64(zf + p, rp - acc);
   }
-  for (int t = gw; t < F.N; t += W) {
-    const int p = F.N - 1 - t;
+  for (int t = gw; t < N; t += W) {
+    const int p = N - 1 - t;
     double acc = 0.0;
     bool ok = true;
     for (int64_t e = F.Lp[p] + lane; e < F.Lp[p + 1]; e += 32) {
-      const int i = F.Li[e];
-      if (!ldl_wait(F.flag + i, fB, C)) { ok = false; break; }
-      acc += __ldcg(F.Lx + e) * __ldcg(F.wb + i);
+      const double l = __ldcg(F.Lx + e);
+      double wi;
+      if (!ldl_take(wb + F.Li[e], wi, C)) { ok = false; break; }
+      acc += l * wi;
     }
-    if (lane == 0 && ok) ok = ldl_wait(F.flag + p, fF, C);
+    double zp = 0.0;
+    if (lane == 0 && ok) ok = ldl_take(zf + p, zp, C);
     if (!__all_sync(0xffffffffu, ok)) return;
     acc = warp_sum(acc);
     if (lane == 0) {
-      const double w = __ldcg(F.zf + p) / __ldcg(F.Dd + p) - acc;
-      __stcg(F.wb + p, w);
-      st_release(F.flag + p, fB);
+      const double w = zp / __ldcg(F.Dd + p) - acc;
+      st_relaxed_f64(wb + p, w);
       put(F.perm[p], w);
     }
-    __syncwarp();
+  }
+}
+
+// Start of a solve launch: both buffer pairs emptied (a launch that ended early may have
+// left either half written); the caller's next grid barrier orders this before any sweep.
+__device__ __noinline__ void ldl_reset(const LdlView* __restrict__ V) {
+  const LdlDev& F = V->F;
+  unsigned long long* z = reinterpret_cast<unsigned long long*>(F.zf);
+  unsigned long long* w = reinterpret_cast<unsigned long long*>(F.wb);
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < 2 * F.N; i += gridDim.x * blockDim.x) {
+    z[i] = kLdlEmpty;
+    w[i] = kLdlEmpty;
   }
 }
 
@@ -707,6 +759,7 @@ struct Solver {
       return true;
     };
 
+    if (D.ldl_N > 0) ldl_reset(D.ldlv);   // evaluate's grid barrier follows
     if (!evaluate(false)) return;
     for (;;) {
       // inner stop, Eq. inner-stop: ||Q u - v||^2 <= mu
