@@ -28,7 +28,7 @@ namespace ldl_host {
 
 // Limits of the analysis: past them the factor is not worth forming on this path.
 constexpr int64_t kMaxFactorNnz = 400000000;        // entries of L (3.2 GB of FP64 values)
-constexpr int64_t kMaxWork = 6000000000;            // merge steps of the elimination graph
+constexpr int64_t kMaxWork = 1000000000;            // merge steps of the elimination graph (a few seconds)
 
 struct Symbolic {
   int n = 0, m = 0, N = 0;
