@@ -119,9 +119,11 @@ typedef struct {
                                confirmations of the Sec. 4.1 tests (each screen pass that comes
                                sooner waits); 1 = confirm whenever the screen passes */
     int32_t grid_ctas;      /* 0: automatic; else the persistent grid size (tests) */
-    int64_t barrier_limit_ns; /* sparse (PCG) path: wall-clock limit of one grid-barrier wait in
-                                 the persistent kernel; a wait past it ends the solve with
-                                 ABIP_E_TIMEOUT (the kernel returns).  0: 4 s (default) */
+    int64_t barrier_limit_ns; /* sparse paths: wall-clock limit of one grid-barrier wait in the
+                                 persistent kernel, and of one wait of the direct projection's
+                                 factorisation and sweeps on an entry another warp computes; a
+                                 wait past it ends the call with ABIP_E_TIMEOUT (the kernel
+                                 returns).  0: 4 s (default) */
     int32_t bb_beta;        /* 1: choose beta at the start of every outer iteration by the
                                Barzilai-Borwein spectral rule with safeguarding and the heuristic
                                selection of Sec. 4.3 (two trial ADMM updates per estimate, a redo
