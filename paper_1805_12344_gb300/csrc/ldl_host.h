@@ -14,6 +14,7 @@
 #pragma once
 
 #include <algorithm>
+#include <climits>
 #include <cstdint>
 #include <functional>
 #include <queue>
@@ -49,6 +50,7 @@ struct Symbolic {
 // the number of other remaining nodes) the rest is ordered by node number.
 // Returns false (with `why`) past kMaxFactorNnz or kMaxWork.
 inline bool analyze(const sell_host::HostCSR& A, Symbolic& S, std::string& why) {
+  if ((int64_t)A.m + A.n > (int64_t)INT32_MAX) { why = "m + n does not fit the factor's 32-bit indices"; return false; }
   const int m = A.m, n = A.n, N = m + n;
   S.n = n; S.m = m; S.N = N;
   std::vector<std::vector<int32_t>> adj(N);
