@@ -3,6 +3,7 @@
     python -m paper_1805_12344_gb300.cli shared --m 2048 --nd 8192 --batch 64 --precision bf16
     python -m paper_1805_12344_gb300.cli batch --count 64 --precision mixed
     python -m paper_1805_12344_gb300.cli svm --precision mixed --max-admm 4000
+    python -m paper_1805_12344_gb300.cli flow --side 16 --linsys ldl --precision f64
 
 Prints one JSON line per run: statuses, ADMM updates, device time of setup and
 iterations as the library reports them (abip_info.setup_s / kernel_s).
@@ -39,7 +40,10 @@ def main(argv=None):
     sv.add_argument("--d", type=int, default=64)
     sv.add_argument("--N", type=int, default=512)
     sv.add_argument("--batch", type=int, default=0, help="solve this many instances (seeds seed..seed+batch-1) in one batch")
-    for p in (sh, bt, sv):
+    fl = sub.add_parser("flow", help="planted min-cost flow LP on a grid (sparse path, PCG or the direct projection)")
+    fl.add_argument("--side", type=int, default=16)
+    fl.add_argument("--linsys", choices=["pcg", "ldl"], default="ldl")
+    for p in (sh, bt, sv, fl):
         p.add_argument("--precision", choices=sorted(PRECISION), default="mixed")
         p.add_argument("--max-admm", type=int, default=1000000)
         p.add_argument("--eps", type=float, default=1e-6)
@@ -63,6 +67,18 @@ def main(argv=None):
         infos, *_ = abip.abip_solve_batch([l.A for l in lps], [l.b for l in lps], [l.c for l in lps], prm,
                                           want_solution=False)
         out = _summary("batch_uneven", infos, time.time() - t0, dict(precision=a.precision))
+    elif a.cmd == "flow":
+        lp = W.grid_flow(a.side, seed=a.seed)
+        linsys = abip.ABIP_LINSYS_SPARSE_LDL if a.linsys == "ldl" else abip.ABIP_LINSYS_PCG
+        s = abip.Solver(lp.A, lp.b, lp.c, linsys=linsys, precision=PRECISION[a.precision], max_admm_iters=a.max_admm,
+                        eps=a.eps)
+        t0 = time.time()
+        info, *_ = s.solve()
+        s.close()
+        out = _summary("grid_flow", [info], time.time() - t0,
+                       dict(side=a.side, m=lp.m, n=lp.n, linsys=a.linsys, precision=a.precision,
+                            cg_iters_per_update=info["cg_iters"] / max(1, info["admm_iters"]),
+                            us_per_update=1e6 * info["kernel_s"] / max(1, info["admm_iters"])))
     elif a.batch > 0:
         base = W.seed_for(W.L1_SVM) if a.seed is None else a.seed
         lps = [W.l1_svm(d=a.d, N=a.N, seed=base + k) for k in range(a.batch)]
