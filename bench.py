@@ -187,7 +187,7 @@ def leg_basis_pursuit(abip, W, args):
 
 
 def leg_svm_backward(abip, W, args):
-    """Config 4's differentiation: 128 L1-SVM LPs (512 x 1154) solved in one launch
+    """Differentiation of 128 L1-SVM LPs (512 x 1154) solved in one launch
     (mixed precision, `--svm-cap` updates, then MAX_ITER or optimal), then the gradients of
     ||x* - x_t||^2 with respect to c, b and A at each final iterate in one
     abip_backward_batch launch (Newton polish onto the central point of the final mu, then
@@ -211,7 +211,7 @@ def leg_svm_backward(abip, W, args):
 
 
 def leg_bb_beta(abip, W, args):
-    """Barzilai-Borwein beta (Sec. 4.3) against a fixed beta on 64 LPs of config 3's recipe,
+    """Barzilai-Borwein beta (Sec. 4.3) against a fixed beta on 64 LPs of the uneven-batch recipe,
     dense FP64 path, same cap and tolerance: LPs solved, ADMM updates and wall time of
     abip_solve_batch."""
     import time as _t

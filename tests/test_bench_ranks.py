@@ -82,8 +82,8 @@ def test_algorithmic_bytes_follow_the_minimum_passes():
 
 
 def test_both_arms_print_one_workload_config(monkeypatch):
-    """The reference arm and the GPU arm build `config` from the same helper, so the driver's
-    ratio compares the same LP and the same solver parameters."""
+    """The reference arm and the GPU arm build `config` from the same helper, so a ratio of
+    the two lines compares the same LP and the same solver parameters."""
     sys.path.insert(0, ROOT)
     import bench
     monkeypatch.setattr(sys, "argv", ["bench.py", "--max-admm", "300", "--gamma", "0.2"])
