@@ -171,3 +171,31 @@ def test_quasi_definite_ldl_reproduces_the_projection(name, A):
     zy, zx = O.solve_M(P, O.DenseCholesky(P), ry, rx)
     np.testing.assert_allclose(y, zy, atol=1e-10)
     np.testing.assert_allclose(x, zx, atol=1e-10)
+
+
+@pytest.mark.parametrize("side", [2, 3, 5])
+def test_grid_flow_structure_and_planted_pair(side):
+    """Node-arc incidence with one row dropped: every arc column holds +1 at its tail and
+    -1 at its head (one of them absent when it touches the dropped node), A has full row
+    rank (Sec. 2's assumption), and the planted pair is optimal by construction:
+    x0, s0 >= 0, x0 o s0 = 0, b = A x0, c = A^T y0 + s0."""
+    lp = W.grid_flow(side)
+    A = lp.A.to_dense()
+    nodes = side * side
+    assert lp.m == nodes - 1 and lp.n == 4 * side * (side - 1)
+    assert set(np.unique(A)) <= {-1.0, 0.0, 1.0}
+    sums = A.sum(axis=0)
+    dropped = np.abs(A).sum(axis=0) == 1          # arcs touching the dropped node
+    assert np.all(sums[~dropped] == 0) and np.all(np.abs(sums[dropped]) == 1)
+    assert np.linalg.matrix_rank(A) == lp.m
+    assert np.all(lp.x0 >= 0) and np.all(lp.s0 >= 0) and np.all(lp.x0 * lp.s0 == 0)
+    np.testing.assert_allclose(A @ lp.x0, lp.b, atol=1e-12)
+    np.testing.assert_allclose(A.T @ lp.y0 + lp.s0, lp.c, atol=1e-12)
+
+
+def test_oracle_reaches_the_grid_flow_optimum():
+    """The oracle (exact projection) solves the 3 x 3 grid flow LP to the planted optimum."""
+    lp = W.grid_flow(3)
+    r = O.solve(lp.A.to_dense(), lp.b, lp.c, O.Params(linsys=0))
+    assert r.status == O.OPTIMAL
+    assert abs(r.obj - lp.p_star) <= 1e-5 * max(1.0, abs(lp.p_star))
